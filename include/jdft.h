@@ -1,0 +1,178 @@
+/*
+ * jdft.h -- C ABI of the GB300 plane-wave Hamiltonian library (libjdft.so).
+ *
+ * The library applies the Kohn-Sham Hamiltonian of plane-wave density
+ * functional theory to blocks of bands, and computes the electron density and
+ * the subspace matrices, on one NVIDIA GB300 GPU.  Its operators are those of
+ * the algebraic ("DFT++") formulation the JDFTx paper builds on (Sec. 2.1,
+ * Software Architecture): I and J move fields between reciprocal and real
+ * space by FFT, O is the overlap, diagonal in the plane-wave basis, and the
+ * pseudopotential projectors (Sec. 2.2) give the nonlocal term.  The paper
+ * prints no formula for them; the library uses the standard readings:
+ *
+ *   lattice vectors a_d = columns of R, Omega = |det R|, B = 2 pi R^{-T};
+ *   FFT box S = (S0,S1,S2), N = S0 S1 S2, linear index j2 + S2 (j1 + S1 j0);
+ *   basis at k: integer triples iG with (1/2)|B(iG + k)|^2 <= E_cut, ordered
+ *     lexicographically by (i0, i1, i2) (k in fractional coordinates);
+ *   (I X)_j = sum_G X_G exp(+2 pi i iG.j/S), (J x)_G = (1/N) sum_j x_j exp(-2 pi i iG.j/S),
+ *   Idag = N J, Jdag = I / N, O = Omega;
+ *   H C = Omega [ (1/2)|k+G|^2 C + J(V . I C) ] + P D P^dag C;
+ *   n(r_j) += w_k sum_b f_b |(I C_b)_j|^2.
+ *
+ * Conventions for every call
+ *   - Complex numbers are interleaved (re, im).  Precision JDFT_FP64 takes
+ *     complex128 coefficient blocks; the other precisions take complex64
+ *     coefficient blocks and keep V, D, densities and subspace matrices in FP64.
+ *   - A coefficient block C of nb bands is band-major: band b occupies
+ *     C[b*ldc .. b*ldc + npw - 1] (complex elements), ldc >= npw.
+ *   - Real-space boxes are N contiguous elements per band, j2 fastest.
+ *   - Pointers marked "device" are GPU global memory owned by the caller; the
+ *     library only borrows them for the call.  Pointers marked "host" are
+ *     ordinary host memory.  `stream` is a cudaStream_t (NULL = legacy
+ *     default stream).  Compute calls are asynchronous on that stream:
+ *     argument errors are reported synchronously by the return value; a
+ *     kernel launch error is reported as JDFT_ERR_CUDA.
+ *   - A basis handle owns device copies of its maps, potential and
+ *     projectors, and a workspace that grows on demand (growth calls
+ *     cudaMalloc, which synchronises the device).  One basis must not be used
+ *     from two host threads at once.
+ *   - On any status other than JDFT_OK, jdft_last_error() returns a message
+ *     (thread-local, valid until the next call on that thread).
+ */
+#ifndef JDFT_H
+#define JDFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jdft_basis_s* jdft_basis_t;
+
+typedef enum {
+    JDFT_OK = 0,
+    JDFT_ERR_ARG = 1,          /* invalid argument (null pointer, size, index, alignment) */
+    JDFT_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    JDFT_ERR_OOM = 3,          /* device or host allocation failed */
+    JDFT_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    JDFT_ERR_NOT_POSDEF = 5,   /* overlap matrix not positive definite */
+    JDFT_ERR_NOT_CONVERGED = 6,/* minimiser hit its iteration limit */
+    JDFT_ERR_UNSUPPORTED = 7   /* valid request this build does not handle */
+} jdft_status;
+
+typedef enum {
+    JDFT_FP64 = 0,   /* everything in FP64 */
+    JDFT_FP32 = 1,   /* FFT chain in FP32, products FP32 on the CUDA cores */
+    JDFT_TF32X3 = 2, /* FFT chain FP32; GEMMs as 3 TF32 tensor-core products (hi/lo split) */
+    JDFT_BF16X3 = 3  /* FFT chain FP32; GEMMs as split BF16 tensor-core products */
+} jdft_prec;
+
+/* Cell and k-point description (host memory, read during jdft_basis_create only).
+ *   R       row-major 3x3; column d is lattice vector a_d (bohr): R[3*i + d] = (a_d)_i
+ *   S       FFT box; each S_d must be a product of 2, 3 and 5, at most 512, and
+ *           at least 2*max|iG_d| + 1 over the spheres of all k-points
+ *   ecut    plane-wave cutoff (Ha)
+ *   nk      number of k-points (>= 1)
+ *   kfrac   nk x 3, k-points in fractional reciprocal coordinates
+ *   kweight nk weights w_k used by jdft_density (NULL = 1/nk each) */
+typedef struct {
+    double R[9];
+    int S[3];
+    double ecut;
+    int nk;
+    const double* kfrac;
+    const double* kweight;
+} jdft_cell_desc;
+
+/* ---- basis ----------------------------------------------------------- */
+
+/* Build the per-k spheres (Sec. 3, Listing 2's elec-cutoff; Sec. 2's plane-wave
+ * basis) and upload the maps to the current CUDA device.  *out receives a new
+ * handle that the caller releases with jdft_basis_destroy. */
+jdft_status jdft_basis_create(const jdft_cell_desc* desc, jdft_basis_t* out);
+jdft_status jdft_basis_destroy(jdft_basis_t basis);
+
+/* Number of plane waves at k-point ik. */
+jdft_status jdft_basis_npw(jdft_basis_t basis, int ik, int* npw);
+
+/* Sphere of k-point ik: iG (host, npw x 3, int32, row per plane wave, in basis order). */
+jdft_status jdft_basis_gvectors(jdft_basis_t basis, int ik, int32_t* iG);
+
+/* Scalars: Omega (bohr^3), N, number of (i0,i1) disk columns at ik (host outputs; any may be NULL). */
+jdft_status jdft_basis_info(jdft_basis_t basis, int ik, double* omega, int64_t* nbox, int* ncols);
+
+/* ---- potential and projectors ----------------------------------------- */
+
+/* Copy the local potential V(r_j) (device, N doubles, j2 fastest) into the basis. */
+jdft_status jdft_set_potential(jdft_basis_t basis, const double* V, void* stream);
+
+/* Copy the nonlocal projectors of k-point ik into the basis:
+ *   P  device complex128, npw x nproj column-major (projector i at P[i*npw ..]);
+ *   D  device double, nproj x nproj row-major, Hermitian (real symmetric).
+ * nproj = 0 clears the nonlocal term for ik.  (Sec. 2.2, pseudopotentials.) */
+jdft_status jdft_set_projectors(jdft_basis_t basis, int ik, const void* P, int nproj,
+                                const double* D, void* stream);
+
+/* Synthetic local potential on the box: V(r) = -depth sum_a sum_T exp(-|r - R_a - T|^2 / 2 width^2),
+ * summed over every lattice image that comes within 10 bohr of the cell.
+ * atoms: host, natoms x 3 Cartesian (bohr).  V_out: device, N doubles. */
+jdft_status jdft_gaussian_potential(jdft_basis_t basis, int natoms, const double* atoms,
+                                    double depth, double width, double* V_out, void* stream);
+
+/* Synthetic projectors at k-point ik: 4 per atom (s, p_x, p_y, p_z), column 4a + l,
+ * P_{G,(a,l)} = F_l(k+G) exp(-i (k+G).R_a) with F_l the Fourier transform of the
+ * unit-norm Gaussian-type function beta_s = N_s exp(-r^2/2 sigma^2),
+ * beta_p = N_p x_l exp(-r^2/2 sigma^2).  atoms: host natoms x 3.
+ * P_out: device complex128, npw x 4 natoms column-major. */
+jdft_status jdft_gaussian_projectors(jdft_basis_t basis, int ik, int natoms, const double* atoms,
+                                     double sigma, void* P_out, void* stream);
+
+/* ---- algebraic operators (Sec. 2.1) ------------------------------------ */
+
+/* psi = I C: nb bands, C band-major (ldc), psi device nb x N complex. */
+jdft_status jdft_op_I(jdft_basis_t basis, int ik, const void* C, int ldc, void* psi, int nb,
+                      jdft_prec prec, void* stream);
+/* C = J psi (sphere part of the normalised forward transform). */
+jdft_status jdft_op_J(jdft_basis_t basis, int ik, const void* psi, void* C, int ldc, int nb,
+                      jdft_prec prec, void* stream);
+/* C = Idag psi = N J psi. */
+jdft_status jdft_op_Idag(jdft_basis_t basis, int ik, const void* psi, void* C, int ldc, int nb,
+                         jdft_prec prec, void* stream);
+/* psi = Jdag C = I C / N. */
+jdft_status jdft_op_Jdag(jdft_basis_t basis, int ik, const void* C, int ldc, void* psi, int nb,
+                         jdft_prec prec, void* stream);
+/* OC = O C = Omega C. */
+jdft_status jdft_op_O(jdft_basis_t basis, int ik, const void* C, int ldc, void* OC, int ldoc,
+                      int nb, jdft_prec prec, void* stream);
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/* HC = H C for nb bands at k-point ik (kinetic + local + nonlocal terms).
+ * C and HC must not overlap.  Scatter -> inverse 3-D FFT -> x V -> forward
+ * 3-D FFT -> gather, plus kinetic and projector terms. */
+jdft_status jdft_apply_H(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
+                         int nb, jdft_prec prec, void* stream);
+
+/* n_r[j] += w_ik sum_b f[b] |(I C_b)_j|^2.  f: device, nb doubles.  n_r: device, N doubles. */
+jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, const double* f,
+                         int nb, double* n_r, jdft_prec prec, void* stream);
+
+/* CHC = C^dag (HC), COC = C^dag O C = Omega C^dag C: device complex128 nb x nb, row-major,
+ * both triangles written.  Either output may be NULL to skip it. */
+jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
+                          int ldhc, int nb, void* CHC, void* COC, jdft_prec prec, void* stream);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+/* Message of the last non-OK status on this thread ("" if none). */
+const char* jdft_last_error(void);
+
+/* Library version string. */
+const char* jdft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JDFT_H */

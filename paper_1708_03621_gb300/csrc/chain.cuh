@@ -1,0 +1,61 @@
+// Kernels of the scatter -> FFT -> V -> FFT -> gather chain, shared by the
+// operator, Hamiltonian and density entry points.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace jdft {
+
+// Everything a chain kernel needs to know about one sphere on one box.
+struct ChainGeom {
+    int S0, S1, S2;
+    int npw, ncols, nrows, i0min;
+    const int* col_start;      // ncols + 1
+    const int* col_slot01;     // ncols: (row << 16) | (i1 mod S1)
+    const int* row_col_start;  // nrows + 1
+    const int* pw_col;         // npw
+    const int* pw_z;           // npw
+    FftPlan p0, p1, p2;
+};
+
+inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
+    const KSphere& s = b->ks[ik];
+    ChainGeom g;
+    g.S0 = b->S[0]; g.S1 = b->S[1]; g.S2 = b->S[2];
+    g.npw = s.npw; g.ncols = s.ncols; g.nrows = s.nrows; g.i0min = s.i0min;
+    g.col_start = s.col_start; g.col_slot01 = s.col_slot01; g.row_col_start = s.row_col_start;
+    g.pw_col = s.pw_col; g.pw_z = s.pw_z;
+    g.p0 = b->plan[0]; g.p1 = b->plan[1]; g.p2 = b->plan[2];
+    return g;
+}
+
+// Column buffer layout: value of column c, z-slot j2, band b (within the
+// current chunk) at colbuf[(b * S2 + j2) * ncols + c].
+__host__ __device__ inline size_t colbuf_index(const ChainGeom& g, int b, int j2, int c) {
+    return ((size_t)b * g.S2 + j2) * g.ncols + c;
+}
+
+// Launch helpers (defined in chain.cu), all on `stream`, bands [0, nb) of the chunk.
+template <typename T>
+jdft_status launch_zpass_inverse(const ChainGeom& g, const c_t<T>* C, int ldc, c_t<T>* colbuf, int nb,
+                                 const c_t<T>* tw_base, cudaStream_t st);
+// MODE 0: out = omega (kin C + scale y); MODE 1: out = scale y.
+template <typename T, int MODE>
+jdft_status launch_zpass_forward(const ChainGeom& g, const c_t<T>* colbuf, const c_t<T>* C, int ldc, c_t<T>* out,
+                                 int ldo, int nb, const T* kin, T omega, T scale, const c_t<T>* tw_base,
+                                 cudaStream_t st);
+template <typename T>
+jdft_status launch_plane_apply(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
+                               cudaStream_t st);
+template <typename T>
+jdft_status launch_plane_inverse_full(const ChainGeom& g, const c_t<T>* colbuf, c_t<T>* psi, T scale, int nb,
+                                      const c_t<T>* tw_base, cudaStream_t st);
+template <typename T>
+jdft_status launch_plane_forward_full(const ChainGeom& g, const c_t<T>* psi, c_t<T>* colbuf, int nb,
+                                      const c_t<T>* tw_base, cudaStream_t st);
+template <typename T>
+jdft_status launch_plane_density(const ChainGeom& g, const c_t<T>* colbuf, const double* f, double w, double* n_r,
+                                 int nb, const c_t<T>* tw_base, cudaStream_t st);
+
+}  // namespace jdft

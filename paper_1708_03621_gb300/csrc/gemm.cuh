@@ -1,0 +1,30 @@
+// Complex GEMMs of the projector term and the subspace matrices.
+#pragma once
+
+#include "common.cuh"
+
+namespace jdft {
+
+// out[m * ldo + n] += scale * sum_k conj(A[m * lda + k]) * B[n * ldb + k]   (complex128 out)
+// Rows of A and B are K-contiguous (band-major blocks, projector-major P).
+// `out` must be zeroed by the caller when a plain product is wanted; split-K
+// partial sums are added with FP64 atomics.
+template <typename T>
+jdft_status zgemm_cn(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* B, int ldb, double2* out, int ldo,
+                     double scale, cudaStream_t st);
+
+// out[n * ldo + m] += sum_i A[i * lda + m] * Bm[i * ldb + n]
+// A: K rows of length M (projector-major P), Bm: K x N row-major, out band-major.
+template <typename T>
+jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb, c_t<T>* out,
+                         int ldo, cudaStream_t st);
+
+// Workspace bytes the nonlocal term needs for nb bands.
+size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem);
+
+// HC += P D P^dag C for the sphere's projectors (no-op when nproj == 0).
+template <typename T>
+jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                jdft_prec prec, void* work, cudaStream_t st);
+
+}  // namespace jdft

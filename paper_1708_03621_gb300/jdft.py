@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libjdft.so (the C ABI declared in include/jdft.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors; the binding passes their device
+pointers, leading dimensions and the current CUDA stream.  Coefficient blocks
+are (nb, ld) tensors, one band per row (band-major), complex128 for
+``"fp64"`` and complex64 for the other precisions.
+
+If libjdft.so has not been built, importing this module raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjdft.so")
+
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_TIMEOUT",
+          5: "ERR_NOT_POSDEF", 6: "ERR_NOT_CONVERGED", 7: "ERR_UNSUPPORTED"}
+
+
+class JdftError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _CellDesc(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("S", ctypes.c_int * 3), ("ecut", ctypes.c_double),
+                ("nk", ctypes.c_int), ("kfrac", ctypes.POINTER(ctypes.c_double)),
+                ("kweight", ctypes.POINTER(ctypes.c_double))]
+
+
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "jdft_basis_create": [ctypes.POINTER(_CellDesc), ctypes.POINTER(_vp)],
+    "jdft_basis_destroy": [_vp],
+    "jdft_basis_npw": [_vp, _i, ctypes.POINTER(_i)],
+    "jdft_basis_gvectors": [_vp, _i, _vp],
+    "jdft_basis_info": [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_i)],
+    "jdft_set_potential": [_vp, _vp, _vp],
+    "jdft_set_projectors": [_vp, _i, _vp, _i, _vp, _vp],
+    "jdft_gaussian_potential": [_vp, _i, _vp, _d, _d, _vp, _vp],
+    "jdft_gaussian_projectors": [_vp, _i, _i, _vp, _d, _vp, _vp],
+    "jdft_op_I": [_vp, _i, _vp, _i, _vp, _i, _i, _vp],
+    "jdft_op_Jdag": [_vp, _i, _vp, _i, _vp, _i, _i, _vp],
+    "jdft_op_J": [_vp, _i, _vp, _vp, _i, _i, _i, _vp],
+    "jdft_op_Idag": [_vp, _i, _vp, _vp, _i, _i, _i, _vp],
+    "jdft_op_O": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
+    "jdft_apply_H": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
+    "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
+    "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
+}
+#: Every symbol include/jdft.h declares (the loader checks all are exported).
+EXPORTS = sorted(list(_SIGS) + ["jdft_last_error", "jdft_version"])
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if libjdft.so is missing (build it first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libjdft.so not built at {LIB_PATH}: run "
+                              "`python -m paper_1708_03621_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.jdft_last_error.restype = ctypes.c_char_p
+        L.jdft_last_error.argtypes = []
+        L.jdft_version.restype = ctypes.c_char_p
+        L.jdft_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _call(name: str, *args) -> None:
+    L = lib()
+    st = getattr(L, name)(*args)
+    if st != 0:
+        raise JdftError(st, name, L.jdft_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _block(t, prec, name):
+    """(pointer, ld, nb) of a band-major coefficient block."""
+    import torch
+    want = torch.complex128 if _prec(prec) == 0 else torch.complex64
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != want:
+        raise ValueError(f"{name} must be {want} for precision {prec}")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D (nb, ld) with unit stride along the plane waves")
+    return ctypes.c_void_p(t.data_ptr()), t.stride(0) if t.shape[0] > 1 else t.shape[1], t.shape[0]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Basis:
+    """Owner of a jdft_basis_t handle (see jdft_basis_create)."""
+
+    def __init__(self, R, S, ecut, kfrac, kweight=None):
+        R = np.asarray(R, dtype=np.float64)
+        kf = np.ascontiguousarray(np.asarray(kfrac, dtype=np.float64).reshape(-1, 3))
+        desc = _CellDesc()
+        for i in range(3):
+            for d in range(3):
+                desc.R[3 * i + d] = R[i, d]
+            desc.S[i] = int(S[i])
+        desc.ecut = float(ecut)
+        desc.nk = kf.shape[0]
+        self._kf = kf
+        desc.kfrac = kf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if kweight is not None:
+            self._kw = np.ascontiguousarray(np.asarray(kweight, dtype=np.float64))
+            desc.kweight = self._kw.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        _call("jdft_basis_create", ctypes.byref(desc), ctypes.byref(h))
+        self.handle = h
+        self.S = tuple(int(s) for s in S)
+        self.nk = kf.shape[0]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jdft_basis_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def npw(self, ik: int = 0) -> int:
+        n = ctypes.c_int()
+        _call("jdft_basis_npw", self.handle, ik, ctypes.byref(n))
+        return n.value
+
+    def gvectors(self, ik: int = 0) -> np.ndarray:
+        out = np.empty((self.npw(ik), 3), dtype=np.int32)
+        _call("jdft_basis_gvectors", self.handle, ik, ctypes.c_void_p(out.ctypes.data))
+        return out
+
+    def info(self, ik: int = 0):
+        om, n, nc = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int()
+        _call("jdft_basis_info", self.handle, ik, ctypes.byref(om), ctypes.byref(n), ctypes.byref(nc))
+        return {"omega": om.value, "N": n.value, "ncols": nc.value}
+
+
+def jdft_basis_create(R, S, ecut, kfrac, kweight=None) -> Basis:
+    return Basis(R, S, ecut, kfrac, kweight)
+
+
+def jdft_set_potential(basis: Basis, V, stream=None) -> None:
+    _call("jdft_set_potential", basis.handle, _ptr(V), _stream(stream))
+
+
+def jdft_set_projectors(basis: Basis, ik: int, P, D, stream=None) -> None:
+    """P: (nproj, npw) complex128 CUDA tensor (projector-major); D: (nproj, nproj) float64."""
+    nproj = 0 if P is None else P.shape[0]
+    _call("jdft_set_projectors", basis.handle, ik, _ptr(P), nproj, _ptr(D), _stream(stream))
+
+
+def jdft_gaussian_potential(basis: Basis, atoms, V_out, depth=4.0, width=1.0, stream=None) -> None:
+    a = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64))
+    _call("jdft_gaussian_potential", basis.handle, a.shape[0], ctypes.c_void_p(a.ctypes.data), depth, width,
+          _ptr(V_out), _stream(stream))
+
+
+def jdft_gaussian_projectors(basis: Basis, ik: int, atoms, P_out, sigma=1.0, stream=None) -> None:
+    a = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64))
+    _call("jdft_gaussian_projectors", basis.handle, ik, a.shape[0], ctypes.c_void_p(a.ctypes.data), sigma,
+          _ptr(P_out), _stream(stream))
+
+
+def jdft_op_I(basis, ik, C, psi, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_op_I", basis.handle, ik, p, ld, _ptr(psi), nb, _prec(prec), _stream(stream))
+
+
+def jdft_op_Jdag(basis, ik, C, psi, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_op_Jdag", basis.handle, ik, p, ld, _ptr(psi), nb, _prec(prec), _stream(stream))
+
+
+def jdft_op_J(basis, ik, psi, C, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_op_J", basis.handle, ik, _ptr(psi), p, ld, nb, _prec(prec), _stream(stream))
+
+
+def jdft_op_Idag(basis, ik, psi, C, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_op_Idag", basis.handle, ik, _ptr(psi), p, ld, nb, _prec(prec), _stream(stream))
+
+
+def jdft_op_O(basis, ik, C, OC, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    q, ldo, _ = _block(OC, prec, "OC")
+    _call("jdft_op_O", basis.handle, ik, p, ld, q, ldo, nb, _prec(prec), _stream(stream))
+
+
+def jdft_apply_H(basis, ik, C, HC, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, nb2 = _block(HC, prec, "HC")
+    if nb2 != nb:
+        raise ValueError("C and HC must hold the same number of bands")
+    _call("jdft_apply_H", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), _stream(stream))
+
+
+def jdft_density(basis, ik, C, f, n_r, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_density", basis.handle, ik, p, ld, _ptr(f), nb, _ptr(n_r), _prec(prec), _stream(stream))
+
+
+def jdft_subspace(basis, ik, C, HC, CHC, COC, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    if HC is not None:
+        q, ldh, _ = _block(HC, prec, "HC")
+    else:
+        q, ldh = ctypes.c_void_p(0), ld
+    _call("jdft_subspace", basis.handle, ik, p, ld, q, ldh, nb, _ptr(CHC), _ptr(COC), _prec(prec),
+          _stream(stream))
+
+
+def jdft_version() -> str:
+    return lib().jdft_version().decode()

@@ -1,0 +1,67 @@
+"""The C ABI library loads and exports every symbol include/jdft.h declares;
+argument checks that need no GPU return the documented status (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1708_03621_gb300 import jdft
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "jdft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(jdft_\w+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported():
+    L = jdft.lib()
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(jdft.EXPORTS)
+
+
+def test_version_and_empty_error():
+    assert "sm_103a" in jdft.jdft_version()
+    assert jdft.lib().jdft_last_error() == b""
+
+
+def test_null_arguments_rejected():
+    L = jdft.lib()
+    assert L.jdft_basis_create(None, None) == 1
+    assert b"null" in L.jdft_last_error()
+    assert L.jdft_apply_H(None, 0, None, 0, None, 0, 1, 0, None) == 1
+    assert L.jdft_density(None, 0, None, 0, None, 1, None, 0, None) == 1
+    assert L.jdft_subspace(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
+    assert L.jdft_basis_npw(None, 0, None) == 1
+    assert L.jdft_basis_destroy(None) == 0
+
+
+def test_bad_cell_descriptions_rejected():
+    L = jdft.lib()
+    desc = jdft._CellDesc()
+    for i in range(3):
+        desc.R[4 * i] = 6.0
+        desc.S[i] = 12
+    k = (ctypes.c_double * 3)(0.1, 0.2, 0.3)
+    desc.kfrac = ctypes.cast(k, ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    desc.nk = 0
+    desc.ecut = 4.0
+    assert L.jdft_basis_create(ctypes.byref(desc), ctypes.byref(h)) == 1
+    desc.nk = 1
+    desc.ecut = -1.0
+    assert L.jdft_basis_create(ctypes.byref(desc), ctypes.byref(h)) == 1
+    desc.ecut = 4.0
+    desc.S[1] = 14  # 14 = 2 x 7: radix 7 unsupported
+    assert L.jdft_basis_create(ctypes.byref(desc), ctypes.byref(h)) == 7
+    desc.S[1] = 12
+    desc.R[0] = 0.0
+    desc.R[4] = 0.0
+    assert L.jdft_basis_create(ctypes.byref(desc), ctypes.byref(h)) == 1
+    assert not h.value

@@ -1,0 +1,242 @@
+"""GPU parity of the FFT chain, Hamiltonian, density and subspace against the
+FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 path 1e-10 relative (per band, and max-abs over max-abs);
+FP32 path (FFT chain and products in FP32, accumulations in FP64) 1e-5
+relative per band.  Workloads span several FFT lengths (12, 15, 16, 40, 48,
+128 -> radices 2, 3, 4, 5, 8), ragged band counts and column groups, padded
+leading dimensions and several band chunks.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import planewave as pw
+from tests.systems import GpuSystem, OracleSystem, band_rel_err, workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+CTYPE = {"fp64": "complex128", "fp32": "complex64"}
+CASES = ["tiny_cubic", "tiny_ortho", "mid", "small"]
+
+_cache = {}
+
+
+def systems(name):
+    if name not in _cache:
+        w = workload(name)
+        o = OracleSystem(w)
+        g = GpuSystem(w, o.atoms)
+        _cache[name] = (w, o, g)
+    return _cache[name]
+
+
+def to_dev(a, prec, ld=None):
+    t = torch.tensor(a.astype(CTYPE[prec]), device="cuda")
+    if ld is not None and ld > a.shape[1]:
+        big = torch.zeros((a.shape[0], ld), dtype=t.dtype, device="cuda")
+        big[:, :a.shape[1]] = t
+        t = big[:, :a.shape[1]]
+    return t
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def rel_max(got, ref):
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("name", CASES + ["large"])
+def test_gvectors_and_maps(name):
+    w = workload(name)
+    from paper_1708_03621_gb300 import jdft
+    b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac)
+    ob = pw.Basis.build(w.R, w.S, w.kfrac[0], w.ecut)
+    assert b.npw(0) == ob.npw
+    assert np.array_equal(b.gvectors(0), ob.iG)
+    info = b.info(0)
+    assert info["N"] == ob.N
+    assert np.isclose(info["omega"], ob.Omega, rtol=1e-14)
+    assert info["ncols"] == len(pw.column_structure(ob.iG)[0])
+    b.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_gaussian_potential_and_projectors(name):
+    w, o, g = systems(name)
+    V = g.V.cpu().numpy()
+    assert np.max(np.abs(V - o.V)) < 1e-12
+    P = g.P[0].cpu().numpy()
+    assert rel_max(P, o.P.T) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", CASES)
+def test_operators_I_J_Idag_Jdag_O(name, prec):
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    nb = 3
+    C = o.coeffs(nb, seed=77)
+    Cd = to_dev(C, prec)
+    psi = torch.empty((nb, g.N), dtype=Cd.dtype, device="cuda")
+    jdft.jdft_op_I(g.basis, 0, Cd, psi, prec)
+    ref_psi = pw.op_I(o.basis.iG, o.basis.S, C.T).reshape(nb, -1)
+    assert band_rel_err(host(psi), ref_psi) < TOL[prec]
+    jdft.jdft_op_Jdag(g.basis, 0, Cd, psi, prec)
+    assert band_rel_err(host(psi), ref_psi / g.N) < TOL[prec]
+    # forward operators on a random full box
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((nb, g.N)) + 1j * rng.standard_normal((nb, g.N))
+    xd = torch.tensor(x.astype(CTYPE[prec]), device="cuda")
+    out = torch.empty((nb, o.basis.npw), dtype=Cd.dtype, device="cuda")
+    jdft.jdft_op_J(g.basis, 0, xd, out, prec)
+    ref = pw.op_J(o.basis.iG, o.basis.S, x.reshape((nb,) + o.basis.S)).T
+    assert band_rel_err(host(out), ref) < TOL[prec]
+    jdft.jdft_op_Idag(g.basis, 0, xd, out, prec)
+    assert band_rel_err(host(out), ref * g.N) < TOL[prec]
+    jdft.jdft_op_O(g.basis, 0, Cd, out, prec)
+    assert band_rel_err(host(out), o.basis.Omega * C) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", CASES)
+def test_apply_H(name, prec):
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    ref = o.apply_H(C)
+    Cd = to_dev(C, prec)
+    HC = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC, prec)
+    got = host(HC)
+    assert band_rel_err(got, ref) < TOL[prec]
+    if prec == "fp64":
+        assert rel_max(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_H_padded_ld_ragged_chunks(prec, monkeypatch):
+    """ld > npw, an odd band count and a 1 MB chunk budget (several chunks)."""
+    w, o, g = systems("mid")
+    from paper_1708_03621_gb300 import jdft
+    nb = 13
+    C = o.coeffs(nb, seed=5)
+    ref = o.apply_H(C)
+    Cd = to_dev(C, prec, ld=o.basis.npw + 37)
+    HC = to_dev(np.zeros_like(C), prec, ld=o.basis.npw + 5)
+    monkeypatch.setenv("JDFT_CHUNK_MB", "1")
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC, prec)
+    got = host(HC)
+    assert band_rel_err(got, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", CASES)
+def test_density(name, prec):
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    f = np.linspace(2.0, 0.5, C.shape[0])
+    ref = pw.density(o.basis, C.T, f, weight=w.weights()[0])
+    n = torch.full((g.N,), 0.25, dtype=torch.float64, device="cuda")  # accumulates onto existing values
+    jdft.jdft_density(g.basis, 0, to_dev(C, prec), torch.tensor(f, device="cuda"), n, prec)
+    got = n.cpu().numpy() - 0.25
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", CASES)
+def test_subspace(name, prec):
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    HCo = o.apply_H(C)
+    CHC_ref, COC_ref = pw.subspace(o.basis, C.T, HCo.T)
+    nb = C.shape[0]
+    CHC = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    COC = torch.empty_like(CHC)
+    jdft.jdft_subspace(g.basis, 0, to_dev(C, prec), to_dev(HCo, prec), CHC, COC, prec)
+    assert rel_max(CHC.cpu().numpy(), CHC_ref) < TOL[prec]
+    assert rel_max(COC.cpu().numpy(), COC_ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_large_sampled_bands(prec):
+    """128^3 box, 62 759 plane waves, 256 bands, 256 projectors: the whole block
+    runs on the GPU; the oracle checks three sampled bands, the matching
+    subspace columns and the density of those bands."""
+    w = workload("large")
+    o = OracleSystem(w)
+    g = GpuSystem(w, o.atoms)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    Cd = to_dev(C, prec)
+    HC = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC, prec)
+    got = host(HC)
+    sample = [0, 131, 255]
+    ref = o.apply_H(C[sample])
+    assert band_rel_err(got[sample], ref) < TOL[prec]
+    nb = C.shape[0]
+    CHC = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    jdft.jdft_subspace(g.basis, 0, Cd, HC, CHC, None, prec)
+    ref_cols = C.conj() @ ref.T            # (nb, 3): C^dag (H C_b) for sampled b
+    assert rel_max(CHC.cpu().numpy()[:, sample], ref_cols) < 10 * TOL[prec]
+    f = np.zeros(nb)
+    f[sample] = 2.0
+    n = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    jdft.jdft_density(g.basis, 0, Cd, torch.tensor(f, device="cuda"), n, prec)
+    nref = pw.density(o.basis, C[sample].T, f[sample])
+    assert np.max(np.abs(n.cpu().numpy() - nref)) / np.max(nref) < TOL[prec]
+
+
+def test_edge_cases():
+    w, o, g = systems("tiny_cubic")
+    from paper_1708_03621_gb300 import jdft
+    L = jdft.lib()
+    C = to_dev(o.coeffs(2), "fp64")
+    HC = torch.empty_like(C)
+    # nb = 0 is a no-op
+    assert L.jdft_apply_H(g.basis.handle, 0, C.data_ptr(), C.shape[1], HC.data_ptr(), C.shape[1], 0, 0, None) == 0
+    # out-of-range k-point, short leading dimension, misaligned pointer, bad precision
+    assert L.jdft_apply_H(g.basis.handle, 1, C.data_ptr(), C.shape[1], HC.data_ptr(), C.shape[1], 2, 0, None) == 1
+    assert L.jdft_apply_H(g.basis.handle, 0, C.data_ptr(), 3, HC.data_ptr(), C.shape[1], 2, 0, None) == 1
+    assert L.jdft_apply_H(g.basis.handle, 0, C.data_ptr() + 8, C.shape[1], HC.data_ptr(), C.shape[1], 2, 0,
+                          None) == 1
+    assert L.jdft_apply_H(g.basis.handle, 0, C.data_ptr(), C.shape[1], HC.data_ptr(), C.shape[1], 2, 9, None) == 1
+    # a box smaller than the sphere
+    with pytest.raises(jdft.JdftError, match="smaller than the sphere"):
+        jdft.Basis(w.R, (4, 12, 12), w.ecut, w.kfrac)
+    # no potential set yet
+    b2 = jdft.Basis(w.R, w.S, w.ecut, w.kfrac)
+    with pytest.raises(jdft.JdftError, match="no potential"):
+        jdft.jdft_apply_H(b2, 0, C, HC)
+    b2.close()
+    # single band, zero projectors
+    g2 = GpuSystem(w, o.atoms, with_projectors=False)
+    C1 = o.coeffs(1, seed=9)
+    H1 = torch.empty((1, o.basis.npw), dtype=torch.complex128, device="cuda")
+    jdft.jdft_apply_H(g2.basis, 0, to_dev(C1, "fp64"), H1)
+    ref = pw.apply_H(o.basis, o.V, C1.T).T
+    assert band_rel_err(host(H1), ref) < 1e-10
+
+
+def test_free_electron_on_gpu():
+    """V = 0, no projectors: H C = Omega (1/2)|k+G|^2 C exactly (closed form)."""
+    w = workload("tiny_ortho")
+    from paper_1708_03621_gb300 import jdft
+    b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac)
+    V = torch.zeros(int(np.prod(w.S)), dtype=torch.float64, device="cuda")
+    jdft.jdft_set_potential(b, V)
+    ob = pw.Basis.build(w.R, w.S, w.kfrac[0], w.ecut)
+    C = np.random.default_rng(1).standard_normal((4, ob.npw)) + 0j
+    HC = torch.empty((4, ob.npw), dtype=torch.complex128, device="cuda")
+    jdft.jdft_apply_H(b, 0, torch.tensor(C, device="cuda"), HC)
+    assert band_rel_err(host(HC), ob.Omega * ob.T[None, :] * C) < 1e-13
+    b.close()
