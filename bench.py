@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Throughput of the plane-wave Hamiltonian hot path on one GB300 (or N replicas).
+
+One step = one pass of the hot path over a block of bands of one k-point:
+    H C (scatter -> inverse 3-D FFT -> x V -> forward FFT -> gather, kinetic,
+    nonlocal P D P^dag C), the density n(r) = sum_b f_b |psi_b|^2, and the
+    subspace matrices C^dag H C and C^dag O C,
+on the synthetic 128^3 workload: cubic cell L = 20 bohr, E_cut = 30 Ha
+(62 759 plane waves at k = (0.1, 0.2, 0.3)), 64 Gaussian atoms, 256
+projectors, 256 bands.  Metric: band-applies per second (bands x steps / s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64|...]
+    python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+Under torchrun each rank runs its own replica of the workload (independent
+problems, no data-path collective); the value is the sum over ranks divided by
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Hψ band-applies/s & time to |ΔE|<1e-6 Ha: mixed+learned vs FP64, 1 GB300"
+UNIT = "band-applies/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--workload", default="large")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.idx = int(vis.split(",")[local_rank]) if vis else local_rank
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the workload
+# ---------------------------------------------------------------------------
+class Problem:
+    """Device-resident inputs and outputs of one step, built through the C ABI."""
+
+    def __init__(self, wname: str, prec: str, device):
+        import torch
+
+        from paper_1708_03621_gb300 import jdft
+        from synth import WORKLOADS, atom_positions, random_coefficients
+        self.jdft = jdft
+        self.prec = prec
+        w = WORKLOADS[wname]
+        self.w = w
+        self.dev = device
+        atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+        self.basis = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+        self.N = int(np.prod(w.S))
+        self.npw = self.basis.npw(0)
+        self.info = self.basis.info(0)
+        V = torch.empty(self.N, dtype=torch.float64, device=device)
+        jdft.jdft_gaussian_potential(self.basis, atoms, V)
+        jdft.jdft_set_potential(self.basis, V)
+        self.nproj = 4 * w.natoms
+        P = torch.empty((self.nproj, self.npw), dtype=torch.complex128, device=device)
+        jdft.jdft_gaussian_projectors(self.basis, 0, atoms, P)
+        D = torch.tensor(np.diag(np.tile([0.5, -0.3, -0.3, -0.3], w.natoms)), device=device)
+        jdft.jdft_set_projectors(self.basis, 0, P, D)
+        del P, V
+        # kinetic energies for the damping of the random block: from the library's own sphere
+        iG = self.basis.gvectors(0).astype(np.float64)
+        self.nrows = int(iG[:, 0].max() - iG[:, 0].min() + 1)   # i0 rows the sphere touches
+        q = (iG + np.asarray(w.kfrac[0])) @ (2 * np.pi * np.linalg.inv(w.R).T).T
+        Y = random_coefficients(np.sum(q * q, 1), w.nbands, w.seed_coeffs)
+        Y /= np.sqrt(self.info["omega"] * np.sum(np.abs(Y) ** 2, axis=1, keepdims=True))
+        ct = torch.complex128 if prec == "fp64" else torch.complex64
+        self.C_host = torch.tensor(Y.astype(np.complex128 if prec == "fp64" else np.complex64)).pin_memory()
+        self.C = self.C_host.to(device)
+        self.HC = torch.empty_like(self.C)
+        self.nb = w.nbands
+        self.f = torch.full((self.nb,), 2.0, dtype=torch.float64, device=device)
+        self.n = torch.zeros(self.N, dtype=torch.float64, device=device)
+        self.CHC = torch.empty((self.nb, self.nb), dtype=torch.complex128, device=device)
+        self.COC = torch.empty_like(self.CHC)
+        self.ctype = ct
+
+    def step(self, stream=None):
+        j = self.jdft
+        j.jdft_apply_H(self.basis, 0, self.C, self.HC, self.prec, stream)
+        self.n.zero_()
+        j.jdft_density(self.basis, 0, self.C, self.f, self.n, self.prec, stream)
+        j.jdft_subspace(self.basis, 0, self.C, self.HC, self.CHC, self.COC, self.prec, stream)
+
+    def io_bytes(self):
+        e = self.C.element_size()
+        return (self.nb * self.npw * e,
+                self.nb * self.npw * e + 2 * self.nb * self.nb * 16 + self.N * 8)
+
+
+def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, float]:
+    """Algorithmic (flops, bytes) of ONE launch of kernel `name`, averaged over the step.
+
+    FFT flops use the nominal 5 n log2 n per complex length-n transform; bytes
+    are the minimum DRAM traffic (inputs read once, outputs written once).
+    """
+    S0, S1, S2 = p.w.S
+    ncols = p.info["ncols"]
+    nrows = p.nrows
+    e = p.C.element_size()
+    per_launch_bands = nb / max(1, launches)
+    l2 = math.log2
+    if name == "plane_apply":
+        fl = 5 * S2 * (2 * nrows * S1 * l2(S1) + 2 * S1 * S0 * l2(S0))
+        by = 2 * S2 * ncols * e
+        return fl * per_launch_bands, by * per_launch_bands + p.N * (8 if e == 16 else 4)
+    if name == "plane_density":
+        fl = 5 * S2 * (nrows * S1 * l2(S1) + S1 * S0 * l2(S0))
+        return fl * per_launch_bands, S2 * ncols * e * per_launch_bands + p.N * 8
+    if name in ("zpass_inverse", "zpass_forward"):
+        fl = 5 * ncols * S2 * l2(S2)
+        by = (p.npw + S2 * ncols) * e + (p.npw * e if name == "zpass_forward" else 0)
+        return fl * per_launch_bands, by * per_launch_bands
+    if name == "zgemm_cn":  # P^dag C, C^dag HC, C^dag C: all nb x nb (nproj = nb here) over npw
+        M = N = p.nb
+        return 8.0 * M * N * p.npw, 2.0 * p.nb * p.npw * e
+    if name == "zgemm_nn":
+        return 8.0 * p.npw * p.nb * p.nproj, (2.0 * p.nb + p.nproj) * p.npw * e
+    return 0.0, 0.0
+
+
+def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:
+    if prec == "fp64":
+        return FP64_NOMINAL_TFLOPS
+    return SMS * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    from paper_1708_03621_gb300 import jdft
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    p = Problem(args.workload, args.prec, dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        p.step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K steps, events on the launching stream ----
+    clocks = Clocks(local)
+    clocks.start()
+    jdft.jdft_profile_read()
+    jdft.jdft_profile_enable(True)
+    launches0 = jdft.jdft_launch_count()
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        p.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    launches = jdft.jdft_launch_count() - launches0
+    jdft.jdft_profile_enable(False)
+    prof = jdft.jdft_profile_read()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(pg, ms)
+    units = p.nb * args.steps * world
+    value = units / (ms_max / 1e3)
+
+    # ---- per-kernel roofline from the live events ----
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    kernels = []
+    for name, (n, kms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        per_step_launches = n / args.steps
+        fl, by = kernel_work(p, name, per_step_launches, p.nb)
+        avg_s = kms / n / 1e3
+        kernels.append({"name": name, "launches": n, "ms": round(kms, 3), "share": round(kms / ms, 4),
+                        "gflop_per_launch": round(fl / 1e9, 4), "mb_per_launch": round(by / 1e6, 3),
+                        "achieved_tflops": round(fl / avg_s / 1e12, 3) if fl else None,
+                        "achieved_gbs": round(by / avg_s / 1e9, 1) if by else None})
+    top = kernels[0]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alu_peak = fp_peak_tflops(args.prec, 2070.0)
+    if top["achieved_tflops"] is not None and top["achieved_tflops"] / alu_peak >= top["achieved_gbs"] / hbm_peak:
+        roof = {"bound": "alu", "kernel": top["name"], "achieved": top["achieved_tflops"], "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s", "frac": round(top["achieved_tflops"] / alu_peak, 4),
+                "peak_source": ("FP32 lanes 128/SM x 152 SMs x 2 x 2070 MHz" if args.prec != "fp64"
+                                else "FP64 nominal 1.25 TFLOP/s")}
+    else:
+        roof = {"bound": "hbm", "kernel": top["name"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(top["achieved_gbs"] / hbm_peak, 4),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["traffic"] = None
+
+    # ---- end to end through the public API with host buffers ----
+    Bi, Bo = p.io_bytes()
+    HC_host = torch.empty_like(p.HC, device="cpu").pin_memory()
+    n_host = torch.empty_like(p.n, device="cpu").pin_memory()
+    CHC_host = torch.empty_like(p.CHC, device="cpu").pin_memory()
+    COC_host = torch.empty_like(p.COC, device="cpu").pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p.C.copy_(p.C_host, non_blocking=True)
+        p.step()
+        HC_host.copy_(p.HC, non_blocking=True)
+        n_host.copy_(p.n, non_blocking=True)
+        CHC_host.copy_(p.CHC, non_blocking=True)
+        COC_host.copy_(p.COC, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    e2e = {"value": round(p.nb * e2e_steps * world / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": Bi,
+           "d2h_bytes_per_step": Bo}
+
+    # ---- the FP64 path on the same workload, for the mixed-vs-FP64 comparison ----
+    fp64 = None
+    if not args.no_fp64 and args.prec != "fp64":
+        del p
+        torch.cuda.empty_cache()
+        q = Problem(args.workload, "fp64", dev)
+        q.step()
+        torch.cuda.synchronize()
+        k64 = max(2, args.steps // 10)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(k64):
+            q.step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t64 = a0.elapsed_time(a1)
+        fp64 = {"value": round(q.nb * k64 / (t64 / 1e3), 1), "ms_per_step": round(t64 / k64, 3), "steps": k64}
+        p = q
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "f32+tf32x3", "bf16x3": "f32+bf16x3"}[args.prec],
+        "data": "synthetic (seeded Gaussian atoms, random damped coefficients)",
+        "config": {"workload": "cubic L=20 bohr, Ecut=30 Ha, box 128^3, 62759 PW, 64 atoms, 256 projectors, "
+                               "256 bands, 1 k-point; step = apply_H + density + subspace",
+                   "precision": args.prec, "npw": p.npw, "nbands": p.nb, "nproj": p.nproj,
+                   "l2": "working set ~0.5 GB > 126 MB L2 (C, HC, P re-read every step)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
+        "fp64_path": fp64,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def oracle_sample_step(o, C):
+    """The oracle's version of one step on a sample of bands (band-major C)."""
+    from oracle import planewave as pw
+    HC = o.apply_H(C)
+    pw.density(o.basis, C.T, np.full(C.shape[0], 2.0))
+    pw.subspace(o.basis, C.T, HC.T)
+    return HC
+
+
+def cpu_baseline(wname: str, seconds: float) -> dict:
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of bands."""
+    from oracle import cfft
+    from tests.systems import OracleSystem, workload
+    o = OracleSystem(workload(wname))
+    C = o.coeffs()
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        oracle_sample_step(o, C[done % C.shape[0]:done % C.shape[0] + 1])
+        done += 1
+        if time.perf_counter() - t0 > seconds or done >= C.shape[0]:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 4), "unit": UNIT, "cores": cfft.num_threads(), "kind": "oracle",
+            "sample": f"{done} of {C.shape[0]} bands, one band per oracle call (apply_H + density + "
+                      f"subspace row), {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import cfft
+    from tests.systems import OracleSystem, workload
+    o = OracleSystem(workload(args.workload))
+    C = o.coeffs()
+    per_step = 1
+    for i in range(args.warmup):
+        oracle_sample_step(o, C[i % C.shape[0]:i % C.shape[0] + per_step])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle_sample_step(o, C[i % C.shape[0]:i % C.shape[0] + per_step])
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "cubic L=20 bohr, Ecut=30 Ha, box 128^3, 62759 PW, 64 atoms, 256 projectors, "
+                                  "256 bands, 1 k-point; step = apply_H + density + subspace",
+                      "sample": f"{per_step} band per step (bounded sample of the 256-band block)"},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cfft.num_threads(), "kind": "oracle",
+                            "sample": f"{per_step} band per step, {args.steps} steps"},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -163,7 +163,20 @@ jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, con
 jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
                           int ldhc, int nb, void* CHC, void* COC, jdft_prec prec, void* stream);
 
-/* ---- diagnostics -------------------------------------------------------- */
+/* ---- diagnostics and tracing ------------------------------------------- */
+
+/* Turn per-kernel timing on (1) or off (0).  While on, every kernel launch of
+ * the library is bracketed by two CUDA events recorded on its stream. */
+jdft_status jdft_profile_enable(int on);
+
+/* Wait for the recorded events and write one line per kernel name,
+ * "name launches total_ms\n", into buf (host, buflen bytes, NUL-terminated);
+ * then forget the records.  JDFT_ERR_ARG if buf is too small. */
+jdft_status jdft_profile_read(char* buf, int buflen);
+
+/* Number of kernels the library has launched in this process (all calls). */
+long long jdft_launch_count(void);
+
 
 /* Message of the last non-OK status on this thread ("" if none). */
 const char* jdft_last_error(void);

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace jdft {
 
@@ -358,7 +359,11 @@ jdft_status jdft_set_potential(jdft_basis_t b, const double* V, void* stream) {
         JDFT_CUDA_TRY(cudaMalloc(&b->V, b->N * sizeof(double)));
         JDFT_CUDA_TRY(cudaMalloc(&b->V32, b->N * sizeof(float)));
     }
-    permute_potential<<<grid_for(b->N, 256), 256, 0, (cudaStream_t)stream>>>(V, b->V, b->V32, b->S[0], b->S[1], b->S[2]);
+    {
+        Trace tr_("permute_potential", (cudaStream_t)stream);
+        permute_potential<<<grid_for(b->N, 256), 256, 0, (cudaStream_t)stream>>>(V, b->V, b->V32, b->S[0], b->S[1],
+                                                                                 b->S[2]);
+    }
     b->have_V = true;
     return check_launch("permute_potential");
 }
@@ -384,7 +389,10 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     cudaStream_t st = (cudaStream_t)stream;
     JDFT_CUDA_TRY(cudaMemcpyAsync(s.P, P, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     JDFT_CUDA_TRY(cudaMemcpyAsync(s.D, D, (size_t)nproj * nproj * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    to_complex64<<<grid_for((int64_t)n, 256), 256, 0, st>>>((const double2*)s.P, (float2*)s.P32, (int64_t)n);
+    {
+        Trace tr_("to_complex64", st);
+        to_complex64<<<grid_for((int64_t)n, 256), 256, 0, st>>>((const double2*)s.P, (float2*)s.P32, (int64_t)n);
+    }
     return check_launch("to_complex64");
 }
 
@@ -406,8 +414,11 @@ jdft_status jdft_gaussian_potential(jdft_basis_t b, int natoms, const double* at
     cudaStream_t st = (cudaStream_t)stream;
     JDFT_CUDA_TRY(cudaMalloc(&d_atoms, std::max(1, natoms) * 3 * sizeof(double)));
     if (natoms) JDFT_CUDA_TRY(cudaMemcpyAsync(d_atoms, atoms, natoms * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
-    gaussian_potential_kernel<<<grid_for(b->N, 128), 128, 0, st>>>(cell, d_atoms, natoms, depth,
-                                                                    1.0 / (2 * width * width), cut * cut, V_out);
+    {
+        Trace tr_("gaussian_potential", st);
+        gaussian_potential_kernel<<<grid_for(b->N, 128), 128, 0, st>>>(cell, d_atoms, natoms, depth,
+                                                                        1.0 / (2 * width * width), cut * cut, V_out);
+    }
     jdft_status s = check_launch("gaussian_potential_kernel");
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_atoms);
@@ -426,8 +437,11 @@ jdft_status jdft_gaussian_projectors(jdft_basis_t b, int ik, int natoms, const d
     JDFT_CUDA_TRY(cudaMalloc(&d_atoms, natoms * 3 * sizeof(double)));
     JDFT_CUDA_TRY(cudaMemcpyAsync(d_atoms, atoms, natoms * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
     const KSphere& s = b->ks[ik];
-    gaussian_projectors_kernel<<<grid_for(s.npw, 128), 128, 0, st>>>(s.kvec, s.npw, d_atoms, natoms, sigma,
-                                                                      (double2*)P_out);
+    {
+        Trace tr_("gaussian_projectors", st);
+        gaussian_projectors_kernel<<<grid_for(s.npw, 128), 128, 0, st>>>(s.kvec, s.npw, d_atoms, natoms, sigma,
+                                                                          (double2*)P_out);
+    }
     jdft_status r = check_launch("gaussian_projectors_kernel");
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(d_atoms);

@@ -20,6 +20,7 @@
 #include <cstdlib>
 
 #include "chain.cuh"
+#include "profile.cuh"
 #include "gemm.cuh"
 
 namespace jdft {
@@ -343,7 +344,10 @@ jdft_status launch_zpass_inverse(const ChainGeom& g, const c_t<T>* C, int ldc, c
     jdft_status s = prepare(zpass_inverse_kernel<T>, smem, "zpass_inverse");
     if (s != JDFT_OK) return s;
     dim3 grid((g.ncols + cpb - 1) / cpb, nb);
-    zpass_inverse_kernel<T><<<grid, kThreads, smem, st>>>(g, C, ldc, colbuf, cpb, tw_base + g.p2.tw_offset);
+    {
+        Trace tr_("zpass_inverse", st);
+        zpass_inverse_kernel<T><<<grid, kThreads, smem, st>>>(g, C, ldc, colbuf, cpb, tw_base + g.p2.tw_offset);
+    }
     return check_launch("zpass_inverse");
 }
 
@@ -356,8 +360,11 @@ jdft_status launch_zpass_forward(const ChainGeom& g, const c_t<T>* colbuf, const
     jdft_status s = prepare(zpass_forward_kernel<T, MODE>, smem, "zpass_forward");
     if (s != JDFT_OK) return s;
     dim3 grid((g.ncols + cpb - 1) / cpb, nb);
-    zpass_forward_kernel<T, MODE><<<grid, kThreads, smem, st>>>(g, colbuf, C, ldc, out, ldo, kin, omega, scale, cpb,
-                                                                tw_base + g.p2.tw_offset);
+    {
+        Trace tr_("zpass_forward", st);
+        zpass_forward_kernel<T, MODE><<<grid, kThreads, smem, st>>>(g, colbuf, C, ldc, out, ldo, kin, omega, scale, cpb,
+                                                                    tw_base + g.p2.tw_offset);
+    }
     return check_launch("zpass_forward");
 }
 
@@ -369,8 +376,11 @@ jdft_status launch_plane_apply(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, 
     jdft_status s = prepare(plane_apply_kernel<T>, smem, "plane_apply");
     if (s != JDFT_OK) return s;
     dim3 grid(g.S2, nb);
-    plane_apply_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, Vp, sm, tw_base + g.p0.tw_offset,
-                                                        tw_base + g.p1.tw_offset);
+    {
+        Trace tr_("plane_apply", st);
+        plane_apply_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, Vp, sm, tw_base + g.p0.tw_offset,
+                                                            tw_base + g.p1.tw_offset);
+    }
     return check_launch("plane_apply");
 }
 
@@ -382,8 +392,11 @@ jdft_status launch_plane_inverse_full(const ChainGeom& g, const c_t<T>* colbuf, 
     jdft_status s = prepare(plane_inverse_full_kernel<T>, smem, "plane_inverse_full");
     if (s != JDFT_OK) return s;
     dim3 grid(g.S2, nb);
-    plane_inverse_full_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, psi, scale, sm, tw_base + g.p0.tw_offset,
-                                                               tw_base + g.p1.tw_offset);
+    {
+        Trace tr_("plane_inverse_full", st);
+        plane_inverse_full_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, psi, scale, sm, tw_base + g.p0.tw_offset,
+                                                                   tw_base + g.p1.tw_offset);
+    }
     return check_launch("plane_inverse_full");
 }
 
@@ -395,8 +408,11 @@ jdft_status launch_plane_forward_full(const ChainGeom& g, const c_t<T>* psi, c_t
     jdft_status s = prepare(plane_forward_full_kernel<T>, smem, "plane_forward_full");
     if (s != JDFT_OK) return s;
     dim3 grid(g.S2, nb);
-    plane_forward_full_kernel<T><<<grid, kThreads, smem, st>>>(g, psi, colbuf, sm, tw_base + g.p0.tw_offset,
-                                                               tw_base + g.p1.tw_offset);
+    {
+        Trace tr_("plane_forward_full", st);
+        plane_forward_full_kernel<T><<<grid, kThreads, smem, st>>>(g, psi, colbuf, sm, tw_base + g.p0.tw_offset,
+                                                                   tw_base + g.p1.tw_offset);
+    }
     return check_launch("plane_forward_full");
 }
 
@@ -424,8 +440,11 @@ jdft_status launch_plane_density(const ChainGeom& g, const c_t<T>* colbuf, const
     const int per = (nb + groups - 1) / groups;
     groups = (nb + per - 1) / per;
     dim3 grid(g.S2, nsplit, groups);
-    plane_density_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, nb, per, jw, f, w, n_r, sm,
-                                                          tw_base + g.p0.tw_offset, tw_base + g.p1.tw_offset);
+    {
+        Trace tr_("plane_density", st);
+        plane_density_kernel<T><<<grid, kThreads, smem, st>>>(g, colbuf, nb, per, jw, f, w, n_r, sm,
+                                                              tw_base + g.p0.tw_offset, tw_base + g.p1.tw_offset);
+    }
     return check_launch("plane_density");
 }
 
@@ -672,10 +691,16 @@ jdft_status jdft_op_O(jdft_basis_t b, int ik, const void* C, int ldc, void* OC, 
     cudaStream_t st = (cudaStream_t)stream;
     const int grid = 152 * 8;
     if (is_fp64(prec))
-        scale_block_kernel<double><<<grid, 256, 0, st>>>((const double2*)C, ldc, (double2*)OC, ldoc, npw, nb, b->omega);
+        {
+            Trace tr_("scale_block", st);
+            scale_block_kernel<double><<<grid, 256, 0, st>>>((const double2*)C, ldc, (double2*)OC, ldoc, npw, nb, b->omega);
+        }
     else
-        scale_block_kernel<float><<<grid, 256, 0, st>>>((const float2*)C, ldc, (float2*)OC, ldoc, npw, nb,
-                                                         (float)b->omega);
+        {
+            Trace tr_("scale_block", st);
+            scale_block_kernel<float><<<grid, 256, 0, st>>>((const float2*)C, ldc, (float2*)OC, ldoc, npw, nb,
+                                                             (float)b->omega);
+        }
     return check_launch("scale_block");
 }
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "gemm.cuh"
+#include "profile.cuh"
 
 namespace jdft {
 
@@ -78,7 +79,10 @@ jdft_status zgemm_cn(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>
     kchunk = (kchunk + CN_BK - 1) / CN_BK * CN_BK;
     splits = (K + kchunk - 1) / kchunk;
     dim3 grid((M + CN_BM - 1) / CN_BM, (N + CN_BN - 1) / CN_BN, splits);
-    zgemm_cn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, out, ldo, scale);
+    {
+        Trace tr_("zgemm_cn", st);
+        zgemm_cn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, out, ldo, scale);
+    }
     return check_launch("zgemm_cn");
 }
 
@@ -138,7 +142,10 @@ jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_
                          int ldo, cudaStream_t st) {
     if (M == 0 || N == 0 || K == 0) return JDFT_OK;
     dim3 grid((M + NN_BM - 1) / NN_BM, (N + NN_BN - 1) / NN_BN);
-    zgemm_nn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, Bm, ldb, out, ldo);
+    {
+        Trace tr_("zgemm_nn", st);
+        zgemm_nn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, Bm, ldb, out, ldo);
+    }
     return check_launch("zgemm_nn");
 }
 
@@ -184,7 +191,10 @@ jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void*
     JDFT_CUDA_TRY(cudaMemsetAsync(Bc, 0, (size_t)sp.nproj * nb * sizeof(double2), st));
     jdft_status s = zgemm_cn<T>(sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0, st);
     if (s != JDFT_OK) return s;
-    dmul_kernel<T><<<std::min(152 * 8, (sp.nproj * nb + 255) / 256), 256, 0, st>>>(sp.nproj, nb, sp.D, Bc, Bd);
+    {
+        Trace tr_("dmul", st);
+        dmul_kernel<T><<<std::min(152 * 8, (sp.nproj * nb + 255) / 256), 256, 0, st>>>(sp.nproj, nb, sp.D, Bc, Bd);
+    }
     if ((s = check_launch("dmul"))) return s;
     return zgemm_nn_acc<T>(sp.npw, nb, sp.nproj, proj_ptr<T>(sp), sp.npw, Bd, nb, (c_t<T>*)HC, ldhc, st);
 }

@@ -55,9 +55,11 @@ _SIGS = {
     "jdft_apply_H": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
     "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
+    "jdft_profile_enable": [_i],
+    "jdft_profile_read": [ctypes.c_char_p, _i],
 }
 #: Every symbol include/jdft.h declares (the loader checks all are exported).
-EXPORTS = sorted(list(_SIGS) + ["jdft_last_error", "jdft_version"])
+EXPORTS = sorted(list(_SIGS) + ["jdft_last_error", "jdft_version", "jdft_launch_count"])
 
 _lib = None
 
@@ -78,6 +80,8 @@ def lib() -> ctypes.CDLL:
         L.jdft_last_error.argtypes = []
         L.jdft_version.restype = ctypes.c_char_p
         L.jdft_version.argtypes = []
+        L.jdft_launch_count.restype = ctypes.c_longlong
+        L.jdft_launch_count.argtypes = []
         _lib = L
     return _lib
 
@@ -245,3 +249,23 @@ def jdft_subspace(basis, ik, C, HC, CHC, COC, prec="fp64", stream=None):
 
 def jdft_version() -> str:
     return lib().jdft_version().decode()
+
+
+def jdft_profile_enable(on: bool = True) -> None:
+    _call("jdft_profile_enable", 1 if on else 0)
+
+
+def jdft_profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read (waits for the events)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _call("jdft_profile_read", buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out
+
+
+def jdft_launch_count() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().jdft_launch_count())

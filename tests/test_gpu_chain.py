@@ -35,7 +35,7 @@ def systems(name):
 
 
 def to_dev(a, prec, ld=None):
-    t = torch.tensor(a.astype(CTYPE[prec]), device="cuda")
+    t = torch.tensor(np.ascontiguousarray(a.astype(CTYPE[prec])), device="cuda")
     if ld is not None and ld > a.shape[1]:
         big = torch.zeros((a.shape[0], ld), dtype=t.dtype, device="cuda")
         big[:, :a.shape[1]] = t
