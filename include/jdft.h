@@ -163,6 +163,31 @@ jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, con
 jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
                           int ldhc, int nb, void* CHC, void* COC, jdft_prec prec, void* stream);
 
+/* ---- the Hamiltonian without device allocation --------------------------- */
+
+/* Same result as jdft_apply_H (same arguments, layouts and precisions), but the
+ * call allocates no device memory.  The paper has no counterpart: this exists
+ * for callers that cannot let the library call cudaMalloc -- code running under
+ * CUDA stream capture (an allocation is not capturable), applications that own
+ * a fixed device-memory budget or pool, and latency-critical loops where a
+ * synchronising allocation is unacceptable.
+ *
+ * The intermediate column buffer and the projector products live in one static
+ * 32 MiB device array inside libjdft.so, which every GPU that loads the library
+ * holds until the process exits.  Bands are processed in chunks that fit it;
+ * if a single band of this basis needs more than 32 MiB
+ * (S2 x ncols x element size + nproj x (16 + element size) bytes), the call
+ * returns JDFT_ERR_ARG and the caller should use jdft_apply_H.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call shares the one array: calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  The basis must already hold its potential and
+ * projectors (jdft_set_potential / jdft_set_projectors). */
+jdft_status jdft_apply_H_noalloc(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC,
+                                 int ldhc, int nb, jdft_prec prec, void* stream);
+
 /* ---- diagnostics and tracing ------------------------------------------- */
 
 /* Turn per-kernel timing on (1) or off (0).  While on, every kernel launch of

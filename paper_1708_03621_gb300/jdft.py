@@ -55,6 +55,7 @@ _SIGS = {
     "jdft_apply_H": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
     "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
+    "jdft_apply_H_noalloc": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -230,6 +231,15 @@ def jdft_apply_H(basis, ik, C, HC, prec="fp64", stream=None):
     if nb2 != nb:
         raise ValueError("C and HC must hold the same number of bands")
     _call("jdft_apply_H", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), _stream(stream))
+
+
+def jdft_apply_H_noalloc(basis, ik, C, HC, prec="fp64", stream=None):
+    """jdft_apply_H without device allocation (static 32 MiB scratch in the library)."""
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, nb2 = _block(HC, prec, "HC")
+    if nb2 != nb:
+        raise ValueError("C and HC must hold the same number of bands")
+    _call("jdft_apply_H_noalloc", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), _stream(stream))
 
 
 def jdft_density(basis, ik, C, f, n_r, prec="fp64", stream=None):
