@@ -163,6 +163,64 @@ jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, con
 jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
                           int ldhc, int nb, void* CHC, void* COC, jdft_prec prec, void* stream);
 
+/* ---- orthonormalisation, subspace diagonalisation, band minimisation ----- */
+
+/* C <- C L^{-dag} with Omega C^dag C = L L^dag (Cholesky, FP64 on the GPU), so
+ * that C^dag O C = 1 afterwards (O diagonal in the plane-wave basis, Sec. 2.1).
+ * C: device complex128, band-major (ldc >= npw).  Synchronous (returns after
+ * the work is done).  JDFT_ERR_NOT_POSDEF if the bands are linearly dependent.
+ * Allocates a small temporary (nb x ldc complex128 plus nb^2 matrices). */
+jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, void* stream);
+
+/* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
+ * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,
+ * nb doubles.  Synchronous. */
+jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream);
+
+/* Learned per-coefficient preconditioner: a 3 -> 64 -> 64 -> 1 network, SiLU
+ * hidden activations, softplus output (so K > 0).  Parameters, 4481 floats in
+ * this order: W1 (64x3 row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1).
+ * Features per coefficient G of band b: x = (1/2)|k+G|^2 / T_b,
+ * log(1 + T_b), (h_b - min_b h_b) / T_b, with T_b the band kinetic energy and
+ * h_b = (C^dag H C)_bb the band's Rayleigh quotient. */
+typedef struct jdft_mlp_s* jdft_mlp_t;
+
+typedef enum {
+    JDFT_PRECOND_IDENTITY = 0,
+    JDFT_PRECOND_TETER = 1,   /* Teter, Payne & Allan, PRB 40, 12255 (1989) */
+    JDFT_PRECOND_MLP = 2      /* the learned network (opts.mlp) */
+} jdft_precond;
+
+typedef struct {
+    double tol;             /* stop when ||H C - O C (C^dag H C)||_F / sqrt(Omega) < tol (Ha) */
+    int max_iter;           /* iteration limit over all phases */
+    jdft_precond precond;
+    jdft_prec prec;         /* JDFT_FP64, or a mixed mode for the bulk iterations */
+    double switch_tol;      /* mixed modes: promote to FP64 below this residual (0 = 1e-4) */
+    double occupation;      /* f per band (0 = 2) */
+    jdft_mlp_t mlp;         /* weights for JDFT_PRECOND_MLP, else NULL */
+} jdft_min_opts;
+
+typedef struct {
+    int iterations;         /* CG iterations, all phases */
+    int mixed_iterations;   /* of which in the mixed-precision phase */
+    int converged;
+    double energy;          /* f tr(C^dag H C) at exit (Ha) */
+    double residual;        /* the stopping residual at exit (Ha) */
+    double seconds;         /* wall time of the call */
+} jdft_min_report;
+
+/* Preconditioned all-band conjugate-gradient minimisation of E = f tr(C^dag H C)
+ * over O-orthonormal C at fixed potential (Sec. 2.1 Minimize; Sec. 2.2).
+ * C: device complex128 band-major, in: starting guess (any linearly
+ * independent block), out: converged orthonormal block.  eigs: device nb
+ * doubles (NULL to skip): eigenvalues of C^dag H C at exit.  report: host.
+ * Synchronous.  Allocates its working blocks for the duration of the call.
+ * JDFT_ERR_NOT_CONVERGED (with C and report filled) if max_iter is reached. */
+jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, int nb,
+                                const jdft_min_opts* opts, double* eigs, jdft_min_report* report,
+                                void* stream);
+
 /* ---- the Hamiltonian without device allocation --------------------------- */
 
 /* Same result as jdft_apply_H (same arguments, layouts and precisions), but the

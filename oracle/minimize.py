@@ -34,8 +34,9 @@ local potential (non-self-consistent), all bands at once:
   update     Y = C + lambda d, HY = HC + lambda Hd; U = Y^dag O Y = L L^dag
              (Cholesky); C = Y L^{-dag}, HC = HY L^{-dag}.
 
-Preconditioners are plain functions (C, G, basis) -> K G, so the learned one
-plugs in beside Teter and the identity.
+Preconditioners are plain functions (basis, C, G, h) -> K G, h being the
+bands' Rayleigh quotients diag(C^dag H C), so the learned one plugs in beside
+Teter and the identity.
 """
 from __future__ import annotations
 
@@ -58,11 +59,11 @@ def band_kinetic(basis: pw.Basis, C) -> np.ndarray:
     return basis.Omega * np.einsum("g,gb->b", basis.T, np.abs(C) ** 2)
 
 
-def precond_identity(basis, C, G, eps=None):
+def precond_identity(basis, C, G, h=None):
     return G.copy()
 
 
-def precond_teter(basis, C, G, eps=None):
+def precond_teter(basis, C, G, h=None):
     Tb = band_kinetic(basis, C)
     return teter(basis.T[:, None] / Tb[None, :]) * G
 
@@ -99,7 +100,7 @@ def minimize_bands(basis: pw.Basis, Happly, C0, precond=precond_teter, tol=1e-8,
     """Minimise E = f tr(C^dag H C) over O-orthonormal C, starting from C0.
 
     Happly(X) returns H X for an (npw, m) block.  `record`, if given, is
-    called as record(it, C, G, KG, eps) every iteration (training data).
+    called as record(it, C, G, KG, h) every iteration, h = diag(C^dag H C).
     """
     Om = basis.Omega
     C = pw.lowdin(np.asarray(C0, dtype=np.complex128), Om)
@@ -116,10 +117,10 @@ def minimize_bands(basis: pw.Basis, Happly, C0, precond=precond_teter, tol=1e-8,
             return MinResult(C, HC, eps, E, it, True, res, hist)
         if it == max_iter:
             break
-        KG = precond(basis, C, G, eps)
+        KG = precond(basis, C, G, np.real(np.diag(Hs)))
         KG = KG - C @ (Om * (C.conj().T @ KG))
         if record is not None:
-            record(it, C, G, KG, eps)
+            record(it, C, G, KG, np.real(np.diag(Hs)))
         beta = 0.0
         if d_prev is not None:
             beta = np.vdot(G, KG - KG_prev).real / np.vdot(G_prev, KG_prev).real

@@ -1,0 +1,709 @@
+// Band minimisation on the GPU: orthonormalisation and subspace
+// diagonalisation (small FP64 dense linear algebra), and the preconditioned
+// all-band conjugate-gradient minimiser (JDFTx paper, Sec. 2.1 Minimize:
+// nonlinear CG for variational minimisation; Sec. 2.2: variational
+// electronic minimisation).  The paper prints no algorithm; the reading used:
+//
+//   C^dag O C = 1;  E = f tr(C^dag H C);  G = H C - O C (C^dag H C);
+//   residual ||G||_F / sqrt(Omega);  K G per coefficient (Teter, identity or
+//   a learned network), projected O-orthogonal to C;  Polak-Ribiere
+//   direction d (beta reset at < 0), projected;  second-order line step from
+//   a1 = 2 Re<HC, d>, a2 = Re<d, Hd> - Re tr(C^dag H C . d^dag O d), halved
+//   while the new energy rises above E + 64 ulp;  Y = C + l d,
+//   U = Y^dag O Y = L L^dag, C <- Y L^{-dag}, HC <- (HC + l Hd) L^{-dag}.
+//
+// Mixed precision: the bulk iterations can run with FP32 blocks (FFT chain,
+// projector products and block GEMMs in FP32, accumulations of the small
+// matrices and all small linear algebra in FP64); once the residual falls
+// below a switch threshold, or stops improving, the state is promoted to
+// FP64 and refined there to the requested tolerance.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "chain.cuh"
+#include "gemm.cuh"
+#include "minimize.cuh"
+#include "profile.cuh"
+
+namespace jdft {
+
+// ---------------------------------------------------------------------------
+// Block kernels (a block is nb bands x npw, band-major, leading dimension ld)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void blk_axpby_kernel(int npw, int nb, double a, const c_t<T>* __restrict__ x, int ldx, double b,
+                                 const c_t<T>* __restrict__ y, int ldy, c_t<T>* __restrict__ z, int ldz) {
+    const int64_t total = (int64_t)npw * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bb = i / npw, g = i - bb * npw;
+        const c_t<T> u = x[bb * ldx + g];
+        c_t<T> r = mk<T>((T)(a * u.x), (T)(a * u.y));
+        if (y) {
+            const c_t<T> v = y[bb * ldy + g];
+            r.x += (T)(b * v.x);
+            r.y += (T)(b * v.y);
+        }
+        z[bb * ldz + g] = r;
+    }
+}
+
+// out[slot] += Re sum conj(x) y over the whole block (FP64 accumulation).
+template <typename T>
+__global__ void blk_dot_kernel(int npw, int nb, const c_t<T>* __restrict__ x, int ldx, const c_t<T>* __restrict__ y,
+                               int ldy, double* __restrict__ out) {
+    const int64_t total = (int64_t)npw * nb;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bb = i / npw, g = i - bb * npw;
+        const c_t<T> u = x[bb * ldx + g], v = y[bb * ldy + g];
+        acc += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+// Tb[b] = Omega sum_G kin[G] |C_Gb|^2 (one block per band).
+template <typename T>
+__global__ void band_kinetic_kernel(int npw, const c_t<T>* __restrict__ C, int ldc, const double* __restrict__ kin,
+                                    double omega, double* __restrict__ Tb) {
+    const int b = blockIdx.x;
+    double acc = 0.0;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+        const c_t<T> c = C[(size_t)b * ldc + g];
+        acc += kin[g] * ((double)c.x * c.x + (double)c.y * c.y);
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) Tb[b] = omega * acc;
+    }
+}
+
+// KG = K(x) G with x = kin / Tb (Teter) or K = 1 (identity).
+template <typename T>
+__global__ void precond_teter_kernel(int npw, int nb, const c_t<T>* __restrict__ G, int ldg, c_t<T>* __restrict__ KG,
+                                     int ldk, const double* __restrict__ kin, const double* __restrict__ Tb,
+                                     int identity) {
+    const int64_t total = (int64_t)npw * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bb = i / npw, g = i - bb * npw;
+        double k = 1.0;
+        if (!identity) {
+            const double x = kin[g] / Tb[bb];
+            const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+            k = num / (num + 16.0 * x * x * x * x);
+        }
+        const c_t<T> v = G[bb * ldg + g];
+        KG[bb * ldk + g] = mk<T>((T)(k * v.x), (T)(k * v.y));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small nb x nb matrices (complex128, row-major)
+// ---------------------------------------------------------------------------
+// A = (A + A^dag)/2; scal[0] = Re tr A
+__global__ void hermitize_kernel(int n, double2* A, double* trace) {
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (i < j) {
+            double2 a = A[i * n + j], b = A[j * n + i];
+            double2 m = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+            A[i * n + j] = m;
+            A[j * n + i] = make_double2(m.x, -m.y);
+        } else if (i == j) {
+            A[i * n + i].y = 0.0;
+            acc += A[i * n + i].x;
+        }
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        *trace = s;
+    }
+}
+
+// out = alpha * A, converted to the block type
+template <typename T>
+__global__ void small_scale_kernel(int n, const double2* __restrict__ A, double alpha, c_t<T>* __restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x)
+        out[e] = mk<T>((T)(alpha * A[e].x), (T)(alpha * A[e].y));
+}
+
+// *out = Re tr(A B) for Hermitian A, B: sum_ij A_ij B_ji = sum_ij A_ij conj(B_ij)
+__global__ void trace_prod_kernel(int n, const double2* __restrict__ A, const double2* __restrict__ B, double* out) {
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double2 a = A[i * n + j], b = B[j * n + i];
+        acc += a.x * b.x - a.y * b.y;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        *out = s;
+    }
+}
+
+// One block: U = L L^dag (lower L, overwriting the work copy), then
+// X = L^{-1} by forward substitution, W = X^dag (upper), written as the block
+// type.  status = JDFT_ERR_NOT_POSDEF if a pivot is not positive.
+template <typename T>
+__global__ void cholesky_winv_kernel(int n, const double2* __restrict__ U, double2* __restrict__ L,
+                                     double2* __restrict__ X, c_t<T>* __restrict__ W, int* status) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = U[e];
+    __syncthreads();
+    __shared__ double piv;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int j = 0; j < n; ++j) {
+        // diagonal
+        if (threadIdx.x == 0) {
+            // a pivot that is not positive, or that lost all but ~1e-13 of the
+            // diagonal to earlier columns, means linearly dependent bands
+            const double ujj = L[j * n + j].x;
+            double d = ujj;
+            for (int k = 0; k < j; ++k) d -= L[j * n + k].x * L[j * n + k].x + L[j * n + k].y * L[j * n + k].y;
+            if (!(d > 1e-13 * ujj)) { bad = 1; d = 1.0; }
+            piv = sqrt(d);
+            L[j * n + j] = make_double2(piv, 0.0);
+        }
+        __syncthreads();
+        // column below the diagonal: L_ij = (U_ij - sum_k L_ik conj(L_jk)) / L_jj
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double2 s = L[i * n + j];
+            for (int k = 0; k < j; ++k) {
+                const double2 a = L[i * n + k], b = L[j * n + k];
+                s.x -= a.x * b.x + a.y * b.y;
+                s.y -= a.y * b.x - a.x * b.y;
+            }
+            L[i * n + j] = make_double2(s.x / piv, s.y / piv);
+        }
+        __syncthreads();
+    }
+    // forward substitution, one column c of the identity per thread: L X = I
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int i = 0; i < n; ++i) {
+            if (i < c) { X[i * n + c] = make_double2(0.0, 0.0); continue; }
+            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
+            for (int k = c; k < i; ++k) {
+                const double2 a = L[i * n + k], x = X[k * n + c];
+                s.x -= a.x * x.x - a.y * x.y;
+                s.y -= a.x * x.y + a.y * x.x;
+            }
+            const double d = L[i * n + i].x;
+            X[i * n + c] = make_double2(s.x / d, s.y / d);
+        }
+    }
+    __syncthreads();
+    // W = X^dag
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double2 x = X[j * n + i];
+        W[e] = mk<T>((T)x.x, (T)(-x.y));
+    }
+    if (threadIdx.x == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
+}
+
+// Eigenvalues of a Hermitian matrix by cyclic Jacobi rotations (one block,
+// in-place on A of size m x m, m even, round-robin pairs; indices >= n are a
+// decoupled pad).  eigs receives the sorted diagonal.
+__global__ void jacobi_eig_kernel(int n, int m, double2* A, int sweeps, double* eigs) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    double2* ph = reinterpret_cast<double2*>(sm_raw);   // m/2 phases
+    double* cs = reinterpret_cast<double*>(ph + m / 2);  // m/2 cosines
+    double* sn = cs + m / 2;                             // m/2 sines
+    int* idx = reinterpret_cast<int*>(sn + m / 2);       // m tournament slots
+    int* pp = idx + m;                                   // m/2 pair indices
+    int* qq = pp + m / 2;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) idx[i] = i;
+    __syncthreads();
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int step = 0; step < m - 1; ++step) {
+            for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
+                int p = idx[k], q = idx[m - 1 - k];
+                if (p > q) { int t = p; p = q; q = t; }
+                pp[k] = p; qq[k] = q;
+                double c = 1.0, s = 0.0;
+                double2 e = make_double2(1.0, 0.0);
+                if (q < n) {
+                    const double2 apq = A[p * m + q];
+                    const double ac = hypot(apq.x, apq.y);
+                    if (ac > 1e-300) {
+                        e = make_double2(apq.x / ac, apq.y / ac);
+                        const double th = (A[q * m + q].x - A[p * m + p].x) / (2.0 * ac);
+                        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                }
+                cs[k] = c; sn[k] = s; ph[k] = e;
+            }
+            __syncthreads();
+            // columns: A[:,p] = c A_p - s conj(e) A_q ; A[:,q] = s A_p + c conj(e) A_q
+            for (int w = threadIdx.x; w < (m / 2) * m; w += blockDim.x) {
+                const int k = w / m, i = w % m;
+                if (sn[k] == 0.0) continue;
+                const int p = pp[k], q = qq[k];
+                const double c = cs[k], s = sn[k];
+                const double2 e = ph[k], a = A[i * m + p], b = A[i * m + q];
+                const double2 eb = make_double2(e.x * b.x + e.y * b.y, e.x * b.y - e.y * b.x);  // conj(e) b
+                A[i * m + p] = make_double2(c * a.x - s * eb.x, c * a.y - s * eb.y);
+                A[i * m + q] = make_double2(s * a.x + c * eb.x, s * a.y + c * eb.y);
+            }
+            __syncthreads();
+            // rows: A[p,:] = c A_p - s e A_q ; A[q,:] = s A_p + c e A_q
+            for (int w = threadIdx.x; w < (m / 2) * m; w += blockDim.x) {
+                const int k = w / m, j = w % m;
+                if (sn[k] == 0.0) continue;
+                const int p = pp[k], q = qq[k];
+                const double c = cs[k], s = sn[k];
+                const double2 e = ph[k], a = A[p * m + j], b = A[q * m + j];
+                const double2 eb = make_double2(e.x * b.x - e.y * b.y, e.x * b.y + e.y * b.x);  // e b
+                A[p * m + j] = make_double2(c * a.x - s * eb.x, c * a.y - s * eb.y);
+                A[q * m + j] = make_double2(s * a.x + c * eb.x, s * a.y + c * eb.y);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {  // rotate the tournament: keep idx[0], shift the rest
+                const int last = idx[m - 1];
+                for (int i = m - 1; i > 1; --i) idx[i] = idx[i - 1];
+                idx[1] = last;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {  // insertion sort of the n real diagonal entries
+        for (int i = 0; i < n; ++i) eigs[i] = A[i * m + i].x;
+        for (int i = 1; i < n; ++i) {
+            const double v = eigs[i];
+            int j = i - 1;
+            while (j >= 0 && eigs[j] > v) { eigs[j + 1] = eigs[j]; --j; }
+            eigs[j + 1] = v;
+        }
+    }
+}
+
+static int blocks_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8); }
+
+template <typename T>
+static jdft_status axpby(int npw, int nb, double a, const c_t<T>* x, int ldx, double b, const c_t<T>* y, int ldy,
+                         c_t<T>* z, int ldz, cudaStream_t st) {
+    {
+        Trace tr_("blk_axpby", st);
+        blk_axpby_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, a, x, ldx, b, y, ldy, z, ldz);
+    }
+    return check_launch("blk_axpby");
+}
+
+template <typename T>
+static jdft_status dot(int npw, int nb, const c_t<T>* x, int ldx, const c_t<T>* y, int ldy, double* out,
+                       cudaStream_t st) {
+    JDFT_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), st));
+    {
+        Trace tr_("blk_dot", st);
+        blk_dot_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, x, ldx, y, ldy, out);
+    }
+    return check_launch("blk_dot");
+}
+
+jdft_status small_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
+                                cudaStream_t st) {
+    Trace tr_("cholesky_winv", st);
+    if (fp64)
+        cholesky_winv_kernel<double><<<1, 256, 0, st>>>(n, U, work, work + (size_t)n * n, (double2*)W, status);
+    else
+        cholesky_winv_kernel<float><<<1, 256, 0, st>>>(n, U, work, work + (size_t)n * n, (float2*)W, status);
+    return check_launch("cholesky_winv");
+}
+
+jdft_status small_jacobi_eigs(int n, const double2* A, double2* work, double* eigs, cudaStream_t st) {
+    const int m = n + (n & 1);
+    JDFT_CUDA_TRY(cudaMemsetAsync(work, 0, (size_t)m * m * sizeof(double2), st));
+    JDFT_CUDA_TRY(cudaMemcpy2DAsync(work, m * sizeof(double2), A, n * sizeof(double2), n * sizeof(double2), n,
+                                    cudaMemcpyDeviceToDevice, st));
+    if (m > n) {
+        const double2 pad = make_double2(1e300, 0.0);
+        JDFT_CUDA_TRY(cudaMemcpyAsync(work + (size_t)n * m + n, &pad, sizeof pad, cudaMemcpyHostToDevice, st));
+        JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const size_t smem = (size_t)(m / 2) * (sizeof(double2) + 2 * sizeof(double) + 2 * sizeof(int)) +
+                        (size_t)m * sizeof(int);
+    const int sweeps = 14;
+    {
+        Trace tr_("jacobi_eig", st);
+        jacobi_eig_kernel<<<1, 256, smem, st>>>(n, m, work, sweeps, eigs);
+    }
+    return check_launch("jacobi_eig");
+}
+
+// ---------------------------------------------------------------------------
+// The minimiser state for one precision
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+template <typename T>
+struct MinState {
+    jdft_basis_s* b;
+    int ik, nb, npw, ld;
+    jdft_prec prec;
+    cudaStream_t st;
+    double omega, f;
+    // blocks
+    c_t<T> *C, *HC, *G, *KG, *KGp, *d, *dp, *Hd, *Y, *HY, *Cn, *HCn;
+    // small
+    double2 *Hs, *Hsn, *Pm, *dOd, *U, *lawork;
+    c_t<T>* Bm;  // scaled small matrix in block type
+    c_t<T>* W;
+    double *Tb, *scal;
+    int* status;
+    DevBuf mem;
+    const double* kin;
+
+    jdft_status alloc() {
+        const size_t blk = (size_t)nb * ld * sizeof(c_t<T>);
+        const size_t sm = (size_t)nb * nb * sizeof(double2);
+        const int m = nb + (nb & 1);
+        const size_t total = 12 * blk + 5 * sm + 2 * (size_t)m * m * sizeof(double2) + 2 * (size_t)nb * nb * sizeof(c_t<T>) +
+                             (size_t)nb * sizeof(double) + 64 * sizeof(double) + 64 + 16 * 256;
+        JDFT_CUDA_TRY(cudaMalloc(&mem.p, total));
+        char* q = (char*)mem.p;
+        auto take = [&](size_t n) { char* r = q; q += (n + 255) / 256 * 256; return (void*)r; };
+        C = (c_t<T>*)take(blk); HC = (c_t<T>*)take(blk); G = (c_t<T>*)take(blk); KG = (c_t<T>*)take(blk);
+        KGp = (c_t<T>*)take(blk); d = (c_t<T>*)take(blk); dp = (c_t<T>*)take(blk); Hd = (c_t<T>*)take(blk);
+        Y = (c_t<T>*)take(blk); HY = (c_t<T>*)take(blk); Cn = (c_t<T>*)take(blk); HCn = (c_t<T>*)take(blk);
+        Hs = (double2*)take(sm); Hsn = (double2*)take(sm); Pm = (double2*)take(sm); dOd = (double2*)take(sm);
+        U = (double2*)take(sm); lawork = (double2*)take(2 * (size_t)m * m * sizeof(double2));
+        Bm = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>)); W = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>));
+        Tb = (double*)take(nb * sizeof(double)); scal = (double*)take(64 * sizeof(double)); status = (int*)take(64);
+        JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        return JDFT_OK;
+    }
+
+    jdft_status applyH(const c_t<T>* X, c_t<T>* HX) {
+        return jdft_apply_H(b, ik, X, ld, HX, ld, nb, prec, st);
+    }
+    // out (nb x nb complex128) = alpha X^dag Y
+    jdft_status cn(const c_t<T>* X, const c_t<T>* Yb, double2* out, double alpha) {
+        JDFT_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)nb * nb * sizeof(double2), st));
+        return zgemm_cn<T>(nb, nb, npw, X, ld, Yb, ld, out, nb, alpha, st);
+    }
+    // Z += X . (alpha A)   (A small complex128)
+    jdft_status nn_acc(const c_t<T>* X, const double2* A, double alpha, c_t<T>* Z) {
+        {
+            Trace tr_("small_scale", st);
+            small_scale_kernel<T><<<blocks_for((int64_t)nb * nb), 256, 0, st>>>(nb, A, alpha, Bm);
+        }
+        jdft_status s = check_launch("small_scale");
+        if (s != JDFT_OK) return s;
+        return zgemm_nn_acc<T>(npw, nb, nb, X, ld, Bm, nb, Z, ld, st);
+    }
+    // Z = X . W  (W already in block type)
+    jdft_status rotate(const c_t<T>* X, c_t<T>* Z) {
+        JDFT_CUDA_TRY(cudaMemsetAsync(Z, 0, (size_t)nb * ld * sizeof(c_t<T>), st));
+        return zgemm_nn_acc<T>(npw, nb, nb, X, ld, W, nb, Z, ld, st);
+    }
+    jdft_status hermitize(double2* A, double* tr) {
+        {
+            Trace tr_("hermitize", st);
+            hermitize_kernel<<<1, 256, 0, st>>>(nb, A, tr);
+        }
+        return check_launch("hermitize");
+    }
+    // X <- X - C (Omega C^dag X)
+    jdft_status project(c_t<T>* X) {
+        jdft_status s = cn(C, X, Pm, omega);
+        if (s != JDFT_OK) return s;
+        return nn_acc(C, Pm, -1.0, X);
+    }
+    jdft_status read_scal(double* host, int n) {
+        JDFT_CUDA_TRY(cudaMemcpyAsync(host, scal, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+        return JDFT_OK;
+    }
+    jdft_status read_status() {
+        int s = 0;
+        JDFT_CUDA_TRY(cudaMemcpyAsync(&s, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+        if (s != 0) return set_error((jdft_status)s, "overlap matrix not positive definite in the minimiser");
+        return JDFT_OK;
+    }
+    // Orthonormalise X -> C (Cholesky of Omega X^dag X), then HC = H C, Hs = C^dag HC.
+    jdft_status start_from(const c_t<T>* X) {
+        jdft_status s;
+        if ((s = cn(X, X, U, omega))) return s;
+        if ((s = small_cholesky_winv(nb, U, lawork, W, std::is_same<T, double>::value, status, st))) return s;
+        if ((s = read_status())) return s;
+        if ((s = rotate(X, C))) return s;
+        if ((s = applyH(C, HC))) return s;
+        if ((s = cn(C, HC, Hs, 1.0))) return s;
+        return hermitize(Hs, scal + 0);
+    }
+};
+
+// scal slots
+enum { S_TR = 0, S_GG = 1, S_GKG = 2, S_GKGP = 3, S_A1 = 4, S_DHD = 5, S_HSDOD = 6, S_TRN = 7 };
+
+template <typename T>
+static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop_res, bool allow_stall_exit,
+                             int max_iter, jdft_min_report* rep, double* res_out, double* E_out) {
+    jdft_status s;
+    const int npw = M.npw, nb = M.nb, ld = M.ld;
+    cudaStream_t st = M.st;
+    double h[8];
+    double gkgp_prev = 0.0;
+    bool have_prev = false;
+    double best = 1e300;
+    int stall = 0;
+    for (int it = 0;; ++it) {
+        // gradient and residual
+        if ((s = axpby<T>(npw, nb, 1.0, M.HC, ld, 0.0, nullptr, 0, M.G, ld, st))) return s;
+        if ((s = M.nn_acc(M.C, M.Hs, -M.omega, M.G))) return s;
+        if ((s = dot<T>(npw, nb, M.G, ld, M.G, ld, M.scal + S_GG, st))) return s;
+        if ((s = M.read_scal(h, 2))) return s;
+        const double E = M.f * h[S_TR];
+        const double res = std::sqrt(std::max(h[S_GG], 0.0) / M.omega);
+        *res_out = res;
+        *E_out = E;
+        if (res < stop_res) return JDFT_OK;
+        if (allow_stall_exit) {
+            if (res < 0.7 * best) { best = res; stall = 0; }
+            else if (++stall >= 8) return JDFT_OK;
+        }
+        if (it >= max_iter || rep->iterations >= o.max_iter)
+            return set_error(JDFT_ERR_NOT_CONVERGED, "band minimiser reached its iteration limit");
+        rep->iterations++;
+        // preconditioned gradient, projected
+        {
+            Trace tr_("band_kinetic", st);
+            band_kinetic_kernel<T><<<nb, 256, 0, st>>>(npw, M.C, ld, M.kin, M.omega, M.Tb);
+        }
+        if ((s = check_launch("band_kinetic"))) return s;
+        if (o.precond == JDFT_PRECOND_MLP) {
+            if ((s = mlp_precondition<T>(o.mlp, npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, M.Hs, st))) return s;
+        } else {
+            Trace tr_("precond_teter", st);
+            precond_teter_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(
+                npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, o.precond == JDFT_PRECOND_IDENTITY);
+        }
+        if ((s = check_launch("precondition"))) return s;
+        if ((s = M.project(M.KG))) return s;
+        // Polak-Ribiere
+        if ((s = dot<T>(npw, nb, M.G, ld, M.KG, ld, M.scal + S_GKG, st))) return s;
+        if (have_prev && (s = dot<T>(npw, nb, M.G, ld, M.KGp, ld, M.scal + S_GKGP, st))) return s;
+        if ((s = M.read_scal(h, 4))) return s;
+        double beta = 0.0;
+        if (have_prev && gkgp_prev != 0.0) beta = std::max(0.0, (h[S_GKG] - h[S_GKGP]) / gkgp_prev);
+        const double gkg = h[S_GKG];
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (beta > 0.0) {
+                if ((s = axpby<T>(npw, nb, -1.0, M.KG, ld, beta, M.dp, ld, M.d, ld, st))) return s;
+            } else {
+                if ((s = axpby<T>(npw, nb, -1.0, M.KG, ld, 0.0, nullptr, 0, M.d, ld, st))) return s;
+            }
+            if ((s = M.project(M.d))) return s;
+            if ((s = M.applyH(M.d, M.Hd))) return s;
+            if ((s = dot<T>(npw, nb, M.HC, ld, M.d, ld, M.scal + S_A1, st))) return s;
+            if ((s = dot<T>(npw, nb, M.d, ld, M.Hd, ld, M.scal + S_DHD, st))) return s;
+            if ((s = M.cn(M.d, M.d, M.dOd, M.omega))) return s;
+            {
+                Trace tr_("trace_prod", st);
+                trace_prod_kernel<<<1, 256, 0, st>>>(nb, M.Hs, M.dOd, M.scal + S_HSDOD);
+            }
+            if ((s = check_launch("trace_prod"))) return s;
+            if ((s = M.read_scal(h, 7))) return s;
+            if (2.0 * h[S_A1] < 0.0 || beta == 0.0) break;
+            beta = 0.0;  // not a descent direction: restart along -KG
+        }
+        const double a1 = 2.0 * h[S_A1];
+        const double a2 = h[S_DHD] - h[S_HSDOD];
+        double lam = (a2 > 0.0) ? -a1 / (2.0 * a2) : 1.0;
+        // rounding level of the energy: 64 ulp in FP64; 16 ulp of FP32 when the blocks are FP32
+        const double noise = (std::is_same<T, double>::value ? 64.0 * 2.220446049250313e-16
+                                                             : 16.0 * 1.1920928955078125e-7) * std::fabs(E);
+        bool accepted = false;
+        for (int tries = 0; tries < 30; ++tries) {
+            if ((s = axpby<T>(npw, nb, 1.0, M.C, ld, lam, M.d, ld, M.Y, ld, st))) return s;
+            if ((s = axpby<T>(npw, nb, 1.0, M.HC, ld, lam, M.Hd, ld, M.HY, ld, st))) return s;
+            if ((s = M.cn(M.Y, M.Y, M.U, M.omega))) return s;
+            if ((s = small_cholesky_winv(nb, M.U, M.lawork, M.W, std::is_same<T, double>::value, M.status, st)))
+                return s;
+            if ((s = M.read_status())) return s;
+            if ((s = M.rotate(M.Y, M.Cn))) return s;
+            if ((s = M.rotate(M.HY, M.HCn))) return s;
+            if ((s = M.cn(M.Cn, M.HCn, M.Hsn, 1.0))) return s;
+            if ((s = M.hermitize(M.Hsn, M.scal + S_TRN))) return s;
+            if ((s = M.read_scal(h, 8))) return s;
+            if (M.f * h[S_TRN] <= E + noise) { accepted = true; break; }
+            lam *= 0.5;
+        }
+        if (!accepted) { *res_out = res; return JDFT_OK; }  // no lower energy along d: stationary to rounding
+        std::swap(M.C, M.Cn);
+        std::swap(M.HC, M.HCn);
+        std::swap(M.Hs, M.Hsn);
+        JDFT_CUDA_TRY(cudaMemcpyAsync(M.scal + S_TR, M.scal + S_TRN, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::swap(M.d, M.dp);
+        std::swap(M.KG, M.KGp);
+        gkgp_prev = gkg;
+        have_prev = true;
+    }
+}
+
+template <typename T>
+static jdft_status setup_state(MinState<T>& M, jdft_basis_s* b, int ik, int nb, jdft_prec prec, double f,
+                               cudaStream_t st) {
+    M.b = b; M.ik = ik; M.nb = nb; M.npw = b->ks[ik].npw; M.ld = M.npw; M.prec = prec; M.st = st;
+    M.omega = b->omega; M.f = f; M.kin = b->ks[ik].kin;
+    return M.alloc();
+}
+
+template <typename Src, typename Dst>
+__global__ void convert_block_kernel(int npw, int nb, const c_t<Src>* __restrict__ a, int lda, c_t<Dst>* __restrict__ z,
+                                     int ldz) {
+    const int64_t total = (int64_t)npw * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bb = i / npw, g = i - bb * npw;
+        const c_t<Src> v = a[bb * lda + g];
+        z[bb * ldz + g] = mk<Dst>((Dst)v.x, (Dst)v.y);
+    }
+}
+
+}  // namespace jdft
+
+using namespace jdft;
+
+extern "C" {
+
+jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C, "null argument");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int npw = b->ks[ik].npw;
+    const int m = nb + (nb & 1);
+    DevBuf mem;
+    const size_t sm = (size_t)nb * nb * sizeof(double2);
+    JDFT_CUDA_TRY(cudaMalloc(&mem.p, 3 * sm + 2 * (size_t)m * m * sizeof(double2) + (size_t)nb * ldc * sizeof(double2) +
+                                         1024));
+    double2* U = (double2*)mem.p;
+    double2* W = U + (size_t)nb * nb;
+    double2* work = W + (size_t)nb * nb;
+    double2* tmp = work + 2 * (size_t)m * m;
+    int* status = (int*)(tmp + (size_t)nb * ldc);
+    JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, sm, st));
+    jdft_status s = zgemm_cn<double>(nb, nb, npw, (const double2*)C, ldc, (const double2*)C, ldc, U, nb, b->omega, st);
+    if (s != JDFT_OK) return s;
+    if ((s = small_cholesky_winv(nb, U, work, W, true, status, st))) return s;
+    JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    JDFT_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nb * ldc * sizeof(double2), st));
+    if ((s = zgemm_nn_acc<double>(npw, nb, nb, tmp, ldc, W, nb, (double2*)C, ldc, st))) return s;
+    int hs = 0;
+    JDFT_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs) return set_error(JDFT_ERR_NOT_POSDEF, "C^dag O C is not positive definite");
+    return JDFT_OK;
+}
+
+jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(nb >= 1 && A && eigs, "bad arguments");
+    const int m = nb + (nb & 1);
+    DevBuf mem;
+    JDFT_CUDA_TRY(cudaMalloc(&mem.p, (size_t)m * m * sizeof(double2)));
+    cudaStream_t st = (cudaStream_t)stream;
+    jdft_status s = small_jacobi_eigs(nb, (const double2*)A, (double2*)mem.p, eigs, st);
+    if (s != JDFT_OK) return s;
+    JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+    return JDFT_OK;
+}
+
+jdft_status jdft_minimize_bands(jdft_basis_t b, int ik, void* C, int ldc, int nb, const jdft_min_opts* opts,
+                                double* eigs, jdft_min_report* report, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C && opts && report, "null argument");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    const int npw = b->ks[ik].npw;
+    JDFT_CHECK_ARG(nb >= 1 && nb <= npw && ldc >= npw, "bad block shape");
+    JDFT_CHECK_ARG(opts->tol > 0 && opts->max_iter >= 1, "bad tolerance or iteration limit");
+    JDFT_CHECK_ARG(opts->precond >= JDFT_PRECOND_IDENTITY && opts->precond <= JDFT_PRECOND_MLP, "bad preconditioner");
+    JDFT_CHECK_ARG(opts->precond != JDFT_PRECOND_MLP || opts->mlp, "MLP preconditioner needs weights");
+    if (!b->have_V) return set_error(JDFT_ERR_ARG, "no potential set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double f = opts->occupation > 0 ? opts->occupation : 2.0;
+    *report = jdft_min_report();
+    auto t0 = std::chrono::steady_clock::now();
+    double res = 0.0, E = 0.0;
+    jdft_status s;
+    MinState<double> M64;
+    if ((s = setup_state(M64, b, ik, nb, JDFT_FP64, f, st))) return s;
+    JDFT_CUDA_TRY(cudaMemcpy2DAsync(M64.Y, (size_t)npw * sizeof(double2), C, (size_t)ldc * sizeof(double2),
+                                    (size_t)npw * sizeof(double2), nb, cudaMemcpyDeviceToDevice, st));
+    if (opts->prec != JDFT_FP64) {
+        // bulk iterations with FP32 blocks, then promote
+        MinState<float> M32;
+        if ((s = setup_state(M32, b, ik, nb, opts->prec, f, st))) return s;
+        {
+            Trace tr_("convert_block", st);
+            convert_block_kernel<double, float><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, M64.Y, npw,
+                                                                                             M32.Y, npw);
+        }
+        if ((s = check_launch("convert_block"))) return s;
+        if ((s = M32.start_from(M32.Y))) return s;
+        const double sw = opts->switch_tol > 0 ? opts->switch_tol : 1e-4;
+        s = run_phase<float>(M32, *opts, std::max(sw, opts->tol), true, opts->max_iter, report, &res, &E);
+        if (s != JDFT_OK && s != JDFT_ERR_NOT_CONVERGED) return s;
+        report->mixed_iterations = report->iterations;
+        {
+            Trace tr_("convert_block", st);
+            convert_block_kernel<float, double><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, M32.C, npw,
+                                                                                             M64.Y, npw);
+        }
+        if ((s = check_launch("convert_block"))) return s;
+    }
+    if ((s = M64.start_from(M64.Y))) return s;
+    jdft_min_opts o64 = *opts;
+    s = run_phase<double>(M64, o64, opts->tol, false, opts->max_iter, report, &res, &E);
+    report->residual = res;
+    report->energy = E;
+    report->converged = (s == JDFT_OK && res < opts->tol) ? 1 : 0;
+    if (s != JDFT_OK && s != JDFT_ERR_NOT_CONVERGED) return s;
+    // outputs: converged block and subspace eigenvalues
+    JDFT_CUDA_TRY(cudaMemcpy2DAsync(C, (size_t)ldc * sizeof(double2), M64.C, (size_t)npw * sizeof(double2),
+                                    (size_t)npw * sizeof(double2), nb, cudaMemcpyDeviceToDevice, st));
+    if (eigs) {
+        jdft_status s2 = small_jacobi_eigs(nb, M64.Hs, M64.lawork, eigs, st);
+        if (s2 != JDFT_OK) return s2;
+    }
+    JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+    report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (!report->converged) return set_error(JDFT_ERR_NOT_CONVERGED, "band minimiser reached its iteration limit");
+    return JDFT_OK;
+}
+
+}  // extern "C"

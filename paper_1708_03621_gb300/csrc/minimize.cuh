@@ -1,0 +1,15 @@
+// Internal interfaces between the minimiser and the learned preconditioner.
+#pragma once
+
+#include "common.cuh"
+
+namespace jdft {
+
+// KG = K_theta(features) G for every coefficient (see jdft_mlp_t in jdft.h):
+// features from kin (FP64 per plane wave), Tb (band kinetic energies) and the
+// diagonal of Hs (complex128 nb x nb).
+template <typename T>
+jdft_status mlp_precondition(jdft_mlp_t mlp, int npw, int nb, const c_t<T>* G, int ldg, c_t<T>* KG, int ldk,
+                             const double* kin, const double* Tb, const double2* Hs, cudaStream_t st);
+
+}  // namespace jdft

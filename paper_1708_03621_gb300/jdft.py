@@ -36,6 +36,22 @@ class _CellDesc(ctypes.Structure):
                 ("kweight", ctypes.POINTER(ctypes.c_double))]
 
 
+class MinOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
+                ("prec", ctypes.c_int), ("switch_tol", ctypes.c_double), ("occupation", ctypes.c_double),
+                ("mlp", ctypes.c_void_p)]
+
+
+class MinReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("mixed_iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("energy", ctypes.c_double), ("residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PRECOND = {"identity": 0, "teter": 1, "mlp": 2}
+
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _SIGS = {
     "jdft_basis_create": [ctypes.POINTER(_CellDesc), ctypes.POINTER(_vp)],
@@ -56,6 +72,9 @@ _SIGS = {
     "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
     "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
     "jdft_apply_H_noalloc": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
+    "jdft_orthonormalize": [_vp, _i, _vp, _i, _i, _vp],
+    "jdft_subspace_eigs": [_i, _vp, _vp, _vp],
+    "jdft_minimize_bands": [_vp, _i, _vp, _i, _i, ctypes.POINTER(MinOpts), _vp, ctypes.POINTER(MinReport), _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -255,6 +274,34 @@ def jdft_subspace(basis, ik, C, HC, CHC, COC, prec="fp64", stream=None):
         q, ldh = ctypes.c_void_p(0), ld
     _call("jdft_subspace", basis.handle, ik, p, ld, q, ldh, nb, _ptr(CHC), _ptr(COC), _prec(prec),
           _stream(stream))
+
+
+def jdft_orthonormalize(basis, ik, C, stream=None):
+    """C <- C L^{-dag}, Omega C^dag C = L L^dag (complex128 block)."""
+    p, ld, nb = _block(C, "fp64", "C")
+    _call("jdft_orthonormalize", basis.handle, ik, p, ld, nb, _stream(stream))
+
+
+def jdft_subspace_eigs(A, eigs, stream=None):
+    """Eigenvalues of the Hermitian complex128 (nb, nb) CUDA tensor A into eigs (float64, nb)."""
+    _call("jdft_subspace_eigs", A.shape[0], _ptr(A), _ptr(eigs), _stream(stream))
+
+
+def jdft_minimize_bands(basis, ik, C, eigs=None, tol=1e-8, max_iter=1000, precond="teter", prec="fp64",
+                        switch_tol=0.0, occupation=2.0, mlp=None, stream=None, check=True) -> dict:
+    """Preconditioned band CG in place on the complex128 block C; returns the report as a dict."""
+    p, ld, nb = _block(C, "fp64", "C")
+    o = MinOpts(tol, max_iter, PRECOND[precond] if isinstance(precond, str) else int(precond), _prec(prec),
+                switch_tol, occupation, ctypes.c_void_p(0 if mlp is None else mlp.handle.value))
+    r = MinReport()
+    L = lib()
+    st = L.jdft_minimize_bands(basis.handle, ik, p, ld, nb, ctypes.byref(o), _ptr(eigs), ctypes.byref(r),
+                               _stream(stream))
+    out = r.as_dict()
+    out["status"] = STATUS.get(st, st)
+    if check and st != 0:
+        raise JdftError(st, "jdft_minimize_bands", L.jdft_last_error().decode())
+    return out
 
 
 def jdft_version() -> str:
