@@ -185,6 +185,31 @@ jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream
  * h_b = (C^dag H C)_bb the band's Rayleigh quotient. */
 typedef struct jdft_mlp_s* jdft_mlp_t;
 
+/* Create a network from 4481 host floats (copied; the caller keeps ownership
+ * of params).  The network keeps an FP32 master copy, the BF16 copy its
+ * kernels compute with, and Adam moments. */
+jdft_status jdft_mlp_create(const float* params, jdft_mlp_t* out);
+jdft_status jdft_mlp_destroy(jdft_mlp_t mlp);
+/* Copy the FP32 master parameters to host memory (4481 floats). */
+jdft_status jdft_mlp_get_params(jdft_mlp_t mlp, float* params);
+/* K for `rows` feature triples: feats device float rows x 3, K device float rows. */
+jdft_status jdft_mlp_forward(jdft_mlp_t mlp, int64_t rows, const float* feats, float* K, void* stream);
+/* Loss and gradient over training rows (device float rows x 5: f1, f2, f3, a, q):
+ * loss = sum (K^2 a - 2 K q) / sum a.  grad: device float 4481 (overwritten);
+ * loss: device double[2] (loss, sum a; overwritten). */
+jdft_status jdft_mlp_loss_grad(jdft_mlp_t mlp, int64_t rows, const float* data, float* grad,
+                               double* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with a device gradient. */
+jdft_status jdft_mlp_adam_step(jdft_mlp_t mlp, const float* grad, float lr, void* stream);
+/* Training rows from a minimiser snapshot C (device complex128, nb bands,
+ * ld = npw) and the converged block Cstar: for coefficients
+ * i = offset + r*stride of the band-major block, (f1, f2, f3, |R|^2, Re(conj(R) t))
+ * with R = H C - O C (C^dag H C) and t = C - Cstar (Cstar^dag O C).
+ * rows_out = NULL only returns the row count in *nrows.  Synchronous. */
+jdft_status jdft_mlp_rows(jdft_basis_t basis, int ik, const void* C, const void* Cstar, int nb,
+                          int64_t stride, int64_t offset, float* rows_out, int64_t* nrows,
+                          void* stream);
+
 typedef enum {
     JDFT_PRECOND_IDENTITY = 0,
     JDFT_PRECOND_TETER = 1,   /* Teter, Payne & Allan, PRB 40, 12255 (1989) */

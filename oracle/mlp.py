@@ -99,15 +99,6 @@ def grad(theta, rows):
     return pack(gW1, gb1, gW2, gb2, gW3, gb3)
 
 
-def init(seed: int) -> np.ndarray:
-    """Seeded start: normal weights scaled 1/sqrt(fan-in), zero biases, b3 = 0."""
-    rng = np.random.default_rng(seed)
-    W1 = rng.standard_normal((H, 3)) / np.sqrt(3.0)
-    W2 = rng.standard_normal((H, H)) / np.sqrt(H)
-    W3 = rng.standard_normal(H) / np.sqrt(H)
-    return pack(W1, np.zeros(H), W2, np.zeros(H), W3, 0.0)
-
-
 def features(kin, Tb, h):
     """Feature rows for every (G, b): returns (npw, nb, 3)."""
     kin = np.asarray(kin)[:, None]

@@ -380,6 +380,7 @@ struct MinState {
     c_t<T>* Bm;  // scaled small matrix in block type
     c_t<T>* W;
     double *Tb, *scal;
+    float* bf;  // per-band features of the learned preconditioner
     int* status;
     DevBuf mem;
     const double* kin;
@@ -389,7 +390,8 @@ struct MinState {
         const size_t sm = (size_t)nb * nb * sizeof(double2);
         const int m = nb + (nb & 1);
         const size_t total = 12 * blk + 5 * sm + 2 * (size_t)m * m * sizeof(double2) + 2 * (size_t)nb * nb * sizeof(c_t<T>) +
-                             (size_t)nb * sizeof(double) + 64 * sizeof(double) + 64 + 16 * 256;
+                             (size_t)nb * sizeof(double) + 64 * sizeof(double) + 64 + 3 * (size_t)nb * sizeof(float) +
+                             17 * 256;
         JDFT_CUDA_TRY(cudaMalloc(&mem.p, total));
         char* q = (char*)mem.p;
         auto take = [&](size_t n) { char* r = q; q += (n + 255) / 256 * 256; return (void*)r; };
@@ -400,6 +402,7 @@ struct MinState {
         U = (double2*)take(sm); lawork = (double2*)take(2 * (size_t)m * m * sizeof(double2));
         Bm = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>)); W = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>));
         Tb = (double*)take(nb * sizeof(double)); scal = (double*)take(64 * sizeof(double)); status = (int*)take(64);
+        bf = (float*)take(3 * (size_t)nb * sizeof(float));
         JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
         return JDFT_OK;
     }
@@ -504,7 +507,7 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
         }
         if ((s = check_launch("band_kinetic"))) return s;
         if (o.precond == JDFT_PRECOND_MLP) {
-            if ((s = mlp_precondition<T>(o.mlp, npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, M.Hs, st))) return s;
+            if ((s = mlp_precondition<T>(o.mlp, npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, M.Hs, M.bf, st))) return s;
         } else {
             Trace tr_("precond_teter", st);
             precond_teter_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(

@@ -75,6 +75,13 @@ _SIGS = {
     "jdft_orthonormalize": [_vp, _i, _vp, _i, _i, _vp],
     "jdft_subspace_eigs": [_i, _vp, _vp, _vp],
     "jdft_minimize_bands": [_vp, _i, _vp, _i, _i, ctypes.POINTER(MinOpts), _vp, ctypes.POINTER(MinReport), _vp],
+    "jdft_mlp_create": [_vp, ctypes.POINTER(_vp)],
+    "jdft_mlp_destroy": [_vp],
+    "jdft_mlp_get_params": [_vp, _vp],
+    "jdft_mlp_forward": [_vp, ctypes.c_int64, _vp, _vp, _vp],
+    "jdft_mlp_loss_grad": [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp],
+    "jdft_mlp_adam_step": [_vp, _vp, ctypes.c_float, _vp],
+    "jdft_mlp_rows": [_vp, _i, _vp, _vp, _i, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -301,6 +308,63 @@ def jdft_minimize_bands(basis, ik, C, eigs=None, tol=1e-8, max_iter=1000, precon
     out["status"] = STATUS.get(st, st)
     if check and st != 0:
         raise JdftError(st, "jdft_minimize_bands", L.jdft_last_error().decode())
+    return out
+
+
+MLP_NPARAM = 4481
+
+
+class Mlp:
+    """Owner of a jdft_mlp_t (the learned preconditioner network)."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if p.size != MLP_NPARAM:
+            raise ValueError(f"need {MLP_NPARAM} parameters")
+        h = ctypes.c_void_p()
+        _call("jdft_mlp_create", ctypes.c_void_p(p.ctypes.data), ctypes.byref(h))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jdft_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_NPARAM, dtype=np.float32)
+        _call("jdft_mlp_get_params", self.handle, ctypes.c_void_p(out.ctypes.data))
+        return out
+
+
+def jdft_mlp_forward(mlp, feats, K, stream=None):
+    _call("jdft_mlp_forward", mlp.handle, feats.shape[0], _ptr(feats), _ptr(K), _stream(stream))
+
+
+def jdft_mlp_loss_grad(mlp, rows, grad, loss, stream=None):
+    """rows: (n, 5) float32 CUDA tensor; grad: float32 (4481,); loss: float64 (2,)."""
+    _call("jdft_mlp_loss_grad", mlp.handle, rows.shape[0], _ptr(rows), _ptr(grad), _ptr(loss), _stream(stream))
+
+
+def jdft_mlp_adam_step(mlp, grad, lr, stream=None):
+    _call("jdft_mlp_adam_step", mlp.handle, _ptr(grad), float(lr), _stream(stream))
+
+
+def jdft_mlp_rows(basis, ik, C, Cstar, stride=1, offset=0, stream=None):
+    """Training rows (float32 CUDA tensor (n, 5)) from snapshot C and converged Cstar (complex128, ld = npw)."""
+    import torch
+    nb = C.shape[0]
+    n = ctypes.c_int64()
+    _call("jdft_mlp_rows", basis.handle, ik, _ptr(C), _ptr(Cstar), nb, stride, offset, ctypes.c_void_p(0),
+          ctypes.byref(n), _stream(stream))
+    out = torch.empty((n.value, 5), dtype=torch.float32, device=C.device)
+    _call("jdft_mlp_rows", basis.handle, ik, _ptr(C), _ptr(Cstar), nb, stride, offset, _ptr(out), ctypes.byref(n),
+          _stream(stream))
     return out
 
 

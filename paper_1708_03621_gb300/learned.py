@@ -1,0 +1,137 @@
+"""Training pipeline of the learned preconditioner (argument marshalling only).
+
+Every numerical step runs in libjdft's kernels: the Teter-preconditioned band
+minimiser produces trajectories on seeded cells, jdft_mlp_rows turns snapshots
+of them into (features, residual, correction) rows, and jdft_mlp_loss_grad /
+jdft_mlp_adam_step train the BF16 network.  PyTorch only holds device memory
+and shuffles row indices.
+
+    python -m paper_1708_03621_gb300.learned --cells 200 --out weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import time
+
+import numpy as np
+
+from . import jdft
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "precond_mlp.npy")
+
+
+def build_cell(w, device):
+    """Basis, potential and projectors of a synthetic workload, set up on the GPU."""
+    import torch
+    from synth import atom_positions
+    b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+    atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+    V = torch.empty(int(np.prod(w.S)), dtype=torch.float64, device=device)
+    jdft.jdft_gaussian_potential(b, atoms, V)
+    jdft.jdft_set_potential(b, V)
+    for ik in range(w.nk):
+        P = torch.empty((4 * w.natoms, b.npw(ik)), dtype=torch.complex128, device=device)
+        jdft.jdft_gaussian_projectors(b, ik, atoms, P)
+        D = torch.tensor(np.diag(np.tile([0.5, -0.3, -0.3, -0.3], w.natoms)), device=device)
+        jdft.jdft_set_projectors(b, ik, P, D)
+    return b
+
+
+def start_block(b, w, ik=0, nb=None, seed=None):
+    """Seeded random starting block (complex128, band-major) damped by 1 + |k+G|^2."""
+    from synth import random_coefficients
+    iG = b.gvectors(ik).astype(np.float64)
+    q = (iG + np.asarray(w.kfrac[ik])) @ (2 * np.pi * np.linalg.inv(w.R).T).T
+    return random_coefficients(np.sum(q * q, 1), w.nbands if nb is None else nb,
+                               w.seed_coeffs if seed is None else seed)
+
+
+def generate_rows(cells, snapshots=(2, 5, 10, 20, 40), rows_per_snapshot=40000, prec="fp32", tol=1e-7,
+                  device="cuda", log=print):
+    """Training rows from Teter-minimiser trajectories on the given cells."""
+    import torch
+    out = []
+    for ci, w in enumerate(cells):
+        t0 = time.time()
+        b = build_cell(w, device)
+        C0 = torch.tensor(start_block(b, w), device=device)
+        Cs = C0.clone()
+        rep = jdft.jdft_minimize_bands(b, 0, Cs, tol=tol, max_iter=3000, precond="teter", prec=prec, check=False)
+        n = 0
+        for k in snapshots:
+            if k >= rep["iterations"]:
+                break
+            Ck = C0.clone()
+            jdft.jdft_minimize_bands(b, 0, Ck, tol=1e-30, max_iter=k, precond="teter", prec=prec, check=False)
+            total = Ck.shape[0] * Ck.shape[1]
+            stride = max(1, total // rows_per_snapshot)
+            rows = jdft.jdft_mlp_rows(b, 0, Ck, Cs, stride=stride, offset=(ci * 7919 + k) % stride)
+            out.append(rows)
+            n += rows.shape[0]
+        b.close()
+        log(f"cell {ci} {w.name}: L={w.L[0]:.2f} nb={w.nbands} npw={Cs.shape[1]} iters={rep['iterations']} "
+            f"rows={n} {time.time() - t0:.1f}s")
+    return torch.cat(out, 0) if out else torch.empty((0, 5), device=device)
+
+
+def train(mlp, rows, epochs=20, batch=65536, lr=3e-3, seed=0, log=print):
+    """Adam on shuffled mini-batches of the rows; returns the per-epoch mean loss."""
+    import torch
+    gen = torch.Generator(device=rows.device)
+    gen.manual_seed(seed)
+    grad = torch.empty(jdft.MLP_NPARAM, dtype=torch.float32, device=rows.device)
+    loss = torch.empty(2, dtype=torch.float64, device=rows.device)
+    hist = []
+    for ep in range(epochs):
+        perm = torch.randperm(rows.shape[0], generator=gen, device=rows.device)
+        tot, cnt = 0.0, 0
+        for s in range(0, rows.shape[0], batch):
+            bt = rows[perm[s:s + batch]].contiguous()
+            jdft.jdft_mlp_loss_grad(mlp, bt, grad, loss)
+            jdft.jdft_mlp_adam_step(mlp, grad, lr)
+            tot += float(loss[0].item())
+            cnt += 1
+        hist.append(tot / max(cnt, 1))
+        log(f"epoch {ep}: loss {hist[-1]:.6f}")
+    return hist
+
+
+def evaluation_loss(mlp, rows):
+    import torch
+    grad = torch.empty(jdft.MLP_NPARAM, dtype=torch.float32, device=rows.device)
+    loss = torch.empty(2, dtype=torch.float64, device=rows.device)
+    jdft.jdft_mlp_loss_grad(mlp, rows, grad, loss)
+    return float(loss[0].item())
+
+
+def load_weights(path=WEIGHTS):
+    return np.load(path).astype(np.float32) if os.path.exists(path) else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cells", type=int, default=200)
+    ap.add_argument("--seed0", type=int, default=1000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--init-seed", type=int, default=7)
+    args = ap.parse_args()
+    import torch
+    from synth import mlp_init, training_cells
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    rows = generate_rows(training_cells(args.cells, args.seed0))
+    held = generate_rows(training_cells(10, 2000))
+    print(f"rows: train {rows.shape[0]} held-out {held.shape[0]} ({time.time() - t0:.0f}s)")
+    mlp = jdft.Mlp(mlp_init(args.init_seed))
+    print(f"held-out loss before: {evaluation_loss(mlp, held):.6f}")
+    train(mlp, rows, epochs=args.epochs)
+    print(f"held-out loss after: {evaluation_loss(mlp, held):.6f}")
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.save(args.out, mlp.params())
+    print(f"saved {args.out} ({time.time() - t0:.0f}s)")
+
+
+if __name__ == "__main__":
+    main()

@@ -115,3 +115,27 @@ def random_cells(n: int, seed: int, L_range=(8.0, 16.0), ecut: float = 20.0):
                               (tuple(rng.uniform(-0.5, 0.5, size=3)),), natoms, nb,
                               seed * 100 + 2 * c, seed * 100 + 2 * c + 1))
     return cells
+
+
+def mlp_init(seed: int, hidden: int = 64) -> np.ndarray:
+    """Seeded starting parameters of the preconditioner network (4481 floats for
+    hidden = 64): weights N(0, 1/fan_in), zero biases, in the order
+    W1 (hidden x 3), b1, W2 (hidden x hidden), b2, W3 (hidden), b3."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((hidden, 3)) / np.sqrt(3.0)
+    W2 = rng.standard_normal((hidden, hidden)) / np.sqrt(hidden)
+    W3 = rng.standard_normal(hidden) / np.sqrt(hidden)
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), W3, [0.0]])
+
+
+def training_cells(n: int, seed0: int = 1000, L_range=(16.0, 24.0), ecut: float = 20.0):
+    """Seeded cells for the preconditioner's training data: cubic L ~ U(L_range),
+    n_atoms = round(8 (L/10)^3) uniform in the cell, n_bands = 2 n_atoms, k = 0."""
+    cells = []
+    for c in range(n):
+        rng = np.random.default_rng(seed0 + c)
+        L = float(rng.uniform(*L_range))
+        natoms = int(round(8 * (L / 10.0) ** 3))
+        cells.append(Workload(f"train{seed0 + c}", (L, L, L), ecut, (box_for(L, ecut),) * 3, ((0.0, 0.0, 0.0),),
+                              natoms, 2 * natoms, seed0 + c, 10 ** 6 + seed0 + c))
+    return cells

@@ -7,6 +7,7 @@ import pytest
 from oracle import minimize as mn
 from oracle import mlp
 from oracle import planewave as pw
+from synth import mlp_init
 from tests.systems import OracleSystem, workload
 
 rng = np.random.default_rng(9)
@@ -32,7 +33,7 @@ def test_activation_closed_forms():
 
 
 def test_gradient_matches_finite_differences():
-    theta = mlp.init(3)
+    theta = mlp_init(3)
     theta[mlp.NPARAM - 1] = 0.3
     rows = random_rows(40)
     g = mlp.grad(theta, rows)
@@ -74,7 +75,7 @@ def test_network_preconditioner_reaches_same_minimum():
     o = OracleSystem(workload("tiny_cubic"))
     Hf = lambda X: pw.apply_H(o.basis, o.V, X, o.P, o.D)
     exact = np.linalg.eigvalsh(pw.dense_H(o.basis, o.V, o.P, o.D) / o.basis.Omega)[:6]
-    res = mn.minimize_bands(o.basis, Hf, o.coeffs(6).T, precond=mlp.make_precond(mlp.init(5)), tol=1e-9,
+    res = mn.minimize_bands(o.basis, Hf, o.coeffs(6).T, precond=mlp.make_precond(mlp_init(5)), tol=1e-9,
                             max_iter=1500)
     assert res.converged
     assert np.max(np.abs(np.sort(res.eigs) - exact)) < 1e-11
