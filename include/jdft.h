@@ -204,8 +204,12 @@ jdft_status jdft_mlp_adam_step(jdft_mlp_t mlp, const float* grad, float lr, void
 /* Training rows from a minimiser snapshot C (device complex128, nb bands,
  * ld = npw) and the converged block Cstar: for coefficients
  * i = offset + r*stride of the band-major block, (f1, f2, f3, |R|^2, Re(conj(R) t))
- * with R = H C - O C (C^dag H C) and t = C - Cstar (Cstar^dag O C).
- * rows_out = NULL only returns the row count in *nrows.  Synchronous. */
+ * with R = H C - O C (C^dag H C) and t = C - Cstar (Cstar^dag O C); the q
+ * column is then scaled by sum(a)/sum(q) over the emitted rows, so the best
+ * constant K is 1 (the minimiser's line step makes the overall scale of the
+ * preconditioner irrelevant; this keeps targets of different cells and
+ * iterations on one scale).  rows_out = NULL only returns the row count in
+ * *nrows.  Synchronous. */
 jdft_status jdft_mlp_rows(jdft_basis_t basis, int ik, const void* C, const void* Cstar, int nb,
                           int64_t stride, int64_t offset, float* rows_out, int64_t* nrows,
                           void* stream);

@@ -304,6 +304,30 @@ __global__ void rows_scale_kernel(int n, const double2* __restrict__ A, double a
         B[e] = make_double2(alpha * A[e].x, alpha * A[e].y);
 }
 
+// sums[0] += a, sums[1] += q over the rows
+__global__ void rows_sums_kernel(int64_t n, const float* __restrict__ rows, double* __restrict__ sums) {
+    double a = 0.0, q = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        a += rows[5 * r + 3];
+        q += rows[5 * r + 4];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        q += __shfl_down_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], a);
+        atomicAdd(&sums[1], q);
+    }
+}
+
+// q <- q * sum(a) / sum(q): the best constant K of the scaled rows is 1
+__global__ void rows_normalize_kernel(int64_t n, float* __restrict__ rows, const double* __restrict__ sums) {
+    const double s = sums[1] != 0.0 ? sums[0] / sums[1] : 1.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        rows[5 * r + 4] = (float)(rows[5 * r + 4] * s);
+}
+
 static int grid_rows(int64_t rows, int per) {
     return (int)std::min<int64_t>(std::max<int64_t>((rows + per - 1) / per, 1), 152 * 8);
 }
@@ -455,7 +479,9 @@ jdft_status jdft_mlp_rows(jdft_basis_t b, int ik, const void* C, const void* Cst
     double2* Bm = (double2*)alloc((size_t)nb * nb * sizeof(double2));
     double* Tb = (double*)alloc(nb * sizeof(double));
     float* bf = (float*)alloc(3 * (size_t)nb * sizeof(float));
-    if (!HC || !G || !Tt || !Hs || !M || !Bm || !Tb || !bf) return done(set_error(JDFT_ERR_OOM, "jdft_mlp_rows"));
+    double* sums = (double*)alloc(2 * sizeof(double));
+    if (!HC || !G || !Tt || !Hs || !M || !Bm || !Tb || !bf || !sums)
+        return done(set_error(JDFT_ERR_OOM, "jdft_mlp_rows"));
     const double2* Cd = (const double2*)C;
     const double2* Cs = (const double2*)Cstar;
     jdft_status s;
@@ -496,6 +522,20 @@ jdft_status jdft_mlp_rows(jdft_basis_t b, int ik, const void* C, const void* Cst
                                                            rows_out);
     }
     if ((s = check_launch("make_rows"))) return done(s);
+    if (n > 0) {
+        if (cudaMemsetAsync(sums, 0, 2 * sizeof(double), st) != cudaSuccess)
+            return done(set_error(JDFT_ERR_CUDA, "memset"));
+        {
+            Trace tr_("mlp_rows_sums", st);
+            rows_sums_kernel<<<grid_rows(n, 256), 256, 0, st>>>(n, rows_out, sums);
+        }
+        if ((s = check_launch("rows_sums"))) return done(s);
+        {
+            Trace tr_("mlp_rows_normalize", st);
+            rows_normalize_kernel<<<grid_rows(n, 256), 256, 0, st>>>(n, rows_out, sums);
+        }
+        if ((s = check_launch("rows_normalize"))) return done(s);
+    }
     *nrows = n;
     return done(JDFT_OK);
 }

@@ -47,9 +47,15 @@ def start_block(b, w, ik=0, nb=None, seed=None):
                                w.seed_coeffs if seed is None else seed)
 
 
-def generate_rows(cells, snapshots=(2, 5, 10, 20, 40), rows_per_snapshot=40000, prec="fp32", tol=1e-7,
+def generate_rows(cells, snapshots=(10, 20, 40, 60), rows_per_snapshot=40000, prec="fp32", tol=1e-7,
                   device="cuda", log=print):
-    """Training rows from Teter-minimiser trajectories on the given cells."""
+    """Training rows from Teter-minimiser trajectories on the given cells.
+
+    Snapshots come from the later part of each trajectory (from iteration 10
+    on), where the correction to the converged subspace is close to the
+    linear response to the residual; the first few iterations of a random
+    start teach the network a shape that slows convergence near the minimum.
+    """
     import torch
     out = []
     for ci, w in enumerate(cells):
