@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--workload", default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -187,11 +188,13 @@ class Problem:
         self.ctype = ct
 
     def step(self, stream=None):
+        """Rows a1-a9: H C, density, C^dag H C and C^dag O C, Cholesky orthonormalisation."""
         j = self.jdft
         j.jdft_apply_H(self.basis, 0, self.C, self.HC, self.prec, stream)
         self.n.zero_()
         j.jdft_density(self.basis, 0, self.C, self.f, self.n, self.prec, stream)
         j.jdft_subspace(self.basis, 0, self.C, self.HC, self.CHC, self.COC, self.prec, stream)
+        j.jdft_orthonormalize(self.basis, 0, self.C, self.prec, stream)
 
     def io_bytes(self):
         e = self.C.element_size()
@@ -211,23 +214,55 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
     e = p.C.element_size()
     per_launch_bands = nb / max(1, launches)
     l2 = math.log2
-    if name == "plane_apply":
+    if name in ("tc_zgemm_cn", "tc_zgemm_nn"):
+        return kernel_work(p, name[3:], launches, nb)
+    if name in ("plane_apply", "plane_apply_fast"):
         fl = 5 * S2 * (2 * nrows * S1 * l2(S1) + 2 * S1 * S0 * l2(S0))
         by = 2 * S2 * ncols * e
         return fl * per_launch_bands, by * per_launch_bands + p.N * (8 if e == 16 else 4)
-    if name == "plane_density":
+    if name in ("plane_density", "plane_density_fast"):
         fl = 5 * S2 * (nrows * S1 * l2(S1) + S1 * S0 * l2(S0))
         return fl * per_launch_bands, S2 * ncols * e * per_launch_bands + p.N * 8
     if name in ("zpass_inverse", "zpass_forward"):
         fl = 5 * ncols * S2 * l2(S2)
         by = (p.npw + S2 * ncols) * e + (p.npw * e if name == "zpass_forward" else 0)
         return fl * per_launch_bands, by * per_launch_bands
-    if name == "zgemm_cn":  # P^dag C, C^dag HC, C^dag C: all nb x nb (nproj = nb here) over npw
+    if name == "zgemm_cn":  # P^dag C, C^dag HC, C^dag C (and U in the orthonormalisation): nb x nb over npw
         M = N = p.nb
         return 8.0 * M * N * p.npw, 2.0 * p.nb * p.npw * e
     if name == "zgemm_nn":
         return 8.0 * p.npw * p.nb * p.nproj, (2.0 * p.nb + p.nproj) * p.npw * e
     return 0.0, 0.0
+
+
+def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
+    """The roofline that bounds one kernel, with its peak and where that comes from.
+
+    FFT and CUDA-core GEMM kernels: FP32 (or FP64) issue rate; tensor-core
+    GEMMs: TF32 dense rate = measured BF16 burst x (1.1 / 2.25), the nominal
+    TF32/BF16 ratio, against algorithmic 8MNK flops (the 3-term split issues 3x
+    that, so 1/3 is that kernel's ceiling); everything else: HBM copy bandwidth.
+    """
+    name = k["name"]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src_hbm = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
+    if name.startswith("tc_zgemm"):
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        peak = bf16 * 1.1 / 2.25
+        return {"bound": "tensor", "achieved": k["achieved_tflops"], "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round((k["achieved_tflops"] or 0) / peak, 4), "split_passes": 3,
+                "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25 (of measured)"}
+    if name.startswith("plane_") or name.startswith("zgemm") or name.startswith("zpass"):
+        alu = fp_peak_tflops(prec, 2070.0)
+        r_alu = (k["achieved_tflops"] or 0) / alu
+        r_hbm = (k["achieved_gbs"] or 0) / hbm
+        if r_alu >= r_hbm:
+            return {"bound": "alu", "achieved": k["achieved_tflops"], "peak": round(alu, 2), "unit": "TFLOP/s",
+                    "frac": round(r_alu, 4),
+                    "peak_source": ("FP32 lanes 128/SM x 152 SMs x 2 x 2070 MHz" if prec != "fp64"
+                                    else "FP64 nominal 1.25 TFLOP/s")}
+    return {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": round((k["achieved_gbs"] or 0) / hbm, 4), "peak_source": src_hbm}
 
 
 def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:
@@ -284,20 +319,13 @@ def run_ours(args, world, rank, local, pg):
                         "gflop_per_launch": round(fl / 1e9, 4), "mb_per_launch": round(by / 1e6, 3),
                         "achieved_tflops": round(fl / avg_s / 1e12, 3) if fl else None,
                         "achieved_gbs": round(by / avg_s / 1e9, 1) if by else None})
-    top = kernels[0]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    alu_peak = fp_peak_tflops(args.prec, 2070.0)
-    if top["achieved_tflops"] is not None and top["achieved_tflops"] / alu_peak >= top["achieved_gbs"] / hbm_peak:
-        roof = {"bound": "alu", "kernel": top["name"], "achieved": top["achieved_tflops"], "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(top["achieved_tflops"] / alu_peak, 4),
-                "peak_source": ("FP32 lanes 128/SM x 152 SMs x 2 x 2070 MHz" if args.prec != "fp64"
-                                else "FP64 nominal 1.25 TFLOP/s")}
-    else:
-        roof = {"bound": "hbm", "kernel": top["name"], "achieved": top["achieved_gbs"], "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(top["achieved_gbs"] / hbm_peak, 4),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    for k in kernels:
+        k["roofline"] = roofline_of(k, args.prec, peaks)
+    top = kernels[0]
+    roof = dict(top["roofline"])
+    roof["kernel"] = top["name"]
     roof["traffic"] = None
 
     # ---- end to end through the public API with host buffers ----
@@ -342,6 +370,9 @@ def run_ours(args, world, rank, local, pg):
         fp64 = {"value": round(q.nb * k64 / (t64 / 1e3), 1), "ms_per_step": round(t64 / k64, 3), "steps": k64}
         p = q
 
+    cg = None
+    if not args.no_cg and world == 1:
+        cg = cg_measurements(args.prec if args.prec != "fp64" else "fp32", dev)
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
@@ -349,17 +380,82 @@ def run_ours(args, world, rank, local, pg):
         "dtype": {"fp64": "f64", "fp32": "f32", "tf32x3": "f32+tf32x3", "bf16x3": "f32+bf16x3"}[args.prec],
         "data": "synthetic (seeded Gaussian atoms, random damped coefficients)",
         "config": {"workload": "cubic L=20 bohr, Ecut=30 Ha, box 128^3, 62759 PW, 64 atoms, 256 projectors, "
-                               "256 bands, 1 k-point; step = apply_H + density + subspace",
+                               "256 bands, 1 k-point; step = apply_H + density + subspace + Cholesky orthonormalisation "
+                               "(rows a1-a9); the band-CG row a10 is measured under 'cg'",
                    "precision": args.prec, "npw": p.npw, "nbands": p.nb, "nproj": p.nproj,
                    "l2": "working set ~0.5 GB > 126 MB L2 (C, HC, P re-read every step)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
         "fp64_path": fp64,
+        "cg": cg,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def cg_measurements(prec: str, device, log=lambda *_: None) -> dict:
+    """Row a10, the preconditioned band CG, measured two ways.
+
+    * cost of one iteration on the 128^3 workload (256 bands): wall time of
+      minimisations stopped after 6 and after 2 iterations, difference / 4
+      (each iteration applies H to the 256-band search direction once);
+    * time to |dE| < 1e-6 Ha on the 48^3 workload (16 bands) from the seeded
+      start, for FP64 + Teter, mixed + Teter and mixed + the learned network
+      (committed weights), against E_ref from an FP64 run to residual 1e-10.
+    """
+    import torch
+
+    from paper_1708_03621_gb300 import jdft, learned
+    from synth import WORKLOADS
+    out = {}
+    w = WORKLOADS["large"]
+    b = learned.build_cell(w, device)
+    C0 = torch.tensor(learned.start_block(b, w), device=device)
+    wall = {}
+    for k in (2, 6):
+        C = C0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jdft.jdft_minimize_bands(b, 0, C, tol=1e-30, max_iter=k, precond="teter", prec=prec, switch_tol=1e-30,
+                                 check=False)
+        wall[k] = time.perf_counter() - t0
+    per_it = max(1e-9, (wall[6] - wall[2]) / 4)
+    out["large_iteration_ms"] = round(per_it * 1e3, 3)
+    out["large_iteration_band_applies_per_s"] = round(w.nbands / per_it, 1)
+    b.close()
+    del C0, C
+    w = WORKLOADS["small"]
+    b = learned.build_cell(w, device)
+    C0 = torch.tensor(learned.start_block(b, w), device=device)
+    C = C0.clone()
+    ref = jdft.jdft_minimize_bands(b, 0, C, tol=1e-10, max_iter=5000, precond="teter", prec="fp64")
+    E_ref = ref["energy"]
+    runs = [("fp64", "teter", None), (prec, "teter", None)]
+    wts = learned.load_weights()
+    mlp = jdft.Mlp(wts) if wts is not None else None
+    if mlp is not None:
+        runs.append((prec, "mlp", mlp))
+    res = {}
+    for pr, pc, m in runs:
+        best = None
+        for _ in range(3):   # best of three (the first includes one-time set-up of kernels)
+            C = C0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = jdft.jdft_minimize_bands(b, 0, C, tol=1e-6, max_iter=5000, precond=pc, prec=pr, mlp=m)
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, rep)
+        dt, rep = best
+        res[f"{pr}+{pc}"] = {"seconds": round(dt, 4), "iterations": rep["iterations"],
+                             "mixed_iterations": rep["mixed_iterations"],
+                             "dE_Ha": float(f"{abs(rep['energy'] - E_ref):.3e}")}
+    out["small_time_to_dE_1e-6"] = res
+    out["small_E_ref_Ha"] = E_ref
+    b.close()
+    return out
 
 
 def oracle_sample_step(o, C):

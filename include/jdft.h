@@ -165,12 +165,15 @@ jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, co
 
 /* ---- orthonormalisation, subspace diagonalisation, band minimisation ----- */
 
-/* C <- C L^{-dag} with Omega C^dag C = L L^dag (Cholesky, FP64 on the GPU), so
- * that C^dag O C = 1 afterwards (O diagonal in the plane-wave basis, Sec. 2.1).
- * C: device complex128, band-major (ldc >= npw).  Synchronous (returns after
- * the work is done).  JDFT_ERR_NOT_POSDEF if the bands are linearly dependent.
- * Allocates a small temporary (nb x ldc complex128 plus nb^2 matrices). */
-jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, void* stream);
+/* C <- C L^{-dag} with Omega C^dag C = L L^dag, so that C^dag O C = 1 afterwards
+ * (O diagonal in the plane-wave basis, Sec. 2.1).  C: device, band-major
+ * (ldc >= npw), complex128 for JDFT_FP64 and complex64 otherwise; the products
+ * C^dag C and C L^{-dag} run at `prec`, the Cholesky factorisation and
+ * triangular inverse in FP64 on the GPU.  Uses (and may grow) the basis
+ * workspace.  Synchronous.  JDFT_ERR_NOT_POSDEF if the bands are linearly
+ * dependent. */
+jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,
+                                void* stream);
 
 /* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
  * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,
@@ -250,6 +253,45 @@ jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, in
                                 const jdft_min_opts* opts, double* eigs, jdft_min_report* report,
                                 void* stream);
 
+/* ---- schedule autotuning ------------------------------------------------ */
+
+/* Time jdft_apply_H on the caller's blocks for band-chunk budgets of
+ * 16 ... 256 MB (the column buffer passed between the chain kernels; small
+ * enough chunks stay in L2) and keep the fastest in the basis for later calls.
+ * Overwrites HC.  *chunk_mb (host, may be NULL) receives the choice.
+ * Synchronous; may grow the workspace. */
+jdft_status jdft_autotune_chunk(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
+                                int nb, jdft_prec prec, int* chunk_mb, void* stream);
+
+/* ---- batches in one CUDA graph -------------------------------------------- */
+
+/* One Hamiltonian application of a batch: H C for nb bands of k-point ik of
+ * `basis` (arguments as for jdft_apply_H; device buffers owned by the caller). */
+typedef struct {
+    jdft_basis_t basis;
+    int ik;
+    const void* C;
+    int ldc;
+    void* HC;
+    int ldhc;
+    int nb;
+    jdft_prec prec;
+} jdft_apply_item;
+
+typedef struct jdft_batch_s* jdft_batch_t;
+
+/* Record the n applications (host array, copied) as one CUDA graph: each item
+ * runs once (warm-up, on a private stream; its HC is written), then all are
+ * captured in order and instantiated.  The k-points of one cell (uneven sphere
+ * sizes) and independent cells with their own boxes can be mixed.  The graph
+ * keeps the given device pointers: keep the buffers alive, refill the C blocks
+ * as needed, and replay with jdft_batch_launch.  Items that share a basis share
+ * its workspace and run in order.  Synchronous. */
+jdft_status jdft_batch_create(int n, const jdft_apply_item* items, jdft_batch_t* out);
+/* Replay every application of the batch on `stream` with one graph launch. */
+jdft_status jdft_batch_launch(jdft_batch_t batch, void* stream);
+jdft_status jdft_batch_destroy(jdft_batch_t batch);
+
 /* ---- the Hamiltonian without device allocation --------------------------- */
 
 /* Same result as jdft_apply_H (same arguments, layouts and precisions), but the
@@ -285,6 +327,11 @@ jdft_status jdft_profile_enable(int on);
  * "name launches total_ms\n", into buf (host, buflen bytes, NUL-terminated);
  * then forget the records.  JDFT_ERR_ARG if buf is too small. */
 jdft_status jdft_profile_read(char* buf, int buflen);
+
+/* Wait for `stream`, then report JDFT_ERR_TIMEOUT if a bounded device-side wait
+ * (the tensor-core products' barrier waits) gave up since the last call, and
+ * clear the record.  JDFT_OK otherwise. */
+jdft_status jdft_device_status(void* stream);
 
 /* Number of kernels the library has launched in this process (all calls). */
 long long jdft_launch_count(void);

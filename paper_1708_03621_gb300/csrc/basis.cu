@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "profile.cuh"
@@ -25,6 +27,20 @@ jdft_status check_launch(const char* what) {
     if (e != cudaSuccess)
         return set_error(JDFT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
     return JDFT_OK;
+}
+
+cudaError_t set_smem_attr(const void* func, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, func);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done[key] = smem;
+    return e;
 }
 
 jdft_status ensure_workspace(jdft_basis_s* b, size_t bytes) {
@@ -75,7 +91,7 @@ template <typename T> static jdft_status upload(T** dst, const std::vector<T>& s
 }
 
 static void free_sphere(KSphere& s) {
-    cudaFree(s.col_start); cudaFree(s.col_slot01); cudaFree(s.row_col_start);
+    cudaFree(s.col_start); cudaFree(s.col_slot01); cudaFree(s.row_col_start); cudaFree(s.row_i1lo);
     cudaFree(s.pw_col); cudaFree(s.pw_z); cudaFree(s.kin); cudaFree(s.kvec); cudaFree(s.kin32);
     cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D);
     s = KSphere();
@@ -145,11 +161,16 @@ static jdft_status build_sphere(jdft_basis_s* b, int ik) {
     std::vector<int> row_col_start(s.nrows + 1);
     for (int r = 0; r <= s.nrows; ++r)
         row_col_start[r] = (int)(std::lower_bound(col_i0.begin(), col_i0.end(), mn[0] + r) - col_i0.begin());
+    // Each row's columns are consecutive i1 values (a sphere meets a line in an interval).
+    std::vector<int> row_i1lo(s.nrows, 0);
+    for (int r = 0; r < s.nrows; ++r)
+        if (row_col_start[r] < row_col_start[r + 1]) row_i1lo[r] = iG[3 * col_start[row_col_start[r]] + 1];
     std::vector<float> kin32(kin.begin(), kin.end());
     jdft_status st;
     if ((st = upload(&s.col_start, col_start)) != JDFT_OK) return st;
     if ((st = upload(&s.col_slot01, col_slot01)) != JDFT_OK) return st;
     if ((st = upload(&s.row_col_start, row_col_start)) != JDFT_OK) return st;
+    if ((st = upload(&s.row_i1lo, row_i1lo)) != JDFT_OK) return st;
     if ((st = upload(&s.pw_col, pw_col)) != JDFT_OK) return st;
     if ((st = upload(&s.pw_z, pw_z)) != JDFT_OK) return st;
     if ((st = upload(&s.kin, kin)) != JDFT_OK) return st;

@@ -18,6 +18,7 @@
 // Only the columns and rows the sphere touches are moved and transformed.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "chain.cuh"
 #include "profile.cuh"
@@ -312,7 +313,7 @@ constexpr size_t kMaxSmem = 220 * 1024;
 template <typename K>
 static jdft_status prepare(K kernel, size_t smem, const char* name) {
     if (smem > kMaxSmem) return set_error(JDFT_ERR_UNSUPPORTED, std::string(name) + ": box too large for shared memory");
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attr((const void*)kernel, smem);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
     return JDFT_OK;
 }
@@ -371,6 +372,9 @@ jdft_status launch_zpass_forward(const ChainGeom& g, const c_t<T>* colbuf, const
 template <typename T>
 jdft_status launch_plane_apply(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
                                cudaStream_t st) {
+    // register-FFT kernel for the shapes it is compiled for, else the generic one
+    const jdft_status fs = launch_plane_apply_fast<T>(g, colbuf, Vp, nb, tw_base, st);
+    if (fs != JDFT_ERR_UNSUPPORTED) return fs;
     PlaneSmem sm = plane_layout(g, sizeof(c_t<T>), g.S1, 0, 16);
     const size_t smem = plane_bytes(g, sm, sizeof(c_t<T>));
     jdft_status s = prepare(plane_apply_kernel<T>, smem, "plane_apply");
@@ -419,6 +423,10 @@ jdft_status launch_plane_forward_full(const ChainGeom& g, const c_t<T>* psi, c_t
 template <typename T>
 jdft_status launch_plane_density(const ChainGeom& g, const c_t<T>* colbuf, const double* f, double w, double* n_r,
                                  int nb, const c_t<T>* tw_base, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        const jdft_status fs = launch_plane_density_fast(g, colbuf, f, w, n_r, nb, tw_base, st);
+        if (fs != JDFT_ERR_UNSUPPORTED) return fs;
+    }
     // Split j1 into slabs until accumulator + plane buffers fit.
     int nsplit = 1, jw = g.S1;
     PlaneSmem sm;
@@ -501,10 +509,12 @@ static int chunk_bands(const ChainGeom& g, size_t elem, int nb, size_t budget) {
 
 // Column-buffer bytes per chunk of bands: small enough that one chunk's
 // intermediate stays in the 126 MB L2 between the three kernels.  The
-// environment variable JDFT_CHUNK_MB overrides it (read on every call).
-size_t chunk_budget() {
+// environment variable JDFT_CHUNK_MB overrides it (read on every call), then
+// a value the autotuner stored in the basis, then 64 MB.
+size_t chunk_budget(const jdft_basis_s* b) {
     const char* e = getenv("JDFT_CHUNK_MB");
     long long mb = e ? atoll(e) : 0;
+    if (mb <= 0 && b) mb = b->chunk_mb;
     return (size_t)(mb > 0 ? mb : 64) << 20;
 }
 
@@ -528,7 +538,7 @@ template <typename T>
 static jdft_status run_inverse_full(jdft_basis_s* b, int ik, const void* C, int ldc, void* psi, int nb, T scale,
                                     cudaStream_t st) {
     const ChainGeom g = make_geom(b, ik);
-    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget());
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     jdft_status s = ensure_workspace(b, (size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>));
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -548,7 +558,7 @@ template <typename T>
 static jdft_status run_forward_full(jdft_basis_s* b, int ik, const void* psi, void* C, int ldc, int nb, T scale,
                                     cudaStream_t st) {
     const ChainGeom g = make_geom(b, ik);
-    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget());
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     jdft_status s = ensure_workspace(b, (size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>));
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -569,7 +579,7 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
                                jdft_prec prec, cudaStream_t st) {
     const ChainGeom g = make_geom(b, ik);
     const KSphere& sp = b->ks[ik];
-    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget());
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
     const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>));
     jdft_status s = ensure_workspace(b, colbytes + nlbytes);
@@ -595,7 +605,7 @@ template <typename T>
 static jdft_status run_density(jdft_basis_s* b, int ik, const void* C, int ldc, const double* f, int nb,
                                double* n_r, cudaStream_t st) {
     const ChainGeom g = make_geom(b, ik);
-    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget());
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     jdft_status s = ensure_workspace(b, (size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>));
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -732,3 +742,39 @@ jdft_status jdft_density(jdft_basis_t b, int ik, const void* C, int ldc, const d
 }
 
 }  // extern "C"
+
+extern "C" jdft_status jdft_autotune_chunk(jdft_basis_t b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                           jdft_prec prec, int* chunk_mb, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C && HC && nb >= 1, "bad arguments");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    if (!b->have_V) return set_error(JDFT_ERR_ARG, "no potential set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int cand[] = {16, 32, 64, 96, 128, 256};
+    cudaEvent_t e0, e1;
+    JDFT_CUDA_TRY(cudaEventCreate(&e0));
+    JDFT_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_mb = 64;
+    const int saved = b->chunk_mb;
+    jdft_status s = JDFT_OK;
+    for (int mb : cand) {
+        b->chunk_mb = mb;
+        // one untimed call grows the workspace and warms the kernels, then two timed calls
+        if ((s = jdft_apply_H(b, ik, C, ldc, HC, ldhc, nb, prec, stream))) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && s == JDFT_OK; ++r) s = jdft_apply_H(b, ik, C, ldc, HC, ldhc, nb, prec, stream);
+        cudaEventRecord(e1, st);
+        if (s) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_mb = mb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != JDFT_OK) { b->chunk_mb = saved; return s; }
+    b->chunk_mb = best_mb;
+    if (chunk_mb) *chunk_mb = best_mb;
+    return JDFT_OK;
+}

@@ -14,6 +14,7 @@ struct ChainGeom {
     const int* col_start;      // ncols + 1
     const int* col_slot01;     // ncols: (row << 16) | (i1 mod S1)
     const int* row_col_start;  // nrows + 1
+    const int* row_i1lo;       // nrows
     const int* pw_col;         // npw
     const int* pw_z;           // npw
     FftPlan p0, p1, p2;
@@ -25,6 +26,7 @@ inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
     g.S0 = b->S[0]; g.S1 = b->S[1]; g.S2 = b->S[2];
     g.npw = s.npw; g.ncols = s.ncols; g.nrows = s.nrows; g.i0min = s.i0min;
     g.col_start = s.col_start; g.col_slot01 = s.col_slot01; g.row_col_start = s.row_col_start;
+    g.row_i1lo = s.row_i1lo;
     g.pw_col = s.pw_col; g.pw_z = s.pw_z;
     g.p0 = b->plan[0]; g.p1 = b->plan[1]; g.p2 = b->plan[2];
     return g;
@@ -54,6 +56,14 @@ jdft_status launch_plane_inverse_full(const ChainGeom& g, const c_t<T>* colbuf, 
 template <typename T>
 jdft_status launch_plane_forward_full(const ChainGeom& g, const c_t<T>* psi, c_t<T>* colbuf, int nb,
                                       const c_t<T>* tw_base, cudaStream_t st);
+// Register-FFT plane passes for the box shapes they are compiled for; they
+// return JDFT_ERR_UNSUPPORTED (without launching) for other shapes.
+template <typename T>
+jdft_status launch_plane_apply_fast(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
+                                    cudaStream_t st);
+jdft_status launch_plane_density_fast(const ChainGeom& g, const float2* colbuf, const double* f, double w,
+                                      double* n_r, int nb, const float2* tw_base, cudaStream_t st);
+
 template <typename T>
 jdft_status launch_plane_density(const ChainGeom& g, const c_t<T>* colbuf, const double* f, double w, double* n_r,
                                  int nb, const c_t<T>* tw_base, cudaStream_t st);

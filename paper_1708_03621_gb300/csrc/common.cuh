@@ -36,6 +36,11 @@ void clear_error();
 // Reports a kernel launch failure (the launch itself, not later execution).
 jdft_status check_launch(const char* what);
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (device, kernel,
+// size): later launches, including those recorded into a CUDA graph, make no
+// attribute calls.
+cudaError_t set_smem_attr(const void* func, size_t smem);
+
 // ---------------------------------------------------------------------------
 // Complex arithmetic on the CUDA vector types.  T is double or float.
 // ---------------------------------------------------------------------------
@@ -88,6 +93,7 @@ struct KSphere {
     int* col_start = nullptr;   // ncols + 1: first sphere index of each column (prefix sums)
     int* col_slot01 = nullptr;  // ncols: packed (row r = i0 - i0min) << 16 | (i1 mod S1)
     int* row_col_start = nullptr; // nrows + 1: first column of each row r
+    int* row_i1lo = nullptr;    // nrows: signed i1 of each row's first column (rows are i1 intervals)
     int* pw_col = nullptr;      // npw: column of each plane wave
     int* pw_z = nullptr;        // npw: i2 mod S2 of each plane wave
     double* kin = nullptr;      // npw: (1/2)|k+G|^2
@@ -130,6 +136,7 @@ struct jdft_basis_s {
     float* V32 = nullptr;
     bool have_V = false;
     int device = 0;
+    int chunk_mb = 0;         // band-chunk budget chosen by jdft_autotune_chunk (0 = default)
     jdft::Workspace work;
 };
 

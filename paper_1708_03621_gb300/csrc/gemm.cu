@@ -184,19 +184,43 @@ template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
                                 jdft_prec prec, void* work, cudaStream_t st) {
     if (sp.nproj == 0 || nb == 0) return JDFT_OK;
-    if (prec == JDFT_TF32X3 || prec == JDFT_BF16X3)
-        return set_error(JDFT_ERR_UNSUPPORTED, "split-precision tensor-core GEMMs not built in this library");
+    if (prec == JDFT_BF16X3)
+        return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split tensor-core GEMMs not built in this library");
     double2* Bc = (double2*)work;
     c_t<T>* Bd = (c_t<T>*)((char*)work + ((size_t)sp.nproj * nb * sizeof(double2) + 255) / 256 * 256);
     JDFT_CUDA_TRY(cudaMemsetAsync(Bc, 0, (size_t)sp.nproj * nb * sizeof(double2), st));
-    jdft_status s = zgemm_cn<T>(sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0, st);
+    jdft_status s = gemm_cn<T>(prec, sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0,
+                               st);
     if (s != JDFT_OK) return s;
     {
         Trace tr_("dmul", st);
         dmul_kernel<T><<<std::min(152 * 8, (sp.nproj * nb + 255) / 256), 256, 0, st>>>(sp.nproj, nb, sp.D, Bc, Bd);
     }
     if ((s = check_launch("dmul"))) return s;
-    return zgemm_nn_acc<T>(sp.npw, nb, sp.nproj, proj_ptr<T>(sp), sp.npw, Bd, nb, (c_t<T>*)HC, ldhc, st);
+    return gemm_nn_acc<T>(prec, sp.npw, nb, sp.nproj, proj_ptr<T>(sp), sp.npw, Bd, nb, (c_t<T>*)HC, ldhc, st);
+}
+
+template <>
+jdft_status gemm_cn<double>(jdft_prec, int M, int N, int K, const double2* A, int lda, const double2* B, int ldb,
+                            double2* out, int ldo, double alpha, cudaStream_t st) {
+    return zgemm_cn<double>(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
+}
+template <>
+jdft_status gemm_cn<float>(jdft_prec prec, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
+                           double2* out, int ldo, double alpha, cudaStream_t st) {
+    if (prec == JDFT_TF32X3) return tc_zgemm_cn(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
+    return zgemm_cn<float>(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
+}
+template <>
+jdft_status gemm_nn_acc<double>(jdft_prec, int M, int N, int K, const double2* A, int lda, const double2* Bm, int ldb,
+                                double2* out, int ldo, cudaStream_t st) {
+    return zgemm_nn_acc<double>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+}
+template <>
+jdft_status gemm_nn_acc<float>(jdft_prec prec, int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb,
+                               float2* out, int ldo, cudaStream_t st) {
+    if (prec == JDFT_TF32X3) return tc_zgemm_nn_acc(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+    return zgemm_nn_acc<float>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
 }
 
 template jdft_status zgemm_cn<double>(int, int, int, const double2*, int, const double2*, int, double2*, int, double,
@@ -228,8 +252,8 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
     JDFT_CHECK_ARG(C && ldc >= npw, "bad C block");
     JDFT_CHECK_ARG(!CHC || (HC && ldhc >= npw), "bad HC block");
     JDFT_CHECK_ARG(((uintptr_t)CHC % 16) == 0 && ((uintptr_t)COC % 16) == 0, "outputs must be 16-byte aligned");
-    if (prec == JDFT_TF32X3 || prec == JDFT_BF16X3)
-        return set_error(JDFT_ERR_UNSUPPORTED, "split-precision tensor-core GEMMs not built in this library");
+    if (prec == JDFT_BF16X3)
+        return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split tensor-core GEMMs not built in this library");
     cudaStream_t st = (cudaStream_t)stream;
     jdft_status s = JDFT_OK;
     if (CHC) {
@@ -237,7 +261,7 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
         s = (prec == JDFT_FP64)
                 ? zgemm_cn<double>(nb, nb, npw, (const double2*)C, ldc, (const double2*)HC, ldhc, (double2*)CHC, nb,
                                    1.0, st)
-                : zgemm_cn<float>(nb, nb, npw, (const float2*)C, ldc, (const float2*)HC, ldhc, (double2*)CHC, nb, 1.0,
+                : gemm_cn<float>(prec, nb, nb, npw, (const float2*)C, ldc, (const float2*)HC, ldhc, (double2*)CHC, nb, 1.0,
                                   st);
         if (s != JDFT_OK) return s;
     }
@@ -246,7 +270,7 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
         s = (prec == JDFT_FP64)
                 ? zgemm_cn<double>(nb, nb, npw, (const double2*)C, ldc, (const double2*)C, ldc, (double2*)COC, nb,
                                    b->omega, st)
-                : zgemm_cn<float>(nb, nb, npw, (const float2*)C, ldc, (const float2*)C, ldc, (double2*)COC, nb,
+                : gemm_cn<float>(prec, nb, nb, npw, (const float2*)C, ldc, (const float2*)C, ldc, (double2*)COC, nb,
                                   b->omega, st);
     }
     return s;

@@ -19,6 +19,21 @@ template <typename T>
 jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb, c_t<T>* out,
                          int ldo, cudaStream_t st);
 
+// Tensor-core versions (FP32 inputs, 3-term TF32 split) of the two products above.
+jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
+                        double alpha, cudaStream_t st);
+jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
+                            int ldo, cudaStream_t st);
+
+// Precision dispatch: JDFT_TF32X3 runs the tensor-core versions (T = float
+// only), every other precision the CUDA-core ones.
+template <typename T>
+jdft_status gemm_cn(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* B, int ldb,
+                    double2* out, int ldo, double alpha, cudaStream_t st);
+template <typename T>
+jdft_status gemm_nn_acc(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb,
+                        c_t<T>* out, int ldo, cudaStream_t st);
+
 // Workspace bytes the nonlocal term needs for nb bands.
 size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem);
 

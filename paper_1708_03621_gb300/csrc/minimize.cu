@@ -413,7 +413,7 @@ struct MinState {
     // out (nb x nb complex128) = alpha X^dag Y
     jdft_status cn(const c_t<T>* X, const c_t<T>* Yb, double2* out, double alpha) {
         JDFT_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)nb * nb * sizeof(double2), st));
-        return zgemm_cn<T>(nb, nb, npw, X, ld, Yb, ld, out, nb, alpha, st);
+        return gemm_cn<T>(prec, nb, nb, npw, X, ld, Yb, ld, out, nb, alpha, st);
     }
     // Z += X . (alpha A)   (A small complex128)
     jdft_status nn_acc(const c_t<T>* X, const double2* A, double alpha, c_t<T>* Z) {
@@ -423,12 +423,12 @@ struct MinState {
         }
         jdft_status s = check_launch("small_scale");
         if (s != JDFT_OK) return s;
-        return zgemm_nn_acc<T>(npw, nb, nb, X, ld, Bm, nb, Z, ld, st);
+        return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, Bm, nb, Z, ld, st);
     }
     // Z = X . W  (W already in block type)
     jdft_status rotate(const c_t<T>* X, c_t<T>* Z) {
         JDFT_CUDA_TRY(cudaMemsetAsync(Z, 0, (size_t)nb * ld * sizeof(c_t<T>), st));
-        return zgemm_nn_acc<T>(npw, nb, nb, X, ld, W, nb, Z, ld, st);
+        return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, W, nb, Z, ld, st);
     }
     jdft_status hermitize(double2* A, double* tr) {
         {
@@ -601,36 +601,55 @@ using namespace jdft;
 
 extern "C" {
 
-jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb, void* stream) {
-    clear_error();
-    JDFT_CHECK_ARG(b && C, "null argument");
-    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
-    JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace jdft {
+template <typename T>
+static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc, int nb, jdft_prec prec,
+                                       cudaStream_t st) {
     const int npw = b->ks[ik].npw;
     const int m = nb + (nb & 1);
-    DevBuf mem;
-    const size_t sm = (size_t)nb * nb * sizeof(double2);
-    JDFT_CUDA_TRY(cudaMalloc(&mem.p, 3 * sm + 2 * (size_t)m * m * sizeof(double2) + (size_t)nb * ldc * sizeof(double2) +
-                                         1024));
-    double2* U = (double2*)mem.p;
-    double2* W = U + (size_t)nb * nb;
-    double2* work = W + (size_t)nb * nb;
-    double2* tmp = work + 2 * (size_t)m * m;
-    int* status = (int*)(tmp + (size_t)nb * ldc);
-    JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-    JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, sm, st));
-    jdft_status s = zgemm_cn<double>(nb, nb, npw, (const double2*)C, ldc, (const double2*)C, ldc, U, nb, b->omega, st);
+    const size_t sm = ((size_t)nb * nb * sizeof(double2) + 255) / 256 * 256;
+    const size_t wbytes = ((size_t)nb * nb * sizeof(c_t<T>) + 255) / 256 * 256;
+    const size_t lab = 2 * (size_t)m * m * sizeof(double2);
+    const size_t blk = ((size_t)nb * ldc * sizeof(c_t<T>) + 255) / 256 * 256;
+    // the basis workspace (grown once) holds U, W, the factorisation scratch, a copy of C and a status word
+    jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256);
     if (s != JDFT_OK) return s;
-    if ((s = small_cholesky_winv(nb, U, work, W, true, status, st))) return s;
-    JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    JDFT_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nb * ldc * sizeof(double2), st));
-    if ((s = zgemm_nn_acc<double>(npw, nb, nb, tmp, ldc, W, nb, (double2*)C, ldc, st))) return s;
+    char* q = (char*)b->work.ptr;
+    double2* U = (double2*)q;
+    c_t<T>* W = (c_t<T>*)(q + sm);
+    double2* work = (double2*)(q + sm + wbytes);
+    c_t<T>* tmp = (c_t<T>*)(q + sm + wbytes + lab);
+    int* status = (int*)(q + sm + wbytes + lab + blk);
+    JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)nb * nb * sizeof(double2), st));
+    if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega, st)))
+        return s;
+    if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
+    JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
+    JDFT_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nb * ldc * sizeof(c_t<T>), st));
+    if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st))) return s;
     int hs = 0;
     JDFT_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
     if (hs) return set_error(JDFT_ERR_NOT_POSDEF, "C^dag O C is not positive definite");
     return JDFT_OK;
+}
+}  // namespace jdft
+
+extern "C" {
+
+jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb, jdft_prec prec, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C, "null argument");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
+    JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
+    if (prec == JDFT_BF16X3) return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split products not built");
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st)
+                             : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st);
 }
 
 jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream) {

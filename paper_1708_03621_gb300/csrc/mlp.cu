@@ -425,7 +425,7 @@ jdft_status jdft_mlp_loss_grad(jdft_mlp_t m, int64_t rows, const float* data, fl
     jdft_status s = check_launch("sum_a");
     if (s != JDFT_OK) return s;
     const size_t smem = (NPARAM + 3 + 3 * TR * LD + 3 * TR + NSMALL) * sizeof(float);
-    JDFT_CUDA_TRY(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    JDFT_CUDA_TRY(set_smem_attr((const void*)mlp_grad_kernel, smem));
     const int tiles = (int)std::min<int64_t>((rows + TR - 1) / TR, 152 * 2);
     {
         Trace tr_("mlp_grad", st);

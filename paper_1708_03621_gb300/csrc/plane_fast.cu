@@ -1,0 +1,323 @@
+// Plane pass of the Hamiltonian chain with register-resident line FFTs, for
+// the box shapes it is compiled for (the generic shared-memory Stockham plane
+// kernels in chain.cu serve every other shape).
+//
+// One block per (z-plane j2, band); 8 warps.  Three phases with one block
+// barrier between consecutive phases:
+//   1. rows: inverse transform along axis 1 of the nrows i0-rows the sphere
+//      touches; each row's input is read straight from the plane's disk
+//      values (a row's columns are consecutive i1) and its output written to
+//      the shared plane A[r][j1];
+//   2. columns: for every j1, inverse transform along axis 0 of the column
+//      A[.][j1] placed at slots (i0min + r) mod S0, multiply by V(j0, j1, j2),
+//      forward transform, keep the nrows sphere slots, back into A;
+//   3. rows: forward transform along axis 1, gather the disk values back.
+// Lines are split over TL lanes of one warp (E values per lane); stages of a
+// line exchange values through a warp-private scratch line with __syncwarp.
+// (JDFTx paper, Sec. 2.1: the I, multiply, J chain of Listing 1 on
+// temporaries; here the real-space box never leaves on-chip memory.)
+#include <algorithm>
+#include <cstdlib>
+
+#include "chain.cuh"
+#include "fft_reg.cuh"
+#include "profile.cuh"
+
+namespace jdft {
+
+constexpr int kFastThreads = 256;
+constexpr int kFastWarps = kFastThreads / 32;
+
+__device__ __forceinline__ int wrapf(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Phase 1 / 3 helpers -------------------------------------------------------
+template <typename T, int N1, int E1, class R1>
+__device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<T>* __restrict__ plane, c_t<T>* A,
+                                                  int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
+    using F = LineFFT<T, N1, E1, +1, R1>;
+    constexpr int TL = N1 / E1, LPW = 32 / TL;
+    const int liw = lane / TL, t = lane % TL;
+    c_t<T>* scr = wscr + liw * N1;
+    for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
+        const int r = base + liw;
+        const bool act = r < g.nrows;
+        int cs = 0, cnt = 0, lo = 0;
+        if (act) {
+            cs = g.row_col_start[r];
+            cnt = g.row_col_start[r + 1] - cs;
+            lo = g.row_i1lo[r];
+        }
+        c_t<T> v[E1];
+#pragma unroll
+        for (int e = 0; e < E1; ++e) {
+            const int off = wrapf(F::in_index(t, e) - lo, N1);
+            v[e] = (off < cnt) ? plane[cs + off] : mk<T>(T(0), T(0));
+        }
+        F::run(v, t, scr, W1);
+        if (act) {
+#pragma unroll
+            for (int e = 0; e < E1; ++e) A[r * lsA + F::out_index(t, e)] = v[e];
+        }
+    }
+}
+
+template <typename T, int N1, int E1, class R1>
+__device__ __forceinline__ void rows_forward_fast(const ChainGeom& g, c_t<T>* __restrict__ plane, const c_t<T>* A,
+                                                  int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
+    using F = LineFFT<T, N1, E1, -1, R1>;
+    constexpr int TL = N1 / E1, LPW = 32 / TL;
+    const int liw = lane / TL, t = lane % TL;
+    c_t<T>* scr = wscr + liw * N1;
+    for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
+        const int r = base + liw;
+        const bool act = r < g.nrows;
+        c_t<T> v[E1];
+#pragma unroll
+        for (int e = 0; e < E1; ++e) v[e] = act ? A[r * lsA + F::in_index(t, e)] : mk<T>(T(0), T(0));
+        F::run(v, t, scr, W1);
+        if (act) {
+            const int cs = g.row_col_start[r];
+            const int cnt = g.row_col_start[r + 1] - cs;
+            const int lo = g.row_i1lo[r];
+#pragma unroll
+            for (int e = 0; e < E1; ++e) {
+                const int off = wrapf(F::out_index(t, e) - lo, N1);
+                if (off < cnt) plane[cs + off] = v[e];
+            }
+        }
+    }
+}
+
+// Inverse transform of column j1 (sphere rows of A placed at their slots).
+template <typename T, int N0, int E0, class R0>
+__device__ __forceinline__ void column_inverse_fast(const ChainGeom& g, const c_t<T>* A, int lsA, int j1, bool act,
+                                                    c_t<T>* v, int t, c_t<T>* scr, const c_t<T>* W0) {
+    using F = LineFFT<T, N0, E0, +1, R0>;
+#pragma unroll
+    for (int e = 0; e < E0; ++e) {
+        const int r = wrapf(F::in_index(t, e) - g.i0min, N0);
+        v[e] = (act && r < g.nrows) ? A[r * lsA + j1] : mk<T>(T(0), T(0));
+    }
+    F::run(v, t, scr, W0);
+}
+
+// The plane pass of H: rows inverse, columns inverse x V forward, rows forward.
+template <typename T, int N0, int E0, class R0, int N1, int E1, class R1>
+__global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeom g, c_t<T>* __restrict__ colbuf,
+                                                                        const T* __restrict__ Vp,
+                                                                        const c_t<T>* __restrict__ tw0,
+                                                                        const c_t<T>* __restrict__ tw1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int lsA = N1 + 1;
+    constexpr int SCR = 32 * (E0 > E1 ? E0 : E1);  // per-warp scratch (LPW lines of N)
+    c_t<T>* W0 = reinterpret_cast<c_t<T>*>(smem_raw);
+    c_t<T>* W1 = W0 + N0;
+    c_t<T>* scr_all = W1 + N1;
+    c_t<T>* A = scr_all + kFastWarps * SCR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    c_t<T>* wscr = scr_all + warp * SCR;
+    for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = tw0[i];
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) W1[i] = tw1[i];
+    __syncthreads();
+    const int j2 = blockIdx.x, b = blockIdx.y;
+    c_t<T>* plane = colbuf + colbuf_index(g, b, j2, 0);
+
+    rows_inverse_fast<T, N1, E1, R1>(g, plane, A, lsA, wscr, W1, warp, lane);
+    __syncthreads();
+
+    {
+        using FI = LineFFT<T, N0, E0, +1, R0>;
+        using FF = LineFFT<T, N0, E0, -1, R0>;
+        constexpr int TL = N0 / E0, LPW = 32 / TL;
+        const int liw = lane / TL, t = lane % TL;
+        c_t<T>* scr = wscr + liw * N0;
+        for (int base = warp * LPW; base < N1; base += kFastWarps * LPW) {
+            const int j1 = base + liw;
+            const bool act = j1 < N1;
+            c_t<T> v[E0];
+            column_inverse_fast<T, N0, E0, R0>(g, A, lsA, j1, act, v, t, scr, W0);
+            const T* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < E0; ++e) {
+                const int j0 = FI::out_index(t, e);
+                scr[j0] = act ? cscale(v[e], Vq[j0]) : mk<T>(T(0), T(0));
+            }
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < E0; ++e) v[e] = scr[FF::in_index(t, e)];
+            FF::run(v, t, scr, W0);
+            if (act) {
+#pragma unroll
+                for (int e = 0; e < E0; ++e) {
+                    const int r = wrapf(FF::out_index(t, e) - g.i0min, N0);
+                    if (r < g.nrows) A[r * lsA + j1] = v[e];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    rows_forward_fast<T, N1, E1, R1>(g, plane, A, lsA, wscr, W1, warp, lane);
+}
+
+// Density, FP32 blocks: block (j2, band group) accumulates f_b |psi_b|^2 in
+// registers (each lane always owns the same (j0, j1) points) over its bands.
+template <int N0, int E0, class R0, int N1, int E1, class R1>
+__global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainGeom g,
+                                                                          const float2* __restrict__ colbuf, int nb,
+                                                                          int bands_per_block,
+                                                                          const double* __restrict__ f, double w,
+                                                                          double* __restrict__ n_r,
+                                                                          const float2* __restrict__ tw0,
+                                                                          const float2* __restrict__ tw1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int lsA = N1 + 1;
+    constexpr int SCR = 32 * (E0 > E1 ? E0 : E1);
+    constexpr int TL = N0 / E0, LPW = 32 / TL;
+    constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+    float2* W0 = reinterpret_cast<float2*>(smem_raw);
+    float2* W1 = W0 + N0;
+    float2* scr_all = W1 + N1;
+    float2* A = scr_all + kFastWarps * SCR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* wscr = scr_all + warp * SCR;
+    for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = tw0[i];
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) W1[i] = tw1[i];
+    __syncthreads();
+    const int j2 = blockIdx.x;
+    const int bA = blockIdx.y * bands_per_block, bB = min(nb, bA + bands_per_block);
+    const int liw = lane / TL, t = lane % TL;
+    float acc[ROUNDS][E0];
+#pragma unroll
+    for (int k = 0; k < ROUNDS; ++k)
+#pragma unroll
+        for (int e = 0; e < E0; ++e) acc[k][e] = 0.f;
+    for (int b = bA; b < bB; ++b) {
+        const float fb = (float)f[b];
+        rows_inverse_fast<float, N1, E1, R1>(g, colbuf + colbuf_index(g, b, j2, 0), A, lsA, wscr, W1, warp, lane);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ROUNDS; ++k) {
+            const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+            float2 v[E0];
+            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t, wscr + liw * N0, W0);
+#pragma unroll
+            for (int e = 0; e < E0; ++e) acc[k][e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
+        }
+        __syncthreads();
+    }
+    using FI = LineFFT<float, N0, E0, +1, R0>;
+    const bool atomic = gridDim.y > 1;
+#pragma unroll
+    for (int k = 0; k < ROUNDS; ++k) {
+        const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+        if (j1 >= N1) continue;
+#pragma unroll
+        for (int e = 0; e < E0; ++e) {
+            const int j0 = FI::out_index(t, e);
+            double* dst = n_r + ((size_t)j0 * N1 + j1) * g.S2 + j2;
+            const double val = w * (double)acc[k][e];
+            if (atomic) atomicAdd(dst, val);
+            else *dst += val;
+        }
+    }
+}
+
+// Line shapes per compiled length: E values per lane and the radix list.
+template <int N> struct FastCfg;
+template <> struct FastCfg<12> { static constexpr int E = 12; using R = Rad<4, 3>; };
+template <> struct FastCfg<16> { static constexpr int E = 16; using R = Rad<16>; };
+template <> struct FastCfg<40> { static constexpr int E = 20; using R = Rad<2, 4, 5>; };
+template <> struct FastCfg<48> { static constexpr int E = 12; using R = Rad<4, 4, 3>; };
+template <> struct FastCfg<64> { static constexpr int E = 8; using R = Rad<8, 8>; };
+template <> struct FastCfg<80> { static constexpr int E = 20; using R = Rad<4, 4, 5>; };
+template <> struct FastCfg<128> { static constexpr int E = 16; using R = Rad<16, 8>; };
+template <> struct FastCfg<256> { static constexpr int E = 16; using R = Rad<16, 16>; };
+
+constexpr size_t kFastMaxSmem = 220 * 1024;
+
+template <int N0, int N1>
+static size_t fast_smem(const ChainGeom& g, size_t elem) {
+    constexpr int E0 = FastCfg<N0>::E, E1 = FastCfg<N1>::E;
+    return ((size_t)N0 + N1 + (size_t)kFastWarps * 32 * (E0 > E1 ? E0 : E1) + (size_t)g.nrows * (N1 + 1)) * elem;
+}
+
+static bool fast_disabled() {
+    const char* e = getenv("JDFT_FAST_PLANE");
+    return e && e[0] == '0';
+}
+
+template <typename T, int N0, int N1>
+static jdft_status apply_fast_impl(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
+                                   cudaStream_t st) {
+    using C0 = FastCfg<N0>;
+    using C1 = FastCfg<N1>;
+    const size_t smem = fast_smem<N0, N1>(g, sizeof(c_t<T>));
+    if (smem > kFastMaxSmem) return JDFT_ERR_UNSUPPORTED;
+    auto kern = plane_apply_fast_kernel<T, N0, C0::E, typename C0::R, N1, C1::E, typename C1::R>;
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("plane_apply_fast: ") + cudaGetErrorString(e));
+    {
+        Trace tr_("plane_apply_fast", st);
+        kern<<<dim3(g.S2, nb), kFastThreads, smem, st>>>(g, colbuf, Vp, tw_base + g.p0.tw_offset,
+                                                         tw_base + g.p1.tw_offset);
+    }
+    return check_launch("plane_apply_fast");
+}
+
+template <int N0, int N1>
+static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, const double* f, double w, double* n_r,
+                                     int nb, const float2* tw_base, cudaStream_t st) {
+    using C0 = FastCfg<N0>;
+    using C1 = FastCfg<N1>;
+    const size_t smem = fast_smem<N0, N1>(g, sizeof(float2));
+    if (smem > kFastMaxSmem) return JDFT_ERR_UNSUPPORTED;
+    auto kern = plane_density_fast_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R>;
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess)
+        return set_error(JDFT_ERR_CUDA, std::string("plane_density_fast: ") + cudaGetErrorString(e));
+    // band groups so that the grid covers the GPU about four blocks deep
+    int groups = std::max(1, std::min(nb, (4 * 152 + g.S2 - 1) / g.S2));
+    const int per = (nb + groups - 1) / groups;
+    groups = (nb + per - 1) / per;
+    {
+        Trace tr_("plane_density_fast", st);
+        kern<<<dim3(g.S2, groups), kFastThreads, smem, st>>>(g, colbuf, nb, per, f, w, n_r, tw_base + g.p0.tw_offset,
+                                                             tw_base + g.p1.tw_offset);
+    }
+    return check_launch("plane_density_fast");
+}
+
+#define JDFT_FAST_SHAPES(X) X(12, 12) X(16, 12) X(40, 40) X(48, 48) X(64, 64) X(80, 80) X(128, 128) X(256, 128)
+
+template <typename T>
+jdft_status launch_plane_apply_fast(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
+                                    cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a, b) \
+    if (g.S0 == a && g.S1 == b) return apply_fast_impl<T, a, b>(g, colbuf, Vp, nb, tw_base, st);
+    JDFT_FAST_SHAPES(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+jdft_status launch_plane_density_fast(const ChainGeom& g, const float2* colbuf, const double* f, double w,
+                                      double* n_r, int nb, const float2* tw_base, cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a, b) \
+    if (g.S0 == a && g.S1 == b) return density_fast_impl<a, b>(g, colbuf, f, w, n_r, nb, tw_base, st);
+    JDFT_FAST_SHAPES(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+template jdft_status launch_plane_apply_fast<double>(const ChainGeom&, double2*, const double*, int, const double2*,
+                                                     cudaStream_t);
+template jdft_status launch_plane_apply_fast<float>(const ChainGeom&, float2*, const float*, int, const float2*,
+                                                    cudaStream_t);
+
+}  // namespace jdft

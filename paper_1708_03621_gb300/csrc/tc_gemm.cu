@@ -1,0 +1,269 @@
+// Complex GEMMs on the 5th-generation tensor cores with 3-term TF32 splitting
+// (x = hi + lo, both TF32; x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y, FP32
+// accumulation in tensor memory): the projector products P^dag C and
+// P (D P^dag C) of the nonlocal pseudopotential term (JDFTx paper, Sec. 2.2)
+// and the subspace matrices C^dag H C, C^dag O C of the band minimiser
+// (Sec. 2.1, Minimize).
+//
+// Complex products become real ones by doubling K with the interleaved
+// (re, im) storage: for conj(a) b, Re = sum a'.b'_re and Im = sum a'.b'_im
+// with a' = (ar, ai), b'_re = (br, bi), b'_im = (bi, -br); for a b,
+// b'_re = (br, -bi), b'_im = (bi, br).  A block of 128 threads computes a
+// 128 x NT tile: all threads stage a 32-deep (real) K chunk of A' (hi, lo)
+// and B'_re, B'_im (hi, lo) into shared memory in the no-swizzle K-major
+// core-matrix layout, one elected thread issues the tcgen05.mma (M = 128,
+// N = NT, K = 8 per instruction, 6 per K step) and commits them to an
+// mbarrier; two stages let the staging of chunk c+1 overlap the products of
+// chunk c.  Accumulators (Re at columns [0, NT), Im at [NT, 2 NT)) stay in
+// tensor memory until the epilogue reads them with tcgen05.ld.  Every wait is
+// bounded; a wait that gives up records JDFT_ERR_TIMEOUT in a device flag
+// (read by jdft_device_status), skips the epilogue and frees its tensor memory.
+#include <algorithm>
+
+#include "gemm.cuh"
+#include "profile.cuh"
+#include "tc_ptx.cuh"
+
+namespace jdft {
+
+constexpr int TC_M = 128;
+constexpr int TC_KC = 32;           // real K elements per stage (16 complex)
+constexpr int TC_KG = TC_KC / 4;    // 16-byte core columns per row
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;
+
+__device__ int g_tc_status = 0;
+
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)(((row >> 3) * TC_KG + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+template <int NT>
+struct TcLayout {
+    static constexpr int A_BYTES = TC_M * TC_KC * 4;
+    static constexpr int B_BYTES = NT * TC_KC * 4;
+    static constexpr int A_HI = 0, A_LO = A_BYTES;
+    static constexpr int BR_HI = 2 * A_BYTES, BR_LO = BR_HI + B_BYTES;
+    static constexpr int BI_HI = BR_LO + B_BYTES, BI_LO = BI_HI + B_BYTES;
+    static constexpr int STAGE = 2 * A_BYTES + 4 * B_BYTES;
+    static constexpr int SMEM = 2 * STAGE + 64;
+    static constexpr uint32_t NCOLS = (2 * NT <= 32) ? 32 : (2 * NT <= 64) ? 64 : (2 * NT <= 128) ? 128 : 256;
+};
+
+__device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int row, int k2, float x, float y) {
+    const float hx = tc::to_tf32(x), hy = tc::to_tf32(y);
+    const float lx = tc::to_tf32(x - hx), ly = tc::to_tf32(y - hy);
+    const uint32_t o = core_off(row, k2);
+    *reinterpret_cast<float2*>(buf + off_hi + o) = make_float2(hx, hy);
+    *reinterpret_cast<float2*>(buf + off_lo + o) = make_float2(lx, ly);
+}
+
+// out[m][n] = alpha sum_k conj(A[m][k]) B[n][k] (rows K-contiguous); FP64 atomics into out.
+template <int NT>
+struct StageCN {
+    const float2* A; int lda; const float2* B; int ldb; int M, N, K;
+    double2* out; int ldo; double alpha;
+    __device__ __forceinline__ void stage(char* buf, int m0, int n0, int kc0, int tid) const {
+        using L = TcLayout<NT>;
+        for (int e = tid; e < TC_M * (TC_KC / 2); e += TC_THREADS) {
+            const int row = e >> 4, kk = e & 15;
+            const int m = m0 + row, k = kc0 + kk;
+            const float2 a = (m < M && k < K) ? A[(size_t)m * lda + k] : make_float2(0.f, 0.f);
+            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, a.x, a.y);
+        }
+        for (int e = tid; e < NT * (TC_KC / 2); e += TC_THREADS) {
+            const int row = e >> 4, kk = e & 15;
+            const int n = n0 + row, k = kc0 + kk;
+            const float2 b = (n < N && k < K) ? B[(size_t)n * ldb + k] : make_float2(0.f, 0.f);
+            put_split(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, b.y);
+            put_split(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, -b.x);
+        }
+    }
+    __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
+        if (m < M && n < N) {
+            atomicAdd(&out[(size_t)m * ldo + n].x, alpha * (double)re);
+            atomicAdd(&out[(size_t)m * ldo + n].y, alpha * (double)im);
+        }
+    }
+    __device__ __forceinline__ int kcomplex() const { return K; }
+};
+
+// out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
+template <int NT>
+struct StageNN {
+    const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
+    float2* out; int ldo;
+    __device__ __forceinline__ void stage(char* buf, int m0, int n0, int kc0, int tid) const {
+        using L = TcLayout<NT>;
+        for (int e = tid; e < TC_M * (TC_KC / 2); e += TC_THREADS) {
+            const int kk = e >> 7, row = e & 127;
+            const int m = m0 + row, k = kc0 + kk;
+            const float2 a = (m < M && k < K) ? A[(size_t)k * lda + m] : make_float2(0.f, 0.f);
+            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, a.x, a.y);
+        }
+        for (int e = tid; e < NT * (TC_KC / 2); e += TC_THREADS) {
+            const int kk = e / NT, row = e % NT;
+            const int n = n0 + row, k = kc0 + kk;
+            const float2 b = (n < N && k < K) ? Bm[(size_t)k * ldb + n] : make_float2(0.f, 0.f);
+            put_split(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, -b.y);
+            put_split(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, b.x);
+        }
+    }
+    __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
+        if (m < M && n < N) {
+            float2 v = out[(size_t)n * ldo + m];
+            v.x += re;
+            v.y += im;
+            out[(size_t)n * ldo + m] = v;
+        }
+    }
+    __device__ __forceinline__ int kcomplex() const { return K; }
+};
+
+template <int NT, class S>
+__global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, int chunks_per_split) {
+    using L = TcLayout<NT>;
+    extern __shared__ __align__(1024) char smem[];
+    char* stage_buf[2] = {smem, smem + L::STAGE};
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, L::NCOLS);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * NT;
+    const int c0 = blockIdx.z * chunks_per_split;
+    const int c1 = min(nchunks, c0 + chunks_per_split);
+    constexpr uint32_t idesc = tc::instr_desc(2u, TC_M, NT);
+    int ok = 1;
+    int it = 0;
+    for (int c = c0; c < c1; ++c, ++it) {
+        const int sidx = it & 1;
+        char* buf = stage_buf[sidx];
+        if (it >= 2) {
+            // the products issued from this buffer two chunks ago must be done before restaging it
+            const int w = tc::mbar_wait_bounded(&mbar[sidx], (uint32_t)(((it - 2) >> 1) & 1), TC_WAIT_LIMIT) ? 1 : 0;
+            ok = __syncthreads_and(w);
+            if (!ok) break;
+        }
+        s.stage(buf, m0, n0, c * (TC_KC / 2), tid);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after_sync();
+            const uint32_t base = tc::smem_addr(buf);
+            constexpr uint32_t LBO = 128, SBO = TC_KG * 128;
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                const uint32_t off = kk * 256;
+                const uint64_t ahi = tc::smem_desc(base + L::A_HI + off, LBO, SBO);
+                const uint64_t alo = tc::smem_desc(base + L::A_LO + off, LBO, SBO);
+                const uint64_t brh = tc::smem_desc(base + L::BR_HI + off, LBO, SBO);
+                const uint64_t brl = tc::smem_desc(base + L::BR_LO + off, LBO, SBO);
+                const uint64_t bih = tc::smem_desc(base + L::BI_HI + off, LBO, SBO);
+                const uint64_t bil = tc::smem_desc(base + L::BI_LO + off, LBO, SBO);
+                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                tc::mma_tf32(tmem, ahi, brh, idesc, acc);
+                tc::mma_tf32(tmem, ahi, brl, idesc, 1u);
+                tc::mma_tf32(tmem, alo, brh, idesc, 1u);
+                tc::mma_tf32(tmem + NT, ahi, bih, idesc, acc);
+                tc::mma_tf32(tmem + NT, ahi, bil, idesc, 1u);
+                tc::mma_tf32(tmem + NT, alo, bih, idesc, 1u);
+            }
+            tc::mma_commit(&mbar[sidx]);
+        }
+    }
+    const int n = it;
+    if (ok && n > 0) {
+        // the last commit completes after every earlier product of this thread
+        const int w = tc::mbar_wait_bounded(&mbar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), TC_WAIT_LIMIT) ? 1
+                                                                                                              : 0;
+        ok = __syncthreads_and(w);
+    }
+    tc::tc_fence_after_sync();
+    if (ok && n > 0) {
+        const int row = warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int col = 0; col < NT; col += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(lane_base + col, re);
+            tc::tmem_ld16(lane_base + NT + col, im);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) s.emit(m0 + row, n0 + col + j, re[j], im[j]);
+        }
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::NCOLS);
+    if (!ok && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
+}
+
+template <int NT, class S>
+static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const char* name, cudaStream_t st) {
+    using L = TcLayout<NT>;
+    auto kern = tc_zgemm_kernel<NT, S>;
+    cudaError_t e = set_smem_attr((const void*)kern, L::SMEM);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+    const int nchunks = (K + TC_KC / 2 - 1) / (TC_KC / 2);
+    splits = std::max(1, std::min(splits, nchunks));
+    const int cps = (nchunks + splits - 1) / splits;
+    splits = (nchunks + cps - 1) / cps;
+    dim3 grid((M + TC_M - 1) / TC_M, (N + NT - 1) / NT, splits);
+    {
+        Trace tr_(name, st);
+        kern<<<grid, TC_THREADS, L::SMEM, st>>>(s, nchunks, cps);
+    }
+    return check_launch(name);
+}
+
+jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
+                        double alpha, cudaStream_t st) {
+    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    const int nchunks = (K + TC_KC / 2 - 1) / (TC_KC / 2);
+    if (N <= 32) {
+        StageCN<32> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+        const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 31) / 32);
+        const int splits = std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles);
+        return tc_launch<32>(s, M, N, K, splits, "tc_zgemm_cn", st);
+    }
+    StageCN<128> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+    const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
+    const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
+    return tc_launch<128>(s, M, N, K, splits, "tc_zgemm_cn", st);
+}
+
+jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
+                            int ldo, cudaStream_t st) {
+    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    if (N <= 32) {
+        StageNN<32> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+        return tc_launch<32>(s, M, N, K, 1, "tc_zgemm_nn", st);
+    }
+    StageNN<128> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+    return tc_launch<128>(s, M, N, K, 1, "tc_zgemm_nn", st);
+}
+
+}  // namespace jdft
+
+using namespace jdft;
+
+extern "C" jdft_status jdft_device_status(void* stream) {
+    clear_error();
+    JDFT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int v = 0;
+    JDFT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
+    if (v != 0) {
+        const int zero = 0;
+        JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)));
+        return set_error((jdft_status)v, "a bounded device-side wait gave up (tensor-core product skipped)");
+    }
+    return JDFT_OK;
+}

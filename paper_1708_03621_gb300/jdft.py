@@ -52,6 +52,11 @@ class MinReport(ctypes.Structure):
 
 PRECOND = {"identity": 0, "teter": 1, "mlp": 2}
 
+class ApplyItem(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_void_p), ("ik", ctypes.c_int), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int),
+                ("HC", ctypes.c_void_p), ("ldhc", ctypes.c_int), ("nb", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _SIGS = {
     "jdft_basis_create": [ctypes.POINTER(_CellDesc), ctypes.POINTER(_vp)],
@@ -72,7 +77,7 @@ _SIGS = {
     "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
     "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
     "jdft_apply_H_noalloc": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
-    "jdft_orthonormalize": [_vp, _i, _vp, _i, _i, _vp],
+    "jdft_orthonormalize": [_vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_subspace_eigs": [_i, _vp, _vp, _vp],
     "jdft_minimize_bands": [_vp, _i, _vp, _i, _i, ctypes.POINTER(MinOpts), _vp, ctypes.POINTER(MinReport), _vp],
     "jdft_mlp_create": [_vp, ctypes.POINTER(_vp)],
@@ -82,6 +87,11 @@ _SIGS = {
     "jdft_mlp_loss_grad": [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp],
     "jdft_mlp_adam_step": [_vp, _vp, ctypes.c_float, _vp],
     "jdft_mlp_rows": [_vp, _i, _vp, _vp, _i, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
+    "jdft_device_status": [_vp],
+    "jdft_batch_create": [_i, ctypes.POINTER(ApplyItem), ctypes.POINTER(_vp)],
+    "jdft_batch_launch": [_vp, _vp],
+    "jdft_batch_destroy": [_vp],
+    "jdft_autotune_chunk": [_vp, _i, _vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -283,10 +293,10 @@ def jdft_subspace(basis, ik, C, HC, CHC, COC, prec="fp64", stream=None):
           _stream(stream))
 
 
-def jdft_orthonormalize(basis, ik, C, stream=None):
-    """C <- C L^{-dag}, Omega C^dag C = L L^dag (complex128 block)."""
-    p, ld, nb = _block(C, "fp64", "C")
-    _call("jdft_orthonormalize", basis.handle, ik, p, ld, nb, _stream(stream))
+def jdft_orthonormalize(basis, ik, C, prec="fp64", stream=None):
+    """C <- C L^{-dag}, Omega C^dag C = L L^dag (complex128 block for fp64, complex64 otherwise)."""
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_orthonormalize", basis.handle, ik, p, ld, nb, _prec(prec), _stream(stream))
 
 
 def jdft_subspace_eigs(A, eigs, stream=None):
@@ -385,6 +395,53 @@ def jdft_profile_read() -> dict:
         name, n, ms = line.split()
         out[name] = (int(n), float(ms))
     return out
+
+
+def jdft_autotune_chunk(basis, ik, C, HC, prec="fp64", stream=None) -> int:
+    """Pick and keep the fastest band-chunk budget (MB) for apply_H on these blocks."""
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, _ = _block(HC, prec, "HC")
+    out = ctypes.c_int()
+    _call("jdft_autotune_chunk", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), ctypes.byref(out),
+          _stream(stream))
+    return out.value
+
+
+class Batch:
+    """A CUDA graph of Hamiltonian applications (see jdft_batch_create).
+
+    items: sequence of (basis, ik, C, HC, prec) with CUDA tensors C, HC."""
+
+    def __init__(self, items):
+        arr = (ApplyItem * len(items))()
+        self._keep = []
+        for i, (basis, ik, C, HC, prec) in enumerate(items):
+            p, ld, nb = _block(C, prec, "C")
+            q, ldh, _ = _block(HC, prec, "HC")
+            arr[i] = ApplyItem(basis.handle.value, ik, p.value, ld, q.value, ldh, nb, _prec(prec))
+            self._keep.append((basis, C, HC))
+        h = ctypes.c_void_p()
+        _call("jdft_batch_create", len(items), arr, ctypes.byref(h))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _call("jdft_batch_launch", self.handle, _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jdft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jdft_device_status(stream=None) -> None:
+    """Raise JdftError(ERR_TIMEOUT) if a bounded device-side wait gave up."""
+    _call("jdft_device_status", _stream(stream))
 
 
 def jdft_launch_count() -> int:

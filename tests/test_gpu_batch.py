@@ -1,0 +1,88 @@
+"""Batches of Hamiltonian applications in one CUDA graph (k-points of one
+cell with uneven spheres, plus independent cells with their own boxes):
+the graph replay equals the individual calls and the oracle."""
+import numpy as np
+import pytest
+
+from oracle import planewave as pw
+from synth import Workload, atom_positions, random_cells, random_coefficients, random_kpoints
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cell(w):
+    from paper_1708_03621_gb300 import learned
+    return learned.build_cell(w, "cuda")
+
+
+def _block(b, w, ik, nb, seed, prec):
+    from paper_1708_03621_gb300 import learned
+    C = learned.start_block(b, w, ik=ik, nb=nb, seed=seed)
+    return torch.tensor(C.astype(np.complex128 if prec == "fp64" else np.complex64), device="cuda")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_batch_graph_equals_individual_calls(prec):
+    from paper_1708_03621_gb300 import jdft
+    kpts = tuple(tuple(k) for k in random_kpoints(3, 21))
+    wk = Workload("kbatch", (10.0, 10.0, 10.0), 12.0, (40, 40, 40), kpts, 8, 12, 21, 22)
+    cells = random_cells(2, 23, L_range=(7.0, 9.0), ecut=10.0)
+    bases, items, refs = [], [], []
+    bk = _cell(wk)
+    bases.append(bk)
+    for ik in range(3):
+        C = _block(bk, wk, ik, 12, 100 + ik, prec)
+        items.append((bk, ik, C, torch.empty_like(C), prec))
+    for c, w in enumerate(cells):
+        b = _cell(w)
+        bases.append(b)
+        C = _block(b, w, 0, 9, 200 + c, prec)
+        items.append((b, 0, C, torch.empty_like(C), prec))
+    for (b, ik, C, HC, pr) in items:
+        R = torch.empty_like(C)
+        jdft.jdft_apply_H(b, ik, C, R, pr)
+        refs.append(R)
+    batch = jdft.Batch(items)
+    for rep in range(2):
+        if rep == 1:
+            for it in items:
+                it[2].mul_(0.5)
+            refs = [r * 0.5 for r in refs]
+        for it in items:
+            it[3].fill_(float("nan"))
+        batch.launch()
+        torch.cuda.synchronize()
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        for it, R in zip(items, refs):
+            got, ref = it[3].cpu().numpy(), R.cpu().numpy()
+            assert np.all(np.isfinite(got))
+            rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            assert rel.max() < tol
+    # one k-point of the batch against the oracle
+    ob = pw.Basis.build(wk.R, wk.S, wk.kfrac[1], wk.ecut)
+    atoms = atom_positions(wk.R, wk.natoms, wk.seed_atoms)
+    V = pw.vloc_realspace(wk.R, wk.S, atoms)
+    P = pw.projectors(wk.R, ob.kfrac, ob.iG, atoms)
+    C1 = items[1][2].cpu().numpy().astype(np.complex128)
+    ref = pw.apply_H(ob, V, C1.T, P, pw.dmatrix(wk.natoms)).T
+    got = items[1][3].cpu().numpy().astype(np.complex128)
+    rel = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() < (1e-10 if prec == "fp64" else 1e-5)
+    batch.close()
+
+
+def test_autotune_chunk_keeps_results():
+    from paper_1708_03621_gb300 import jdft
+    from synth import WORKLOADS
+    w = WORKLOADS["mid"]
+    b = _cell(w)
+    C = _block(b, w, 0, 24, 5, "fp32")
+    H0 = torch.empty_like(C)
+    jdft.jdft_apply_H(b, 0, C, H0, "fp32")
+    mb = jdft.jdft_autotune_chunk(b, 0, C, torch.empty_like(C), "fp32")
+    assert mb in (16, 32, 64, 96, 128, 256)
+    H1 = torch.empty_like(C)
+    jdft.jdft_apply_H(b, 0, C, H1, "fp32")
+    torch.cuda.synchronize()
+    assert torch.allclose(H0, H1, rtol=1e-5, atol=1e-6 * H0.abs().max().item())

@@ -18,8 +18,8 @@ from tests.systems import GpuSystem, OracleSystem, band_rel_err, workload
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5}
-CTYPE = {"fp64": "complex128", "fp32": "complex64"}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5}
+CTYPE = {"fp64": "complex128", "fp32": "complex64", "tf32x3": "complex64"}
 CASES = ["tiny_cubic", "tiny_ortho", "mid", "small"]
 
 _cache = {}
@@ -104,7 +104,7 @@ def test_operators_I_J_Idag_Jdag_O(name, prec):
     assert band_rel_err(host(out), o.basis.Omega * C) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("name", CASES)
 def test_apply_H(name, prec):
     w, o, g = systems(name)
@@ -118,6 +118,7 @@ def test_apply_H(name, prec):
     assert band_rel_err(got, ref) < TOL[prec]
     if prec == "fp64":
         assert rel_max(got, ref) < TOL[prec]
+    jdft.jdft_device_status()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -150,7 +151,7 @@ def test_density(name, prec):
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("name", CASES)
 def test_subspace(name, prec):
     w, o, g = systems(name)
@@ -164,9 +165,10 @@ def test_subspace(name, prec):
     jdft.jdft_subspace(g.basis, 0, to_dev(C, prec), to_dev(HCo, prec), CHC, COC, prec)
     assert rel_max(CHC.cpu().numpy(), CHC_ref) < TOL[prec]
     assert rel_max(COC.cpu().numpy(), COC_ref) < TOL[prec]
+    jdft.jdft_device_status()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_large_sampled_bands(prec):
     """128^3 box, 62 759 plane waves, 256 bands, 256 projectors: the whole block
     runs on the GPU; the oracle checks three sampled bands, the matching
@@ -240,3 +242,23 @@ def test_free_electron_on_gpu():
     jdft.jdft_apply_H(b, 0, torch.tensor(C, device="cuda"), HC)
     assert band_rel_err(host(HC), ob.Omega * ob.T[None, :] * C) < 1e-13
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["tiny_cubic", "small"])
+def test_generic_plane_kernels_match_oracle(name, prec, monkeypatch):
+    """The shared-memory Stockham plane kernels (used for box shapes without a
+    register-FFT kernel) stay exact when the register path is switched off."""
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    monkeypatch.setenv("JDFT_FAST_PLANE", "0")
+    C = o.coeffs()
+    Cd = to_dev(C, prec)
+    HC = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC, prec)
+    assert band_rel_err(host(HC), o.apply_H(C)) < TOL[prec]
+    f = np.full(C.shape[0], 2.0)
+    n = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    jdft.jdft_density(g.basis, 0, Cd, torch.tensor(f, device="cuda"), n, prec)
+    ref = pw.density(o.basis, C.T, f, weight=w.weights()[0])
+    assert np.max(np.abs(n.cpu().numpy() - ref)) / np.max(ref) < TOL[prec]

@@ -43,18 +43,20 @@ def test_subspace_eigs_match_lapack():
         assert np.max(np.abs(e.cpu().numpy() - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
 
 
-def test_orthonormalize_spans_same_subspace():
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_orthonormalize_spans_same_subspace(prec):
     from paper_1708_03621_gb300 import jdft
     w, o, g = systems("mid")
     C = o.coeffs(13, seed=31)
-    Cd = torch.tensor(C, device="cuda")
-    jdft.jdft_orthonormalize(g.basis, 0, Cd)
-    Q = Cd.cpu().numpy().T                                     # (npw, nb)
-    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(13), atol=1e-12)
+    Cd = torch.tensor(C.astype(np.complex128 if prec == "fp64" else np.complex64), device="cuda")
+    jdft.jdft_orthonormalize(g.basis, 0, Cd, prec)
+    Q = Cd.cpu().numpy().astype(np.complex128).T               # (npw, nb)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(13), atol=tol)
     L = pw.lowdin(C.T, o.basis.Omega)                          # oracle's orthonormal basis of the same span
     P1 = Q @ Q.conj().T
     P2 = L @ L.conj().T
-    assert np.max(np.abs(P1 - P2)) < 1e-12 * np.max(np.abs(P2))
+    assert np.max(np.abs(P1 - P2)) < tol * np.max(np.abs(P2))
 
 
 def test_orthonormalize_rejects_dependent_bands():
@@ -82,7 +84,7 @@ def test_minimize_tiny_reaches_dense_eigenvalues(precond):
     assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(nb), atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_minimize_small_cell_energy_within_1e6(prec):
     """The 48^3, 16-band system: |E - E_ref| < 1e-6 Ha, eigenvalues to 1e-7."""
     from paper_1708_03621_gb300 import jdft
@@ -93,7 +95,7 @@ def test_minimize_small_cell_energy_within_1e6(prec):
     assert rep["converged"], rep
     assert abs(rep["energy"] - GOLDEN["E_ref"]) < 1e-6
     assert np.max(np.abs(eigs.cpu().numpy() - np.array(GOLDEN["eigs"][:16]))) < 1e-7
-    if prec == "fp32":
+    if prec != "fp64":
         assert rep["mixed_iterations"] > 0
 
 
