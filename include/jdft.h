@@ -286,7 +286,8 @@ typedef struct jdft_batch_s* jdft_batch_t;
  * sizes) and independent cells with their own boxes can be mixed.  The graph
  * keeps the given device pointers: keep the buffers alive, refill the C blocks
  * as needed, and replay with jdft_batch_launch.  Items that share a basis share
- * its workspace and run in order.  Synchronous. */
+ * its workspace and run in order; a replay must not overlap other calls on the
+ * same bases.  Synchronous: waits for all earlier work on the device first. */
 jdft_status jdft_batch_create(int n, const jdft_apply_item* items, jdft_batch_t* out);
 /* Replay every application of the batch on `stream` with one graph launch. */
 jdft_status jdft_batch_launch(jdft_batch_t batch, void* stream);

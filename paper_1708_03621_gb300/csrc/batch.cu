@@ -48,6 +48,10 @@ jdft_status jdft_batch_create(int n, const jdft_apply_item* items, jdft_batch_t*
         delete bt;
         return set_error(s, msg);
     };
+    // the warm-up runs on a private stream and shares each basis workspace with
+    // earlier calls on other streams: let all earlier device work finish first
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return fail(set_error(JDFT_ERR_CUDA, "jdft_batch_create: earlier device work failed"));
     if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess)
         return fail(set_error(JDFT_ERR_CUDA, "jdft_batch_create: stream"));
     jdft_status s = run_items(bt->items, bt->stream);  // warm-up: workspaces reach their final size

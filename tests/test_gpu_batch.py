@@ -43,6 +43,7 @@ def test_batch_graph_equals_individual_calls(prec):
         R = torch.empty_like(C)
         jdft.jdft_apply_H(b, ik, C, R, pr)
         refs.append(R)
+    torch.cuda.synchronize()
     batch = jdft.Batch(items)
     for rep in range(2):
         if rep == 1:
