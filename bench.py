@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32x3", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--nbands", type=int, default=0, help="bands of the block (0 = the workload's)")
     ap.add_argument("--workload", default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -146,7 +148,7 @@ class Clocks:
 class Problem:
     """Device-resident inputs and outputs of one step, built through the C ABI."""
 
-    def __init__(self, wname: str, prec: str, device):
+    def __init__(self, wname: str, prec: str, device, nbands: int = 0):
         import torch
 
         from paper_1708_03621_gb300 import jdft
@@ -174,13 +176,13 @@ class Problem:
         iG = self.basis.gvectors(0).astype(np.float64)
         self.nrows = int(iG[:, 0].max() - iG[:, 0].min() + 1)   # i0 rows the sphere touches
         q = (iG + np.asarray(w.kfrac[0])) @ (2 * np.pi * np.linalg.inv(w.R).T).T
-        Y = random_coefficients(np.sum(q * q, 1), w.nbands, w.seed_coeffs)
+        Y = random_coefficients(np.sum(q * q, 1), nbands or w.nbands, w.seed_coeffs)
         Y /= np.sqrt(self.info["omega"] * np.sum(np.abs(Y) ** 2, axis=1, keepdims=True))
         ct = torch.complex128 if prec == "fp64" else torch.complex64
         self.C_host = torch.tensor(Y.astype(np.complex128 if prec == "fp64" else np.complex64)).pin_memory()
         self.C = self.C_host.to(device)
         self.HC = torch.empty_like(self.C)
-        self.nb = w.nbands
+        self.nb = Y.shape[0]
         self.f = torch.full((self.nb,), 2.0, dtype=torch.float64, device=device)
         self.n = torch.zeros(self.N, dtype=torch.float64, device=device)
         self.CHC = torch.empty((self.nb, self.nb), dtype=torch.complex128, device=device)
@@ -227,11 +229,17 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
         fl = 5 * ncols * S2 * l2(S2)
         by = (p.npw + S2 * ncols) * e + (p.npw * e if name == "zpass_forward" else 0)
         return fl * per_launch_bands, by * per_launch_bands
-    if name == "zgemm_cn":  # P^dag C, C^dag HC, C^dag C (and U in the orthonormalisation): nb x nb over npw
-        M = N = p.nb
-        return 8.0 * M * N * p.npw, 2.0 * p.nb * p.npw * e
+    if name == "zgemm_cn":
+        # per step: P^dag C (nproj x nb), C^dag HC, C^dag C and the orthonormaliser's C^dag C (nb x nb), over npw
+        per_step = [(p.nproj, p.nb), (p.nb, p.nb), (p.nb, p.nb), (p.nb, p.nb)]
+        fl = sum(8.0 * M * N * p.npw for M, N in per_step) / len(per_step)
+        by = sum((M + N) * p.npw * e for M, N in per_step) / len(per_step)
+        return fl, by
     if name == "zgemm_nn":
-        return 8.0 * p.npw * p.nb * p.nproj, (2.0 * p.nb + p.nproj) * p.npw * e
+        # per step: HC += P (D P^dag C) (K = nproj) and the orthonormaliser's C L^{-dag} (K = nb)
+        fl = 8.0 * p.npw * p.nb * (p.nproj + p.nb) / 2
+        by = ((2.0 * p.nb + p.nproj) + (2.0 * p.nb + p.nb)) * p.npw * e / 2
+        return fl, by
     return 0.0, 0.0
 
 
@@ -277,7 +285,7 @@ def run_ours(args, world, rank, local, pg):
     from paper_1708_03621_gb300 import jdft
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    p = Problem(args.workload, args.prec, dev)
+    p = Problem(args.workload, args.prec, dev, args.nbands)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         p.step()
@@ -355,7 +363,7 @@ def run_ours(args, world, rank, local, pg):
     if not args.no_fp64 and args.prec != "fp64":
         del p
         torch.cuda.empty_cache()
-        q = Problem(args.workload, "fp64", dev)
+        q = Problem(args.workload, "fp64", dev, args.nbands)
         q.step()
         torch.cuda.synchronize()
         k64 = max(2, args.steps // 10)
@@ -370,6 +378,9 @@ def run_ours(args, world, rank, local, pg):
         fp64 = {"value": round(q.nb * k64 / (t64 / 1e3), 1), "ms_per_step": round(t64 / k64, 3), "steps": k64}
         p = q
 
+    batch = None
+    if not args.no_batch and world == 1:
+        batch = batch_measurements(args.prec, dev)
     cg = None
     if not args.no_cg and world == 1:
         cg = cg_measurements(args.prec if args.prec != "fp64" else "fp32", dev)
@@ -388,6 +399,7 @@ def run_ours(args, world, rank, local, pg):
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernels": kernels,
         "fp64_path": fp64,
         "cg": cg,
+        "batch": batch,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
@@ -455,6 +467,67 @@ def cg_measurements(prec: str, device, log=lambda *_: None) -> dict:
     out["small_time_to_dE_1e-6"] = res
     out["small_E_ref_Ha"] = E_ref
     b.close()
+    return out
+
+
+def batch_measurements(prec: str, device, reps: int = 3) -> dict:
+    """Batched Hamiltonian applications replayed as one CUDA graph each.
+
+    * 32 k-points uniform in the Brillouin zone of the L = 20 bohr, E_cut = 30 Ha
+      cell (128^3 box, 64 atoms), 128 bands each: uneven sphere sizes;
+    * 8 independent cubic cells, L ~ U[8, 16] bohr, E_cut = 20 Ha, boxes 40^3..80^3,
+      16..128 bands, 4..32 atoms.
+    Band-applies per second of the graph replay (events on the launch stream).
+    """
+    import torch
+
+    from paper_1708_03621_gb300 import jdft, learned
+    from synth import Workload, random_cells, random_kpoints
+    ct = torch.complex128 if prec == "fp64" else torch.complex64
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(batch, units):
+        batch.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            batch.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return round(units / (ms / 1e3), 1), round(ms, 3)
+
+    kp = tuple(tuple(k) for k in random_kpoints(32, 21))
+    wk = Workload("kbatch32", (20.0, 20.0, 20.0), 30.0, (128, 128, 128), kp, 64, 128, 11, 12)
+    b = learned.build_cell(wk, device)
+    npws = [b.npw(ik) for ik in range(wk.nk)]
+    items = []
+    for ik in range(wk.nk):
+        C = torch.tensor(learned.start_block(b, wk, ik=ik, seed=1000 + ik), device=device).to(ct)
+        items.append((b, ik, C, torch.empty_like(C), prec))
+    bt = jdft.Batch(items)
+    v, ms = timed(bt, wk.nk * wk.nbands)
+    out["kpoints32"] = {"band_applies_per_s": v, "ms_per_launch": ms, "nk": wk.nk, "nbands": wk.nbands,
+                        "npw_min": min(npws), "npw_max": max(npws)}
+    bt.close()
+    del items
+    b.close()
+    torch.cuda.empty_cache()
+    cells = random_cells(8, 29)
+    items, bases = [], []
+    for w in cells:
+        bc = learned.build_cell(w, device)
+        bases.append(bc)
+        C = torch.tensor(learned.start_block(bc, w), device=device).to(ct)
+        items.append((bc, 0, C, torch.empty_like(C), prec))
+    bt = jdft.Batch(items)
+    units = sum(w.nbands for w in cells)
+    v, ms = timed(bt, units)
+    out["cells8"] = {"band_applies_per_s": v, "ms_per_launch": ms, "bands": units,
+                     "boxes": [w.S[0] for w in cells], "nbands": [w.nbands for w in cells]}
+    bt.close()
     return out
 
 

@@ -1,0 +1,17 @@
+// Blocked FP64 Cholesky + triangular inverse on many blocks (see chol.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace jdft {
+
+// double2 elements of workspace blocked_cholesky_winv needs for an n x n matrix.
+size_t chol_work_elems(int n);
+
+// U (n x n complex128 row-major, Hermitian positive definite) = L L^dag;
+// W (n x n row-major, complex128 if fp64 else complex64) = L^{-dag}.
+// *status receives JDFT_ERR_NOT_POSDEF on a non-positive pivot (device word).
+jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
+                                  cudaStream_t st);
+
+}  // namespace jdft

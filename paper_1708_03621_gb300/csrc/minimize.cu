@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "chain.cuh"
+#include "chol.cuh"
 #include "gemm.cuh"
 #include "minimize.cuh"
 #include "profile.cuh"
@@ -328,8 +329,11 @@ static jdft_status dot(int npw, int nb, const c_t<T>* x, int ldx, const c_t<T>* 
     return check_launch("blk_dot");
 }
 
+// work: chol_work_elems(n) double2 elements.  Small matrices factor in one
+// block; larger ones use the blocked multi-block version.
 jdft_status small_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
                                 cudaStream_t st) {
+    if (n > 32) return blocked_cholesky_winv(n, U, work, W, fp64, status, st);
     Trace tr_("cholesky_winv", st);
     if (fp64)
         cholesky_winv_kernel<double><<<1, 256, 0, st>>>(n, U, work, work + (size_t)n * n, (double2*)W, status);
@@ -389,7 +393,8 @@ struct MinState {
         const size_t blk = (size_t)nb * ld * sizeof(c_t<T>);
         const size_t sm = (size_t)nb * nb * sizeof(double2);
         const int m = nb + (nb & 1);
-        const size_t total = 12 * blk + 5 * sm + 2 * (size_t)m * m * sizeof(double2) + 2 * (size_t)nb * nb * sizeof(c_t<T>) +
+        const size_t lab = std::max(2 * (size_t)m * m, chol_work_elems(nb)) * sizeof(double2);
+        const size_t total = 12 * blk + 5 * sm + lab + 2 * (size_t)nb * nb * sizeof(c_t<T>) +
                              (size_t)nb * sizeof(double) + 64 * sizeof(double) + 64 + 3 * (size_t)nb * sizeof(float) +
                              17 * 256;
         JDFT_CUDA_TRY(cudaMalloc(&mem.p, total));
@@ -399,7 +404,7 @@ struct MinState {
         KGp = (c_t<T>*)take(blk); d = (c_t<T>*)take(blk); dp = (c_t<T>*)take(blk); Hd = (c_t<T>*)take(blk);
         Y = (c_t<T>*)take(blk); HY = (c_t<T>*)take(blk); Cn = (c_t<T>*)take(blk); HCn = (c_t<T>*)take(blk);
         Hs = (double2*)take(sm); Hsn = (double2*)take(sm); Pm = (double2*)take(sm); dOd = (double2*)take(sm);
-        U = (double2*)take(sm); lawork = (double2*)take(2 * (size_t)m * m * sizeof(double2));
+        U = (double2*)take(sm); lawork = (double2*)take(lab);
         Bm = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>)); W = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>));
         Tb = (double*)take(nb * sizeof(double)); scal = (double*)take(64 * sizeof(double)); status = (int*)take(64);
         bf = (float*)take(3 * (size_t)nb * sizeof(float));
@@ -611,7 +616,7 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
     const int m = nb + (nb & 1);
     const size_t sm = ((size_t)nb * nb * sizeof(double2) + 255) / 256 * 256;
     const size_t wbytes = ((size_t)nb * nb * sizeof(c_t<T>) + 255) / 256 * 256;
-    const size_t lab = 2 * (size_t)m * m * sizeof(double2);
+    const size_t lab = ((std::max(2 * (size_t)m * m, chol_work_elems(nb)) * sizeof(double2)) + 255) / 256 * 256;
     const size_t blk = ((size_t)nb * ldc * sizeof(c_t<T>) + 255) / 256 * 256;
     // the basis workspace (grown once) holds U, W, the factorisation scratch, a copy of C and a status word
     jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256);

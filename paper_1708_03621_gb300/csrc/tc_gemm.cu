@@ -34,14 +34,18 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;
 
 __device__ int g_tc_status = 0;
 
+// 8-row groups are TC_SBO bytes apart (the 1024 bytes of their core matrices
+// plus 16, so consecutive groups start on different banks).
+constexpr int TC_SBO = TC_KG * 128 + 16;
+
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-    return (uint32_t)(((row >> 3) * TC_KG + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((row >> 3) * TC_SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
 template <int NT>
 struct TcLayout {
-    static constexpr int A_BYTES = TC_M * TC_KC * 4;
-    static constexpr int B_BYTES = NT * TC_KC * 4;
+    static constexpr int A_BYTES = (TC_M / 8) * TC_SBO;
+    static constexpr int B_BYTES = (NT / 8) * TC_SBO;
     static constexpr int A_HI = 0, A_LO = A_BYTES;
     static constexpr int BR_HI = 2 * A_BYTES, BR_LO = BR_HI + B_BYTES;
     static constexpr int BI_HI = BR_LO + B_BYTES, BI_LO = BI_HI + B_BYTES;
@@ -59,24 +63,51 @@ __device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int
 }
 
 // out[m][n] = alpha sum_k conj(A[m][k]) B[n][k] (rows K-contiguous); FP64 atomics into out.
+// Staging: lane -> (row, complex pair kp of the 16-complex chunk); the loads of
+// a chunk go to registers first (load), the TF32 splits to shared memory after
+// (store), so the next chunk's loads overlap the current chunk's products.
 template <int NT>
 struct StageCN {
     const float2* A; int lda; const float2* B; int ldb; int M, N, K;
     double2* out; int ldo; double alpha;
-    __device__ __forceinline__ void stage(char* buf, int m0, int n0, int kc0, int tid) const {
-        using L = TcLayout<NT>;
-        for (int e = tid; e < TC_M * (TC_KC / 2); e += TC_THREADS) {
-            const int row = e >> 4, kk = e & 15;
-            const int m = m0 + row, k = kc0 + kk;
-            const float2 a = (m < M && k < K) ? A[(size_t)m * lda + k] : make_float2(0.f, 0.f);
-            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, a.x, a.y);
+    static constexpr int PA = TC_M * 8 / TC_THREADS;  // pairs per thread
+    static constexpr int PB = NT * 8 / TC_THREADS;
+    struct Regs { float2 a[PA][2]; float2 b[PB][2]; };
+    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int tid) const {
+#pragma unroll
+        for (int i = 0; i < PA; ++i) {
+            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
+            const int m = m0 + row, k = kc0 + 2 * kp;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                r.a[i][h] = (m < M && k + h < K) ? A[(size_t)m * lda + k + h] : make_float2(0.f, 0.f);
         }
-        for (int e = tid; e < NT * (TC_KC / 2); e += TC_THREADS) {
-            const int row = e >> 4, kk = e & 15;
-            const int n = n0 + row, k = kc0 + kk;
-            const float2 b = (n < N && k < K) ? B[(size_t)n * ldb + k] : make_float2(0.f, 0.f);
-            put_split(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, b.y);
-            put_split(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, -b.x);
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
+            const int n = n0 + row, k = kc0 + 2 * kp;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                r.b[i][h] = (n < N && k + h < K) ? B[(size_t)n * ldb + k + h] : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
+        using L = TcLayout<NT>;
+#pragma unroll
+        for (int i = 0; i < PA; ++i) {
+            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) put_split(buf, L::A_HI, L::A_LO, row, 4 * kp + 2 * h, r.a[i][h].x, r.a[i][h].y);
+        }
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 b = r.b[i][h];
+                put_split(buf, L::BR_HI, L::BR_LO, row, 4 * kp + 2 * h, b.x, b.y);
+                put_split(buf, L::BI_HI, L::BI_LO, row, 4 * kp + 2 * h, b.y, -b.x);
+            }
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -85,26 +116,43 @@ struct StageCN {
             atomicAdd(&out[(size_t)m * ldo + n].y, alpha * (double)im);
         }
     }
-    __device__ __forceinline__ int kcomplex() const { return K; }
 };
 
 // out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
+// Staging: lane -> (k, row) with consecutive lanes on consecutive rows (the
+// operands are contiguous along M and N).
 template <int NT>
 struct StageNN {
     const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
     float2* out; int ldo;
-    __device__ __forceinline__ void stage(char* buf, int m0, int n0, int kc0, int tid) const {
-        using L = TcLayout<NT>;
-        for (int e = tid; e < TC_M * (TC_KC / 2); e += TC_THREADS) {
-            const int kk = e >> 7, row = e & 127;
+    static constexpr int PA = TC_M * 16 / TC_THREADS;
+    static constexpr int PB = NT * 16 / TC_THREADS;
+    struct Regs { float2 a[PA]; float2 b[PB]; };
+    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int tid) const {
+#pragma unroll
+        for (int i = 0; i < PA; ++i) {
+            const int e = tid + TC_THREADS * i, kk = e >> 7, row = e & 127;
             const int m = m0 + row, k = kc0 + kk;
-            const float2 a = (m < M && k < K) ? A[(size_t)k * lda + m] : make_float2(0.f, 0.f);
-            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, a.x, a.y);
+            r.a[i] = (m < M && k < K) ? A[(size_t)k * lda + m] : make_float2(0.f, 0.f);
         }
-        for (int e = tid; e < NT * (TC_KC / 2); e += TC_THREADS) {
-            const int kk = e / NT, row = e % NT;
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+            const int e = tid + TC_THREADS * i, kk = e / NT, row = e % NT;
             const int n = n0 + row, k = kc0 + kk;
-            const float2 b = (n < N && k < K) ? Bm[(size_t)k * ldb + n] : make_float2(0.f, 0.f);
+            r.b[i] = (n < N && k < K) ? Bm[(size_t)k * ldb + n] : make_float2(0.f, 0.f);
+        }
+    }
+    __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
+        using L = TcLayout<NT>;
+#pragma unroll
+        for (int i = 0; i < PA; ++i) {
+            const int e = tid + TC_THREADS * i, kk = e >> 7, row = e & 127;
+            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, r.a[i].x, r.a[i].y);
+        }
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+            const int e = tid + TC_THREADS * i, kk = e / NT, row = e % NT;
+            const float2 b = r.b[i];
             put_split(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, -b.y);
             put_split(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, b.x);
         }
@@ -117,7 +165,6 @@ struct StageNN {
             out[(size_t)n * ldo + m] = v;
         }
     }
-    __device__ __forceinline__ int kcomplex() const { return K; }
 };
 
 template <int NT, class S>
@@ -144,6 +191,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     constexpr uint32_t idesc = tc::instr_desc(2u, TC_M, NT);
     int ok = 1;
     int it = 0;
+    typename S::Regs regs;
+    if (c0 < c1) s.load(regs, m0, n0, c0 * (TC_KC / 2), tid);
     for (int c = c0; c < c1; ++c, ++it) {
         const int sidx = it & 1;
         char* buf = stage_buf[sidx];
@@ -153,13 +202,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             ok = __syncthreads_and(w);
             if (!ok) break;
         }
-        s.stage(buf, m0, n0, c * (TC_KC / 2), tid);
+        s.store(regs, buf, tid);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
             tc::tc_fence_after_sync();
             const uint32_t base = tc::smem_addr(buf);
-            constexpr uint32_t LBO = 128, SBO = TC_KG * 128;
+            constexpr uint32_t LBO = 128, SBO = TC_SBO;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 8; ++kk) {
                 const uint32_t off = kk * 256;
@@ -179,6 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             }
             tc::mma_commit(&mbar[sidx]);
         }
+        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * (TC_KC / 2), tid);  // overlaps the products just issued
     }
     const int n = it;
     if (ok && n > 0) {

@@ -43,27 +43,30 @@ def test_subspace_eigs_match_lapack():
         assert np.max(np.abs(e.cpu().numpy() - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("nb", [13, 70])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
-def test_orthonormalize_spans_same_subspace(prec):
+def test_orthonormalize_spans_same_subspace(prec, nb):
+    """13 bands: one-block factorisation; 70: the blocked multi-block one (padded to 96)."""
     from paper_1708_03621_gb300 import jdft
     w, o, g = systems("mid")
-    C = o.coeffs(13, seed=31)
+    C = o.coeffs(nb, seed=31)
     Cd = torch.tensor(C.astype(np.complex128 if prec == "fp64" else np.complex64), device="cuda")
     jdft.jdft_orthonormalize(g.basis, 0, Cd, prec)
     Q = Cd.cpu().numpy().astype(np.complex128).T               # (npw, nb)
     tol = 1e-12 if prec == "fp64" else 2e-5
-    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(13), atol=tol)
+    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(nb), atol=tol)
     L = pw.lowdin(C.T, o.basis.Omega)                          # oracle's orthonormal basis of the same span
     P1 = Q @ Q.conj().T
     P2 = L @ L.conj().T
     assert np.max(np.abs(P1 - P2)) < tol * np.max(np.abs(P2))
 
 
-def test_orthonormalize_rejects_dependent_bands():
+@pytest.mark.parametrize("name,nb", [("tiny_cubic", 3), ("mid", 40)])
+def test_orthonormalize_rejects_dependent_bands(name, nb):
     from paper_1708_03621_gb300 import jdft
-    w, o, g = systems("tiny_cubic")
-    C = o.coeffs(3)
-    C[2] = C[0]
+    w, o, g = systems(name)
+    C = o.coeffs(nb)
+    C[nb - 1] = C[0]
     with pytest.raises(jdft.JdftError, match="NOT_POSDEF"):
         jdft.jdft_orthonormalize(g.basis, 0, torch.tensor(C, device="cuda"))
 
