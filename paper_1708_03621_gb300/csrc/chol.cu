@@ -49,6 +49,9 @@ __global__ void chol_init_kernel(int n, int N, const double2* __restrict__ U, do
 }
 
 // Factor the diagonal tile k in shared memory and invert it; writes L_kk (lower) and X_kk = L_kk^{-1}.
+// Right-looking: step j takes the pivot, scales column j and updates the
+// trailing tile in parallel; the inverse is built row by row, every column of
+// a row in parallel.
 __global__ void __launch_bounds__(CT) chol_diag_kernel(int n, int N, int k, double2* __restrict__ L,
                                                        double2* __restrict__ X, const double2* __restrict__ U,
                                                        int* status) {
@@ -65,9 +68,9 @@ __global__ void __launch_bounds__(CT) chol_diag_kernel(int n, int N, int k, doub
     __syncthreads();
     for (int j = 0; j < CB; ++j) {
         if (threadIdx.x == 0) {
+            // a pivot that is not positive, or that lost all but ~1e-13 of the
+            // original diagonal, means linearly dependent bands
             double d = a[j][j].x;
-            for (int m = 0; m < j; ++m) d -= a[j][m].x * a[j][m].x + a[j][m].y * a[j][m].y;
-            // relative to the original diagonal: a pivot that lost all but ~1e-13 of it means dependence
             const int g = r0 + j;
             const double ujj = g < n ? U[(size_t)g * n + g].x : 1.0;
             if (!(d > 1e-13 * ujj)) { bad = 1; d = 1.0; }
@@ -75,32 +78,39 @@ __global__ void __launch_bounds__(CT) chol_diag_kernel(int n, int N, int k, doub
             a[j][j] = make_double2(piv, 0.0);
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < CB; i += CT) {
-            double2 s = a[i][j];
-            for (int m = 0; m < j; ++m) {
-                const double2 t = zmulc(a[i][m], a[j][m]);
-                s.x -= t.x;
-                s.y -= t.y;
+        const double ip = 1.0 / piv;
+        for (int i = j + 1 + threadIdx.x; i < CB; i += CT) a[i][j] = make_double2(a[i][j].x * ip, a[i][j].y * ip);
+        __syncthreads();
+        const int w = CB - j - 1;
+        for (int e = threadIdx.x; e < w * w; e += CT) {
+            const int i = j + 1 + e / w, m = j + 1 + e % w;
+            if (m <= i) {
+                const double2 t = zmulc(a[i][j], a[m][j]);
+                a[i][m].x -= t.x;
+                a[i][m].y -= t.y;
             }
-            a[i][j] = make_double2(s.x / piv, s.y / piv);
         }
         __syncthreads();
     }
-    // inverse of the tile: column c by forward substitution (one thread per column)
-    if (threadIdx.x < CB) {
-        const int c = threadIdx.x;
-        for (int i = 0; i < CB; ++i) {
-            if (i < c) { x[i][c] = make_double2(0.0, 0.0); continue; }
+    // X = L^{-1}: row i, all columns c <= i in parallel
+    for (int i = 0; i < CB; ++i) {
+        for (int c = threadIdx.x; c < CB; c += CT) {
             double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            for (int m = c; m < i; ++m) {
-                const double2 t = zmul(a[i][m], x[m][c]);
-                s.x -= t.x;
-                s.y -= t.y;
+            if (c <= i) {
+                for (int m = c; m < i; ++m) {
+                    const double2 t = zmul(a[i][m], x[m][c]);
+                    s.x -= t.x;
+                    s.y -= t.y;
+                }
+                const double d = 1.0 / a[i][i].x;
+                s = make_double2(s.x * d, s.y * d);
+            } else {
+                s = make_double2(0.0, 0.0);
             }
-            x[i][c] = make_double2(s.x / a[i][i].x, s.y / a[i][i].x);
+            x[i][c] = s;
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = threadIdx.x; e < CB * CB; e += CT) {
         const int i = e / CB, j = e % CB;
         L[(size_t)(r0 + i) * N + r0 + j] = j <= i ? a[i][j] : make_double2(0.0, 0.0);

@@ -47,8 +47,8 @@ def start_block(b, w, ik=0, nb=None, seed=None):
                                w.seed_coeffs if seed is None else seed)
 
 
-def generate_rows(cells, snapshots=(10, 20, 40, 60), rows_per_snapshot=40000, prec="fp32", tol=1e-5,
-                  device="cuda", log=print):
+def generate_rows(cells, snapshots=(10, 20, 40, 60), rows_per_snapshot=40000, prec="tf32x3", tol=1e-5,
+                  device="cuda", log=print, deadline=None):
     """Training rows from Teter-minimiser trajectories on the given cells.
 
     Snapshots come from the later part of each trajectory (from iteration 10
@@ -62,6 +62,9 @@ def generate_rows(cells, snapshots=(10, 20, 40, 60), rows_per_snapshot=40000, pr
     import torch
     out = []
     for ci, w in enumerate(cells):
+        if deadline is not None and time.time() > deadline:
+            log(f"time budget reached after {ci} cells")
+            break
         t0 = time.time()
         b = build_cell(w, device)
         C0 = torch.tensor(start_block(b, w), device=device)
@@ -127,17 +130,20 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--init-seed", type=int, default=7)
     ap.add_argument("--heldout", type=int, default=10)
+    ap.add_argument("--budget", type=float, default=0.0, help="seconds for data generation (0 = no limit)")
     args = ap.parse_args()
     import torch
     from synth import mlp_init, training_cells
     torch.cuda.set_device(0)
     t0 = time.time()
-    rows = generate_rows(training_cells(args.cells, args.seed0))
-    held = generate_rows(training_cells(args.heldout, 2000))
-    print(f"rows: train {rows.shape[0]} held-out {held.shape[0]} ({time.time() - t0:.0f}s)")
+    deadline = t0 + args.budget if args.budget > 0 else None
+    log = lambda *a: print(*a, flush=True)
+    rows = generate_rows(training_cells(args.cells, args.seed0), log=log, deadline=deadline)
+    held = generate_rows(training_cells(args.heldout, 2000), log=log)
+    print(f"rows: train {rows.shape[0]} held-out {held.shape[0]} ({time.time() - t0:.0f}s)", flush=True)
     mlp = jdft.Mlp(mlp_init(args.init_seed))
     print(f"held-out loss before: {evaluation_loss(mlp, held):.6f}")
-    train(mlp, rows, epochs=args.epochs)
+    train(mlp, rows, epochs=args.epochs, log=log)
     print(f"held-out loss after: {evaluation_loss(mlp, held):.6f}")
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, mlp.params())
