@@ -18,6 +18,12 @@ namespace jdft {
 template <int... R>
 struct Rad {};
 
+// Scratch lines are padded with one element after every 16 (and lines are
+// N + N/16 apart): the stage exchanges write index 16 t + r from lane t, which
+// without the pad would put every lane of a warp on the same bank.
+__host__ __device__ constexpr int padx(int idx) { return idx + (idx >> 4); }
+__host__ __device__ constexpr int padded_line(int N) { return N + (N >> 4); }
+
 template <typename T, int SIGN>
 __device__ __forceinline__ void dft16(c_t<T>* v) {
     // 16 = 4 x 4: DFT4 over n2 (stride 4), twiddle W16^{n1 k1}, DFT4 over n1.
@@ -131,7 +137,7 @@ struct StageRunner {
 #pragma unroll
             for (int u = 0; u < E / R; ++u)
 #pragma unroll
-                for (int r = 0; r < R; ++r) scr[stage_out_index<TL, NS, R>(t, u, r)] = v[u * R + r];
+                for (int r = 0; r < R; ++r) scr[padx(stage_out_index<TL, NS, R>(t, u, r))] = v[u * R + r];
             __syncwarp();
             load_next<Rest...>(v, t, scr);
             StageRunner<T, N, TL, E, SIGN, NS * R, Rest...>::run(v, t, scr, W);
@@ -142,7 +148,7 @@ struct StageRunner {
 #pragma unroll
         for (int u = 0; u < E / R2; ++u)
 #pragma unroll
-            for (int r = 0; r < R2; ++r) v[u * R2 + r] = scr[t + TL * u + r * (N / R2)];
+            for (int r = 0; r < R2; ++r) v[u * R2 + r] = scr[padx(t + TL * u + r * (N / R2))];
     }
 };
 

@@ -184,8 +184,6 @@ template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
                                 jdft_prec prec, void* work, cudaStream_t st) {
     if (sp.nproj == 0 || nb == 0) return JDFT_OK;
-    if (prec == JDFT_BF16X3)
-        return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split tensor-core GEMMs not built in this library");
     double2* Bc = (double2*)work;
     c_t<T>* Bd = (c_t<T>*)((char*)work + ((size_t)sp.nproj * nb * sizeof(double2) + 255) / 256 * 256);
     JDFT_CUDA_TRY(cudaMemsetAsync(Bc, 0, (size_t)sp.nproj * nb * sizeof(double2), st));
@@ -208,7 +206,8 @@ jdft_status gemm_cn<double>(jdft_prec, int M, int N, int K, const double2* A, in
 template <>
 jdft_status gemm_cn<float>(jdft_prec prec, int M, int N, int K, const float2* A, int lda, const float2* B, int ldb,
                            double2* out, int ldo, double alpha, cudaStream_t st) {
-    if (prec == JDFT_TF32X3) return tc_zgemm_cn(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
+    if (prec == JDFT_TF32X3 || prec == JDFT_BF16X3)
+        return tc_zgemm_cn(M, N, K, A, lda, B, ldb, out, ldo, alpha, prec == JDFT_BF16X3, st);
     return zgemm_cn<float>(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
 }
 template <>
@@ -219,7 +218,8 @@ jdft_status gemm_nn_acc<double>(jdft_prec, int M, int N, int K, const double2* A
 template <>
 jdft_status gemm_nn_acc<float>(jdft_prec prec, int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb,
                                float2* out, int ldo, cudaStream_t st) {
-    if (prec == JDFT_TF32X3) return tc_zgemm_nn_acc(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+    if (prec == JDFT_TF32X3 || prec == JDFT_BF16X3)
+        return tc_zgemm_nn_acc(M, N, K, A, lda, Bm, ldb, out, ldo, prec == JDFT_BF16X3, st);
     return zgemm_nn_acc<float>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
 }
 
@@ -252,8 +252,6 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
     JDFT_CHECK_ARG(C && ldc >= npw, "bad C block");
     JDFT_CHECK_ARG(!CHC || (HC && ldhc >= npw), "bad HC block");
     JDFT_CHECK_ARG(((uintptr_t)CHC % 16) == 0 && ((uintptr_t)COC % 16) == 0, "outputs must be 16-byte aligned");
-    if (prec == JDFT_BF16X3)
-        return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split tensor-core GEMMs not built in this library");
     cudaStream_t st = (cudaStream_t)stream;
     jdft_status s = JDFT_OK;
     if (CHC) {

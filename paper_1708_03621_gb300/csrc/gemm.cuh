@@ -19,14 +19,15 @@ template <typename T>
 jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb, c_t<T>* out,
                          int ldo, cudaStream_t st);
 
-// Tensor-core versions (FP32 inputs, 3-term TF32 split) of the two products above.
+// Tensor-core versions (FP32 inputs split into hi + lo, 3 products) of the two
+// products above: TF32 pieces (bf16 = false) or BF16 pieces (bf16 = true).
 jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
-                        double alpha, cudaStream_t st);
+                        double alpha, bool bf16, cudaStream_t st);
 jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
-                            int ldo, cudaStream_t st);
+                            int ldo, bool bf16, cudaStream_t st);
 
-// Precision dispatch: JDFT_TF32X3 runs the tensor-core versions (T = float
-// only), every other precision the CUDA-core ones.
+// Precision dispatch: JDFT_TF32X3 and JDFT_BF16X3 run the tensor-core
+// versions (T = float only), the other precisions the CUDA-core ones.
 template <typename T>
 jdft_status gemm_cn(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* B, int ldb,
                     double2* out, int ldo, double alpha, cudaStream_t st);

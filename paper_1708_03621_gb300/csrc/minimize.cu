@@ -651,7 +651,6 @@ jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
     JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
     JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
-    if (prec == JDFT_BF16X3) return set_error(JDFT_ERR_UNSUPPORTED, "BF16-split products not built");
     cudaStream_t st = (cudaStream_t)stream;
     return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st)
                              : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st);

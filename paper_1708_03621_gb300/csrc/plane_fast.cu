@@ -33,6 +33,14 @@ __device__ __forceinline__ int wrapf(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
+// Elements of warp-private scratch: LPW padded lines of the longer axis.
+template <int N0, int E0, int N1, int E1>
+__host__ __device__ constexpr int warp_scratch() {
+    return (32 / (N0 / E0)) * padded_line(N0) > (32 / (N1 / E1)) * padded_line(N1)
+               ? (32 / (N0 / E0)) * padded_line(N0)
+               : (32 / (N1 / E1)) * padded_line(N1);
+}
+
 // Phase 1 / 3 helpers -------------------------------------------------------
 template <typename T, int N1, int E1, class R1>
 __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<T>* __restrict__ plane, c_t<T>* A,
@@ -40,7 +48,7 @@ __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<
     using F = LineFFT<T, N1, E1, +1, R1>;
     constexpr int TL = N1 / E1, LPW = 32 / TL;
     const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = wscr + liw * N1;
+    c_t<T>* scr = wscr + liw * padded_line(N1);
     for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
@@ -70,7 +78,7 @@ __device__ __forceinline__ void rows_forward_fast(const ChainGeom& g, c_t<T>* __
     using F = LineFFT<T, N1, E1, -1, R1>;
     constexpr int TL = N1 / E1, LPW = 32 / TL;
     const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = wscr + liw * N1;
+    c_t<T>* scr = wscr + liw * padded_line(N1);
     for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
                                                                         const c_t<T>* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int lsA = N1 + 1;
-    constexpr int SCR = 32 * (E0 > E1 ? E0 : E1);  // per-warp scratch (LPW lines of N)
+    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();  // per-warp scratch (LPW padded lines)
     c_t<T>* W0 = reinterpret_cast<c_t<T>*>(smem_raw);
     c_t<T>* W1 = W0 + N0;
     c_t<T>* scr_all = W1 + N1;
@@ -133,7 +141,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
         using FF = LineFFT<T, N0, E0, -1, R0>;
         constexpr int TL = N0 / E0, LPW = 32 / TL;
         const int liw = lane / TL, t = lane % TL;
-        c_t<T>* scr = wscr + liw * N0;
+        c_t<T>* scr = wscr + liw * padded_line(N0);
         for (int base = warp * LPW; base < N1; base += kFastWarps * LPW) {
             const int j1 = base + liw;
             const bool act = j1 < N1;
@@ -144,11 +152,11 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
 #pragma unroll
             for (int e = 0; e < E0; ++e) {
                 const int j0 = FI::out_index(t, e);
-                scr[j0] = act ? cscale(v[e], Vq[j0]) : mk<T>(T(0), T(0));
+                scr[padx(j0)] = act ? cscale(v[e], Vq[j0]) : mk<T>(T(0), T(0));
             }
             __syncwarp();
 #pragma unroll
-            for (int e = 0; e < E0; ++e) v[e] = scr[FF::in_index(t, e)];
+            for (int e = 0; e < E0; ++e) v[e] = scr[padx(FF::in_index(t, e))];
             FF::run(v, t, scr, W0);
             if (act) {
 #pragma unroll
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainG
                                                                           const float2* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int lsA = N1 + 1;
-    constexpr int SCR = 32 * (E0 > E1 ? E0 : E1);
+    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
     constexpr int TL = N0 / E0, LPW = 32 / TL;
     constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
     float2* W0 = reinterpret_cast<float2*>(smem_raw);
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainG
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
             float2 v[E0];
-            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t, wscr + liw * N0, W0);
+            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t, wscr + liw * padded_line(N0), W0);
 #pragma unroll
             for (int e = 0; e < E0; ++e) acc[k][e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
         }
@@ -243,7 +251,7 @@ constexpr size_t kFastMaxSmem = 220 * 1024;
 template <int N0, int N1>
 static size_t fast_smem(const ChainGeom& g, size_t elem) {
     constexpr int E0 = FastCfg<N0>::E, E1 = FastCfg<N1>::E;
-    return ((size_t)N0 + N1 + (size_t)kFastWarps * 32 * (E0 > E1 ? E0 : E1) + (size_t)g.nrows * (N1 + 1)) * elem;
+    return ((size_t)N0 + N1 + (size_t)kFastWarps * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * (N1 + 1)) * elem;
 }
 
 static bool fast_disabled() {

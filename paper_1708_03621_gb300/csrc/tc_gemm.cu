@@ -18,6 +18,8 @@
 // tensor memory until the epilogue reads them with tcgen05.ld.  Every wait is
 // bounded; a wait that gives up records JDFT_ERR_TIMEOUT in a device flag
 // (read by jdft_device_status), skips the epilogue and frees its tensor memory.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "gemm.cuh"
@@ -27,25 +29,38 @@
 namespace jdft {
 
 constexpr int TC_M = 128;
-constexpr int TC_KC = 32;           // real K elements per stage (16 complex)
-constexpr int TC_KG = TC_KC / 4;    // 16-byte core columns per row
+constexpr int TC_CPS = 16;          // complex K elements per stage
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;
 
 __device__ int g_tc_status = 0;
 
-// 8-row groups are TC_SBO bytes apart (the 1024 bytes of their core matrices
-// plus 16, so consecutive groups start on different banks).
-constexpr int TC_SBO = TC_KG * 128 + 16;
+// Operand format: FMT 0 = TF32 (4-byte elements, kind::tf32, K = 8 per
+// instruction), FMT 1 = BF16 (2-byte elements, kind::f16, K = 16).  A stage
+// row holds 2 * TC_CPS real values: 8 (TF32) or 4 (BF16) 16-byte core
+// columns; 8-row groups are SBO bytes apart (their core matrices plus 16, so
+// consecutive groups start on different banks); each instruction covers two
+// core columns, so a stage takes KSTEPS = KG / 2 instructions per product.
+template <int FMT>
+struct Fmt {
+    static constexpr int ELEM = FMT ? 2 : 4;
+    static constexpr int PER16 = 16 / ELEM;                 // elements per 16-byte core row
+    static constexpr int KG = 2 * TC_CPS / PER16;           // core columns per row
+    static constexpr int SBO = KG * 128 + 16;
+    static constexpr int KSTEPS = KG / 2;
+    static constexpr uint32_t IDESC_FMT = FMT ? 1u : 2u;
+};
 
+template <int FMT>
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-    return (uint32_t)((row >> 3) * TC_SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+    using F = Fmt<FMT>;
+    return (uint32_t)((row >> 3) * F::SBO + (k / F::PER16) * 128 + (row & 7) * 16 + (k % F::PER16) * F::ELEM);
 }
 
-template <int NT>
+template <int NT, int FMT>
 struct TcLayout {
-    static constexpr int A_BYTES = (TC_M / 8) * TC_SBO;
-    static constexpr int B_BYTES = (NT / 8) * TC_SBO;
+    static constexpr int A_BYTES = (TC_M / 8) * Fmt<FMT>::SBO;
+    static constexpr int B_BYTES = (NT / 8) * Fmt<FMT>::SBO;
     static constexpr int A_HI = 0, A_LO = A_BYTES;
     static constexpr int BR_HI = 2 * A_BYTES, BR_LO = BR_HI + B_BYTES;
     static constexpr int BI_HI = BR_LO + B_BYTES, BI_LO = BI_HI + B_BYTES;
@@ -54,19 +69,29 @@ struct TcLayout {
     static constexpr uint32_t NCOLS = (2 * NT <= 32) ? 32 : (2 * NT <= 64) ? 64 : (2 * NT <= 128) ? 128 : 256;
 };
 
+// Store the hi and lo parts of the complex value (x, y) at (row, k2), k2 even.
+template <int FMT>
 __device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int row, int k2, float x, float y) {
-    const float hx = tc::to_tf32(x), hy = tc::to_tf32(y);
-    const float lx = tc::to_tf32(x - hx), ly = tc::to_tf32(y - hy);
-    const uint32_t o = core_off(row, k2);
-    *reinterpret_cast<float2*>(buf + off_hi + o) = make_float2(hx, hy);
-    *reinterpret_cast<float2*>(buf + off_lo + o) = make_float2(lx, ly);
+    const uint32_t o = core_off<FMT>(row, k2);
+    if constexpr (FMT == 0) {
+        const float hx = tc::to_tf32(x), hy = tc::to_tf32(y);
+        const float lx = tc::to_tf32(x - hx), ly = tc::to_tf32(y - hy);
+        *reinterpret_cast<float2*>(buf + off_hi + o) = make_float2(hx, hy);
+        *reinterpret_cast<float2*>(buf + off_lo + o) = make_float2(lx, ly);
+    } else {
+        const __nv_bfloat16 hx = __float2bfloat16_rn(x), hy = __float2bfloat16_rn(y);
+        const __nv_bfloat16 lx = __float2bfloat16_rn(x - __bfloat162float(hx));
+        const __nv_bfloat16 ly = __float2bfloat16_rn(y - __bfloat162float(hy));
+        *reinterpret_cast<__nv_bfloat162*>(buf + off_hi + o) = __halves2bfloat162(hx, hy);
+        *reinterpret_cast<__nv_bfloat162*>(buf + off_lo + o) = __halves2bfloat162(lx, ly);
+    }
 }
 
 // out[m][n] = alpha sum_k conj(A[m][k]) B[n][k] (rows K-contiguous); FP64 atomics into out.
 // Staging: lane -> (row, complex pair kp of the 16-complex chunk); the loads of
 // a chunk go to registers first (load), the TF32 splits to shared memory after
 // (store), so the next chunk's loads overlap the current chunk's products.
-template <int NT>
+template <int NT, int FMT>
 struct StageCN {
     const float2* A; int lda; const float2* B; int ldb; int M, N, K;
     double2* out; int ldo; double alpha;
@@ -92,12 +117,12 @@ struct StageCN {
         }
     }
     __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
-        using L = TcLayout<NT>;
+        using L = TcLayout<NT, FMT>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) put_split(buf, L::A_HI, L::A_LO, row, 4 * kp + 2 * h, r.a[i][h].x, r.a[i][h].y);
+            for (int h = 0; h < 2; ++h) put_split<FMT>(buf, L::A_HI, L::A_LO, row, 4 * kp + 2 * h, r.a[i][h].x, r.a[i][h].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
@@ -105,8 +130,8 @@ struct StageCN {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float2 b = r.b[i][h];
-                put_split(buf, L::BR_HI, L::BR_LO, row, 4 * kp + 2 * h, b.x, b.y);
-                put_split(buf, L::BI_HI, L::BI_LO, row, 4 * kp + 2 * h, b.y, -b.x);
+                put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 4 * kp + 2 * h, b.x, b.y);
+                put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 4 * kp + 2 * h, b.y, -b.x);
             }
         }
     }
@@ -121,7 +146,7 @@ struct StageCN {
 // out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
 // Staging: lane -> (k, row) with consecutive lanes on consecutive rows (the
 // operands are contiguous along M and N).
-template <int NT>
+template <int NT, int FMT>
 struct StageNN {
     const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
     float2* out; int ldo;
@@ -143,18 +168,18 @@ struct StageNN {
         }
     }
     __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
-        using L = TcLayout<NT>;
+        using L = TcLayout<NT, FMT>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             const int e = tid + TC_THREADS * i, kk = e >> 7, row = e & 127;
-            put_split(buf, L::A_HI, L::A_LO, row, 2 * kk, r.a[i].x, r.a[i].y);
+            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * kk, r.a[i].x, r.a[i].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
             const int e = tid + TC_THREADS * i, kk = e / NT, row = e % NT;
             const float2 b = r.b[i];
-            put_split(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, -b.y);
-            put_split(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, b.x);
+            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, -b.y);
+            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, b.x);
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -167,9 +192,9 @@ struct StageNN {
     }
 };
 
-template <int NT, class S>
+template <int NT, int FMT, class S>
 __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, int chunks_per_split) {
-    using L = TcLayout<NT>;
+    using L = TcLayout<NT, FMT>;
     extern __shared__ __align__(1024) char smem[];
     char* stage_buf[2] = {smem, smem + L::STAGE};
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
@@ -188,11 +213,11 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * NT;
     const int c0 = blockIdx.z * chunks_per_split;
     const int c1 = min(nchunks, c0 + chunks_per_split);
-    constexpr uint32_t idesc = tc::instr_desc(2u, TC_M, NT);
+    constexpr uint32_t idesc = tc::instr_desc(Fmt<FMT>::IDESC_FMT, TC_M, NT);
     int ok = 1;
     int it = 0;
     typename S::Regs regs;
-    if (c0 < c1) s.load(regs, m0, n0, c0 * (TC_KC / 2), tid);
+    if (c0 < c1) s.load(regs, m0, n0, c0 * TC_CPS, tid);
     for (int c = c0; c < c1; ++c, ++it) {
         const int sidx = it & 1;
         char* buf = stage_buf[sidx];
@@ -208,9 +233,9 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
         if (tid == 0) {
             tc::tc_fence_after_sync();
             const uint32_t base = tc::smem_addr(buf);
-            constexpr uint32_t LBO = 128, SBO = TC_SBO;
+            constexpr uint32_t LBO = 128, SBO = Fmt<FMT>::SBO;
 #pragma unroll
-            for (int kk = 0; kk < TC_KC / 8; ++kk) {
+            for (int kk = 0; kk < Fmt<FMT>::KSTEPS; ++kk) {
                 const uint32_t off = kk * 256;
                 const uint64_t ahi = tc::smem_desc(base + L::A_HI + off, LBO, SBO);
                 const uint64_t alo = tc::smem_desc(base + L::A_LO + off, LBO, SBO);
@@ -219,16 +244,25 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
                 const uint64_t bih = tc::smem_desc(base + L::BI_HI + off, LBO, SBO);
                 const uint64_t bil = tc::smem_desc(base + L::BI_LO + off, LBO, SBO);
                 const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                tc::mma_tf32(tmem, ahi, brh, idesc, acc);
-                tc::mma_tf32(tmem, ahi, brl, idesc, 1u);
-                tc::mma_tf32(tmem, alo, brh, idesc, 1u);
-                tc::mma_tf32(tmem + NT, ahi, bih, idesc, acc);
-                tc::mma_tf32(tmem + NT, ahi, bil, idesc, 1u);
-                tc::mma_tf32(tmem + NT, alo, bih, idesc, 1u);
+                if constexpr (FMT == 0) {
+                    tc::mma_tf32(tmem, ahi, brh, idesc, acc);
+                    tc::mma_tf32(tmem, ahi, brl, idesc, 1u);
+                    tc::mma_tf32(tmem, alo, brh, idesc, 1u);
+                    tc::mma_tf32(tmem + NT, ahi, bih, idesc, acc);
+                    tc::mma_tf32(tmem + NT, ahi, bil, idesc, 1u);
+                    tc::mma_tf32(tmem + NT, alo, bih, idesc, 1u);
+                } else {
+                    tc::mma_bf16(tmem, ahi, brh, idesc, acc);
+                    tc::mma_bf16(tmem, ahi, brl, idesc, 1u);
+                    tc::mma_bf16(tmem, alo, brh, idesc, 1u);
+                    tc::mma_bf16(tmem + NT, ahi, bih, idesc, acc);
+                    tc::mma_bf16(tmem + NT, ahi, bil, idesc, 1u);
+                    tc::mma_bf16(tmem + NT, alo, bih, idesc, 1u);
+                }
             }
             tc::mma_commit(&mbar[sidx]);
         }
-        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * (TC_KC / 2), tid);  // overlaps the products just issued
+        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * TC_CPS, tid);  // overlaps the products just issued
     }
     const int n = it;
     if (ok && n > 0) {
@@ -256,13 +290,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     if (!ok && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
 }
 
-template <int NT, class S>
+template <int NT, int FMT, class S>
 static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const char* name, cudaStream_t st) {
-    using L = TcLayout<NT>;
-    auto kern = tc_zgemm_kernel<NT, S>;
+    using L = TcLayout<NT, FMT>;
+    auto kern = tc_zgemm_kernel<NT, FMT, S>;
     cudaError_t e = set_smem_attr((const void*)kern, L::SMEM);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
-    const int nchunks = (K + TC_KC / 2 - 1) / (TC_KC / 2);
+    const int nchunks = (K + TC_CPS - 1) / TC_CPS;
     splits = std::max(1, std::min(splits, nchunks));
     const int cps = (nchunks + splits - 1) / splits;
     splits = (nchunks + cps - 1) / cps;
@@ -274,31 +308,44 @@ static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const 
     return check_launch(name);
 }
 
-jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
-                        double alpha, cudaStream_t st) {
-    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
-    const int nchunks = (K + TC_KC / 2 - 1) / (TC_KC / 2);
+template <int FMT>
+static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
+                         double alpha, cudaStream_t st) {
+    const int nchunks = (K + TC_CPS - 1) / TC_CPS;
     if (N <= 32) {
-        StageCN<32> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+        StageCN<32, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
         const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 31) / 32);
         const int splits = std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles);
-        return tc_launch<32>(s, M, N, K, splits, "tc_zgemm_cn", st);
+        return tc_launch<32, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
     }
-    StageCN<128> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+    StageCN<128, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
     const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
     const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
-    return tc_launch<128>(s, M, N, K, splits, "tc_zgemm_cn", st);
+    return tc_launch<128, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
+}
+
+template <int FMT>
+static jdft_status tc_nn(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out, int ldo,
+                         cudaStream_t st) {
+    if (N <= 32) {
+        StageNN<32, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+        return tc_launch<32, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
+    }
+    StageNN<128, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+    return tc_launch<128, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
+}
+
+jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
+                        double alpha, bool bf16, cudaStream_t st) {
+    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    return bf16 ? tc_cn<1>(M, N, K, A, lda, B, ldb, out, ldo, alpha, st)
+                : tc_cn<0>(M, N, K, A, lda, B, ldb, out, ldo, alpha, st);
 }
 
 jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
-                            int ldo, cudaStream_t st) {
+                            int ldo, bool bf16, cudaStream_t st) {
     if (M == 0 || N == 0 || K == 0) return JDFT_OK;
-    if (N <= 32) {
-        StageNN<32> s{A, lda, Bm, ldb, M, N, K, out, ldo};
-        return tc_launch<32>(s, M, N, K, 1, "tc_zgemm_nn", st);
-    }
-    StageNN<128> s{A, lda, Bm, ldb, M, N, K, out, ldo};
-    return tc_launch<128>(s, M, N, K, 1, "tc_zgemm_nn", st);
+    return bf16 ? tc_nn<1>(M, N, K, A, lda, Bm, ldb, out, ldo, st) : tc_nn<0>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
 }
 
 }  // namespace jdft

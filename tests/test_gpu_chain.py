@@ -18,8 +18,10 @@ from tests.systems import GpuSystem, OracleSystem, band_rel_err, workload
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5}
-CTYPE = {"fp64": "complex128", "fp32": "complex64", "tf32x3": "complex64"}
+# bf16x3: x = hi + lo in BF16 represents x to 2^-18 (3.8e-6) and the dropped lo*lo
+# term is of the same size, so a product is good to ~1.1e-5 in the worst case.
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5}
+CTYPE = {"fp64": "complex128", "fp32": "complex64", "tf32x3": "complex64", "bf16x3": "complex64"}
 CASES = ["tiny_cubic", "tiny_ortho", "mid", "small"]
 
 _cache = {}
@@ -104,7 +106,7 @@ def test_operators_I_J_Idag_Jdag_O(name, prec):
     assert band_rel_err(host(out), o.basis.Omega * C) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("name", CASES)
 def test_apply_H(name, prec):
     w, o, g = systems(name)
@@ -151,7 +153,7 @@ def test_density(name, prec):
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("name", CASES)
 def test_subspace(name, prec):
     w, o, g = systems(name)
@@ -168,7 +170,7 @@ def test_subspace(name, prec):
     jdft.jdft_device_status()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_large_sampled_bands(prec):
     """128^3 box, 62 759 plane waves, 256 bands, 256 projectors: the whole block
     runs on the GPU; the oracle checks three sampled bands, the matching

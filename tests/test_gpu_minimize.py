@@ -87,7 +87,7 @@ def test_minimize_tiny_reaches_dense_eigenvalues(precond):
     assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(nb), atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_minimize_small_cell_energy_within_1e6(prec):
     """The 48^3, 16-band system: |E - E_ref| < 1e-6 Ha, eigenvalues to 1e-7."""
     from paper_1708_03621_gb300 import jdft
