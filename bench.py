@@ -82,13 +82,23 @@ def barrier(pg):
         pg.barrier()
 
 
-def max_over_ranks(pg, x: float) -> float:
-    if pg is None:
-        return x
+def _reduce(pg, x: float, op: str) -> float:
     import torch
     t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
-    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(t, op=getattr(pg.ReduceOp, op))
     return float(t.item())
+
+
+def max_over_ranks(pg, x: float) -> float:
+    return x if pg is None else _reduce(pg, x, "MAX")
+
+
+def job_totals(pg, local_time: float, local_units: float) -> tuple[float, float]:
+    """Whole-job totals over the replicas: the slowest rank's time and the
+    units all ranks processed (their sum)."""
+    if pg is None:
+        return local_time, local_units
+    return _reduce(pg, local_time, "MAX"), _reduce(pg, float(local_units), "SUM")
 
 
 # ---------------------------------------------------------------------------
@@ -312,8 +322,7 @@ def run_ours(args, world, rank, local, pg):
     prof = jdft.jdft_profile_read()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(pg, ms)
-    units = p.nb * args.steps * world
+    ms_max, units = job_totals(pg, ms, p.nb * args.steps)
     value = units / (ms_max / 1e3)
 
     # ---- per-kernel roofline from the live events ----
@@ -354,8 +363,8 @@ def run_ours(args, world, rank, local, pg):
         CHC_host.copy_(p.CHC, non_blocking=True)
         COC_host.copy_(p.COC, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
-    e2e = {"value": round(p.nb * e2e_steps * world / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": Bi,
+    e2e_s, e2e_units = job_totals(pg, time.perf_counter() - t0, p.nb * e2e_steps)
+    e2e = {"value": round(e2e_units / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": Bi,
            "d2h_bytes_per_step": Bo}
 
     # ---- the FP64 path on the same workload, for the mixed-vs-FP64 comparison ----
