@@ -1,15 +1,20 @@
-// Blocked FP64 Cholesky factorisation and triangular inverse of a Hermitian
+// Blocked Cholesky factorisation and triangular inverse of a Hermitian
 // positive-definite n x n matrix on many blocks (the overlap U = Y^dag O Y of
 // the band minimiser, JDFTx paper Sec. 2.1 Minimize; W = L^{-dag} makes
-// Y W orthonormal).  FP64 units are scarce on this GPU (about 8 GFLOP/s per
-// SM), so the work is spread over 32 x 32 tiles on separate blocks:
-//   per diagonal block k:  factor L_kk and invert it (one block, shared memory);
-//                          panel L_ik = A_ik L_kk^{-dag} (one block per i > k);
-//                          trailing A_ij -= L_ik L_jk^dag (one block per i >= j > k)
-//   inverse X = L^{-1}, block row by block row:
-//                          S_ik = sum_{j=k}^{i-1} L_ij X_jk (one block per (k, j), FP64 atomics),
-//                          X_ik = -L_ii^{-1} S_ik (one block per k)
+// Y W orthonormal):
+//   per diagonal tile k:  factor L_kk and invert it (one block, shared memory);
+//                         panel L_ik = A_ik X_kk^dag for i > k;
+//                         trailing A_ij -= L_ik L_jk^dag for i >= j > k
+//   inverse X = L^{-1}, tile row by tile row:
+//                         S_ik = sum_{j=k}^{i-1} L_ij X_jk (atomics over j),
+//                         X_ik = -X_ii S_ik
 //   W = X^dag in the caller's block type.
+// Working precision S: FP64 for FP64 blocks; FP32 for the FP32 blocks of the
+// mixed precisions (U itself is accumulated in FP64 by the caller, and an FP32
+// block carries ~1e-7 relative error whatever W is).  FP64 units are scarce on
+// this GPU (about two FP64 FMAs per clock per SM), so the tile products are
+// split into 16 x 16 output quadrants on separate blocks, and the diagonal
+// tile takes one block barrier per column with each reciprocal taken once.
 // The matrix is padded to a multiple of 32 with identity rows.
 #include <algorithm>
 
@@ -19,273 +24,302 @@
 namespace jdft {
 
 constexpr int CB = 32;   // tile edge
+constexpr int CQ = 16;   // quadrant edge of the tile products
 constexpr int CT = 256;  // threads per block
 
 size_t chol_work_elems(int n) {
     const size_t N = (size_t)((n + CB - 1) / CB) * CB;
-    return 3 * N * N;  // L (N x N), X (N x N), S (N x N)
+    return 3 * N * N + N;  // L, X, S (N x N each) and the diagonal of U, in double2 units
 }
 
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// a * conj(b)
-__device__ __forceinline__ double2 zmulc(double2 a, double2 b) {
-    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
+// A pivot below this fraction of the original diagonal means linearly
+// dependent bands (in FP32 the rounding of the elimination alone reaches
+// ~n eps |U_jj|).
+template <typename S> struct PivotFloor;
+template <> struct PivotFloor<double> { static constexpr double v = 1e-13; };
+template <> struct PivotFloor<float> { static constexpr float v = 2e-4f; };
 
-// L = pad(U): lower triangle of U (both triangles copied; only the lower is used), identity on the pad.
-__global__ void chol_init_kernel(int n, int N, const double2* __restrict__ U, double2* __restrict__ L,
-                                 double2* __restrict__ X, int* status) {
+// L = pad(U) (both triangles copied; only the lower is used), identity on the
+// pad; X = S = 0; dg = the diagonal of U.
+template <typename S>
+__global__ void chol_init_kernel(int n, int N, const double2* __restrict__ U, c_t<S>* __restrict__ L,
+                                 c_t<S>* __restrict__ X, c_t<S>* __restrict__ Sa, S* __restrict__ dg,
+                                 int* status) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * N; e += gridDim.x * blockDim.x) {
         const int i = e / N, j = e % N;
-        double2 v = make_double2(0.0, 0.0);
-        if (i < n && j < n) v = U[(size_t)i * n + j];
-        else if (i == j) v = make_double2(1.0, 0.0);
+        c_t<S> v = mk<S>(S(0), S(0));
+        if (i < n && j < n) v = mk<S>((S)U[(size_t)i * n + j].x, (S)U[(size_t)i * n + j].y);
+        else if (i == j) v = mk<S>(S(1), S(0));
         L[e] = v;
-        X[e] = make_double2(0.0, 0.0);
+        X[e] = mk<S>(S(0), S(0));
+        Sa[e] = mk<S>(S(0), S(0));
+        if (i == j) dg[i] = v.x;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
 }
 
-// Factor the diagonal tile k in shared memory and invert it; writes L_kk (lower) and X_kk = L_kk^{-1}.
-// Right-looking: step j takes the pivot, scales column j and updates the
-// trailing tile in parallel; the inverse is built row by row, every column of
-// a row in parallel.
-__global__ void __launch_bounds__(CT) chol_diag_kernel(int n, int N, int k, double2* __restrict__ L,
-                                                       double2* __restrict__ X, const double2* __restrict__ U,
-                                                       int* status) {
-    __shared__ double2 a[CB][CB + 1];
-    __shared__ double2 x[CB][CB + 1];
-    __shared__ double piv;
+// Factor the diagonal tile k in shared memory and invert it; writes L_kk
+// (lower) and X_kk = L_kk^{-1}.  Right-looking: step j subtracts
+// a_ij conj(a_mj) / d_j from the trailing triangle with the unscaled column j
+// (thread (i, m0) owns a_im for m = m0, m0 + 8, ...); the thread that updates
+// a_{j+1,j+1} then takes the next pivot, so one barrier per column.  Columns
+// are scaled by 1/L_jj at the end.  The inverse runs by columns, 8 threads per
+// column summing over interleaved m.
+template <typename S>
+__global__ void __launch_bounds__(CT) chol_diag_kernel(int N, int k, c_t<S>* __restrict__ L, c_t<S>* __restrict__ X,
+                                                       const S* __restrict__ dg, int* status) {
+    using V = c_t<S>;
+    __shared__ V a[CB][CB + 1];
+    __shared__ S rp[CB];   // 1 / L_jj
+    __shared__ S pv[CB];   // L_jj
+    __shared__ S floor_[CB];
     __shared__ int bad;
-    const int r0 = k * CB;
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
+    const int r0 = k * CB, tid = threadIdx.x;
+    for (int e = tid; e < CB * CB; e += CT) {
         const int i = e / CB, j = e % CB;
         a[i][j] = L[(size_t)(r0 + i) * N + r0 + j];
     }
-    if (threadIdx.x == 0) bad = 0;
+    if (tid < CB) floor_[tid] = PivotFloor<S>::v * dg[r0 + tid];
+    if (tid == 0) bad = 0;
     __syncthreads();
-    for (int j = 0; j < CB; ++j) {
-        if (threadIdx.x == 0) {
-            // a pivot that is not positive, or that lost all but ~1e-13 of the
-            // original diagonal, means linearly dependent bands
-            double d = a[j][j].x;
-            const int g = r0 + j;
-            const double ujj = g < n ? U[(size_t)g * n + g].x : 1.0;
-            if (!(d > 1e-13 * ujj)) { bad = 1; d = 1.0; }
-            piv = sqrt(d);
-            a[j][j] = make_double2(piv, 0.0);
-        }
-        __syncthreads();
-        const double ip = 1.0 / piv;
-        for (int i = j + 1 + threadIdx.x; i < CB; i += CT) a[i][j] = make_double2(a[i][j].x * ip, a[i][j].y * ip);
-        __syncthreads();
-        const int w = CB - j - 1;
-        for (int e = threadIdx.x; e < w * w; e += CT) {
-            const int i = j + 1 + e / w, m = j + 1 + e % w;
-            if (m <= i) {
-                const double2 t = zmulc(a[i][j], a[m][j]);
-                a[i][m].x -= t.x;
-                a[i][m].y -= t.y;
+    auto pivot = [&](int j) {
+        S d = a[j][j].x;
+        if (!(d > floor_[j])) { bad = 1; d = S(1); }
+        const S p = sqrt(d);
+        pv[j] = p;
+        rp[j] = S(1) / p;
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    const int i = tid >> 3, m0 = tid & 7;
+    for (int j = 0; j < CB - 1; ++j) {
+        if (i > j) {
+            const S rd = rp[j] * rp[j];
+            const V aij = cscale(a[i][j], rd);
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q) {
+                const int m = m0 + 8 * q;
+                if (m > j && m <= i) a[i][m] = csub(a[i][m], cmulc(aij, a[m][j]));
             }
+            if (i == j + 1 && m0 == ((j + 1) & 7)) pivot(j + 1);
         }
         __syncthreads();
     }
-    // X = L^{-1}: row i, all columns c <= i in parallel
-    for (int i = 0; i < CB; ++i) {
-        for (int c = threadIdx.x; c < CB; c += CT) {
-            double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-            if (c <= i) {
-                for (int m = c; m < i; ++m) {
-                    const double2 t = zmul(a[i][m], x[m][c]);
-                    s.x -= t.x;
-                    s.y -= t.y;
-                }
-                const double d = 1.0 / a[i][i].x;
-                s = make_double2(s.x * d, s.y * d);
-            } else {
-                s = make_double2(0.0, 0.0);
+    for (int e = tid; e < CB * CB; e += CT) {
+        const int r = e / CB, c = e % CB;
+        V v = mk<S>(S(0), S(0));
+        if (r > c) v = cscale(a[r][c], rp[c]);
+        else if (r == c) v = mk<S>(pv[r], S(0));
+        a[r][c] = v;
+        L[(size_t)(r0 + r) * N + r0 + c] = v;
+    }
+    __syncthreads();
+    // X = L^{-1}: column c = tid / 8, thread sub holds X[m][c] for m = sub + 8 q
+    {
+        const int c = tid >> 3, sub = tid & 7;
+        V xr[CB / 8];
+#pragma unroll
+        for (int q = 0; q < CB / 8; ++q) xr[q] = mk<S>(S(0), S(0));
+        const int rstart = (tid >> 5) * 4;  // the warp's smallest column
+        for (int r = rstart; r < CB; ++r) {
+            V s = mk<S>(S(0), S(0));
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q) {
+                const int m = sub + 8 * q;
+                if (m >= c && m < r) s = cadd(s, cmul(a[r][m], xr[q]));
             }
-            x[i][c] = s;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            V xv = mk<S>(S(0), S(0));
+            if (r >= c) xv = cscale(mk<S>((r == c ? S(1) : S(0)) - s.x, -s.y), rp[r]);
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q)
+                if (r == sub + 8 * q) xr[q] = xv;
         }
-        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < CB / 8; ++q) X[(size_t)(r0 + sub + 8 * q) * N + r0 + c] = xr[q];
     }
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
-        const int i = e / CB, j = e % CB;
-        L[(size_t)(r0 + i) * N + r0 + j] = j <= i ? a[i][j] : make_double2(0.0, 0.0);
-        X[(size_t)(r0 + i) * N + r0 + j] = x[i][j];
-    }
-    if (threadIdx.x == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
+    if (tid == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
 }
 
-// Panel: L_ik = A_ik X_kk^dag for tile rows i > k (blockIdx.x = i - k - 1).
-__global__ void __launch_bounds__(CT) chol_panel_kernel(int N, int k, double2* __restrict__ L,
-                                                        const double2* __restrict__ X) {
-    __shared__ double2 a[CB][CB + 1];
-    __shared__ double2 xi[CB][CB + 1];
-    const int i = k + 1 + blockIdx.x;
-    const int ri = i * CB, rk = k * CB;
+// Panel: L_ik = A_ik X_kk^dag for tile rows i > k (blockIdx.x = i - k - 1),
+// rows [16 h, 16 h + 16) of the tile for blockIdx.y = h (a block overwrites
+// only the rows it read).
+template <typename S>
+__global__ void __launch_bounds__(CT) chol_panel_kernel(int N, int k, c_t<S>* __restrict__ L,
+                                                        const c_t<S>* __restrict__ X) {
+    using V = c_t<S>;
+    __shared__ V a[CQ][CB + 1];
+    __shared__ V xk[CB][CB + 1];
+    const int i = k + 1 + blockIdx.x, h = blockIdx.y;
+    const int ri = i * CB + h * CQ, rk = k * CB;
     for (int e = threadIdx.x; e < CB * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        a[r][c] = L[(size_t)(ri + r) * N + rk + c];
-        xi[r][c] = X[(size_t)(rk + r) * N + rk + c];
+        if (r < CQ) a[r][c] = L[(size_t)(ri + r) * N + rk + c];
+        xk[r][c] = X[(size_t)(rk + r) * N + rk + c];
     }
     __syncthreads();
-    // out[r][c] = sum_m a[r][m] conj(xi[c][m])
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
+    // out[r][c] = sum_{m <= c} a[r][m] conj(xk[c][m])  (xk lower triangular)
+    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        double2 s = make_double2(0.0, 0.0);
-        for (int m = 0; m <= c; ++m) {  // xi is lower triangular
-            const double2 t = zmulc(a[r][m], xi[c][m]);
-            s.x += t.x;
-            s.y += t.y;
-        }
+        V s = mk<S>(S(0), S(0));
+        for (int m = 0; m <= c; ++m) s = cadd(s, cmulc(a[r][m], xk[c][m]));
         L[(size_t)(ri + r) * N + rk + c] = s;
     }
 }
 
-// Trailing update: A_ij -= L_ik L_jk^dag for i >= j > k; blockIdx.x enumerates the pairs.
-__global__ void __launch_bounds__(CT) chol_update_kernel(int N, int k, double2* __restrict__ L) {
-    __shared__ double2 li[CB][CB + 1];
-    __shared__ double2 lj[CB][CB + 1];
-    // decode the lower-triangular pair index p -> (i, j), k < j <= i
-    const int p = blockIdx.x;
-    int ii = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+// Quadrant (qr, qc) = (blockIdx.y >> 1, blockIdx.y & 1) of a tile product;
+// thread (r, c) = (tid / 16, tid % 16) within the quadrant.
+struct Quad {
+    int qr, qc, r, c;
+    __device__ Quad()
+        : qr((int)(blockIdx.y >> 1) * CQ), qc((int)(blockIdx.y & 1) * CQ), r((int)threadIdx.x >> 4),
+          c((int)threadIdx.x & 15) {}
+};
+
+// Lower-triangular pair index p -> (i, j), 0 <= j <= i.
+__device__ __forceinline__ void tri_pair(int p, int& i, int& j) {
+    int ii = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
     while ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
     while (ii * (ii + 1) / 2 > p) --ii;
-    const int jj = p - ii * (ii + 1) / 2;
-    const int i = k + 1 + ii, j = k + 1 + jj;
-    const int rk = k * CB;
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
-        const int r = e / CB, c = e % CB;
-        li[r][c] = L[(size_t)(i * CB + r) * N + rk + c];
-        lj[r][c] = L[(size_t)(j * CB + r) * N + rk + c];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
-        const int r = e / CB, c = e % CB;
-        double2 s = make_double2(0.0, 0.0);
-        for (int m = 0; m < CB; ++m) {
-            const double2 t = zmulc(li[r][m], lj[c][m]);
-            s.x += t.x;
-            s.y += t.y;
-        }
-        double2* dst = &L[(size_t)(i * CB + r) * N + j * CB + c];
-        dst->x -= s.x;
-        dst->y -= s.y;
-    }
+    i = ii;
+    j = p - ii * (ii + 1) / 2;
 }
 
-// Inverse, block row i: S_ik += L_ij X_jk for every k <= j < i (blockIdx.x enumerates the (k, j) pairs).
-__global__ void __launch_bounds__(CT) inv_accum_kernel(int N, int i, const double2* __restrict__ L,
-                                                       const double2* __restrict__ X, double2* __restrict__ S) {
-    __shared__ double2 l[CB][CB + 1];
-    __shared__ double2 x[CB][CB + 1];
-    const int p = blockIdx.x;  // pairs (k, j), 0 <= k <= j < i, enumerated by j then k
-    int j = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
-    while ((j + 1) * (j + 2) / 2 <= p) ++j;
-    while (j * (j + 1) / 2 > p) --j;
-    const int k = p - j * (j + 1) / 2;
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
+// Trailing update: A_ij -= L_ik L_jk^dag for i >= j > k; blockIdx.x enumerates the pairs.
+template <typename S>
+__global__ void __launch_bounds__(CT) chol_update_kernel(int N, int k, c_t<S>* __restrict__ L) {
+    using V = c_t<S>;
+    __shared__ V li[CQ][CB + 1];
+    __shared__ V lj[CQ][CB + 1];
+    int ii, jj;
+    tri_pair(blockIdx.x, ii, jj);
+    const int i = k + 1 + ii, j = k + 1 + jj;
+    const Quad q;
+    const int rk = k * CB;
+    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        l[r][c] = L[(size_t)(i * CB + r) * N + j * CB + c];
-        x[r][c] = X[(size_t)(j * CB + r) * N + k * CB + c];
+        li[r][c] = L[(size_t)(i * CB + q.qr + r) * N + rk + c];
+        lj[r][c] = L[(size_t)(j * CB + q.qc + r) * N + rk + c];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
+    V s = mk<S>(S(0), S(0));
+#pragma unroll 8
+    for (int m = 0; m < CB; ++m) s = cadd(s, cmulc(li[q.r][m], lj[q.c][m]));
+    V* dst = &L[(size_t)(i * CB + q.qr + q.r) * N + j * CB + q.qc + q.c];
+    *dst = csub(*dst, s);
+}
+
+// Inverse, tile row i: S_ik += L_ij X_jk for every k <= j < i (blockIdx.x enumerates the (j, k) pairs).
+template <typename S>
+__global__ void __launch_bounds__(CT) inv_accum_kernel(int N, int i, const c_t<S>* __restrict__ L,
+                                                       const c_t<S>* __restrict__ X, c_t<S>* __restrict__ Sa) {
+    using V = c_t<S>;
+    __shared__ V l[CQ][CB + 1];
+    __shared__ V x[CB][CQ + 1];
+    int j, k;
+    tri_pair(blockIdx.x, j, k);
+    const Quad q;
+    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        double2 s = make_double2(0.0, 0.0);
-        for (int m = 0; m < CB; ++m) {
-            const double2 t = zmul(l[r][m], x[m][c]);
-            s.x += t.x;
-            s.y += t.y;
-        }
-        double2* dst = &S[(size_t)(i * CB + r) * N + k * CB + c];
-        atomicAdd(&dst->x, s.x);
-        atomicAdd(&dst->y, s.y);
+        l[r][c] = L[(size_t)(i * CB + q.qr + r) * N + j * CB + c];
+        const int r2 = e / CQ, c2 = e % CQ;
+        x[r2][c2] = X[(size_t)(j * CB + r2) * N + k * CB + q.qc + c2];
     }
+    __syncthreads();
+    V s = mk<S>(S(0), S(0));
+#pragma unroll 8
+    for (int m = 0; m < CB; ++m) s = cadd(s, cmul(l[q.r][m], x[m][q.c]));
+    V* dst = &Sa[(size_t)(i * CB + q.qr + q.r) * N + k * CB + q.qc + q.c];
+    atomicAdd(&dst->x, s.x);
+    atomicAdd(&dst->y, s.y);
 }
 
 // X_ik = -X_ii S_ik for every k < i (blockIdx.x = k).
-__global__ void __launch_bounds__(CT) inv_finish_kernel(int N, int i, double2* __restrict__ X,
-                                                        const double2* __restrict__ S) {
-    __shared__ double2 d[CB][CB + 1];
-    __shared__ double2 s_[CB][CB + 1];
+template <typename S>
+__global__ void __launch_bounds__(CT) inv_finish_kernel(int N, int i, c_t<S>* __restrict__ X,
+                                                        const c_t<S>* __restrict__ Sa) {
+    using V = c_t<S>;
+    __shared__ V d[CQ][CB + 1];
+    __shared__ V s_[CB][CQ + 1];
     const int k = blockIdx.x;
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
+    const Quad q;
+    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        d[r][c] = X[(size_t)(i * CB + r) * N + i * CB + c];
-        s_[r][c] = S[(size_t)(i * CB + r) * N + k * CB + c];
+        d[r][c] = X[(size_t)(i * CB + q.qr + r) * N + i * CB + c];
+        const int r2 = e / CQ, c2 = e % CQ;
+        s_[r2][c2] = Sa[(size_t)(i * CB + r2) * N + k * CB + q.qc + c2];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < CB * CB; e += CT) {
-        const int r = e / CB, c = e % CB;
-        double2 s = make_double2(0.0, 0.0);
-        for (int m = 0; m <= r; ++m) {  // d lower triangular
-            const double2 t = zmul(d[r][m], s_[m][c]);
-            s.x += t.x;
-            s.y += t.y;
-        }
-        X[(size_t)(i * CB + r) * N + k * CB + c] = make_double2(-s.x, -s.y);
-    }
+    V s = mk<S>(S(0), S(0));
+    const int rr = q.qr + q.r;  // row within the tile; X_ii is lower triangular
+    for (int m = 0; m <= rr; ++m) s = cadd(s, cmul(d[q.r][m], s_[m][q.c]));
+    X[(size_t)(i * CB + rr) * N + k * CB + q.qc + q.c] = mk<S>(-s.x, -s.y);
 }
 
-template <typename T>
-__global__ void chol_out_kernel(int n, int N, const double2* __restrict__ X, c_t<T>* __restrict__ W) {
+template <typename S>
+__global__ void chol_out_kernel(int n, int N, const c_t<S>* __restrict__ X, c_t<S>* __restrict__ W) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
         const int r = e / n, c = e % n;
-        const double2 x = X[(size_t)c * N + r];  // W = X^dag
-        W[e] = mk<T>((T)x.x, (T)(-x.y));
+        const c_t<S> x = X[(size_t)c * N + r];  // W = X^dag
+        W[e] = mk<S>(x.x, -x.y);
     }
 }
 
-jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
-                                  cudaStream_t st) {
+template <typename S>
+static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W, int* status, cudaStream_t st) {
     const int nb = (n + CB - 1) / CB;
     const int N = nb * CB;
-    double2* L = work;
-    double2* X = L + (size_t)N * N;
-    double2* S = X + (size_t)N * N;
+    c_t<S>* L = reinterpret_cast<c_t<S>*>(work);
+    c_t<S>* X = L + (size_t)N * N;
+    c_t<S>* Sa = X + (size_t)N * N;
+    S* dg = reinterpret_cast<S*>(Sa + (size_t)N * N);
     const int g = (int)std::min<int64_t>(((int64_t)N * N + 255) / 256, 152 * 4);
     {
         Trace tr_("chol_init", st);
-        chol_init_kernel<<<g, 256, 0, st>>>(n, N, U, L, X, status);
+        chol_init_kernel<S><<<g, 256, 0, st>>>(n, N, U, L, X, Sa, dg, status);
     }
-    JDFT_CUDA_TRY(cudaMemsetAsync(S, 0, (size_t)N * N * sizeof(double2), st));
     for (int k = 0; k < nb; ++k) {
         {
             Trace tr_("chol_diag", st);
-            chol_diag_kernel<<<1, CT, 0, st>>>(n, N, k, L, X, U, status);
+            chol_diag_kernel<S><<<1, CT, 0, st>>>(N, k, L, X, dg, status);
         }
         const int m = nb - k - 1;
         if (m > 0) {
             {
                 Trace tr_("chol_panel", st);
-                chol_panel_kernel<<<m, CT, 0, st>>>(N, k, L, X);
+                chol_panel_kernel<S><<<dim3(m, CB / CQ), CT, 0, st>>>(N, k, L, X);
             }
             {
                 Trace tr_("chol_update", st);
-                chol_update_kernel<<<m * (m + 1) / 2, CT, 0, st>>>(N, k, L);
+                chol_update_kernel<S><<<dim3(m * (m + 1) / 2, 4), CT, 0, st>>>(N, k, L);
             }
         }
     }
     for (int i = 1; i < nb; ++i) {
         {
             Trace tr_("chol_inv_accum", st);
-            inv_accum_kernel<<<i * (i + 1) / 2, CT, 0, st>>>(N, i, L, X, S);
+            inv_accum_kernel<S><<<dim3(i * (i + 1) / 2, 4), CT, 0, st>>>(N, i, L, X, Sa);
         }
         {
             Trace tr_("chol_inv_finish", st);
-            inv_finish_kernel<<<i, CT, 0, st>>>(N, i, X, S);
+            inv_finish_kernel<S><<<dim3(i, 4), CT, 0, st>>>(N, i, X, Sa);
         }
     }
     {
         Trace tr_("chol_out", st);
-        if (fp64) chol_out_kernel<double><<<g, 256, 0, st>>>(n, N, X, (double2*)W);
-        else chol_out_kernel<float><<<g, 256, 0, st>>>(n, N, X, (float2*)W);
+        chol_out_kernel<S><<<g, 256, 0, st>>>(n, N, X, W);
     }
     return check_launch("blocked_cholesky_winv");
+}
+
+jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
+                                  cudaStream_t st) {
+    if (fp64) return run_blocked<double>(n, U, work, (double2*)W, status, st);
+    return run_blocked<float>(n, U, work, (float2*)W, status, st);
 }
 
 }  // namespace jdft

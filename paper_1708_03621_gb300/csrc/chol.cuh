@@ -1,4 +1,4 @@
-// Blocked FP64 Cholesky + triangular inverse on many blocks (see chol.cu).
+// Blocked Cholesky + triangular inverse on many blocks (see chol.cu).
 #pragma once
 
 #include "common.cuh"
@@ -9,8 +9,10 @@ namespace jdft {
 size_t chol_work_elems(int n);
 
 // U (n x n complex128 row-major, Hermitian positive definite) = L L^dag;
-// W (n x n row-major, complex128 if fp64 else complex64) = L^{-dag}.
-// *status receives JDFT_ERR_NOT_POSDEF on a non-positive pivot (device word).
+// W (n x n row-major, complex128 if fp64 else complex64) = L^{-dag}, factored
+// in FP64 when fp64, else in FP32 (from the FP64 U).
+// *status receives JDFT_ERR_NOT_POSDEF on a pivot below 1e-13 (FP64) or 2e-4
+// (FP32) of the original diagonal (device word).
 jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
                                   cudaStream_t st);
 

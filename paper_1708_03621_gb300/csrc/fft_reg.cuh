@@ -98,6 +98,20 @@ struct LineShape {
     static_assert(N % E == 0 && 32 % (N / E) == 0, "lanes per line must divide the warp");
 };
 
+// Twiddles w[r] = W[r b], r = 1 .. R-1 (r b < N): the table is read at the
+// powers of two r = 1, 2, 4, 8 and the other w[r] are products
+// w[r] = w[r - lowbit(r)] w[lowbit(r)] (at most three roundings), which moves
+// work from the shared-memory pipe to the FMA pipe.
+template <typename T, int R>
+__device__ __forceinline__ void stage_twiddles(c_t<T>* w, int b, const c_t<T>* __restrict__ W) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const int low = r & (-r);
+        if (low == r) w[r] = W[r * b];
+        else w[r] = cmul(w[r - low], w[low]);
+    }
+}
+
 // One stage: v holds the inputs of this lane's butterflies, v[u*R + r].
 template <typename T, int N, int TL, int E, int SIGN, int NS, int R>
 __device__ __forceinline__ void stage_compute(c_t<T>* v, int t, const c_t<T>* __restrict__ W) {
@@ -107,13 +121,34 @@ __device__ __forceinline__ void stage_compute(c_t<T>* v, int t, const c_t<T>* __
         const int j = t + TL * u;
         const int k = j % NS;
         if (NS > 1 && k != 0) {
+            c_t<T> w[R];
+            stage_twiddles<T, R>(w, k * (N / (NS * R)), W);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const c_t<T> w = W[(r * k * (N / (NS * R))) % N];
-                v[u * R + r] = SIGN > 0 ? cmul(v[u * R + r], w) : cmulc(v[u * R + r], w);
-            }
+            for (int r = 1; r < R; ++r) v[u * R + r] = SIGN > 0 ? cmul(v[u * R + r], w[r]) : cmulc(v[u * R + r], w[r]);
         }
         dft_r<T, SIGN, R>(v + u * R);
+    }
+}
+
+// Adjoint of the stage (NS, R) of the transform with sign -SIGN2: the R-point
+// DFT with sign SIGN2 on this lane's butterfly outputs v[u*R + r], then the
+// conjugate twiddles.  On return v[u*R + r] holds the stage's input position
+// j + r N/R (j = t + TL u).
+template <typename T, int N, int TL, int E, int SIGN2, int NS, int R>
+__device__ __forceinline__ void stage_adjoint(c_t<T>* v, int t, const c_t<T>* __restrict__ W) {
+    constexpr int NB = E / R;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        dft_r<T, SIGN2, R>(v + u * R);
+        const int j = t + TL * u;
+        const int k = j % NS;
+        if (NS > 1 && k != 0) {
+            c_t<T> w[R];
+            stage_twiddles<T, R>(w, k * (N / (NS * R)), W);
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                v[u * R + r] = SIGN2 > 0 ? cmul(v[u * R + r], w[r]) : cmulc(v[u * R + r], w[r]);
+        }
     }
 }
 
@@ -152,6 +187,36 @@ struct StageRunner {
     }
 };
 
+template <int R, int... Rest>
+struct FirstRadix {
+    static constexpr int value = R;
+};
+
+// The transform with sign SIGN2 as the adjoint of the sign -SIGN2 flow graph
+// (stages (NS, R), (NS R, Rest...)): the later stages first, then an exchange
+// from their input positions to this stage's output grouping, then this
+// stage's adjoint.
+template <typename T, int N, int TL, int E, int SIGN2, int NS, int R, int... Rest>
+struct AdjRunner {
+    static __device__ __forceinline__ void run(c_t<T>* v, int t, c_t<T>* scr, const c_t<T>* __restrict__ W) {
+        if constexpr (sizeof...(Rest) > 0) {
+            AdjRunner<T, N, TL, E, SIGN2, NS * R, Rest...>::run(v, t, scr, W);
+            constexpr int Rn = FirstRadix<Rest...>::value;
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < E / Rn; ++u)
+#pragma unroll
+                for (int r = 0; r < Rn; ++r) scr[padx(t + TL * u + r * (N / Rn))] = v[u * Rn + r];
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < E / R; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[u * R + r] = scr[padx(stage_out_index<TL, NS, R>(t, u, r))];
+        }
+        stage_adjoint<T, N, TL, E, SIGN2, NS, R>(v, t, W);
+    }
+};
+
 // Input index of value v[u*R + r] of the first stage with radix R.
 template <int N, int TL, int R>
 __device__ __forceinline__ int first_in_index(int t, int u, int r) {
@@ -178,6 +243,11 @@ struct LineFFT<T, N, E, SIGN, Rad<R0, R...>> {
     // v[u*R0 + r] must hold input first_in(t, u, r); on return v[e] holds output out(t, e).
     static __device__ __forceinline__ void run(c_t<T>* v, int t, c_t<T>* scr, const c_t<T>* __restrict__ W) {
         StageRunner<T, N, TL, E, SIGN, 1, R0, R...>::run(v, t, scr, W);
+    }
+    // The transform of sign -SIGN from the layout run() leaves: v[e] must hold
+    // input out(t, e); on return v[e] holds output in(t, e).
+    static __device__ __forceinline__ void run_adjoint(c_t<T>* v, int t, c_t<T>* scr, const c_t<T>* __restrict__ W) {
+        AdjRunner<T, N, TL, E, -SIGN, 1, R0, R...>::run(v, t, scr, W);
     }
     static __device__ __forceinline__ int in_index(int t, int e) {
         return first_in_index<N, TL, R0>(t, e / R0, e % R0);

@@ -42,14 +42,14 @@ __host__ __device__ constexpr int warp_scratch() {
 }
 
 // Phase 1 / 3 helpers -------------------------------------------------------
-template <typename T, int N1, int E1, class R1>
+template <typename T, int N1, int E1, class R1, int NW = kFastWarps>
 __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<T>* __restrict__ plane, c_t<T>* A,
                                                   int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
     using F = LineFFT<T, N1, E1, +1, R1>;
     constexpr int TL = N1 / E1, LPW = 32 / TL;
     const int liw = lane / TL, t = lane % TL;
     c_t<T>* scr = wscr + liw * padded_line(N1);
-    for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
+    for (int base = warp * LPW; base < g.nrows; base += NW * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
         int cs = 0, cnt = 0, lo = 0;
@@ -72,14 +72,14 @@ __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<
     }
 }
 
-template <typename T, int N1, int E1, class R1>
+template <typename T, int N1, int E1, class R1, int NW = kFastWarps>
 __device__ __forceinline__ void rows_forward_fast(const ChainGeom& g, c_t<T>* __restrict__ plane, const c_t<T>* A,
                                                   int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
     using F = LineFFT<T, N1, E1, -1, R1>;
     constexpr int TL = N1 / E1, LPW = 32 / TL;
     const int liw = lane / TL, t = lane % TL;
     c_t<T>* scr = wscr + liw * padded_line(N1);
-    for (int base = warp * LPW; base < g.nrows; base += kFastWarps * LPW) {
+    for (int base = warp * LPW; base < g.nrows; base += NW * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
         c_t<T> v[E1];
@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
 
     {
         using FI = LineFFT<T, N0, E0, +1, R0>;
-        using FF = LineFFT<T, N0, E0, -1, R0>;
         constexpr int TL = N0 / E0, LPW = 32 / TL;
         const int liw = lane / TL, t = lane % TL;
         c_t<T>* scr = wscr + liw * padded_line(N0);
@@ -148,20 +147,15 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
             c_t<T> v[E0];
             column_inverse_fast<T, N0, E0, R0>(g, A, lsA, j1, act, v, t, scr, W0);
             const T* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
-            __syncwarp();
 #pragma unroll
-            for (int e = 0; e < E0; ++e) {
-                const int j0 = FI::out_index(t, e);
-                scr[padx(j0)] = act ? cscale(v[e], Vq[j0]) : mk<T>(T(0), T(0));
-            }
-            __syncwarp();
-#pragma unroll
-            for (int e = 0; e < E0; ++e) v[e] = scr[padx(FF::in_index(t, e))];
-            FF::run(v, t, scr, W0);
+            for (int e = 0; e < E0; ++e) v[e] = act ? cscale(v[e], Vq[FI::out_index(t, e)]) : mk<T>(T(0), T(0));
+            // forward transform as the adjoint of the inverse: starts from the
+            // layout the inverse left, ends in the layout it started from
+            FI::run_adjoint(v, t, scr, W0);
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E0; ++e) {
-                    const int r = wrapf(FF::out_index(t, e) - g.i0min, N0);
+                    const int r = wrapf(FI::in_index(t, e) - g.i0min, N0);
                     if (r < g.nrows) A[r * lsA + j1] = v[e];
                 }
             }
@@ -174,8 +168,8 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
 
 // Density, FP32 blocks: block (j2, band group) accumulates f_b |psi_b|^2 in
 // registers (each lane always owns the same (j0, j1) points) over its bands.
-template <int N0, int E0, class R0, int N1, int E1, class R1>
-__global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainGeom g,
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW>
+__global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g,
                                                                           const float2* __restrict__ colbuf, int nb,
                                                                           int bands_per_block,
                                                                           const double* __restrict__ f, double w,
@@ -186,11 +180,11 @@ __global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainG
     constexpr int lsA = N1 + 1;
     constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
     constexpr int TL = N0 / E0, LPW = 32 / TL;
-    constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+    constexpr int ROUNDS = (N1 + NW * LPW - 1) / (NW * LPW);
     float2* W0 = reinterpret_cast<float2*>(smem_raw);
     float2* W1 = W0 + N0;
     float2* scr_all = W1 + N1;
-    float2* A = scr_all + kFastWarps * SCR;
+    float2* A = scr_all + NW * SCR;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* wscr = scr_all + warp * SCR;
     for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = tw0[i];
@@ -206,11 +200,12 @@ __global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainG
         for (int e = 0; e < E0; ++e) acc[k][e] = 0.f;
     for (int b = bA; b < bB; ++b) {
         const float fb = (float)f[b];
-        rows_inverse_fast<float, N1, E1, R1>(g, colbuf + colbuf_index(g, b, j2, 0), A, lsA, wscr, W1, warp, lane);
+        rows_inverse_fast<float, N1, E1, R1, NW>(g, colbuf + colbuf_index(g, b, j2, 0), A, lsA, wscr, W1, warp,
+                                                 lane);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < ROUNDS; ++k) {
-            const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+            const int j1 = warp * LPW + liw + k * NW * LPW;
             float2 v[E0];
             column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t, wscr + liw * padded_line(N0), W0);
 #pragma unroll
@@ -222,7 +217,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_density_fast_kernel(ChainG
     const bool atomic = gridDim.y > 1;
 #pragma unroll
     for (int k = 0; k < ROUNDS; ++k) {
-        const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+        const int j1 = warp * LPW + liw + k * NW * LPW;
         if (j1 >= N1) continue;
 #pragma unroll
         for (int e = 0; e < E0; ++e) {
@@ -249,10 +244,18 @@ template <> struct FastCfg<256> { static constexpr int E = 16; using R = Rad<16,
 constexpr size_t kFastMaxSmem = 220 * 1024;
 
 template <int N0, int N1>
-static size_t fast_smem(const ChainGeom& g, size_t elem) {
+static size_t fast_smem(const ChainGeom& g, size_t elem, int nw = kFastWarps) {
     constexpr int E0 = FastCfg<N0>::E, E1 = FastCfg<N1>::E;
-    return ((size_t)N0 + N1 + (size_t)kFastWarps * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * (N1 + 1)) * elem;
+    return ((size_t)N0 + N1 + (size_t)nw * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * (N1 + 1)) * elem;
 }
+
+// Warps of a density block: enough that the per-lane accumulators of the
+// plane (N0 N1 / (32 warps) values) stay at 32 or fewer where the shared
+// memory allows (16 warps for 128 x 128), else the 8 of the apply kernel.
+template <int N0, int N1>
+struct DensityWarps {
+    static constexpr int value = (N0 * N1 > 8192 && N0 <= 128) ? 16 : kFastWarps;
+};
 
 static bool fast_disabled() {
     const char* e = getenv("JDFT_FAST_PLANE");
@@ -282,9 +285,10 @@ static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, c
                                      int nb, const float2* tw_base, cudaStream_t st) {
     using C0 = FastCfg<N0>;
     using C1 = FastCfg<N1>;
-    const size_t smem = fast_smem<N0, N1>(g, sizeof(float2));
+    constexpr int NW = DensityWarps<N0, N1>::value;
+    const size_t smem = fast_smem<N0, N1>(g, sizeof(float2), NW);
     if (smem > kFastMaxSmem) return JDFT_ERR_UNSUPPORTED;
-    auto kern = plane_density_fast_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R>;
+    auto kern = plane_density_fast_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, NW>;
     cudaError_t e = set_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess)
         return set_error(JDFT_ERR_CUDA, std::string("plane_density_fast: ") + cudaGetErrorString(e));
@@ -294,8 +298,8 @@ static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, c
     groups = (nb + per - 1) / per;
     {
         Trace tr_("plane_density_fast", st);
-        kern<<<dim3(g.S2, groups), kFastThreads, smem, st>>>(g, colbuf, nb, per, f, w, n_r, tw_base + g.p0.tw_offset,
-                                                             tw_base + g.p1.tw_offset);
+        kern<<<dim3(g.S2, groups), 32 * NW, smem, st>>>(g, colbuf, nb, per, f, w, n_r, tw_base + g.p0.tw_offset,
+                                                        tw_base + g.p1.tw_offset);
     }
     return check_launch("plane_density_fast");
 }

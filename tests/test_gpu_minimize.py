@@ -43,10 +43,11 @@ def test_subspace_eigs_match_lapack():
         assert np.max(np.abs(e.cpu().numpy() - ref)) < 1e-11 * max(1.0, np.max(np.abs(ref)))
 
 
-@pytest.mark.parametrize("nb", [13, 70])
+@pytest.mark.parametrize("nb", [13, 70, 150])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_orthonormalize_spans_same_subspace(prec, nb):
-    """13 bands: one-block factorisation; 70: the blocked multi-block one (padded to 96)."""
+    """13 bands: one-block factorisation; 70 and 150: the blocked multi-block
+    one (padded to 3 and 5 tiles; FP32 factorisation for the FP32 blocks)."""
     from paper_1708_03621_gb300 import jdft
     w, o, g = systems("mid")
     C = o.coeffs(nb, seed=31)
@@ -61,14 +62,16 @@ def test_orthonormalize_spans_same_subspace(prec, nb):
     assert np.max(np.abs(P1 - P2)) < tol * np.max(np.abs(P2))
 
 
-@pytest.mark.parametrize("name,nb", [("tiny_cubic", 3), ("mid", 40)])
-def test_orthonormalize_rejects_dependent_bands(name, nb):
+@pytest.mark.parametrize("name,nb,prec", [("tiny_cubic", 3, "fp64"), ("mid", 40, "fp64"), ("mid", 40, "fp32"),
+                                          ("mid", 100, "tf32x3")])
+def test_orthonormalize_rejects_dependent_bands(name, nb, prec):
     from paper_1708_03621_gb300 import jdft
     w, o, g = systems(name)
     C = o.coeffs(nb)
     C[nb - 1] = C[0]
+    Cd = torch.tensor(C.astype(np.complex128 if prec == "fp64" else np.complex64), device="cuda")
     with pytest.raises(jdft.JdftError, match="NOT_POSDEF"):
-        jdft.jdft_orthonormalize(g.basis, 0, torch.tensor(C, device="cuda"))
+        jdft.jdft_orthonormalize(g.basis, 0, Cd, prec)
 
 
 @pytest.mark.parametrize("precond", ["teter", "identity"])
