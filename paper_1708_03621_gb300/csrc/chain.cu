@@ -340,6 +340,11 @@ static size_t plane_bytes(const ChainGeom& g, const PlaneSmem& sm, size_t elem) 
 template <typename T>
 jdft_status launch_zpass_inverse(const ChainGeom& g, const c_t<T>* C, int ldc, c_t<T>* colbuf, int nb,
                                  const c_t<T>* tw_base, cudaStream_t st) {
+    {
+        // register-FFT kernel for the lengths it is compiled for, else the generic one
+        const jdft_status fs = launch_zpass_inverse_fast<T>(g, C, ldc, colbuf, nb, tw_base + g.p2.tw_offset, st);
+        if (fs != JDFT_ERR_UNSUPPORTED) return fs;
+    }
     const int cpb = zpass_cpb(g.S2, sizeof(c_t<T>));
     const size_t smem = 2 * (size_t)cpb * (g.S2 + 1) * sizeof(c_t<T>);
     jdft_status s = prepare(zpass_inverse_kernel<T>, smem, "zpass_inverse");
@@ -356,6 +361,11 @@ template <typename T, int MODE>
 jdft_status launch_zpass_forward(const ChainGeom& g, const c_t<T>* colbuf, const c_t<T>* C, int ldc, c_t<T>* out,
                                  int ldo, int nb, const T* kin, T omega, T scale, const c_t<T>* tw_base,
                                  cudaStream_t st) {
+    {
+        const jdft_status fs = launch_zpass_forward_fast<T, MODE>(g, colbuf, C, ldc, out, ldo, nb, kin, omega, scale,
+                                                                  tw_base + g.p2.tw_offset, st);
+        if (fs != JDFT_ERR_UNSUPPORTED) return fs;
+    }
     const int cpb = zpass_cpb(g.S2, sizeof(c_t<T>));
     const size_t smem = 2 * (size_t)cpb * (g.S2 + 1) * sizeof(c_t<T>);
     jdft_status s = prepare(zpass_forward_kernel<T, MODE>, smem, "zpass_forward");

@@ -63,6 +63,16 @@ jdft_status launch_plane_apply_fast(const ChainGeom& g, c_t<T>* colbuf, const T*
                                     cudaStream_t st);
 jdft_status launch_plane_density_fast(const ChainGeom& g, const float2* colbuf, const double* f, double w,
                                       double* n_r, int nb, const float2* tw_base, cudaStream_t st);
+// Register-FFT z passes for the lengths S2 they are compiled for (same
+// contract as launch_zpass_*, tw2 = the length-S2 twiddle table); they return
+// JDFT_ERR_UNSUPPORTED (without launching) for other lengths.
+template <typename T>
+jdft_status launch_zpass_inverse_fast(const ChainGeom& g, const c_t<T>* C, int ldc, c_t<T>* colbuf, int nb,
+                                      const c_t<T>* tw2, cudaStream_t st);
+template <typename T, int MODE>
+jdft_status launch_zpass_forward_fast(const ChainGeom& g, const c_t<T>* colbuf, const c_t<T>* C, int ldc, c_t<T>* out,
+                                      int ldo, int nb, const T* kin, T omega, T scale, const c_t<T>* tw2,
+                                      cudaStream_t st);
 
 template <typename T>
 jdft_status launch_plane_density(const ChainGeom& g, const c_t<T>* colbuf, const double* f, double w, double* n_r,

@@ -230,6 +230,95 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
     }
 }
 
+// z passes with register line FFTs: TL lanes per (i0, i1) column of the
+// sphere, LPW columns per warp, 8 warps per block, one band per blockIdx.y.
+// A column's plane waves have consecutive z-slots from pw_z of its first one
+// (modulo S2), so a slot p holds sphere entry (p - z0) mod S2 when that is
+// below the column's count.
+template <typename T, int N2, int E2, class R2>
+__global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainGeom g, const c_t<T>* __restrict__ C,
+                                                                          int ldc, c_t<T>* __restrict__ colbuf,
+                                                                          const c_t<T>* __restrict__ tw2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using F = LineFFT<T, N2, E2, +1, R2>;
+    constexpr int TL = N2 / E2, LPW = 32 / TL;
+    c_t<T>* W = reinterpret_cast<c_t<T>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = lane / TL, t = lane % TL;
+    c_t<T>* scr = W + N2 + (warp * LPW + liw) * padded_line(N2);
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
+    __syncthreads();
+    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int b = blockIdx.y;
+    const bool act = c < g.ncols;
+    int q0 = 0, cnt = 0, z0 = 0;
+    if (act) {
+        q0 = g.col_start[c];
+        cnt = g.col_start[c + 1] - q0;
+        z0 = g.pw_z[q0];
+    }
+    const c_t<T>* Cb = C + (size_t)b * ldc + q0;
+    c_t<T> v[E2];
+#pragma unroll
+    for (int e = 0; e < E2; ++e) {
+        const int off = wrapf(F::in_index(t, e) - z0, N2);
+        v[e] = off < cnt ? Cb[off] : mk<T>(T(0), T(0));
+    }
+    F::run(v, t, scr, W);
+    if (act) {
+#pragma unroll
+        for (int e = 0; e < E2; ++e) colbuf[colbuf_index(g, b, F::out_index(t, e), c)] = v[e];
+    }
+}
+
+// MODE 0: out = omega (kin C + scale y); MODE 1: out = scale y.
+template <typename T, int N2, int E2, class R2, int MODE>
+__global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainGeom g,
+                                                                          const c_t<T>* __restrict__ colbuf,
+                                                                          const c_t<T>* __restrict__ C, int ldc,
+                                                                          c_t<T>* __restrict__ out, int ldo,
+                                                                          const T* __restrict__ kin, T omega, T scale,
+                                                                          const c_t<T>* __restrict__ tw2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using F = LineFFT<T, N2, E2, -1, R2>;
+    constexpr int TL = N2 / E2, LPW = 32 / TL;
+    c_t<T>* W = reinterpret_cast<c_t<T>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = lane / TL, t = lane % TL;
+    c_t<T>* scr = W + N2 + (warp * LPW + liw) * padded_line(N2);
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
+    __syncthreads();
+    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int b = blockIdx.y;
+    const bool act = c < g.ncols;
+    c_t<T> v[E2];
+#pragma unroll
+    for (int e = 0; e < E2; ++e)
+        v[e] = act ? colbuf[colbuf_index(g, b, F::in_index(t, e), c)] : mk<T>(T(0), T(0));
+    F::run(v, t, scr, W);
+    if (act) {
+        const int q0 = g.col_start[c];
+        const int cnt = g.col_start[c + 1] - q0;
+        const int z0 = g.pw_z[q0];
+#pragma unroll
+        for (int e = 0; e < E2; ++e) {
+            const int off = wrapf(F::out_index(t, e) - z0, N2);
+            if (off < cnt) {
+                const int q = q0 + off;
+                c_t<T> r;
+                if (MODE == 0) {
+                    const c_t<T> cq = C[(size_t)b * ldc + q];
+                    const T kq = kin[q];
+                    r = mk<T>(omega * (kq * cq.x + scale * v[e].x), omega * (kq * cq.y + scale * v[e].y));
+                } else {
+                    r = cscale(v[e], scale);
+                }
+                out[(size_t)b * ldo + q] = r;
+            }
+        }
+    }
+}
+
 // Line shapes per compiled length: E values per lane and the radix list.
 template <int N> struct FastCfg;
 template <> struct FastCfg<12> { static constexpr int E = 12; using R = Rad<4, 3>; };
@@ -303,6 +392,88 @@ static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, c
     }
     return check_launch("plane_density_fast");
 }
+
+template <int N2>
+static size_t zpass_fast_smem(size_t elem) {
+    constexpr int TL = N2 / FastCfg<N2>::E, LPW = 32 / TL;
+    return ((size_t)N2 + (size_t)kFastWarps * LPW * padded_line(N2)) * elem;
+}
+
+template <int N2>
+static int zpass_fast_blocks(const ChainGeom& g) {
+    constexpr int TL = N2 / FastCfg<N2>::E, LPW = 32 / TL;
+    return (g.ncols + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+}
+
+template <typename T, int N2>
+static jdft_status zinv_fast_impl(const ChainGeom& g, const c_t<T>* C, int ldc, c_t<T>* colbuf, int nb,
+                                  const c_t<T>* tw2, cudaStream_t st) {
+    using C2 = FastCfg<N2>;
+    auto kern = zpass_inverse_fast_kernel<T, N2, C2::E, typename C2::R>;
+    const size_t smem = zpass_fast_smem<N2>(sizeof(c_t<T>));
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_inverse_fast: ") + cudaGetErrorString(e));
+    {
+        Trace tr_("zpass_inverse", st);
+        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kFastThreads, smem, st>>>(g, C, ldc, colbuf, tw2);
+    }
+    return check_launch("zpass_inverse_fast");
+}
+
+template <typename T, int MODE, int N2>
+static jdft_status zfwd_fast_impl(const ChainGeom& g, const c_t<T>* colbuf, const c_t<T>* C, int ldc, c_t<T>* out,
+                                  int ldo, int nb, const T* kin, T omega, T scale, const c_t<T>* tw2,
+                                  cudaStream_t st) {
+    using C2 = FastCfg<N2>;
+    auto kern = zpass_forward_fast_kernel<T, N2, C2::E, typename C2::R, MODE>;
+    const size_t smem = zpass_fast_smem<N2>(sizeof(c_t<T>));
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_forward_fast: ") + cudaGetErrorString(e));
+    {
+        Trace tr_("zpass_forward", st);
+        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kFastThreads, smem, st>>>(g, colbuf, C, ldc, out, ldo, kin, omega,
+                                                                            scale, tw2);
+    }
+    return check_launch("zpass_forward_fast");
+}
+
+#define JDFT_FAST_LENGTHS(X) X(12) X(16) X(40) X(48) X(64) X(80) X(128) X(256)
+
+template <typename T>
+jdft_status launch_zpass_inverse_fast(const ChainGeom& g, const c_t<T>* C, int ldc, c_t<T>* colbuf, int nb,
+                                      const c_t<T>* tw2, cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a) \
+    if (g.S2 == a) return zinv_fast_impl<T, a>(g, C, ldc, colbuf, nb, tw2, st);
+    JDFT_FAST_LENGTHS(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+template <typename T, int MODE>
+jdft_status launch_zpass_forward_fast(const ChainGeom& g, const c_t<T>* colbuf, const c_t<T>* C, int ldc, c_t<T>* out,
+                                      int ldo, int nb, const T* kin, T omega, T scale, const c_t<T>* tw2,
+                                      cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a) \
+    if (g.S2 == a) return zfwd_fast_impl<T, MODE, a>(g, colbuf, C, ldc, out, ldo, nb, kin, omega, scale, tw2, st);
+    JDFT_FAST_LENGTHS(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+#define JDFT_ZFAST_INST(T)                                                                                         \
+    template jdft_status launch_zpass_inverse_fast<T>(const ChainGeom&, const c_t<T>*, int, c_t<T>*, int,         \
+                                                      const c_t<T>*, cudaStream_t);                               \
+    template jdft_status launch_zpass_forward_fast<T, 0>(const ChainGeom&, const c_t<T>*, const c_t<T>*, int,     \
+                                                         c_t<T>*, int, int, const T*, T, T, const c_t<T>*,        \
+                                                         cudaStream_t);                                           \
+    template jdft_status launch_zpass_forward_fast<T, 1>(const ChainGeom&, const c_t<T>*, const c_t<T>*, int,     \
+                                                         c_t<T>*, int, int, const T*, T, T, const c_t<T>*,        \
+                                                         cudaStream_t);
+JDFT_ZFAST_INST(double)
+JDFT_ZFAST_INST(float)
+#undef JDFT_ZFAST_INST
 
 #define JDFT_FAST_SHAPES(X) X(12, 12) X(16, 12) X(40, 40) X(48, 48) X(64, 64) X(80, 80) X(128, 128) X(256, 128)
 

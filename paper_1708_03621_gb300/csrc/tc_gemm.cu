@@ -8,7 +8,7 @@
 // Complex products become real ones by doubling K with the interleaved
 // (re, im) storage: for conj(a) b, Re = sum a'.b'_re and Im = sum a'.b'_im
 // with a' = (ar, ai), b'_re = (br, bi), b'_im = (bi, -br); for a b,
-// b'_re = (br, -bi), b'_im = (bi, br).  A block of 128 threads computes a
+// b'_re = (br, -bi), b'_im = (bi, br).  A block of 512 threads computes a
 // 128 x NT tile: all threads stage a 32-deep (real) K chunk of A' (hi, lo)
 // and B'_re, B'_im (hi, lo) into shared memory in the no-swizzle K-major
 // core-matrix layout, one elected thread issues the tcgen05.mma (M = 128,
@@ -30,7 +30,8 @@ namespace jdft {
 
 constexpr int TC_M = 128;
 constexpr int TC_CPS = 16;          // complex K elements per stage
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 512;
+constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;
 
 __device__ int g_tc_status = 0;
@@ -87,52 +88,60 @@ __device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int
     }
 }
 
+// Staging slots: the i-th value of a thread is (row, k) = (8 g + lane % 8,
+// 4 q + lane / 8) with (g, q) = (it / 4, it % 4), it = warp + TC_WARPS i.  A
+// warp access covers 8 rows x 4 consecutive complex k: whole 16-byte rows of
+// two TF32 core matrices (or one BF16 core matrix), so the split stores are
+// free of bank conflicts, and each row's 4 values are one 32-byte sector of
+// the global operand.
+__device__ __forceinline__ void stage_slot(int i, int warp, int lane, int& row, int& k) {
+    const int it = warp + TC_WARPS * i;
+    row = 8 * (it >> 2) + (lane & 7);
+    k = 4 * (it & 3) + (lane >> 3);
+}
+
 // out[m][n] = alpha sum_k conj(A[m][k]) B[n][k] (rows K-contiguous); FP64 atomics into out.
-// Staging: lane -> (row, complex pair kp of the 16-complex chunk); the loads of
-// a chunk go to registers first (load), the TF32 splits to shared memory after
-// (store), so the next chunk's loads overlap the current chunk's products.
+// The loads of a chunk go to registers first (load), the splits to shared
+// memory after (store), so the next chunk's loads overlap the current
+// chunk's products.
 template <int NT, int FMT>
 struct StageCN {
     const float2* A; int lda; const float2* B; int ldb; int M, N, K;
     double2* out; int ldo; double alpha;
-    static constexpr int PA = TC_M * 8 / TC_THREADS;  // pairs per thread
-    static constexpr int PB = NT * 8 / TC_THREADS;
-    struct Regs { float2 a[PA][2]; float2 b[PB][2]; };
-    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int tid) const {
+    static constexpr int PA = TC_M * TC_CPS / TC_THREADS;  // complex values per thread
+    static constexpr int PB = NT * TC_CPS / TC_THREADS;
+    struct Regs { float2 a[PA]; float2 b[PB]; };
+    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int warp, int lane) const {
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
-            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
-            const int m = m0 + row, k = kc0 + 2 * kp;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                r.a[i][h] = (m < M && k + h < K) ? A[(size_t)m * lda + k + h] : make_float2(0.f, 0.f);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            const int m = m0 + row;
+            r.a[i] = (m < M && kc0 + k < K) ? A[(size_t)m * lda + kc0 + k] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
-            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
-            const int n = n0 + row, k = kc0 + 2 * kp;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                r.b[i][h] = (n < N && k + h < K) ? B[(size_t)n * ldb + k + h] : make_float2(0.f, 0.f);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            const int n = n0 + row;
+            r.b[i] = (n < N && kc0 + k < K) ? B[(size_t)n * ldb + kc0 + k] : make_float2(0.f, 0.f);
         }
     }
-    __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
+    __device__ __forceinline__ void store(const Regs& r, char* buf, int warp, int lane) const {
         using L = TcLayout<NT, FMT>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
-            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) put_split<FMT>(buf, L::A_HI, L::A_LO, row, 4 * kp + 2 * h, r.a[i][h].x, r.a[i][h].y);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
-            const int e = tid + TC_THREADS * i, row = e >> 3, kp = e & 7;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 b = r.b[i][h];
-                put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 4 * kp + 2 * h, b.x, b.y);
-                put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 4 * kp + 2 * h, b.y, -b.x);
-            }
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            const float2 b = r.b[i];
+            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, b.y);
+            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, -b.x);
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -144,42 +153,46 @@ struct StageCN {
 };
 
 // out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
-// Staging: lane -> (k, row) with consecutive lanes on consecutive rows (the
-// operands are contiguous along M and N).
+// The operands are contiguous along M and N: a warp access reads 8
+// consecutive rows of each of 4 k.
 template <int NT, int FMT>
 struct StageNN {
     const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
     float2* out; int ldo;
-    static constexpr int PA = TC_M * 16 / TC_THREADS;
-    static constexpr int PB = NT * 16 / TC_THREADS;
+    static constexpr int PA = TC_M * TC_CPS / TC_THREADS;
+    static constexpr int PB = NT * TC_CPS / TC_THREADS;
     struct Regs { float2 a[PA]; float2 b[PB]; };
-    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int tid) const {
+    __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int warp, int lane) const {
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
-            const int e = tid + TC_THREADS * i, kk = e >> 7, row = e & 127;
-            const int m = m0 + row, k = kc0 + kk;
-            r.a[i] = (m < M && k < K) ? A[(size_t)k * lda + m] : make_float2(0.f, 0.f);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            const int m = m0 + row;
+            r.a[i] = (m < M && kc0 + k < K) ? A[(size_t)(kc0 + k) * lda + m] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
-            const int e = tid + TC_THREADS * i, kk = e / NT, row = e % NT;
-            const int n = n0 + row, k = kc0 + kk;
-            r.b[i] = (n < N && k < K) ? Bm[(size_t)k * ldb + n] : make_float2(0.f, 0.f);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            const int n = n0 + row;
+            r.b[i] = (n < N && kc0 + k < K) ? Bm[(size_t)(kc0 + k) * ldb + n] : make_float2(0.f, 0.f);
         }
     }
-    __device__ __forceinline__ void store(const Regs& r, char* buf, int tid) const {
+    __device__ __forceinline__ void store(const Regs& r, char* buf, int warp, int lane) const {
         using L = TcLayout<NT, FMT>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
-            const int e = tid + TC_THREADS * i, kk = e >> 7, row = e & 127;
-            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * kk, r.a[i].x, r.a[i].y);
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
+            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
-            const int e = tid + TC_THREADS * i, kk = e / NT, row = e % NT;
+            int row, k;
+            stage_slot(i, warp, lane, row, k);
             const float2 b = r.b[i];
-            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * kk, b.x, -b.y);
-            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * kk, b.y, b.x);
+            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, -b.y);
+            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, b.x);
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -217,7 +230,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     int ok = 1;
     int it = 0;
     typename S::Regs regs;
-    if (c0 < c1) s.load(regs, m0, n0, c0 * TC_CPS, tid);
+    if (c0 < c1) s.load(regs, m0, n0, c0 * TC_CPS, warp, lane);
     for (int c = c0; c < c1; ++c, ++it) {
         const int sidx = it & 1;
         char* buf = stage_buf[sidx];
@@ -227,7 +240,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             ok = __syncthreads_and(w);
             if (!ok) break;
         }
-        s.store(regs, buf, tid);
+        s.store(regs, buf, warp, lane);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -262,7 +275,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             }
             tc::mma_commit(&mbar[sidx]);
         }
-        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * TC_CPS, tid);  // overlaps the products just issued
+        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * TC_CPS, warp, lane);  // overlaps the products just issued
     }
     const int n = it;
     if (ok && n > 0) {
@@ -273,10 +286,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     }
     tc::tc_fence_after_sync();
     if (ok && n > 0) {
-        const int row = warp * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the warp groups
+        // w / 4 take the 16-column slices in turn
+        const int quad = warp & 3, grp = warp >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
 #pragma unroll 1
-        for (int col = 0; col < NT; col += 16) {
+        for (int col = grp * 16; col < NT; col += 16 * (TC_WARPS / 4)) {
             float re[16], im[16];
             tc::tmem_ld16(lane_base + col, re);
             tc::tmem_ld16(lane_base + NT + col, im);
