@@ -229,16 +229,17 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     constexpr uint32_t idesc = tc::instr_desc(Fmt<FMT>::IDESC_FMT, TC_M, NT);
     int ok = 1;
     int it = 0;
-    typename S::Regs regs;
-    if (c0 < c1) s.load(regs, m0, n0, c0 * TC_CPS, warp, lane);
-    for (int c = c0; c < c1; ++c, ++it) {
-        const int sidx = it & 1;
-        char* buf = stage_buf[sidx];
+    // two register sets: the loads of chunk c + 2 are issued right after the
+    // products of chunk c, a full chunk before they are stored
+    typename S::Regs regs0, regs1;
+    if (c0 < c1) s.load(regs0, m0, n0, c0 * TC_CPS, warp, lane);
+    if (c0 + 1 < c1) s.load(regs1, m0, n0, (c0 + 1) * TC_CPS, warp, lane);
+    auto step = [&](typename S::Regs& regs, char* buf, uint64_t* bar) -> bool {
         if (it >= 2) {
             // the products issued from this buffer two chunks ago must be done before restaging it
-            const int w = tc::mbar_wait_bounded(&mbar[sidx], (uint32_t)(((it - 2) >> 1) & 1), TC_WAIT_LIMIT) ? 1 : 0;
+            const int w = tc::mbar_wait_bounded(bar, (uint32_t)(((it - 2) >> 1) & 1), TC_WAIT_LIMIT) ? 1 : 0;
             ok = __syncthreads_and(w);
-            if (!ok) break;
+            if (!ok) return false;
         }
         s.store(regs, buf, warp, lane);
         tc::fence_proxy_async_smem();
@@ -273,9 +274,17 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
                     tc::mma_bf16(tmem + NT, alo, bih, idesc, 1u);
                 }
             }
-            tc::mma_commit(&mbar[sidx]);
+            tc::mma_commit(bar);
         }
-        if (c + 1 < c1) s.load(regs, m0, n0, (c + 1) * TC_CPS, warp, lane);  // overlaps the products just issued
+        const int c = c0 + it;
+        if (c + 2 < c1) s.load(regs, m0, n0, (c + 2) * TC_CPS, warp, lane);  // overlaps the products just issued
+        ++it;
+        return true;
+    };
+    while (c0 + it < c1) {
+        if (!step(regs0, stage_buf[0], &mbar[0])) break;
+        if (c0 + it >= c1) break;
+        if (!step(regs1, stage_buf[1], &mbar[1])) break;
     }
     const int n = it;
     if (ok && n > 0) {
