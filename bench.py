@@ -200,11 +200,11 @@ class Problem:
         self.ctype = ct
 
     def step(self, stream=None):
-        """Rows a1-a9: H C, density, C^dag H C and C^dag O C, Cholesky orthonormalisation."""
+        """Rows a1-a9: H C and the density (one fused call), C^dag H C and
+        C^dag O C, Cholesky orthonormalisation."""
         j = self.jdft
-        j.jdft_apply_H(self.basis, 0, self.C, self.HC, self.prec, stream)
         self.n.zero_()
-        j.jdft_density(self.basis, 0, self.C, self.f, self.n, self.prec, stream)
+        j.jdft_apply_H_density(self.basis, 0, self.C, self.HC, self.f, self.n, self.prec, stream)
         j.jdft_subspace(self.basis, 0, self.C, self.HC, self.CHC, self.COC, self.prec, stream)
         j.jdft_orthonormalize(self.basis, 0, self.C, self.prec, stream)
 
@@ -228,10 +228,12 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
     l2 = math.log2
     if name in ("tc_zgemm_cn", "tc_zgemm_nn"):
         return kernel_work(p, name[3:], launches, nb)
-    if name in ("plane_apply", "plane_apply_fast"):
+    if name in ("plane_apply", "plane_apply_fast", "plane_apply_density_fast"):
+        # the fused kernel does the same transforms; its density adds the n(r) update
         fl = 5 * S2 * (2 * nrows * S1 * l2(S1) + 2 * S1 * S0 * l2(S0))
         by = 2 * S2 * ncols * e
-        return fl * per_launch_bands, by * per_launch_bands + p.N * (8 if e == 16 else 4)
+        extra = p.N * 16 if name == "plane_apply_density_fast" else 0
+        return fl * per_launch_bands, by * per_launch_bands + p.N * (8 if e == 16 else 4) + extra
     if name in ("plane_density", "plane_density_fast"):
         fl = 5 * S2 * (nrows * S1 * l2(S1) + S1 * S0 * l2(S0))
         return fl * per_launch_bands, S2 * ncols * e * per_launch_bands + p.N * 8

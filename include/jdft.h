@@ -158,6 +158,16 @@ jdft_status jdft_apply_H(jdft_basis_t basis, int ik, const void* C, int ldc, voi
 jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, const double* f,
                          int nb, double* n_r, jdft_prec prec, void* stream);
 
+/* H C and the density of the same block in one pass over the box: HC exactly
+ * as jdft_apply_H writes it, and n_r += w_ik sum_b f[b] |(I C_b)_j|^2 exactly
+ * as jdft_density adds it.  The density is taken from the inverse transforms
+ * I C_b that the local-potential term forms anyway (Sec. 2.1 chains
+ * I -> multiply -> J; the paper computes H C and the density in separate
+ * operator calls).  Arguments as for those two calls; HC and C must not
+ * overlap.  Uses (and may grow) the basis workspace. */
+jdft_status jdft_apply_H_density(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
+                                 int nb, const double* f, double* n_r, jdft_prec prec, void* stream);
+
 /* CHC = C^dag (HC), COC = C^dag O C = Omega C^dag C: device complex128 nb x nb, row-major,
  * both triangles written.  Either output may be NULL to skip it. */
 jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
@@ -168,8 +178,9 @@ jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, co
 /* C <- C L^{-dag} with Omega C^dag C = L L^dag, so that C^dag O C = 1 afterwards
  * (O diagonal in the plane-wave basis, Sec. 2.1).  C: device, band-major
  * (ldc >= npw), complex128 for JDFT_FP64 and complex64 otherwise; the products
- * C^dag C and C L^{-dag} run at `prec`, the Cholesky factorisation and
- * triangular inverse in FP64 on the GPU.  Uses (and may grow) the basis
+ * C^dag C and C L^{-dag} run at `prec` (C^dag C accumulated in FP64), the
+ * Cholesky factorisation and triangular inverse on the GPU in FP64 for
+ * JDFT_FP64 and in FP32 for the FP32 precisions.  Uses (and may grow) the basis
  * workspace.  Synchronous.  JDFT_ERR_NOT_POSDEF if the bands are linearly
  * dependent. */
 jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,

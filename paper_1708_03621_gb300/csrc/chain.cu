@@ -611,6 +611,46 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
     return JDFT_OK;
 }
 
+// H C and the density of the same block: per chunk one z pass in, then the
+// fused plane kernel where it exists (else density, then the H plane pass, on
+// the same column buffer), one z pass out; the nonlocal term after.
+template <typename T>
+static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                       const double* f, double* n_r, jdft_prec prec, cudaStream_t st) {
+    const ChainGeom g = make_geom(b, ik);
+    const KSphere& sp = b->ks[ik];
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
+    const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
+    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>));
+    jdft_status s = ensure_workspace(b, colbytes + nlbytes);
+    if (s != JDFT_OK) return s;
+    c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
+    const T omega = (T)b->omega, invN = (T)(1.0 / (double)b->N);
+    const double wk = b->kweight[ik];
+    for (int b0 = 0; b0 < nb; b0 += nc) {
+        const int n = std::min(nc, nb - b0);
+        const c_t<T>* Cc = (const c_t<T>*)C + (size_t)b0 * ldc;
+        c_t<T>* Hc = (c_t<T>*)HC + (size_t)b0 * ldhc;
+        if ((s = launch_zpass_inverse<T>(g, Cc, ldc, colbuf, n, twiddles<T>(b), st))) return s;
+        jdft_status fs = JDFT_ERR_UNSUPPORTED;
+        if constexpr (std::is_same<T, float>::value)
+            fs = launch_plane_apply_density_fast(g, colbuf, potential<float>(b), n, f + b0, wk, n_r, twiddles<float>(b),
+                                                 st);
+        if (fs == JDFT_ERR_UNSUPPORTED) {
+            if ((s = launch_plane_density<T>(g, colbuf, f + b0, wk, n_r, n, twiddles<T>(b), st))) return s;
+            if ((s = launch_plane_apply<T>(g, colbuf, potential<T>(b), n, twiddles<T>(b), st))) return s;
+        } else if (fs != JDFT_OK) {
+            return fs;
+        }
+        if ((s = launch_zpass_forward<T, 0>(g, colbuf, Cc, ldc, Hc, ldhc, n, kinetic<T>(sp), omega, invN,
+                                            twiddles<T>(b), st)))
+            return s;
+    }
+    if (sp.nproj > 0)
+        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st);
+    return JDFT_OK;
+}
+
 template <typename T>
 static jdft_status run_density(jdft_basis_s* b, int ik, const void* C, int ldc, const double* f, int nb,
                                double* n_r, cudaStream_t st) {
@@ -736,6 +776,21 @@ jdft_status jdft_apply_H(jdft_basis_t b, int ik, const void* C, int ldc, void* H
     cudaStream_t st = (cudaStream_t)stream;
     return JDFT_DISPATCH(prec, run_apply_H<double>(b, ik, C, ldc, HC, ldhc, nb, prec, st),
                          run_apply_H<float>(b, ik, C, ldc, HC, ldhc, nb, prec, st));
+}
+
+jdft_status jdft_apply_H_density(jdft_basis_t b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                 const double* f, double* n_r, jdft_prec prec, void* stream) {
+    clear_error();
+    jdft_status s;
+    if ((s = check_common(b, ik, nb)) || (s = check_prec(prec))) return s;
+    const int npw = b->ks[ik].npw;
+    if ((s = check_block(C, ldc, npw, nb, prec, "C")) || (s = check_block(HC, ldhc, npw, nb, prec, "HC"))) return s;
+    JDFT_CHECK_ARG(nb == 0 || (f && n_r), "f or n_r is null");
+    if (!b->have_V) return set_error(JDFT_ERR_ARG, "no potential set (call jdft_set_potential first)");
+    if (nb == 0) return JDFT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return JDFT_DISPATCH(prec, run_apply_H_density<double>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, prec, st),
+                         run_apply_H_density<float>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, prec, st));
 }
 
 jdft_status jdft_density(jdft_basis_t b, int ik, const void* C, int ldc, const double* f, int nb, double* n_r,

@@ -63,6 +63,13 @@ jdft_status launch_plane_apply_fast(const ChainGeom& g, c_t<T>* colbuf, const T*
                                     cudaStream_t st);
 jdft_status launch_plane_density_fast(const ChainGeom& g, const float2* colbuf, const double* f, double w,
                                       double* n_r, int nb, const float2* tw_base, cudaStream_t st);
+// H plane pass and density of the same FP32 column buffer in one kernel (for
+// the box shapes it is compiled for; JDFT_ERR_UNSUPPORTED otherwise):
+// colbuf becomes the plane-pass output as in launch_plane_apply, and
+// n_r += w sum_b f_b |psi_b|^2.
+jdft_status launch_plane_apply_density_fast(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
+                                            const double* f, double w, double* n_r, const float2* tw_base,
+                                            cudaStream_t st);
 // Register-FFT z passes for the lengths S2 they are compiled for (same
 // contract as launch_zpass_*, tw2 = the length-S2 twiddle table); they return
 // JDFT_ERR_UNSUPPORTED (without launching) for other lengths.

@@ -22,6 +22,7 @@
 #include "chain.cuh"
 #include "fft_reg.cuh"
 #include "profile.cuh"
+#include "tc_ptx.cuh"
 
 namespace jdft {
 
@@ -230,6 +231,112 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
     }
 }
 
+// Hamiltonian plane pass and density in one (FP32 blocks, 16 values per lane
+// along axis 0).  A persistent block takes a contiguous range of the
+// plane-major list of (z-plane j2, band) items, runs the plane pass of
+// plane_apply_fast_kernel on each, and adds f_b |psi_b|^2 of the column
+// inverse transforms (the psi_b(r) the pass forms anyway) to FP32 sums held
+// in tensor memory: 128 columns per block, lane quadrant warp % 4, column half
+// warp / 4, 16 columns per column round.  The sums go to n(r) with FP64
+// atomics whenever the block's plane changes and at the end, about twice per
+// block.
+template <int N0, int E0, class R0, int N1, int E1, class R1>
+__global__ void __launch_bounds__(kFastThreads) plane_apply_density_fast_kernel(
+    ChainGeom g, float2* __restrict__ colbuf, const float* __restrict__ Vp, int nb, const double* __restrict__ f,
+    double w, double* __restrict__ n_r, const float2* __restrict__ tw0, const float2* __restrict__ tw1) {
+    static_assert(E0 == 16, "the tensor-memory sums take 16 values per lane and round");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t tslot;
+    constexpr int lsA = N1 + 1;
+    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
+    constexpr int TL = N0 / E0, LPW = 32 / TL;
+    constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+    static_assert(ROUNDS * 16 <= 64, "at most 64 sums per lane");
+    using FI = LineFFT<float, N0, E0, +1, R0>;
+    float2* W0 = reinterpret_cast<float2*>(smem_raw);
+    float2* W1 = W0 + N0;
+    float2* scr_all = W1 + N1;
+    float2* A = scr_all + kFastWarps * SCR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = lane / TL, t = lane % TL;
+    float2* wscr = scr_all + warp * SCR;
+    float2* scr = wscr + liw * padded_line(N0);
+    for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = tw0[i];
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) W1[i] = tw1[i];
+    if (warp == 0) tc::tmem_alloc(&tslot, 128);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tb = tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+    const int64_t items = (int64_t)g.S2 * nb;
+    const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+    auto flush = [&](int j2) {
+#pragma unroll
+        for (int k = 0; k < ROUNDS; ++k) {
+            float acc[16];
+            tc::tmem_ld16(tb + 16 * k, acc);
+            const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+            if (j1 < N1) {
+#pragma unroll
+                for (int e = 0; e < E0; ++e)
+                    atomicAdd(n_r + ((size_t)FI::out_index(t, e) * N1 + j1) * g.S2 + j2, w * (double)acc[e]);
+            }
+        }
+    };
+    auto zero = [&]() {
+        float z[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) z[e] = 0.f;
+#pragma unroll
+        for (int k = 0; k < ROUNDS; ++k) tc::tmem_st16(tb + 16 * k, z);
+        tc::tmem_wait_st();
+    };
+    int cur = -1;
+    for (int64_t it = it0; it < it1; ++it) {
+        const int j2 = (int)(it / nb), b = (int)(it - (int64_t)j2 * nb);
+        if (j2 != cur) {
+            if (cur >= 0) flush(cur);
+            zero();
+            cur = j2;
+        }
+        float2* plane = colbuf + colbuf_index(g, b, j2, 0);
+        rows_inverse_fast<float, N1, E1, R1>(g, plane, A, lsA, wscr, W1, warp, lane);
+        __syncthreads();
+        const float fb = (float)f[b];
+#pragma unroll
+        for (int k = 0; k < ROUNDS; ++k) {
+            const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
+            const bool act = j1 < N1;
+            float2 v[E0];
+            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, act, v, t, scr, W0);
+            float acc[16];
+            tc::tmem_ld16(tb + 16 * k, acc);
+#pragma unroll
+            for (int e = 0; e < E0; ++e) acc[e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
+            tc::tmem_st16(tb + 16 * k, acc);
+            const float* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
+#pragma unroll
+            for (int e = 0; e < E0; ++e) v[e] = act ? cscale(v[e], Vq[FI::out_index(t, e)]) : mk<float>(0.f, 0.f);
+            FI::run_adjoint(v, t, scr, W0);
+            if (act) {
+#pragma unroll
+                for (int e = 0; e < E0; ++e) {
+                    const int r = wrapf(FI::in_index(t, e) - g.i0min, N0);
+                    if (r < g.nrows) A[r * lsA + j1] = v[e];
+                }
+            }
+        }
+        tc::tmem_wait_st();
+        __syncthreads();
+        rows_forward_fast<float, N1, E1, R1>(g, plane, A, lsA, wscr, W1, warp, lane);
+        __syncthreads();
+    }
+    if (cur >= 0) flush(cur);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tslot, 128);
+}
+
 // z passes with register line FFTs: TL lanes per (i0, i1) column of the
 // sphere, LPW columns per warp, 8 warps per block, one band per blockIdx.y.
 // A column's plane waves have consecutive z-slots from pw_z of its first one
@@ -435,6 +542,47 @@ static jdft_status zfwd_fast_impl(const ChainGeom& g, const c_t<T>* colbuf, cons
                                                                             scale, tw2);
     }
     return check_launch("zpass_forward_fast");
+}
+
+// Shared memory requested per fused block: at least 58 KB, so that no more
+// than three blocks share an SM and their tensor-memory sums (128 columns
+// each) fit in its 512 columns.
+template <int N0, int N1>
+static jdft_status apply_density_fast_impl(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
+                                           const double* f, double w, double* n_r, const float2* tw_base,
+                                           cudaStream_t st) {
+    using C0 = FastCfg<N0>;
+    using C1 = FastCfg<N1>;
+    const size_t smem = std::max<size_t>(fast_smem<N0, N1>(g, sizeof(float2)), 58 * 1024);
+    if (smem > kFastMaxSmem) return JDFT_ERR_UNSUPPORTED;
+    auto kern = plane_apply_density_fast_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R>;
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess)
+        return set_error(JDFT_ERR_CUDA, std::string("plane_apply_density_fast: ") + cudaGetErrorString(e));
+    const int64_t items = (int64_t)g.S2 * nb;
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kFastThreads, smem) != cudaSuccess ||
+        resident < 1)
+        resident = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, sms) * resident);
+    {
+        Trace tr_("plane_apply_density_fast", st);
+        kern<<<grid, kFastThreads, smem, st>>>(g, colbuf, Vp, nb, f, w, n_r, tw_base + g.p0.tw_offset,
+                                               tw_base + g.p1.tw_offset);
+    }
+    return check_launch("plane_apply_density_fast");
+}
+
+jdft_status launch_plane_apply_density_fast(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
+                                            const double* f, double w, double* n_r, const float2* tw_base,
+                                            cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+    if (g.S0 == 128 && g.S1 == 128) return apply_density_fast_impl<128, 128>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
+    if (g.S0 == 16 && g.S1 == 12) return apply_density_fast_impl<16, 12>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
+    return JDFT_ERR_UNSUPPORTED;
 }
 
 #define JDFT_FAST_LENGTHS(X) X(12) X(16) X(40) X(48) X(64) X(80) X(128) X(256)

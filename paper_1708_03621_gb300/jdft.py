@@ -75,6 +75,7 @@ _SIGS = {
     "jdft_op_O": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_apply_H": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_density": [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp],
+    "jdft_apply_H_density": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
     "jdft_subspace": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _i, _vp],
     "jdft_apply_H_noalloc": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_orthonormalize": [_vp, _i, _vp, _i, _i, _i, _vp],
@@ -276,6 +277,16 @@ def jdft_apply_H_noalloc(basis, ik, C, HC, prec="fp64", stream=None):
     if nb2 != nb:
         raise ValueError("C and HC must hold the same number of bands")
     _call("jdft_apply_H_noalloc", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), _stream(stream))
+
+
+def jdft_apply_H_density(basis, ik, C, HC, f, n_r, prec="fp64", stream=None):
+    """HC = H C and n_r += w_k sum_b f_b |I C_b|^2 in one pass over the box."""
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, nb2 = _block(HC, prec, "HC")
+    if nb2 != nb:
+        raise ValueError("C and HC must hold the same number of bands")
+    _call("jdft_apply_H_density", basis.handle, ik, p, ld, q, ldh, nb, _ptr(f), _ptr(n_r), _prec(prec),
+          _stream(stream))
 
 
 def jdft_density(basis, ik, C, f, n_r, prec="fp64", stream=None):

@@ -37,6 +37,7 @@ def test_null_arguments_rejected():
     assert b"null" in L.jdft_last_error()
     assert L.jdft_apply_H(None, 0, None, 0, None, 0, 1, 0, None) == 1
     assert L.jdft_density(None, 0, None, 0, None, 1, None, 0, None) == 1
+    assert L.jdft_apply_H_density(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
     assert L.jdft_subspace(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
     assert L.jdft_basis_npw(None, 0, None) == 1
     assert L.jdft_basis_destroy(None) == 0

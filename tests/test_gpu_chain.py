@@ -21,6 +21,9 @@ pytestmark = pytest.mark.gpu
 # bf16x3: x = hi + lo in BF16 represents x to 2^-18 (3.8e-6) and the dropped lo*lo
 # term is of the same size, so a product is good to ~1.1e-5 in the worst case.
 TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5}
+# two runs of the same product: they differ only by the order of FP64 atomic
+# additions (split-K) before the result is rounded to the block type
+SAME = {"fp64": 1e-13, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-6}
 CTYPE = {"fp64": "complex128", "fp32": "complex64", "tf32x3": "complex64", "bf16x3": "complex64"}
 CASES = ["tiny_cubic", "tiny_ortho", "mid", "small"]
 
@@ -155,6 +158,32 @@ def test_density(name, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 @pytest.mark.parametrize("name", CASES)
+def test_apply_H_density(name, prec):
+    """The fused call: HC equal to jdft_apply_H's up to the order of the FP64
+    atomic split-K sums of the nonlocal projections (same plane-pass
+    arithmetic; the 16 x 12 planes of tiny_ortho take the fused kernel, the
+    other boxes density-then-apply on one column buffer) and the density
+    against the oracle's, accumulated onto existing values."""
+    w, o, g = systems(name)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    f = np.linspace(2.0, 0.5, C.shape[0])
+    Cd = to_dev(C, prec)
+    HC = torch.empty_like(Cd)
+    HC1 = torch.empty_like(Cd)
+    n = torch.full((g.N,), 0.25, dtype=torch.float64, device="cuda")
+    jdft.jdft_apply_H_density(g.basis, 0, Cd, HC, torch.tensor(f, device="cuda"), n, prec)
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC1, prec)
+    assert rel_max(host(HC), host(HC1)) < SAME[prec]
+    assert band_rel_err(host(HC), o.apply_H(C)) < TOL[prec]
+    ref = pw.density(o.basis, C.T, f, weight=w.weights()[0])
+    got = n.cpu().numpy() - 0.25
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL[prec]
+    jdft.jdft_device_status()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("name", CASES)
 def test_subspace(name, prec):
     w, o, g = systems(name)
     from paper_1708_03621_gb300 import jdft
@@ -198,6 +227,14 @@ def test_large_sampled_bands(prec):
     jdft.jdft_density(g.basis, 0, Cd, torch.tensor(f, device="cuda"), n, prec)
     nref = pw.density(o.basis, C[sample].T, f[sample])
     assert np.max(np.abs(n.cpu().numpy() - nref)) / np.max(nref) < TOL[prec]
+    # the fused call in the launch configuration the benchmark times (128 x 128
+    # planes: the fused kernel for the FP32 blocks; several band chunks)
+    HC2 = torch.empty_like(Cd)
+    n2 = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    jdft.jdft_apply_H_density(g.basis, 0, Cd, HC2, torch.tensor(f, device="cuda"), n2, prec)
+    assert rel_max(host(HC2), got) < SAME[prec]
+    assert np.max(np.abs(n2.cpu().numpy() - nref)) / np.max(nref) < TOL[prec]
+    jdft.jdft_device_status()
 
 
 def test_edge_cases():
