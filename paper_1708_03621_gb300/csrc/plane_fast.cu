@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
 // atomics whenever the block's plane changes and at the end, about twice per
 // block.
 template <int N0, int E0, class R0, int N1, int E1, class R1>
-__global__ void __launch_bounds__(kFastThreads) plane_apply_density_fast_kernel(
+__global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kernel(
     ChainGeom g, float2* __restrict__ colbuf, const float* __restrict__ Vp, int nb, const double* __restrict__ f,
     double w, double* __restrict__ n_r, const float2* __restrict__ tw0, const float2* __restrict__ tw1) {
     static_assert(E0 == 16, "the tensor-memory sums take 16 values per lane and round");
@@ -307,12 +307,16 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_density_fast_kernel(
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
             const bool act = j1 < N1;
+            // this round's sums are fetched while the column transform runs
+            uint32_t sr[16];
+            tc::tmem_ld16_issue(tb + 16 * k, sr);
             float2 v[E0];
             column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, act, v, t, scr, W0);
+            tc::tmem_wait_ld16(sr);
             float acc[16];
-            tc::tmem_ld16(tb + 16 * k, acc);
 #pragma unroll
-            for (int e = 0; e < E0; ++e) acc[e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
+            for (int e = 0; e < E0; ++e)
+                acc[e] = __uint_as_float(sr[e]) + fb * (v[e].x * v[e].x + v[e].y * v[e].y);
             tc::tmem_st16(tb + 16 * k, acc);
             const float* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
 #pragma unroll
