@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
     const int64_t items = (int64_t)g.S2 * nb;
     const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
     auto flush = [&](int j2) {
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < ROUNDS; ++k) {
             float acc[16];
             tc::tmem_ld16(tb + 16 * k, acc);
@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
         rows_inverse_fast<float, N1, E1, R1>(g, plane, A, lsA, wscr, W1, warp, lane);
         __syncthreads();
         const float fb = (float)f[b];
-#pragma unroll
+        // rolled: four copies of the two column transforms would overflow the instruction cache
+#pragma unroll 1
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
             const bool act = j1 < N1;
@@ -564,10 +565,10 @@ static jdft_status apply_density_fast_impl(const ChainGeom& g, float2* colbuf, c
     if (e != cudaSuccess)
         return set_error(JDFT_ERR_CUDA, std::string("plane_apply_density_fast: ") + cudaGetErrorString(e));
     const int64_t items = (int64_t)g.S2 * nb;
-    int resident = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kFastThreads, smem) != cudaSuccess ||
-        resident < 1)
-        resident = 1;
+    // resident blocks per SM from the footprint: __launch_bounds__(256, 2)
+    // holds registers to 128 a thread, so shared memory decides (228 KB per
+    // SM, 1 KB of it reserved per block)
+    const int resident = std::max(1, std::min(3, (int)((228u * 1024u) / (smem + 1024u))));
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
