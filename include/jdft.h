@@ -110,7 +110,10 @@ jdft_status jdft_set_potential(jdft_basis_t basis, const double* V, void* stream
 /* Copy the nonlocal projectors of k-point ik into the basis:
  *   P  device complex128, npw x nproj column-major (projector i at P[i*npw ..]);
  *   D  device double, nproj x nproj row-major, Hermitian (real symmetric).
- * nproj = 0 clears the nonlocal term for ik.  (Sec. 2.2, pseudopotentials.) */
+ * nproj = 0 clears the nonlocal term for ik.  D is also kept as rows of its
+ * nonzeros (built here, on the host: this call synchronises `stream`), so
+ * that block-diagonal per-atom D costs O(nonzeros) per product.
+ * (Sec. 2.2, pseudopotentials.) */
 jdft_status jdft_set_projectors(jdft_basis_t basis, int ik, const void* P, int nproj,
                                 const double* D, void* stream);
 

@@ -93,7 +93,7 @@ template <typename T> static jdft_status upload(T** dst, const std::vector<T>& s
 static void free_sphere(KSphere& s) {
     cudaFree(s.col_start); cudaFree(s.col_slot01); cudaFree(s.row_col_start); cudaFree(s.row_i1lo);
     cudaFree(s.pw_col); cudaFree(s.pw_z); cudaFree(s.kin); cudaFree(s.kvec); cudaFree(s.kin32);
-    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D);
+    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
     s = KSphere();
 }
 
@@ -397,8 +397,8 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     KSphere& s = b->ks[ik];
     if (s.P) {
         JDFT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D);
-        s.P = s.P32 = nullptr; s.D = nullptr;
+        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
+        s.P = s.P32 = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
     }
     s.nproj = nproj;
     if (nproj == 0) return JDFT_OK;
@@ -410,6 +410,35 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     cudaStream_t st = (cudaStream_t)stream;
     JDFT_CUDA_TRY(cudaMemcpyAsync(s.P, P, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     JDFT_CUDA_TRY(cudaMemcpyAsync(s.D, D, (size_t)nproj * nproj * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    {
+        // ELL copy of D for the products D (P^dag C): nonlocal D matrices couple
+        // only the projectors of one atom, so rows hold a few nonzeros
+        std::vector<double> h((size_t)nproj * nproj);
+        JDFT_CUDA_TRY(cudaMemcpyAsync(h.data(), D, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+        int w = 1;
+        for (int i = 0; i < nproj; ++i) {
+            int c = 0;
+            for (int j = 0; j < nproj; ++j) c += h[(size_t)i * nproj + j] != 0.0;
+            w = std::max(w, c);
+        }
+        std::vector<int> col((size_t)nproj * w, 0);
+        std::vector<double> val((size_t)nproj * w, 0.0);
+        for (int i = 0; i < nproj; ++i) {
+            int c = 0;
+            for (int j = 0; j < nproj; ++j)
+                if (h[(size_t)i * nproj + j] != 0.0) {
+                    col[(size_t)i * w + c] = j;
+                    val[(size_t)i * w + c] = h[(size_t)i * nproj + j];
+                    ++c;
+                }
+        }
+        s.Dw = w;
+        JDFT_CUDA_TRY(cudaMalloc(&s.Dcol, col.size() * sizeof(int)));
+        JDFT_CUDA_TRY(cudaMalloc(&s.Dval, val.size() * sizeof(double)));
+        JDFT_CUDA_TRY(cudaMemcpy(s.Dcol, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+        JDFT_CUDA_TRY(cudaMemcpy(s.Dval, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     {
         Trace tr_("to_complex64", st);
         to_complex64<<<grid_for((int64_t)n, 256), 256, 0, st>>>((const double2*)s.P, (float2*)s.P32, (int64_t)n);

@@ -106,6 +106,11 @@ struct KSphere {
     void* P = nullptr;          // complex128 npw x nproj column-major
     void* P32 = nullptr;        // complex64 copy
     double* D = nullptr;        // nproj x nproj
+    // D as ELL rows: Dw entries per row (the widest row's nonzero count),
+    // columns and values, padded with column 0 and value 0
+    int Dw = 0;
+    int* Dcol = nullptr;        // nproj x Dw
+    double* Dval = nullptr;     // nproj x Dw
 };
 
 // Library-owned scratch buffer that only grows.

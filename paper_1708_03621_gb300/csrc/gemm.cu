@@ -149,20 +149,20 @@ jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_
     return check_launch("zgemm_nn");
 }
 
-// Bd[i][b] = sum_j D[i][j] Bc[j][b], rounded to the product type.
+// Bd[i][b] = sum_j D[i][j] Bc[j][b], rounded to the product type; D as ELL
+// rows (w entries of column index and value per row).
 template <typename T>
-__global__ void dmul_kernel(int nproj, int nb, const double* __restrict__ D, const double2* __restrict__ Bc,
-                            c_t<T>* __restrict__ Bd) {
+__global__ void dmul_kernel(int nproj, int nb, int w, const int* __restrict__ Dcol, const double* __restrict__ Dval,
+                            const double2* __restrict__ Bc, c_t<T>* __restrict__ Bd) {
     const int total = nproj * nb;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int i = e / nb, b = e % nb;
         double re = 0.0, im = 0.0;
-        for (int j = 0; j < nproj; ++j) {
-            const double d = D[(size_t)i * nproj + j];
-            if (d != 0.0) {
-                re += d * Bc[(size_t)j * nb + b].x;
-                im += d * Bc[(size_t)j * nb + b].y;
-            }
+        for (int q = 0; q < w; ++q) {
+            const double d = Dval[(size_t)i * w + q];
+            const double2 x = Bc[(size_t)Dcol[(size_t)i * w + q] * nb + b];
+            re += d * x.x;
+            im += d * x.y;
         }
         Bd[e] = mk<T>((T)re, (T)im);
     }
@@ -192,7 +192,8 @@ jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void*
     if (s != JDFT_OK) return s;
     {
         Trace tr_("dmul", st);
-        dmul_kernel<T><<<std::min(152 * 8, (sp.nproj * nb + 255) / 256), 256, 0, st>>>(sp.nproj, nb, sp.D, Bc, Bd);
+        dmul_kernel<T><<<std::min(152 * 8, (sp.nproj * nb + 255) / 256), 256, 0, st>>>(sp.nproj, nb, sp.Dw, sp.Dcol,
+                                                                                        sp.Dval, Bc, Bd);
     }
     if ((s = check_launch("dmul"))) return s;
     return gemm_nn_acc<T>(prec, sp.npw, nb, sp.nproj, proj_ptr<T>(sp), sp.npw, Bd, nb, (c_t<T>*)HC, ldhc, st);
