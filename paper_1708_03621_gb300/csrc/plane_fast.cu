@@ -42,6 +42,38 @@ __host__ __device__ constexpr int warp_scratch() {
                : (32 / (N1 / E1)) * padded_line(N1);
 }
 
+// Row stride of the plane array A (elements): N1 + pad, with the smallest pad
+// for which both warp access patterns spread evenly over the bank slots
+// (16 eight-byte slots per 128 bytes for float2, 8 sixteen-byte slots for
+// double2): LPW1 rows x TL1 consecutive positions in the row passes, TL0
+// consecutive rows x LPW0 consecutive columns in the column pass.
+template <typename T, int N0, int E0, int N1, int E1>
+__host__ __device__ constexpr int a_stride() {
+    constexpr int SLOTS = 128 / (int)sizeof(c_t<T>);
+    constexpr int TL0 = N0 / E0, TL1 = N1 / E1;
+    int best = 1, bestc = 1 << 30;
+    for (int pad = 1; pad <= SLOTS; ++pad) {
+        const int st = (N1 + pad) % SLOTS;
+        int c1[16] = {}, c2[16] = {};
+        int m1 = 0, m2 = 0;
+        for (int l = 0; l < 32 / TL1; ++l)
+            for (int t = 0; t < TL1; ++t) {
+                const int a = (l * st + t) % SLOTS;
+                if (++c1[a] > m1) m1 = c1[a];
+            }
+        for (int l = 0; l < 32 / TL0; ++l)
+            for (int t = 0; t < TL0; ++t) {
+                const int b = (t * st + l) % SLOTS;
+                if (++c2[b] > m2) m2 = c2[b];
+            }
+        if (m1 + m2 < bestc) {
+            bestc = m1 + m2;
+            best = pad;
+        }
+    }
+    return N1 + best;
+}
+
 // Phase 1 / 3 helpers -------------------------------------------------------
 template <typename T, int N1, int E1, class R1, int NW = kFastWarps>
 __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<T>* __restrict__ plane, c_t<T>* A,
@@ -120,7 +152,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
                                                                         const c_t<T>* __restrict__ tw0,
                                                                         const c_t<T>* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int lsA = N1 + 1;
+    constexpr int lsA = a_stride<T, N0, E0, N1, E1>();
     constexpr int SCR = warp_scratch<N0, E0, N1, E1>();  // per-warp scratch (LPW padded lines)
     c_t<T>* W0 = reinterpret_cast<c_t<T>*>(smem_raw);
     c_t<T>* W1 = W0 + N0;
@@ -178,7 +210,7 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
                                                                           const float2* __restrict__ tw0,
                                                                           const float2* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int lsA = N1 + 1;
+    constexpr int lsA = a_stride<float, N0, E0, N1, E1>();
     constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
     constexpr int TL = N0 / E0, LPW = 32 / TL;
     constexpr int ROUNDS = (N1 + NW * LPW - 1) / (NW * LPW);
@@ -247,7 +279,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
     static_assert(E0 == 16, "the tensor-memory sums take 16 values per lane and round");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t tslot;
-    constexpr int lsA = N1 + 1;
+    constexpr int lsA = a_stride<float, N0, E0, N1, E1>();
     constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
     constexpr int TL = N0 / E0, LPW = 32 / TL;
     constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
@@ -447,7 +479,8 @@ constexpr size_t kFastMaxSmem = 220 * 1024;
 template <int N0, int N1>
 static size_t fast_smem(const ChainGeom& g, size_t elem, int nw = kFastWarps) {
     constexpr int E0 = FastCfg<N0>::E, E1 = FastCfg<N1>::E;
-    return ((size_t)N0 + N1 + (size_t)nw * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * (N1 + 1)) * elem;
+    const int lsA = elem == sizeof(double2) ? a_stride<double, N0, E0, N1, E1>() : a_stride<float, N0, E0, N1, E1>();
+    return ((size_t)N0 + N1 + (size_t)nw * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * lsA) * elem;
 }
 
 // Warps of a density block: enough that the per-lane accumulators of the
