@@ -16,7 +16,10 @@
 // split into 16 x 16 output quadrants on separate blocks, and the diagonal
 // tile takes one block barrier per column with each reciprocal taken once.
 // The matrix is padded to a multiple of 32 with identity rows.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <cstdlib>
 
 #include "chol.cuh"
 #include "profile.cuh"
@@ -269,6 +272,245 @@ __global__ void chol_out_kernel(int n, int N, const c_t<S>* __restrict__ X, c_t<
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 factorisation of n <= 256 in one launch: a cluster of P = ceil(n/32)
+// CTAs, CTA c holding block column c (rows 0 .. 32P-1, 32 columns) and its
+// block column of X = L^{-1} in shared memory.  Step k: CTA k factors its
+// diagonal tile (as chol_diag_kernel) and its panel L_ik = A_ik X_kk^dag; one
+// cluster barrier; CTAs j > k subtract L_ik L_jk^dag from their block column,
+// reading CTA k's panel through distributed shared memory.  Then each CTA
+// forms its block column of X by block forward substitution,
+// X_ic = -X_ii sum_{j=c}^{i-1} L_ij X_jc, with L_ij and X_ii read from the
+// CTAs that hold them, and writes its 32 rows of W = X^dag.
+// ---------------------------------------------------------------------------
+constexpr int CLS = CB + 1;      // row stride of the block-column arrays (complex elements)
+constexpr int CL_MAX = 8;        // portable cluster size: n <= 256
+
+// JDFT_CHOL_CLUSTER=0 forces the multi-block path (read on every call).
+static bool cluster_disabled() {
+    const char* e = getenv("JDFT_CHOL_CLUSTER");
+    return e && e[0] == '0';
+}
+
+size_t chol_cluster_smem(int n) {
+    const int NP = (n + CB - 1) / CB * CB;
+    return (2 * (size_t)NP * CLS + (size_t)CB * CLS) * sizeof(float2);
+}
+
+// Factor the 32 x 32 tile A (stride lda, lower triangle used) in place into
+// L (lower, zero above) and write X = L^{-1} (stride ldx); fl[j] = pivot floor.
+__device__ void cl_factor_tile(float2* A, int lda, float2* X, int ldx, const float* fl, float* rp, float* pv,
+                               int* bad) {
+    const int tid = threadIdx.x;
+    auto at = [&](int i, int j) -> float2& { return A[i * lda + j]; };
+    auto pivot = [&](int j) {
+        float d = at(j, j).x;
+        if (!(d > fl[j])) { *bad = 1; d = 1.f; }
+        const float p = sqrtf(d);
+        pv[j] = p;
+        rp[j] = 1.f / p;
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    const int i = tid >> 3, m0 = tid & 7;
+    for (int j = 0; j < CB - 1; ++j) {
+        if (i > j) {
+            const float2 aij = cscale(at(i, j), rp[j] * rp[j]);
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q) {
+                const int m = m0 + 8 * q;
+                if (m > j && m <= i) at(i, m) = csub(at(i, m), cmulc(aij, at(m, j)));
+            }
+            if (i == j + 1 && m0 == ((j + 1) & 7)) pivot(j + 1);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int r = e / CB, c = e % CB;
+        float2 v = make_float2(0.f, 0.f);
+        if (r > c) v = cscale(at(r, c), rp[c]);
+        else if (r == c) v = make_float2(pv[r], 0.f);
+        at(r, c) = v;
+    }
+    __syncthreads();
+    {
+        const int c = tid >> 3, sub = tid & 7;
+        float2 xr[CB / 8];
+#pragma unroll
+        for (int q = 0; q < CB / 8; ++q) xr[q] = make_float2(0.f, 0.f);
+        const int rstart = (tid >> 5) * 4;
+        for (int r = rstart; r < CB; ++r) {
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q) {
+                const int m = sub + 8 * q;
+                if (m >= c && m < r) s = cadd(s, cmul(at(r, m), xr[q]));
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            float2 xv = make_float2(0.f, 0.f);
+            if (r >= c) xv = cscale(make_float2((r == c ? 1.f : 0.f) - s.x, -s.y), rp[r]);
+#pragma unroll
+            for (int q = 0; q < CB / 8; ++q)
+                if (r == sub + 8 * q) xr[q] = xv;
+        }
+#pragma unroll
+        for (int q = 0; q < CB / 8; ++q) X[(sub + 8 * q) * ldx + c] = xr[q];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(CT, 1) chol_cluster_kernel(int n, int NP, const double2* __restrict__ U,
+                                                              float2* __restrict__ W, int* status) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) float2 cls_sm[];
+    float2* a = cls_sm;              // NP x CLS: block column `me` of A, then of L
+    float2* x = a + NP * CLS;        // NP x CLS: block column `me` of X = L^{-1}
+    float2* t = x + NP * CLS;        // CB x CLS: local copy of L_jk, then S_ic
+    __shared__ float fl[CB], rp[CB], pv[CB];
+    __shared__ int bad;
+    const int me = (int)cl.block_rank();
+    const int P = NP / CB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = CT / 32;
+    const int c0 = me * CB;
+    for (int e = tid; e < NP * CB; e += CT) {
+        const int r = e / CB, c = e % CB, gc = c0 + c;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < n && gc < n) v = make_float2((float)U[(size_t)r * n + gc].x, (float)U[(size_t)r * n + gc].y);
+        else if (r == gc) v = make_float2(1.f, 0.f);
+        a[r * CLS + c] = v;
+        x[r * CLS + c] = make_float2(0.f, 0.f);
+    }
+    if (tid < CB) {
+        const int g = c0 + tid;
+        fl[tid] = PivotFloor<float>::v * (g < n ? (float)U[(size_t)g * n + g].x : 1.f);
+    }
+    if (tid == 0) bad = 0;
+    cl.sync();
+    for (int k = 0; k < P; ++k) {
+        if (me == k) {
+            cl_factor_tile(a + c0 * CLS, CLS, x + c0 * CLS, CLS, fl, rp, pv, &bad);
+            // panel: L_ik[r][c] = sum_{m <= c} A_ik[r][m] conj(X_kk[c][m]), a warp per row
+            const float2* xk = x + c0 * CLS;
+            for (int r = c0 + CB + warp; r < NP; r += NW) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int m = 0; m <= lane; ++m) sum = cadd(sum, cmulc(a[r * CLS + m], xk[lane * CLS + m]));
+                __syncwarp();
+                a[r * CLS + lane] = sum;
+            }
+        }
+        cl.sync();
+        if (me > k) {
+            const float2* rk = cl.map_shared_rank(a, k);  // block column k: the panel L_{:,k}
+            for (int e = tid; e < CB * CB; e += CT) {
+                const int r = e / CB, c = e % CB;
+                t[r * CLS + c] = rk[(c0 + r) * CLS + c];
+            }
+            __syncthreads();
+            // A_ij[r][lane] -= sum_m L_ik[r][m] conj(L_jk[lane][m]), a warp per row of block column me
+            for (int r = c0 + warp; r < NP; r += NW) {
+                const float2 lv = rk[r * CLS + lane];
+                float2 sum = make_float2(0.f, 0.f);
+#pragma unroll 8
+                for (int m = 0; m < CB; ++m) {
+                    float2 b;
+                    b.x = __shfl_sync(0xffffffffu, lv.x, m);
+                    b.y = __shfl_sync(0xffffffffu, lv.y, m);
+                    sum = cadd(sum, cmulc(b, t[lane * CLS + m]));
+                }
+                a[r * CLS + lane] = csub(a[r * CLS + lane], sum);
+            }
+            __syncthreads();
+        }
+    }
+    cl.sync();
+    // X_ic for i > me: S = sum_{j=me}^{i-1} L_ij X_jc, X_ic = -X_ii S
+    {
+        const int r = tid >> 3, cb = tid & 7;
+        for (int i = me + 1; i < P; ++i) {
+            float2 acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+            for (int j = me; j < i; ++j) {
+                const float2* Lj = cl.map_shared_rank(a, j);
+#pragma unroll 4
+                for (int m = 0; m < CB; ++m) {
+                    const float2 l = Lj[(CB * i + r) * CLS + m];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(l, x[(CB * j + m) * CLS + cb + 8 * q]));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[r * CLS + cb + 8 * q] = acc[q];
+            __syncthreads();
+            const float2* Xi = cl.map_shared_rank(x, i);
+            float2 o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = make_float2(0.f, 0.f);
+            for (int m = 0; m <= r; ++m) {
+                const float2 d = Xi[(CB * i + r) * CLS + m];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = cadd(o[q], cmul(d, t[m * CLS + cb + 8 * q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[(CB * i + r) * CLS + cb + 8 * q] = make_float2(-o[q].x, -o[q].y);
+            __syncthreads();
+        }
+    }
+    // rows c0 .. c0 + 31 of W = X^dag
+    for (int e = tid; e < CB * n; e += CT) {
+        const int cc = e / n, rr = e - cc * n;
+        if (c0 + cc < n) {
+            const float2 v = x[rr * CLS + cc];
+            W[(size_t)(c0 + cc) * n + rr] = make_float2(v.x, -v.y);
+        }
+    }
+    if (tid == 0 && bad) atomicExch(status, (int)JDFT_ERR_NOT_POSDEF);
+    cl.sync();  // every CTA's shared memory stays in place until the others' remote reads are done
+}
+
+// One launch of chol_cluster_kernel; JDFT_ERR_UNSUPPORTED (nothing launched)
+// when n is too large or the device cannot hold such a cluster.
+static jdft_status run_cluster(int n, const double2* U, float2* W, int* status, cudaStream_t st) {
+    const int P = (n + CB - 1) / CB;
+    if (P > CL_MAX) return JDFT_ERR_UNSUPPORTED;
+    const int NP = P * CB;
+    const size_t smem = chol_cluster_smem(n);
+    if (set_smem_attr((const void*)chol_cluster_kernel, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return JDFT_ERR_UNSUPPORTED;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P, 1, 1);
+    cfg.blockDim = dim3(CT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)chol_cluster_kernel, &cfg) != cudaSuccess ||
+        clusters < 1) {
+        cudaGetLastError();
+        return JDFT_ERR_UNSUPPORTED;
+    }
+    {
+        Trace tr_("chol_cluster", st);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, chol_cluster_kernel, n, NP, U, W, status);
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("chol_cluster: ") + cudaGetErrorString(e));
+    }
+    return check_launch("chol_cluster");
+}
+
 template <typename S>
 static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W, int* status, cudaStream_t st) {
     const int nb = (n + CB - 1) / CB;
@@ -319,6 +561,12 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W
 jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
                                   cudaStream_t st) {
     if (fp64) return run_blocked<double>(n, U, work, (double2*)W, status, st);
+    if (!cluster_disabled()) {
+        // the status word is cleared here (the multi-block path clears it in chol_init_kernel)
+        JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        const jdft_status s = run_cluster(n, U, (float2*)W, status, st);
+        if (s != JDFT_ERR_UNSUPPORTED) return s;
+    }
     return run_blocked<float>(n, U, work, (float2*)W, status, st);
 }
 

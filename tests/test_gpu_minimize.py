@@ -62,6 +62,23 @@ def test_orthonormalize_spans_same_subspace(prec, nb):
     assert np.max(np.abs(P1 - P2)) < tol * np.max(np.abs(P2))
 
 
+@pytest.mark.parametrize("cluster", ["1", "0"])
+def test_orthonormalize_fp32_factorisations(cluster, monkeypatch):
+    """FP32 blocks of 150 bands (5 tiles): the one-launch cluster factorisation
+    (distributed shared memory) and the multi-block one give the same span."""
+    from paper_1708_03621_gb300 import jdft
+    monkeypatch.setenv("JDFT_CHOL_CLUSTER", cluster)
+    w, o, g = systems("mid")
+    nb = 150
+    C = o.coeffs(nb, seed=37)
+    Cd = torch.tensor(C.astype(np.complex64), device="cuda")
+    jdft.jdft_orthonormalize(g.basis, 0, Cd, "fp32")
+    Q = Cd.cpu().numpy().astype(np.complex128).T
+    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(nb), atol=2e-5)
+    L = pw.lowdin(C.T, o.basis.Omega)
+    assert np.max(np.abs(Q @ Q.conj().T - L @ L.conj().T)) < 2e-5 * np.max(np.abs(L @ L.conj().T))
+
+
 @pytest.mark.parametrize("name,nb,prec", [("tiny_cubic", 3, "fp64"), ("mid", 40, "fp64"), ("mid", 40, "fp32"),
                                           ("mid", 100, "tf32x3")])
 def test_orthonormalize_rejects_dependent_bands(name, nb, prec):
