@@ -294,7 +294,7 @@ static bool cluster_disabled() {
 
 size_t chol_cluster_smem(int n) {
     const int NP = (n + CB - 1) / CB * CB;
-    return (2 * (size_t)NP * CLS + (size_t)CB * CLS) * sizeof(float2);
+    return (3 * (size_t)NP * CLS + (size_t)CB * CLS) * sizeof(float2);
 }
 
 // Factor the 32 x 32 tile A (stride lda, lower triangle used) in place into
@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(CT, 1) chol_cluster_kernel(int n, int NP, cons
     extern __shared__ __align__(16) float2 cls_sm[];
     float2* a = cls_sm;              // NP x CLS: block column `me` of A, then of L
     float2* x = a + NP * CLS;        // NP x CLS: block column `me` of X = L^{-1}
-    float2* t = x + NP * CLS;        // CB x CLS: local copy of L_jk, then S_ic
+    float2* pc = x + NP * CLS;       // NP x CLS: local copy of remote rows (panel; L_ij, X_ii tiles)
+    float2* t = pc + NP * CLS;       // CB x CLS: local copy of L_jk, then S_ic
     __shared__ float fl[CB], rp[CB], pv[CB];
     __shared__ int bad;
     const int me = (int)cl.block_rank();
@@ -406,23 +407,18 @@ __global__ void __launch_bounds__(CT, 1) chol_cluster_kernel(int n, int NP, cons
         }
         cl.sync();
         if (me > k) {
-            const float2* rk = cl.map_shared_rank(a, k);  // block column k: the panel L_{:,k}
-            for (int e = tid; e < CB * CB; e += CT) {
-                const int r = e / CB, c = e % CB;
-                t[r * CLS + c] = rk[(c0 + r) * CLS + c];
+            // rows c0 .. NP-1 of the panel L_{:,k}, copied in one pass (independent remote loads)
+            const float2* rk = cl.map_shared_rank(a, k);
+            for (int e = tid; e < (NP - c0) * CB; e += CT) {
+                const int r = c0 + e / CB, c = e % CB;
+                pc[r * CLS + c] = rk[r * CLS + c];
             }
             __syncthreads();
             // A_ij[r][lane] -= sum_m L_ik[r][m] conj(L_jk[lane][m]), a warp per row of block column me
             for (int r = c0 + warp; r < NP; r += NW) {
-                const float2 lv = rk[r * CLS + lane];
                 float2 sum = make_float2(0.f, 0.f);
 #pragma unroll 8
-                for (int m = 0; m < CB; ++m) {
-                    float2 b;
-                    b.x = __shfl_sync(0xffffffffu, lv.x, m);
-                    b.y = __shfl_sync(0xffffffffu, lv.y, m);
-                    sum = cadd(sum, cmulc(b, t[lane * CLS + m]));
-                }
+                for (int m = 0; m < CB; ++m) sum = cadd(sum, cmulc(pc[r * CLS + m], pc[(c0 + lane) * CLS + m]));
                 a[r * CLS + lane] = csub(a[r * CLS + lane], sum);
             }
             __syncthreads();
@@ -436,11 +432,20 @@ __global__ void __launch_bounds__(CT, 1) chol_cluster_kernel(int n, int NP, cons
             float2 acc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+            // the tiles L_ij (j = me .. i-1, held by CTA j) and X_ii (held by CTA i), copied
+            // in one pass into pc: tile j at rows CB j .., X_ii at rows CB i ..
+            for (int j = me; j <= i; ++j) {
+                const float2* src = j < i ? cl.map_shared_rank(a, j) : cl.map_shared_rank(x, i);
+                for (int e = tid; e < CB * CB; e += CT) {
+                    const int rr = e / CB, c = e % CB;
+                    pc[(CB * j + rr) * CLS + c] = src[(CB * i + rr) * CLS + c];
+                }
+            }
+            __syncthreads();
             for (int j = me; j < i; ++j) {
-                const float2* Lj = cl.map_shared_rank(a, j);
 #pragma unroll 4
                 for (int m = 0; m < CB; ++m) {
-                    const float2 l = Lj[(CB * i + r) * CLS + m];
+                    const float2 l = pc[(CB * j + r) * CLS + m];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[q] = cadd(acc[q], cmul(l, x[(CB * j + m) * CLS + cb + 8 * q]));
                 }
@@ -448,12 +453,11 @@ __global__ void __launch_bounds__(CT, 1) chol_cluster_kernel(int n, int NP, cons
 #pragma unroll
             for (int q = 0; q < 4; ++q) t[r * CLS + cb + 8 * q] = acc[q];
             __syncthreads();
-            const float2* Xi = cl.map_shared_rank(x, i);
             float2 o[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = make_float2(0.f, 0.f);
             for (int m = 0; m <= r; ++m) {
-                const float2 d = Xi[(CB * i + r) * CLS + m];
+                const float2 d = pc[(CB * i + r) * CLS + m];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) o[q] = cadd(o[q], cmul(d, t[m * CLS + cb + 8 * q]));
             }
