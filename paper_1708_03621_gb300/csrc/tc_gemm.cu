@@ -9,8 +9,9 @@
 // (re, im) storage: for conj(a) b, Re = sum a'.b'_re and Im = sum a'.b'_im
 // with a' = (ar, ai), b'_re = (br, bi), b'_im = (bi, -br); for a b,
 // b'_re = (br, -bi), b'_im = (bi, br).  A block of 512 threads computes a
-// 128 x NT tile: all threads stage a 32-deep (real) K chunk of A' (hi, lo)
-// and B'_re, B'_im (hi, lo) into shared memory in the no-swizzle K-major
+// 128 x NT tile (NT = 32, 128, or 256 for BF16 operands): all threads stage a
+// 32-deep (real) K chunk of A' (hi, lo) and B'_re, B'_im (hi, lo) into shared
+// memory in the no-swizzle K-major
 // core-matrix layout, one elected thread issues the tcgen05.mma (M = 128,
 // N = NT, K = 8 per instruction, 6 per K step) and commits them to an
 // mbarrier; two stages let the staging of chunk c+1 overlap the products of
@@ -67,7 +68,8 @@ struct TcLayout {
     static constexpr int BI_HI = BR_LO + B_BYTES, BI_LO = BI_HI + B_BYTES;
     static constexpr int STAGE = 2 * A_BYTES + 4 * B_BYTES;
     static constexpr int SMEM = 2 * STAGE + 64;
-    static constexpr uint32_t NCOLS = (2 * NT <= 32) ? 32 : (2 * NT <= 64) ? 64 : (2 * NT <= 128) ? 128 : 256;
+    static constexpr uint32_t NCOLS =
+        (2 * NT <= 32) ? 32 : (2 * NT <= 64) ? 64 : (2 * NT <= 128) ? 128 : (2 * NT <= 256) ? 256 : 512;
 };
 
 // Store the hi and lo parts of the complex value (x, y) at (row, k2), k2 even.
@@ -343,6 +345,16 @@ static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const fl
         const int splits = std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles);
         return tc_launch<32, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
     }
+    if constexpr (FMT == 1) {
+        // BF16 and more than 128 columns: all 256 in one tile (N = 256 products,
+        // all 512 tensor-memory columns), so each A row is staged once
+        if (N > 128 && N <= 256) {
+            StageCN<256, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+            const int tiles = (M + TC_M - 1) / TC_M;
+            const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
+            return tc_launch<256, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
+        }
+    }
     StageCN<128, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
     const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
     const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
@@ -355,6 +367,12 @@ static jdft_status tc_nn(int M, int N, int K, const float2* A, int lda, const fl
     if (N <= 32) {
         StageNN<32, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
         return tc_launch<32, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
+    }
+    if constexpr (FMT == 1) {
+        if (N > 128 && N <= 256) {
+            StageNN<256, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+            return tc_launch<256, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
+        }
     }
     StageNN<128, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
     return tc_launch<128, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);

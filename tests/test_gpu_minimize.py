@@ -44,7 +44,7 @@ def test_subspace_eigs_match_lapack():
 
 
 @pytest.mark.parametrize("nb", [13, 70, 150])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_orthonormalize_spans_same_subspace(prec, nb):
     """13 bands: one-block factorisation; 70 and 150: the blocked multi-block
     one (padded to 3 and 5 tiles; FP32 factorisation for the FP32 blocks)."""
