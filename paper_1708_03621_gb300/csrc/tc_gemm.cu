@@ -39,30 +39,30 @@ __device__ int g_tc_status = 0;
 
 // Operand format: FMT 0 = TF32 (4-byte elements, kind::tf32, K = 8 per
 // instruction), FMT 1 = BF16 (2-byte elements, kind::f16, K = 16).  A stage
-// row holds 2 * TC_CPS real values: 8 (TF32) or 4 (BF16) 16-byte core
+// row holds 2 * CPS real values (CPS = 16 complex): 8 (TF32) or 4 (BF16) 16-byte core
 // columns; 8-row groups are SBO bytes apart (their core matrices plus 16, so
 // consecutive groups start on different banks); each instruction covers two
 // core columns, so a stage takes KSTEPS = KG / 2 instructions per product.
-template <int FMT>
+template <int FMT, int CPS = TC_CPS>
 struct Fmt {
     static constexpr int ELEM = FMT ? 2 : 4;
     static constexpr int PER16 = 16 / ELEM;                 // elements per 16-byte core row
-    static constexpr int KG = 2 * TC_CPS / PER16;           // core columns per row
+    static constexpr int KG = 2 * CPS / PER16;              // core columns per row
     static constexpr int SBO = KG * 128 + 16;
     static constexpr int KSTEPS = KG / 2;
     static constexpr uint32_t IDESC_FMT = FMT ? 1u : 2u;
 };
 
-template <int FMT>
+template <int FMT, int CPS>
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-    using F = Fmt<FMT>;
+    using F = Fmt<FMT, CPS>;
     return (uint32_t)((row >> 3) * F::SBO + (k / F::PER16) * 128 + (row & 7) * 16 + (k % F::PER16) * F::ELEM);
 }
 
-template <int NT, int FMT>
+template <int NT, int FMT, int CPS = TC_CPS>
 struct TcLayout {
-    static constexpr int A_BYTES = (TC_M / 8) * Fmt<FMT>::SBO;
-    static constexpr int B_BYTES = (NT / 8) * Fmt<FMT>::SBO;
+    static constexpr int A_BYTES = (TC_M / 8) * Fmt<FMT, CPS>::SBO;
+    static constexpr int B_BYTES = (NT / 8) * Fmt<FMT, CPS>::SBO;
     static constexpr int A_HI = 0, A_LO = A_BYTES;
     static constexpr int BR_HI = 2 * A_BYTES, BR_LO = BR_HI + B_BYTES;
     static constexpr int BI_HI = BR_LO + B_BYTES, BI_LO = BI_HI + B_BYTES;
@@ -73,9 +73,9 @@ struct TcLayout {
 };
 
 // Store the hi and lo parts of the complex value (x, y) at (row, k2), k2 even.
-template <int FMT>
+template <int FMT, int CPS>
 __device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int row, int k2, float x, float y) {
-    const uint32_t o = core_off<FMT>(row, k2);
+    const uint32_t o = core_off<FMT, CPS>(row, k2);
     if constexpr (FMT == 0) {
         const float hx = tc::to_tf32(x), hy = tc::to_tf32(y);
         const float lx = tc::to_tf32(x - hx), ly = tc::to_tf32(y - hy);
@@ -96,54 +96,57 @@ __device__ __forceinline__ void put_split(char* buf, int off_hi, int off_lo, int
 // two TF32 core matrices (or one BF16 core matrix), so the split stores are
 // free of bank conflicts, and each row's 4 values are one 32-byte sector of
 // the global operand.
+template <int CPS>
 __device__ __forceinline__ void stage_slot(int i, int warp, int lane, int& row, int& k) {
+    constexpr int KQ = CPS / 4;  // quads of k per row
     const int it = warp + TC_WARPS * i;
-    row = 8 * (it >> 2) + (lane & 7);
-    k = 4 * (it & 3) + (lane >> 3);
+    row = 8 * (it / KQ) + (lane & 7);
+    k = 4 * (it % KQ) + (lane >> 3);
 }
 
 // out[m][n] = alpha sum_k conj(A[m][k]) B[n][k] (rows K-contiguous); FP64 atomics into out.
 // The loads of a chunk go to registers first (load), the splits to shared
 // memory after (store), so the next chunk's loads overlap the current
 // chunk's products.
-template <int NT, int FMT>
+template <int NT, int FMT, int CPS_ = TC_CPS>
 struct StageCN {
+    static constexpr int CPS = CPS_;
     const float2* A; int lda; const float2* B; int ldb; int M, N, K;
     double2* out; int ldo; double alpha;
-    static constexpr int PA = TC_M * TC_CPS / TC_THREADS;  // complex values per thread
-    static constexpr int PB = NT * TC_CPS / TC_THREADS;
+    static constexpr int PA = TC_M * CPS / TC_THREADS;  // complex values per thread
+    static constexpr int PB = NT * CPS / TC_THREADS;
     struct Regs { float2 a[PA]; float2 b[PB]; };
     __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int warp, int lane) const {
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const int m = m0 + row;
             r.a[i] = (m < M && kc0 + k < K) ? A[(size_t)m * lda + kc0 + k] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const int n = n0 + row;
             r.b[i] = (n < N && kc0 + k < K) ? B[(size_t)n * ldb + kc0 + k] : make_float2(0.f, 0.f);
         }
     }
     __device__ __forceinline__ void store(const Regs& r, char* buf, int warp, int lane) const {
-        using L = TcLayout<NT, FMT>;
+        using L = TcLayout<NT, FMT, CPS>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
-            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
+            stage_slot<CPS>(i, warp, lane, row, k);
+            put_split<FMT, CPS>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const float2 b = r.b[i];
-            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, b.y);
-            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, -b.x);
+            put_split<FMT, CPS>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, b.y);
+            put_split<FMT, CPS>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, -b.x);
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -157,44 +160,45 @@ struct StageCN {
 // out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
 // The operands are contiguous along M and N: a warp access reads 8
 // consecutive rows of each of 4 k.
-template <int NT, int FMT>
+template <int NT, int FMT, int CPS_ = TC_CPS>
 struct StageNN {
+    static constexpr int CPS = CPS_;
     const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
     float2* out; int ldo;
-    static constexpr int PA = TC_M * TC_CPS / TC_THREADS;
-    static constexpr int PB = NT * TC_CPS / TC_THREADS;
+    static constexpr int PA = TC_M * CPS / TC_THREADS;
+    static constexpr int PB = NT * CPS / TC_THREADS;
     struct Regs { float2 a[PA]; float2 b[PB]; };
     __device__ __forceinline__ void load(Regs& r, int m0, int n0, int kc0, int warp, int lane) const {
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const int m = m0 + row;
             r.a[i] = (m < M && kc0 + k < K) ? A[(size_t)(kc0 + k) * lda + m] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const int n = n0 + row;
             r.b[i] = (n < N && kc0 + k < K) ? Bm[(size_t)(kc0 + k) * ldb + n] : make_float2(0.f, 0.f);
         }
     }
     __device__ __forceinline__ void store(const Regs& r, char* buf, int warp, int lane) const {
-        using L = TcLayout<NT, FMT>;
+        using L = TcLayout<NT, FMT, CPS>;
 #pragma unroll
         for (int i = 0; i < PA; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
-            put_split<FMT>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
+            stage_slot<CPS>(i, warp, lane, row, k);
+            put_split<FMT, CPS>(buf, L::A_HI, L::A_LO, row, 2 * k, r.a[i].x, r.a[i].y);
         }
 #pragma unroll
         for (int i = 0; i < PB; ++i) {
             int row, k;
-            stage_slot(i, warp, lane, row, k);
+            stage_slot<CPS>(i, warp, lane, row, k);
             const float2 b = r.b[i];
-            put_split<FMT>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, -b.y);
-            put_split<FMT>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, b.x);
+            put_split<FMT, CPS>(buf, L::BR_HI, L::BR_LO, row, 2 * k, b.x, -b.y);
+            put_split<FMT, CPS>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, b.x);
         }
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
@@ -209,7 +213,9 @@ struct StageNN {
 
 template <int NT, int FMT, class S>
 __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, int chunks_per_split) {
-    using L = TcLayout<NT, FMT>;
+    constexpr int CPS = S::CPS;
+    using L = TcLayout<NT, FMT, CPS>;
+    using F = Fmt<FMT, CPS>;
     extern __shared__ __align__(1024) char smem[];
     char* stage_buf[2] = {smem, smem + L::STAGE};
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
@@ -228,14 +234,14 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * NT;
     const int c0 = blockIdx.z * chunks_per_split;
     const int c1 = min(nchunks, c0 + chunks_per_split);
-    constexpr uint32_t idesc = tc::instr_desc(Fmt<FMT>::IDESC_FMT, TC_M, NT);
+    constexpr uint32_t idesc = tc::instr_desc(F::IDESC_FMT, TC_M, NT);
     int ok = 1;
     int it = 0;
     // two register sets: the loads of chunk c + 2 are issued right after the
     // products of chunk c, a full chunk before they are stored
     typename S::Regs regs0, regs1;
-    if (c0 < c1) s.load(regs0, m0, n0, c0 * TC_CPS, warp, lane);
-    if (c0 + 1 < c1) s.load(regs1, m0, n0, (c0 + 1) * TC_CPS, warp, lane);
+    if (c0 < c1) s.load(regs0, m0, n0, c0 * CPS, warp, lane);
+    if (c0 + 1 < c1) s.load(regs1, m0, n0, (c0 + 1) * CPS, warp, lane);
     auto step = [&](typename S::Regs& regs, char* buf, uint64_t* bar) -> bool {
         if (it >= 2) {
             // the products issued from this buffer two chunks ago must be done before restaging it
@@ -249,9 +255,9 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
         if (tid == 0) {
             tc::tc_fence_after_sync();
             const uint32_t base = tc::smem_addr(buf);
-            constexpr uint32_t LBO = 128, SBO = Fmt<FMT>::SBO;
+            constexpr uint32_t LBO = 128, SBO = F::SBO;
 #pragma unroll
-            for (int kk = 0; kk < Fmt<FMT>::KSTEPS; ++kk) {
+            for (int kk = 0; kk < F::KSTEPS; ++kk) {
                 const uint32_t off = kk * 256;
                 const uint64_t ahi = tc::smem_desc(base + L::A_HI + off, LBO, SBO);
                 const uint64_t alo = tc::smem_desc(base + L::A_LO + off, LBO, SBO);
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             tc::mma_commit(bar);
         }
         const int c = c0 + it;
-        if (c + 2 < c1) s.load(regs, m0, n0, (c + 2) * TC_CPS, warp, lane);  // overlaps the products just issued
+        if (c + 2 < c1) s.load(regs, m0, n0, (c + 2) * CPS, warp, lane);  // overlaps the products just issued
         ++it;
         return true;
     };
@@ -319,11 +325,12 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
 
 template <int NT, int FMT, class S>
 static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const char* name, cudaStream_t st) {
-    using L = TcLayout<NT, FMT>;
+    using L = TcLayout<NT, FMT, S::CPS>;
+    static_assert(L::SMEM <= 227 * 1024, "tensor-core GEMM stages exceed shared memory");
     auto kern = tc_zgemm_kernel<NT, FMT, S>;
     cudaError_t e = set_smem_attr((const void*)kern, L::SMEM);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
-    const int nchunks = (K + TC_CPS - 1) / TC_CPS;
+    const int nchunks = (K + S::CPS - 1) / S::CPS;
     splits = std::max(1, std::min(splits, nchunks));
     const int cps = (nchunks + splits - 1) / splits;
     splits = (nchunks + cps - 1) / cps;
@@ -338,26 +345,20 @@ static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const 
 template <int FMT>
 static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
                          double alpha, cudaStream_t st) {
-    const int nchunks = (K + TC_CPS - 1) / TC_CPS;
+    const int nchunks = (K + TC_CPS - 1) / TC_CPS;  // at the default stage depth
     if (N <= 32) {
         StageCN<32, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
         const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 31) / 32);
         const int splits = std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles);
         return tc_launch<32, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
     }
-    if constexpr (FMT == 1) {
-        // BF16 and more than 128 columns: all 256 in one tile (N = 256 products,
-        // all 512 tensor-memory columns), so each A row is staged once
-        if (N > 128 && N <= 256) {
-            StageCN<256, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
-            const int tiles = (M + TC_M - 1) / TC_M;
-            const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
-            return tc_launch<256, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
-        }
-    }
-    StageCN<128, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+    // 16 complex K per stage (32 for BF16, 256 contiguous bytes per operand
+    // row, measured 10 % slower on the 256 x 256 x 62 759 products)
+    constexpr int CPS = TC_CPS;
+    StageCN<128, FMT, CPS> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
     const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
-    const int splits = std::min(nchunks / 4 + 1, (152 + tiles - 1) / tiles);
+    const int nck = (K + CPS - 1) / CPS;
+    const int splits = std::min(nck / 4 + 1, (152 + tiles - 1) / tiles);
     return tc_launch<128, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
 }
 
@@ -369,6 +370,8 @@ static jdft_status tc_nn(int M, int N, int K, const float2* A, int lda, const fl
         return tc_launch<32, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
     }
     if constexpr (FMT == 1) {
+        // BF16 and more than 128 columns: all 256 in one tile (N = 256 products,
+        // all 512 tensor-memory columns), so each row of P or C is staged once
         if (N > 128 && N <= 256) {
             StageNN<256, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
             return tc_launch<256, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
