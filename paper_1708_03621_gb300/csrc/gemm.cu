@@ -95,7 +95,7 @@ constexpr int NN_BM = 64, NN_BN = 16, NN_BK = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) zgemm_nn_kernel(int M, int N, int K, const c_t<T>* __restrict__ A, int lda,
                                                        const c_t<T>* __restrict__ Bm, int ldb, c_t<T>* __restrict__ out,
-                                                       int ldo) {
+                                                       int ldo, bool accumulate) {
     __shared__ c_t<T> As[NN_BK][NN_BM];
     __shared__ c_t<T> Bs[NN_BK][NN_BN];
     const int m0 = blockIdx.x * NN_BM, n0 = blockIdx.y * NN_BN;
@@ -132,19 +132,25 @@ __global__ void __launch_bounds__(256) zgemm_nn_kernel(int M, int N, int K, cons
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tq * 4 + j;
-            if (n < N) out[(size_t)n * ldo + m] = cadd(out[(size_t)n * ldo + m], acc[j]);
+            if (n < N) out[(size_t)n * ldo + m] = accumulate ? cadd(out[(size_t)n * ldo + m], acc[j]) : acc[j];
         }
     }
 }
 
 template <typename T>
 jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb, c_t<T>* out,
-                         int ldo, cudaStream_t st) {
-    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+                         int ldo, cudaStream_t st, bool accumulate) {
+    if (M == 0 || N == 0) return JDFT_OK;
+    if (K == 0) {
+        if (!accumulate)
+            for (int n = 0; n < N; ++n)
+                JDFT_CUDA_TRY(cudaMemsetAsync(out + (size_t)n * ldo, 0, (size_t)M * sizeof(c_t<T>), st));
+        return JDFT_OK;
+    }
     dim3 grid((M + NN_BM - 1) / NN_BM, (N + NN_BN - 1) / NN_BN);
     {
         Trace tr_("zgemm_nn", st);
-        zgemm_nn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, Bm, ldb, out, ldo);
+        zgemm_nn_kernel<T><<<grid, 256, 0, st>>>(M, N, K, A, lda, Bm, ldb, out, ldo, accumulate);
     }
     return check_launch("zgemm_nn");
 }
@@ -213,15 +219,15 @@ jdft_status gemm_cn<float>(jdft_prec prec, int M, int N, int K, const float2* A,
 }
 template <>
 jdft_status gemm_nn_acc<double>(jdft_prec, int M, int N, int K, const double2* A, int lda, const double2* Bm, int ldb,
-                                double2* out, int ldo, cudaStream_t st) {
-    return zgemm_nn_acc<double>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+                                double2* out, int ldo, cudaStream_t st, bool accumulate) {
+    return zgemm_nn_acc<double>(M, N, K, A, lda, Bm, ldb, out, ldo, st, accumulate);
 }
 template <>
 jdft_status gemm_nn_acc<float>(jdft_prec prec, int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb,
-                               float2* out, int ldo, cudaStream_t st) {
+                               float2* out, int ldo, cudaStream_t st, bool accumulate) {
     if (prec == JDFT_TF32X3 || prec == JDFT_BF16X3)
-        return tc_zgemm_nn_acc(M, N, K, A, lda, Bm, ldb, out, ldo, prec == JDFT_BF16X3, st);
-    return zgemm_nn_acc<float>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+        return tc_zgemm_nn_acc(M, N, K, A, lda, Bm, ldb, out, ldo, prec == JDFT_BF16X3, st, accumulate);
+    return zgemm_nn_acc<float>(M, N, K, A, lda, Bm, ldb, out, ldo, st, accumulate);
 }
 
 template jdft_status zgemm_cn<double>(int, int, int, const double2*, int, const double2*, int, double2*, int, double,
@@ -229,9 +235,9 @@ template jdft_status zgemm_cn<double>(int, int, int, const double2*, int, const 
 template jdft_status zgemm_cn<float>(int, int, int, const float2*, int, const float2*, int, double2*, int, double,
                                      cudaStream_t);
 template jdft_status zgemm_nn_acc<double>(int, int, int, const double2*, int, const double2*, int, double2*, int,
-                                          cudaStream_t);
+                                          cudaStream_t, bool);
 template jdft_status zgemm_nn_acc<float>(int, int, int, const float2*, int, const float2*, int, float2*, int,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template jdft_status nonlocal_accumulate<double>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,
                                                  cudaStream_t);
 template jdft_status nonlocal_accumulate<float>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,

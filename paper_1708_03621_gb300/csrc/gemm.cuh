@@ -13,18 +13,18 @@ template <typename T>
 jdft_status zgemm_cn(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* B, int ldb, double2* out, int ldo,
                      double scale, cudaStream_t st);
 
-// out[n * ldo + m] += sum_i A[i * lda + m] * Bm[i * ldb + n]
+// out[n * ldo + m] += sum_i A[i * lda + m] * Bm[i * ldb + n]   (= instead of += when !accumulate)
 // A: K rows of length M (projector-major P), Bm: K x N row-major, out band-major.
 template <typename T>
 jdft_status zgemm_nn_acc(int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb, c_t<T>* out,
-                         int ldo, cudaStream_t st);
+                         int ldo, cudaStream_t st, bool accumulate = true);
 
 // Tensor-core versions (FP32 inputs split into hi + lo, 3 products) of the two
 // products above: TF32 pieces (bf16 = false) or BF16 pieces (bf16 = true).
 jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
                         double alpha, bool bf16, cudaStream_t st);
 jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
-                            int ldo, bool bf16, cudaStream_t st);
+                            int ldo, bool bf16, cudaStream_t st, bool accumulate = true);
 
 // Precision dispatch: JDFT_TF32X3 and JDFT_BF16X3 run the tensor-core
 // versions (T = float only), the other precisions the CUDA-core ones.
@@ -33,7 +33,7 @@ jdft_status gemm_cn(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int ld
                     double2* out, int ldo, double alpha, cudaStream_t st);
 template <typename T>
 jdft_status gemm_nn_acc(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb,
-                        c_t<T>* out, int ldo, cudaStream_t st);
+                        c_t<T>* out, int ldo, cudaStream_t st, bool accumulate = true);
 
 // Workspace bytes the nonlocal term needs for nb bands.
 size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem);

@@ -432,8 +432,7 @@ struct MinState {
     }
     // Z = X . W  (W already in block type)
     jdft_status rotate(const c_t<T>* X, c_t<T>* Z) {
-        JDFT_CUDA_TRY(cudaMemsetAsync(Z, 0, (size_t)nb * ld * sizeof(c_t<T>), st));
-        return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, W, nb, Z, ld, st);
+        return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, W, nb, Z, ld, st, false);
     }
     jdft_status hermitize(double2* A, double* tr) {
         {
@@ -633,8 +632,7 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
         return s;
     if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
     JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
-    JDFT_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nb * ldc * sizeof(c_t<T>), st));
-    if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st))) return s;
+    if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st, false))) return s;
     int hs = 0;
     JDFT_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));

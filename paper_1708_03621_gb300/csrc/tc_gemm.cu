@@ -164,7 +164,7 @@ template <int NT, int FMT, int CPS_ = TC_CPS>
 struct StageNN {
     static constexpr int CPS = CPS_;
     const float2* A; int lda; const float2* Bm; int ldb; int M, N, K;
-    float2* out; int ldo;
+    float2* out; int ldo; bool accumulate;
     static constexpr int PA = TC_M * CPS / TC_THREADS;
     static constexpr int PB = NT * CPS / TC_THREADS;
     struct Regs { float2 a[PA]; float2 b[PB]; };
@@ -203,7 +203,7 @@ struct StageNN {
     }
     __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
         if (m < M && n < N) {
-            float2 v = out[(size_t)n * ldo + m];
+            float2 v = accumulate ? out[(size_t)n * ldo + m] : make_float2(0.f, 0.f);
             v.x += re;
             v.y += im;
             out[(size_t)n * ldo + m] = v;
@@ -364,20 +364,20 @@ static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const fl
 
 template <int FMT>
 static jdft_status tc_nn(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out, int ldo,
-                         cudaStream_t st) {
+                         bool accumulate, cudaStream_t st) {
     if (N <= 32) {
-        StageNN<32, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+        StageNN<32, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo, accumulate};
         return tc_launch<32, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
     }
     if constexpr (FMT == 1) {
         // BF16 and more than 128 columns: all 256 in one tile (N = 256 products,
         // all 512 tensor-memory columns), so each row of P or C is staged once
         if (N > 128 && N <= 256) {
-            StageNN<256, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+            StageNN<256, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo, accumulate};
             return tc_launch<256, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
         }
     }
-    StageNN<128, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo};
+    StageNN<128, FMT> s{A, lda, Bm, ldb, M, N, K, out, ldo, accumulate};
     return tc_launch<128, FMT>(s, M, N, K, 1, "tc_zgemm_nn", st);
 }
 
@@ -389,9 +389,11 @@ jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const flo
 }
 
 jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
-                            int ldo, bool bf16, cudaStream_t st) {
-    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
-    return bf16 ? tc_nn<1>(M, N, K, A, lda, Bm, ldb, out, ldo, st) : tc_nn<0>(M, N, K, A, lda, Bm, ldb, out, ldo, st);
+                            int ldo, bool bf16, cudaStream_t st, bool accumulate) {
+    if (M == 0 || N == 0) return JDFT_OK;
+    if (K == 0) return accumulate ? JDFT_OK : zgemm_nn_acc<float>(M, N, 0, A, lda, Bm, ldb, out, ldo, st, false);
+    return bf16 ? tc_nn<1>(M, N, K, A, lda, Bm, ldb, out, ldo, accumulate, st)
+                : tc_nn<0>(M, N, K, A, lda, Bm, ldb, out, ldo, accumulate, st);
 }
 
 }  // namespace jdft
