@@ -304,6 +304,14 @@ def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
             "frac": round((k["achieved_gbs"] or 0) / hbm, 4), "peak_source": src_hbm}
 
 
+# DRAM bytes (read + write) per band of the dominant kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of a 34-band launch on
+# the 128^3 workload; profiles/plane_apply_density_fast_128cubed_bf16x3.md).
+# ncu replays with cold caches, so this is an upper bound on the warm traffic.
+# Only valid for the kernel version it was taken on: set to None when it changes.
+TRAFFIC_PER_BAND = {"plane_apply_density_fast": (91.659776e6 + 27.659264e6) / 34}
+
+
 def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:
     if prec == "fp64":
         return FP64_NOMINAL_TFLOPS
@@ -364,7 +372,9 @@ def run_ours(args, world, rank, local, pg):
     top = kernels[0]
     roof = dict(top["roofline"])
     roof["kernel"] = top["name"]
-    roof["traffic"] = None
+    tpb = TRAFFIC_PER_BAND.get(top["name"]) if args.workload == "large" else None
+    # per launch, like `achieved`: bytes per band x the bands one launch processes on average
+    roof["traffic"] = round(tpb * p.nb * args.steps / top["launches"]) if tpb else None
 
     # ---- end to end through the public API with host buffers ----
     Bi, Bo = p.io_bytes()
