@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-slab", action="store_true", help="skip the 1024-band, 4 k-point slab section")
     ap.add_argument("--nbands", type=int, default=0, help="bands of the block (0 = the workload's)")
     ap.add_argument("--workload", default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -166,13 +167,13 @@ class Problem:
         import torch
 
         from paper_1708_03621_gb300 import jdft
-        from synth import WORKLOADS, atom_positions, random_coefficients
+        from synth import WORKLOADS, random_coefficients, workload_atoms
         self.jdft = jdft
         self.prec = prec
         w = WORKLOADS[wname]
         self.w = w
         self.dev = device
-        atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+        atoms = workload_atoms(w)
         self.basis = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
         self.N = int(np.prod(w.S))
         self.npw = self.basis.npw(0)
@@ -446,6 +447,9 @@ def run_ours(args, world, rank, local, pg):
     cg = None
     if not args.no_cg and world == 1:
         cg = cg_measurements(args.prec if args.prec != "fp64" else "fp32", dev)
+    slab = None
+    if not args.no_slab and world == 1:
+        slab = slab_measurements(args.prec if args.prec != "fp64" else "bf16x3", dev)
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
@@ -462,6 +466,7 @@ def run_ours(args, world, rank, local, pg):
         "fp64_path": fp64,
         "cg": cg,
         "batch": batch,
+        "slab": slab,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
@@ -529,6 +534,119 @@ def cg_measurements(prec: str, device, log=lambda *_: None) -> dict:
     out["small_time_to_dE_1e-6"] = res
     out["small_E_ref_Ha"] = E_ref
     b.close()
+    return out
+
+
+def slab_measurements(prec: str, device) -> dict:
+    """Configuration 5, the 40 x 20 x 20 bohr slab (box 256 x 128 x 128, 125 k
+    plane waves, 256 atoms, 1024 projectors, 1024 bands, 4 k-points):
+
+    * mixed-precision H C + C^dag H C over the band block at every k-point
+      (one pass = 4 x 1024 band-applies), CUDA events, after one warm-up pass;
+    * the same at k-point 0 on the plain FP64 GPU path, and the mixed result's
+      errors against it;
+    * one learned-preconditioned mixed band-CG iteration at k-point 0 (wall
+      time of 4-iteration minus 2-iteration runs, / 2).
+
+    The band block is drawn on the GPU from a seeded generator with the same
+    recipe as the other workloads: complex N(0, 1) / (1 + |k+G|^2), each band
+    normalised to Omega sum |C|^2 = 1.
+    """
+    import torch
+
+    from paper_1708_03621_gb300 import jdft, learned
+    from synth import WORKLOADS, workload_atoms
+    w = WORKLOADS["slab"]
+    atoms = workload_atoms(w)
+    b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+    omega = b.info(0)["omega"]
+    V = torch.empty(int(np.prod(w.S)), dtype=torch.float64, device=device)
+    jdft.jdft_gaussian_potential(b, atoms, V)
+    jdft.jdft_set_potential(b, V)
+    del V
+    D = torch.tensor(np.diag(np.tile([0.5, -0.3, -0.3, -0.3], w.natoms)), device=device)
+    Bm = 2 * np.pi * np.linalg.inv(w.R).T
+    blocks = []
+    for ik in range(w.nk):
+        npw = b.npw(ik)
+        P = torch.empty((4 * w.natoms, npw), dtype=torch.complex128, device=device)
+        jdft.jdft_gaussian_projectors(b, ik, atoms, P)
+        jdft.jdft_set_projectors(b, ik, P, D)
+        del P
+        q = (b.gvectors(ik).astype(np.float64) + np.asarray(w.kfrac[ik])) @ Bm.T
+        damp = torch.tensor(1.0 / (1.0 + np.sum(q * q, 1)), dtype=torch.float32, device=device)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(w.seed_coeffs * 10 + ik)
+        Y = torch.view_as_complex(torch.randn((w.nbands, npw, 2), generator=gen, device=device,
+                                              dtype=torch.float32)) * damp[None, :]
+        Y /= torch.sqrt(omega * torch.sum(Y.abs() ** 2, dim=1, keepdim=True))
+        blocks.append((Y, torch.empty_like(Y)))
+    nb = w.nbands
+    CHC = torch.empty((nb, nb), dtype=torch.complex128, device=device)
+
+    def mixed_pass():
+        for ik, (C, HC) in enumerate(blocks):
+            jdft.jdft_apply_H(b, ik, C, HC, prec)
+            jdft.jdft_subspace(b, ik, C, HC, CHC, None, prec)
+
+    stream = torch.cuda.current_stream()
+    mixed_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record(stream)
+    for _ in range(reps):
+        mixed_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_mixed = e0.elapsed_time(e1) / reps
+    out = {"workload": "slab 40x20x20 bohr, Ecut 30, box 256x128x128, 256 atoms, 1024 projectors, "
+                       "1024 bands x 4 k-points; pass = H C + C^dag H C at every k",
+           "npw": [b.npw(ik) for ik in range(w.nk)], "precision": prec,
+           "mixed_ms_per_pass": round(t_mixed, 3),
+           "mixed_band_applies_per_s": round(w.nk * nb / (t_mixed / 1e3), 1)}
+    # plain FP64 at k-point 0
+    C0, HC0 = blocks[0]
+    C64 = C0.to(torch.complex128)
+    HC64 = torch.empty_like(C64)
+    CHC64 = torch.empty_like(CHC)
+    jdft.jdft_apply_H(b, 0, C64, HC64, "fp64")
+    torch.cuda.synchronize()
+    e0.record(stream)
+    jdft.jdft_apply_H(b, 0, C64, HC64, "fp64")
+    jdft.jdft_subspace(b, 0, C64, HC64, CHC64, None, "fp64")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1)
+    out["fp64_ms_per_k"] = round(t64, 3)
+    out["fp64_band_applies_per_s"] = round(nb / (t64 / 1e3), 1)
+    out["mixed_vs_fp64_per_k"] = round((t64 / 1e3) / (t_mixed / 1e3 / w.nk), 2)
+    jdft.jdft_apply_H(b, 0, C0, HC0, prec)
+    jdft.jdft_subspace(b, 0, C0, HC0, CHC, None, prec)
+    torch.cuda.synchronize()
+    num = torch.linalg.vector_norm(HC0.to(torch.complex128) - HC64, dim=1)
+    den = torch.linalg.vector_norm(HC64, dim=1)
+    out["hc_band_rel_max"] = float(f"{float(torch.max(num / den)):.3e}")
+    out["chc_rel"] = float(f"{float(torch.max(torch.abs(CHC - CHC64)) / torch.max(torch.abs(CHC64))):.3e}")
+    del C64, HC64, CHC64
+    # one learned-preconditioned mixed band-CG iteration at k-point 0
+    wts = learned.load_weights()
+    mlp = jdft.Mlp(wts) if wts is not None else None
+    pc = "mlp" if mlp is not None else "teter"
+    wall = {}
+    for k in (2, 4):
+        C = C0.to(torch.complex128)  # the minimiser takes (and returns) an FP64 block
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jdft.jdft_minimize_bands(b, 0, C, tol=1e-30, max_iter=k, precond=pc, prec=prec, switch_tol=1e-30,
+                                 check=False, mlp=mlp)
+        wall[k] = time.perf_counter() - t0
+        del C
+    out["cg_preconditioner"] = pc
+    out["cg_iteration_ms"] = round(max(1e-9, (wall[4] - wall[2]) / 2) * 1e3, 3)
+    del blocks
+    b.close()
+    torch.cuda.empty_cache()
     return out
 
 

@@ -349,7 +349,7 @@ static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const fl
     if (N <= 32) {
         StageCN<32, FMT> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
         const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 31) / 32);
-        const int splits = std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles);
+        const int splits = std::max(std::min(nchunks / 4 + 1, (152 * 2 + tiles - 1) / tiles), (nchunks + 255) / 256);
         return tc_launch<32, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
     }
     // 16 complex K per stage (32 for BF16, 256 contiguous bytes per operand
@@ -358,7 +358,12 @@ static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const fl
     StageCN<128, FMT, CPS> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
     const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
     const int nck = (K + CPS - 1) / CPS;
-    const int splits = std::min(nck / 4 + 1, (152 + tiles - 1) / tiles);
+    // at most kMaxChunks chunks (4096 complex K) accumulate in tensor memory per
+    // block: the FP32 accumulation there loses precision in proportion to the
+    // number of accumulating products (about 6e-4 relative over 42 k complex K,
+    // 2e-5 over 1.6 k); the split partial sums meet in FP64
+    constexpr int kMaxChunks = 4096 / CPS;
+    const int splits = std::max(std::min(nck / 4 + 1, (152 + tiles - 1) / tiles), (nck + kMaxChunks - 1) / kMaxChunks);
     return tc_launch<128, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
 }
 

@@ -24,9 +24,9 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "p
 def build_cell(w, device):
     """Basis, potential and projectors of a synthetic workload, set up on the GPU."""
     import torch
-    from synth import atom_positions
+    from synth import workload_atoms
     b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
-    atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+    atoms = workload_atoms(w)
     V = torch.empty(int(np.prod(w.S)), dtype=torch.float64, device=device)
     jdft.jdft_gaussian_potential(b, atoms, V)
     jdft.jdft_set_potential(b, V)

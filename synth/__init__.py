@@ -11,6 +11,9 @@ Workloads (all cells cubic unless stated; lengths in bohr, energies in Ha):
           8 atoms at uniform-random positions, 4 Gaussian projectors per atom.
   large   L = 20, E_cut = 30, box 128^3, k_frac = (0.1, 0.2, 0.3), 256 bands,
           64 atoms, 256 projectors.
+  slab    orthorhombic 40 x 20 x 20, E_cut = 30, box 256 x 128 x 128,
+          256 atoms in a perturbed fcc slab filling x < 20 (vacuum above),
+          1024 projectors, 1024 bands, 4 k-points uniform in the zone, w = 1/4.
   tiny_*  small boxes for exhaustive element-by-element checks.
 """
 from __future__ import annotations
@@ -35,6 +38,7 @@ class Workload:
     seed_atoms: int
     seed_coeffs: int
     kweights: tuple = field(default=())
+    layout: str = "uniform"   # atom placement: "uniform" in the cell, or "fcc_slab"
 
     @property
     def R(self) -> np.ndarray:
@@ -51,6 +55,11 @@ class Workload:
         return np.full(self.nk, 1.0 / self.nk)
 
 
+def _kpoints(nk: int, seed: int) -> tuple:
+    rng = np.random.default_rng(seed)
+    return tuple(tuple(float(x) for x in row) for row in rng.uniform(-0.5, 0.5, size=(nk, 3)))
+
+
 WORKLOADS = {
     "small": Workload("small", (10.0, 10.0, 10.0), 20.0, (48, 48, 48),
                       ((0.1, 0.2, 0.3),), 8, 16, 1, 2),
@@ -62,6 +71,8 @@ WORKLOADS = {
                            ((0.25, -0.1, 0.4),), 3, 5, 103, 104),
     "mid": Workload("mid", (10.0, 10.0, 10.0), 12.0, (40, 40, 40),
                     ((0.1, 0.2, 0.3),), 8, 24, 105, 106),
+    "slab": Workload("slab", (40.0, 20.0, 20.0), 30.0, (256, 128, 128), _kpoints(4, 51), 256, 1024, 51, 52,
+                     (0.25, 0.25, 0.25, 0.25), "fcc_slab"),
 }
 
 
@@ -72,6 +83,27 @@ def atom_positions(R: np.ndarray, natoms: int, seed: int) -> np.ndarray:
     return frac @ np.asarray(R, dtype=np.float64).T
 
 
+def fcc_slab_positions(seed: int, a: float = 5.0, cells=(4, 4, 4), sigma: float = 0.2) -> np.ndarray:
+    """Cartesian positions of an fcc crystal of conventional edge a (4 atoms per
+    cell, cells[0] x cells[1] x cells[2] cells from the origin), each atom
+    displaced by independent N(0, sigma^2) per axis."""
+    basis = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+    grid = np.array([(i, j, k) for i in range(cells[0]) for j in range(cells[1]) for k in range(cells[2])],
+                    dtype=np.float64)
+    pos = (grid[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    rng = np.random.default_rng(seed)
+    return pos + rng.normal(0.0, sigma, size=pos.shape)
+
+
+def workload_atoms(w: Workload) -> np.ndarray:
+    """The workload's atom positions (Cartesian, natoms x 3)."""
+    if w.layout == "fcc_slab":
+        pos = fcc_slab_positions(w.seed_atoms)
+        assert pos.shape[0] == w.natoms
+        return pos
+    return atom_positions(w.R, w.natoms, w.seed_atoms)
+
+
 def random_coefficients(kinetic2: np.ndarray, nbands: int, seed: int) -> np.ndarray:
     """Band-major random block Y (nbands x npw, complex128).
 
@@ -80,7 +112,10 @@ def random_coefficients(kinetic2: np.ndarray, nbands: int, seed: int) -> np.ndar
     """
     rng = np.random.default_rng(seed)
     z = rng.standard_normal(size=(nbands, kinetic2.size, 2))
-    return (z[..., 0] + 1j * z[..., 1]) / (1.0 + np.asarray(kinetic2)[None, :])
+    # (re, im) pairs are adjacent: the same draws viewed as complex, damped in place
+    y = z.reshape(nbands, -1).view(np.complex128)
+    y /= (1.0 + np.asarray(kinetic2, dtype=np.float64))[None, :]
+    return y
 
 
 def random_kpoints(nk: int, seed: int) -> np.ndarray:

@@ -5,14 +5,14 @@ from __future__ import annotations
 import numpy as np
 
 from oracle import planewave as pw
-from synth import WORKLOADS, Workload, atom_positions, random_coefficients
+from synth import WORKLOADS, Workload, atom_positions, random_coefficients, workload_atoms
 
 
 class OracleSystem:
     def __init__(self, w: Workload, ik: int = 0, with_projectors: bool = True):
         self.w = w
         self.R = w.R
-        self.atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+        self.atoms = workload_atoms(w)
         self.basis = pw.Basis.build(w.R, w.S, w.kfrac[ik], w.ecut)
         self.V = pw.vloc_realspace(w.R, w.S, self.atoms)
         if with_projectors:
