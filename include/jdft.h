@@ -182,10 +182,11 @@ jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, co
  * (O diagonal in the plane-wave basis, Sec. 2.1).  C: device, band-major
  * (ldc >= npw), complex128 for JDFT_FP64 and complex64 otherwise; the products
  * C^dag C and C L^{-dag} run at `prec` (C^dag C accumulated in FP64), the
- * Cholesky factorisation and triangular inverse on the GPU in FP64 for
- * JDFT_FP64 and in FP32 for the FP32 precisions (n <= 256: one launch of a
- * thread-block cluster sharing the matrix through distributed shared memory;
- * JDFT_CHOL_CLUSTER=0 selects the multi-block path).  Uses (and may grow) the basis
+ * Cholesky factorisation and triangular inverse on the GPU in FP64 for every
+ * precision (L^{-dag} rounded to the block type).  JDFT_CHOL_FP32=1 factors
+ * FP32 blocks in FP32 instead (n <= 256: one launch of a thread-block cluster
+ * sharing the matrix through distributed shared memory; JDFT_CHOL_CLUSTER=0
+ * selects the multi-block path).  Uses (and may grow) the basis
  * workspace.  Synchronous.  JDFT_ERR_NOT_POSDEF if the bands are linearly
  * dependent. */
 jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,

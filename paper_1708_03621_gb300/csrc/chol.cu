@@ -9,17 +9,18 @@
 //                         S_ik = sum_{j=k}^{i-1} L_ij X_jk (atomics over j),
 //                         X_ik = -X_ii S_ik
 //   W = X^dag in the caller's block type.
-// Working precision S: FP64 for FP64 blocks; FP32 for the FP32 blocks of the
-// mixed precisions (U itself is accumulated in FP64 by the caller, and an FP32
-// block carries ~1e-7 relative error whatever W is).  FP64 units are scarce on
-// this GPU (about two FP64 FMAs per clock per SM), so the tile products are
-// split into 16 x 16 output quadrants on separate blocks, and the diagonal
-// tile takes one block barrier per column with each reciprocal taken once.
+// Working precision S: FP64 for every block precision (W is rounded to the
+// block type at the end); FP32 for FP32 blocks only on request
+// (JDFT_CHOL_FP32=1).  FP64 units are scarce on this GPU (about two FP64 FMAs
+// per clock per SM), so the tile products are split into 16 x 16 output
+// quadrants on separate blocks, and the diagonal tile takes one block barrier
+// per column with each reciprocal taken once.
 // The matrix is padded to a multiple of 32 with identity rows.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "chol.cuh"
 #include "profile.cuh"
@@ -148,6 +149,101 @@ __global__ void __launch_bounds__(CT) chol_diag_kernel(int N, int k, c_t<S>* __r
     if (tid == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
 }
 
+// FP64 diagonal tile.  FP64 warp instructions occupy the SM's FP64 units for
+// the same time whatever the number of active lanes, so the work is packed
+// into full warps:
+//  * factor: step j updates the active pairs (i, m), j < m <= i, read from a
+//    table of the 528 lower-triangle pairs ordered by m descending (the
+//    active pairs of step j are its first (31 - j)(32 - j) / 2 entries);
+//  * inverse of the 2 x 2 block form L = [[A, 0], [B, C]] (16 x 16 blocks):
+//    A^{-1} and C^{-1} by column substitution on two warps at once, then
+//    X_21 = -C^{-1} (B A^{-1}) as two dense 16 x 16 products on all threads.
+__global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* __restrict__ L,
+                                                         double2* __restrict__ X, const double* __restrict__ dg,
+                                                         int* status) {
+    constexpr int H = CB / 2;
+    __shared__ double2 a[CB][CB + 1];
+    __shared__ double2 x[CB][CB + 1];
+    __shared__ double2 tq[H][H + 1];
+    __shared__ unsigned short pr[CB * (CB + 1) / 2];
+    __shared__ double rp[CB], pv[CB], fl[CB];
+    __shared__ int bad;
+    const int r0 = k * CB, tid = threadIdx.x;
+    for (int e = tid; e < CB * CB; e += CT) {
+        const int i = e / CB, j = e % CB;
+        a[i][j] = L[(size_t)(r0 + i) * N + r0 + j];
+        x[i][j] = make_double2(0.0, 0.0);
+    }
+    // pair table: m descending, then i ascending; entry = i << 8 | m
+    if (tid < CB) {
+        const int m = CB - 1 - tid;                   // rank of m in descending order
+        int off = 0;
+        for (int mm = CB - 1; mm > m; --mm) off += CB - mm;
+        for (int i = m; i < CB; ++i) pr[off + i - m] = (unsigned short)(i << 8 | m);
+        fl[tid] = PivotFloor<double>::v * dg[r0 + tid];
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    auto pivot = [&](int j) {
+        double d = a[j][j].x;
+        if (!(d > fl[j])) { bad = 1; d = 1.0; }
+        const double p = sqrt(d);
+        pv[j] = p;
+        rp[j] = 1.0 / p;
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    for (int j = 0; j < CB - 1; ++j) {
+        const int cnt = (CB - 1 - j) * (CB - j) / 2;  // pairs with m > j
+        const double rd = rp[j] * rp[j];
+        for (int e = tid; e < cnt; e += CT) {
+            const int i = pr[e] >> 8, m = pr[e] & 0xff;
+            a[i][m] = csub(a[i][m], cmulc(cscale(a[i][j], rd), a[m][j]));
+            if (i == j + 1 && m == j + 1) pivot(j + 1);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < CB * CB; e += CT) {
+        const int r = e / CB, c = e % CB;
+        double2 v = make_double2(0.0, 0.0);
+        if (r > c) v = cscale(a[r][c], rp[c]);
+        else if (r == c) v = make_double2(pv[r], 0.0);
+        a[r][c] = v;
+        L[(size_t)(r0 + r) * N + r0 + c] = v;
+    }
+    __syncthreads();
+    // A^{-1} (warp 0) and C^{-1} (warp 1): lane c < 16 computes column c top-down
+    {
+        const int w = tid >> 5, c = tid & 31;
+        if (w < 2 && c < H) {
+            const int o = w * H;
+            for (int r = c; r < H; ++r) {
+                double2 sum = make_double2(r == c ? 1.0 : 0.0, 0.0);
+                for (int m = c; m < r; ++m) sum = csub(sum, cmul(a[o + r][o + m], x[o + m][o + c]));
+                x[o + r][o + c] = cscale(sum, rp[o + r]);
+            }
+        }
+    }
+    __syncthreads();
+    // T = B A^{-1}, then X_21 = -C^{-1} T (thread = one of the 16 x 16 outputs)
+    {
+        const int r = tid >> 4, c = tid & 15;
+        double2 sum = make_double2(0.0, 0.0);
+        for (int m = c; m < H; ++m) sum = cadd(sum, cmul(a[H + r][m], x[m][c]));  // A^{-1} lower: m >= c
+        tq[r][c] = sum;
+        __syncthreads();
+        double2 o = make_double2(0.0, 0.0);
+        for (int m = 0; m <= r; ++m) o = cadd(o, cmul(x[H + r][H + m], tq[m][c]));  // C^{-1} lower: m <= r
+        x[H + r][c] = make_double2(-o.x, -o.y);
+    }
+    __syncthreads();
+    for (int e = tid; e < CB * CB; e += CT) {
+        const int i = e / CB, j = e % CB;
+        X[(size_t)(r0 + i) * N + r0 + j] = x[i][j];
+    }
+    if (tid == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
+}
+
 // Panel: L_ik = A_ik X_kk^dag for tile rows i > k (blockIdx.x = i - k - 1),
 // rows [16 h, 16 h + 16) of the tile for blockIdx.y = h (a block overwrites
 // only the rows it read).
@@ -263,12 +359,12 @@ __global__ void __launch_bounds__(CT) inv_finish_kernel(int N, int i, c_t<S>* __
     X[(size_t)(i * CB + rr) * N + k * CB + q.qc + q.c] = mk<S>(-s.x, -s.y);
 }
 
-template <typename S>
-__global__ void chol_out_kernel(int n, int N, const c_t<S>* __restrict__ X, c_t<S>* __restrict__ W) {
+template <typename S, typename T>
+__global__ void chol_out_kernel(int n, int N, const c_t<S>* __restrict__ X, c_t<T>* __restrict__ W) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
         const int r = e / n, c = e % n;
-        const c_t<S> x = X[(size_t)c * N + r];  // W = X^dag
-        W[e] = mk<S>(x.x, -x.y);
+        const c_t<S> x = X[(size_t)c * N + r];  // W = X^dag, rounded to the block type
+        W[e] = mk<T>((T)x.x, (T)(-x.y));
     }
 }
 
@@ -286,7 +382,13 @@ __global__ void chol_out_kernel(int n, int N, const c_t<S>* __restrict__ X, c_t<
 constexpr int CLS = CB + 1;      // row stride of the block-column arrays (complex elements)
 constexpr int CL_MAX = 8;        // portable cluster size: n <= 256
 
-// JDFT_CHOL_CLUSTER=0 forces the multi-block path (read on every call).
+// JDFT_CHOL_FP32=1 factors the overlap of FP32 blocks in FP32 (read on every
+// call; the default keeps FP64 for every precision); JDFT_CHOL_CLUSTER=0 then
+// forces the multi-block path over the one-launch cluster one.
+static bool fp32_factorisation() {
+    const char* e = getenv("JDFT_CHOL_FP32");
+    return e && e[0] == '1';
+}
 static bool cluster_disabled() {
     const char* e = getenv("JDFT_CHOL_CLUSTER");
     return e && e[0] == '0';
@@ -515,8 +617,8 @@ static jdft_status run_cluster(int n, const double2* U, float2* W, int* status, 
     return check_launch("chol_cluster");
 }
 
-template <typename S>
-static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W, int* status, cudaStream_t st) {
+template <typename S, typename T>
+static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W, int* status, cudaStream_t st) {
     const int nb = (n + CB - 1) / CB;
     const int N = nb * CB;
     c_t<S>* L = reinterpret_cast<c_t<S>*>(work);
@@ -531,7 +633,10 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W
     for (int k = 0; k < nb; ++k) {
         {
             Trace tr_("chol_diag", st);
-            chol_diag_kernel<S><<<1, CT, 0, st>>>(N, k, L, X, dg, status);
+            if constexpr (std::is_same<S, double>::value)
+                chol_diag64_kernel<<<1, CT, 0, st>>>(N, k, L, X, dg, status);
+            else
+                chol_diag_kernel<S><<<1, CT, 0, st>>>(N, k, L, X, dg, status);
         }
         const int m = nb - k - 1;
         if (m > 0) {
@@ -557,21 +662,22 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<S>* W
     }
     {
         Trace tr_("chol_out", st);
-        chol_out_kernel<S><<<g, 256, 0, st>>>(n, N, X, W);
+        chol_out_kernel<S, T><<<g, 256, 0, st>>>(n, N, X, W);
     }
     return check_launch("blocked_cholesky_winv");
 }
 
 jdft_status blocked_cholesky_winv(int n, const double2* U, double2* work, void* W, bool fp64, int* status,
                                   cudaStream_t st) {
-    if (fp64) return run_blocked<double>(n, U, work, (double2*)W, status, st);
+    if (fp64) return run_blocked<double, double>(n, U, work, (double2*)W, status, st);
+    if (!fp32_factorisation()) return run_blocked<double, float>(n, U, work, (float2*)W, status, st);
     if (!cluster_disabled()) {
         // the status word is cleared here (the multi-block path clears it in chol_init_kernel)
         JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
         const jdft_status s = run_cluster(n, U, (float2*)W, status, st);
         if (s != JDFT_ERR_UNSUPPORTED) return s;
     }
-    return run_blocked<float>(n, U, work, (float2*)W, status, st);
+    return run_blocked<float, float>(n, U, work, (float2*)W, status, st);
 }
 
 }  // namespace jdft

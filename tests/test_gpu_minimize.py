@@ -62,11 +62,13 @@ def test_orthonormalize_spans_same_subspace(prec, nb):
     assert np.max(np.abs(P1 - P2)) < tol * np.max(np.abs(P2))
 
 
-@pytest.mark.parametrize("cluster", ["1", "0"])
-def test_orthonormalize_fp32_factorisations(cluster, monkeypatch):
-    """FP32 blocks of 150 bands (5 tiles): the one-launch cluster factorisation
-    (distributed shared memory) and the multi-block one give the same span."""
+@pytest.mark.parametrize("fp32,cluster", [("0", "1"), ("1", "1"), ("1", "0")])
+def test_orthonormalize_fp32_factorisations(fp32, cluster, monkeypatch):
+    """FP32 blocks of 150 bands (5 tiles): the default FP64 factorisation, and on
+    request the FP32 ones (one-launch cluster with distributed shared memory,
+    and multi-block) give the same span."""
     from paper_1708_03621_gb300 import jdft
+    monkeypatch.setenv("JDFT_CHOL_FP32", fp32)
     monkeypatch.setenv("JDFT_CHOL_CLUSTER", cluster)
     w, o, g = systems("mid")
     nb = 150
@@ -89,6 +91,20 @@ def test_orthonormalize_rejects_dependent_bands(name, nb, prec):
     Cd = torch.tensor(C.astype(np.complex128 if prec == "fp64" else np.complex64), device="cuda")
     with pytest.raises(jdft.JdftError, match="NOT_POSDEF"):
         jdft.jdft_orthonormalize(g.basis, 0, Cd, prec)
+
+
+@pytest.mark.parametrize("cluster", ["1", "0"])
+def test_orthonormalize_fp32_factorisation_rejects_dependent_bands(cluster, monkeypatch):
+    """The FP32 factorisation's pivot floor (2e-4 of the original diagonal) on
+    100 bands with a duplicate."""
+    from paper_1708_03621_gb300 import jdft
+    monkeypatch.setenv("JDFT_CHOL_FP32", "1")
+    monkeypatch.setenv("JDFT_CHOL_CLUSTER", cluster)
+    w, o, g = systems("mid")
+    C = o.coeffs(100)
+    C[99] = C[3]
+    with pytest.raises(jdft.JdftError, match="NOT_POSDEF"):
+        jdft.jdft_orthonormalize(g.basis, 0, torch.tensor(C.astype(np.complex64), device="cuda"), "fp32")
 
 
 @pytest.mark.parametrize("precond", ["teter", "identity"])
