@@ -149,22 +149,31 @@ __global__ void __launch_bounds__(CT) chol_diag_kernel(int N, int k, c_t<S>* __r
     if (tid == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
 }
 
+// 1/sqrt(d) for d > 0 in FP64: an FP32 estimate refined by two Newton steps
+// y <- y (3 - d y^2) / 2 (each squares the relative error: ~1e-7 -> 1e-14 ->
+// FP64 rounding), a handful of FP64 operations on the pivot's critical path.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);  // outside the FP32 estimate's range
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
 // FP64 diagonal tile.  FP64 warp instructions occupy the SM's FP64 units for
 // the same time whatever the number of active lanes, so the work is packed
 // into full warps:
 //  * factor: step j updates the active pairs (i, m), j < m <= i, read from a
 //    table of the 528 lower-triangle pairs ordered by m descending (the
 //    active pairs of step j are its first (31 - j)(32 - j) / 2 entries);
-//  * inverse of the 2 x 2 block form L = [[A, 0], [B, C]] (16 x 16 blocks):
-//    A^{-1} and C^{-1} by column substitution on two warps at once, then
-//    X_21 = -C^{-1} (B A^{-1}) as two dense 16 x 16 products on all threads.
+//  * inverse X = L^{-1} by right-looking elimination: once row j of X is
+//    final, every row i > j subtracts L_ij times it, over the (i, c) pairs
+//    c <= j < i (5 456 complex MACs in all, in full warps).
 __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* __restrict__ L,
                                                          double2* __restrict__ X, const double* __restrict__ dg,
                                                          int* status) {
-    constexpr int H = CB / 2;
     __shared__ double2 a[CB][CB + 1];
     __shared__ double2 x[CB][CB + 1];
-    __shared__ double2 tq[H][H + 1];
     __shared__ unsigned short pr[CB * (CB + 1) / 2];
     __shared__ double rp[CB], pv[CB], fl[CB];
     __shared__ int bad;
@@ -172,11 +181,11 @@ __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* 
     for (int e = tid; e < CB * CB; e += CT) {
         const int i = e / CB, j = e % CB;
         a[i][j] = L[(size_t)(r0 + i) * N + r0 + j];
-        x[i][j] = make_double2(0.0, 0.0);
+        x[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
     // pair table: m descending, then i ascending; entry = i << 8 | m
     if (tid < CB) {
-        const int m = CB - 1 - tid;                   // rank of m in descending order
+        const int m = CB - 1 - tid;
         int off = 0;
         for (int mm = CB - 1; mm > m; --mm) off += CB - mm;
         for (int i = m; i < CB; ++i) pr[off + i - m] = (unsigned short)(i << 8 | m);
@@ -187,9 +196,9 @@ __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* 
     auto pivot = [&](int j) {
         double d = a[j][j].x;
         if (!(d > fl[j])) { bad = 1; d = 1.0; }
-        const double p = sqrt(d);
-        pv[j] = p;
-        rp[j] = 1.0 / p;
+        const double y = rsqrt_newton(d);
+        rp[j] = y;      // 1 / L_jj
+        pv[j] = d * y;  // L_jj = sqrt(d)
     };
     if (tid == 0) pivot(0);
     __syncthreads();
@@ -212,31 +221,18 @@ __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* 
         L[(size_t)(r0 + r) * N + r0 + c] = v;
     }
     __syncthreads();
-    // A^{-1} (warp 0) and C^{-1} (warp 1): lane c < 16 computes column c top-down
-    {
-        const int w = tid >> 5, c = tid & 31;
-        if (w < 2 && c < H) {
-            const int o = w * H;
-            for (int r = c; r < H; ++r) {
-                double2 sum = make_double2(r == c ? 1.0 : 0.0, 0.0);
-                for (int m = c; m < r; ++m) sum = csub(sum, cmul(a[o + r][o + m], x[o + m][o + c]));
-                x[o + r][o + c] = cscale(sum, rp[o + r]);
-            }
-        }
-    }
-    __syncthreads();
-    // T = B A^{-1}, then X_21 = -C^{-1} T (thread = one of the 16 x 16 outputs)
-    {
-        const int r = tid >> 4, c = tid & 15;
-        double2 sum = make_double2(0.0, 0.0);
-        for (int m = c; m < H; ++m) sum = cadd(sum, cmul(a[H + r][m], x[m][c]));  // A^{-1} lower: m >= c
-        tq[r][c] = sum;
+    // X = L^{-1}: x starts as the identity; at step j row j is scaled by 1/L_jj
+    // (its entries c <= j are final) and rows i > j lose L_ij times it
+    for (int j = 0; j < CB; ++j) {
+        if (tid <= j) x[j][tid] = cscale(x[j][tid], rp[j]);
         __syncthreads();
-        double2 o = make_double2(0.0, 0.0);
-        for (int m = 0; m <= r; ++m) o = cadd(o, cmul(x[H + r][H + m], tq[m][c]));  // C^{-1} lower: m <= r
-        x[H + r][c] = make_double2(-o.x, -o.y);
+        const int w = j + 1, cnt = (CB - 1 - j) * w;  // pairs (i, c), i > j, c <= j
+        for (int e = tid; e < cnt; e += CT) {
+            const int i = j + 1 + e / w, c = e % w;
+            x[i][c] = csub(x[i][c], cmul(a[i][j], x[j][c]));
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < CB * CB; e += CT) {
         const int i = e / CB, j = e % CB;
         X[(size_t)(r0 + i) * N + r0 + j] = x[i][j];
@@ -261,12 +257,22 @@ __global__ void __launch_bounds__(CT) chol_panel_kernel(int N, int k, c_t<S>* __
         xk[r][c] = X[(size_t)(rk + r) * N + rk + c];
     }
     __syncthreads();
-    // out[r][c] = sum_{m <= c} a[r][m] conj(xk[c][m])  (xk lower triangular)
-    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
-        const int r = e / CB, c = e % CB;
-        V s = mk<S>(S(0), S(0));
-        for (int m = 0; m <= c; ++m) s = cadd(s, cmulc(a[r][m], xk[c][m]));
-        L[(size_t)(ri + r) * N + rk + c] = s;
+    // out[r][c] = sum_{m <= c} a[r][m] conj(xk[c][m])  (xk lower triangular).
+    // Warp w takes columns c = w + 8 q; its lanes are 16 rows x 2 halves of the
+    // m range (equal lengths, so no lane idles through a longer one), and a
+    // shuffle adds the halves.
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int r = lane & 15, hf = lane >> 4;
+        for (int c = warp; c < CB; c += CT / 32) {
+            const int mid = (c + 2) / 2;
+            const int mlo = hf ? mid : 0, mhi = hf ? c + 1 : mid;
+            V sum = mk<S>(S(0), S(0));
+            for (int m = mlo; m < mhi; ++m) sum = cadd(sum, cmulc(a[r][m], xk[c][m]));
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 16);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 16);
+            if (hf == 0) L[(size_t)(ri + r) * N + rk + c] = sum;
+        }
     }
 }
 
