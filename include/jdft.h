@@ -280,6 +280,30 @@ jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, in
 jdft_status jdft_autotune_chunk(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
                                 int nb, jdft_prec prec, int* chunk_mb, void* stream);
 
+/* Split-K schedule of the tensor-core product out = A^dag B (M x N over K;
+ * A: M rows of K, B: N rows of K, device complex64, row strides lda, ldb):
+ * times the default split count and multiples of it (never fewer splits than
+ * keep <= 4096 complex K per block accumulating in tensor memory) and keeps
+ * the fastest for this (M, N, K, operand type) in a process-wide table that
+ * later products of that shape use.  prec JDFT_TF32X3 or JDFT_BF16X3 (other
+ * precisions have no schedule: *splits = 0).  *splits (host, may be NULL)
+ * receives the choice.  Synchronous; allocates an M x N scratch. */
+jdft_status jdft_autotune_gemm(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                               jdft_prec prec, int* splits, void* stream);
+
+typedef struct {
+    int chunk_mb;          /* band-chunk budget kept for the chain kernels */
+    int splits_subspace;   /* split-K count kept for the nb x nb x npw products (0: no schedule) */
+    int splits_projector;  /* the same for the nproj x nb x npw projection P^dag C (0: none) */
+} jdft_tune_report;
+
+/* Autotune everything the Hamiltonian, density and subspace calls of this
+ * block use: the band-chunk budget of the FFT chain (jdft_autotune_chunk) and
+ * the split-K schedules of the block's subspace and projector products
+ * (jdft_autotune_gemm).  Overwrites HC.  Synchronous; may grow the workspace. */
+jdft_status jdft_autotune(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                          jdft_prec prec, jdft_tune_report* report, void* stream);
+
 /* ---- batches in one CUDA graph -------------------------------------------- */
 
 /* One Hamiltonian application of a batch: H C for nb bands of k-point ik of

@@ -843,3 +843,21 @@ extern "C" jdft_status jdft_autotune_chunk(jdft_basis_t b, int ik, const void* C
     if (chunk_mb) *chunk_mb = best_mb;
     return JDFT_OK;
 }
+
+extern "C" jdft_status jdft_autotune(jdft_basis_t b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                     jdft_prec prec, jdft_tune_report* report, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C && HC && report && nb >= 1, "bad arguments");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    *report = jdft_tune_report{0, 0, 0};
+    int mb = 0;
+    jdft_status s = jdft_autotune_chunk(b, ik, C, ldc, HC, ldhc, nb, prec, &mb, stream);
+    if (s != JDFT_OK) return s;
+    report->chunk_mb = mb;
+    if (prec != JDFT_TF32X3 && prec != JDFT_BF16X3) return JDFT_OK;
+    const KSphere& sp = b->ks[ik];
+    if ((s = jdft_autotune_gemm(nb, nb, sp.npw, C, ldc, C, ldc, prec, &report->splits_subspace, stream))) return s;
+    if (sp.nproj > 0)
+        s = jdft_autotune_gemm(sp.nproj, nb, sp.npw, sp.P32, sp.npw, C, ldc, prec, &report->splits_projector, stream);
+    return s;
+}

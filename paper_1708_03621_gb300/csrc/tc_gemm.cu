@@ -22,6 +22,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "gemm.cuh"
 #include "profile.cuh"
@@ -342,6 +346,33 @@ static jdft_status tc_launch(const S& s, int M, int N, int K, int splits, const 
     return check_launch(name);
 }
 
+// Split-K schedules chosen by jdft_autotune_gemm, per product shape (M, N, K,
+// operand format); absent shapes use the default schedule.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cn;
+}  // namespace
+
+static int tuned_cn_splits(int M, int N, int K, int fmt) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cn.find(std::make_tuple(M, N, K, fmt));
+    return it == g_tune_cn.end() ? 0 : it->second;
+}
+
+// Default split-K count of the 128-column C^dag B schedule and the smallest
+// count the accuracy cap allows (at most 4096 complex K accumulate in tensor
+// memory per block: the FP32 accumulation there loses precision in
+// proportion to the number of accumulating products, about 6e-4 relative
+// over 42 k complex K and 2e-5 over 1.6 k; the split partial sums meet in
+// FP64).
+static void cn_schedule(int M, int N, int K, int& dflt, int& capmin) {
+    const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
+    const int nck = (K + TC_CPS - 1) / TC_CPS;
+    constexpr int kMaxChunks = 4096 / TC_CPS;
+    capmin = (nck + kMaxChunks - 1) / kMaxChunks;
+    dflt = std::max(std::min(nck / 4 + 1, (152 + tiles - 1) / tiles), capmin);
+}
+
 template <int FMT>
 static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, double2* out, int ldo,
                          double alpha, cudaStream_t st) {
@@ -354,16 +385,11 @@ static jdft_status tc_cn(int M, int N, int K, const float2* A, int lda, const fl
     }
     // 16 complex K per stage (32 for BF16, 256 contiguous bytes per operand
     // row, measured 10 % slower on the 256 x 256 x 62 759 products)
-    constexpr int CPS = TC_CPS;
-    StageCN<128, FMT, CPS> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
-    const int tiles = ((M + TC_M - 1) / TC_M) * ((N + 127) / 128);
-    const int nck = (K + CPS - 1) / CPS;
-    // at most kMaxChunks chunks (4096 complex K) accumulate in tensor memory per
-    // block: the FP32 accumulation there loses precision in proportion to the
-    // number of accumulating products (about 6e-4 relative over 42 k complex K,
-    // 2e-5 over 1.6 k); the split partial sums meet in FP64
-    constexpr int kMaxChunks = 4096 / CPS;
-    const int splits = std::max(std::min(nck / 4 + 1, (152 + tiles - 1) / tiles), (nck + kMaxChunks - 1) / kMaxChunks);
+    StageCN<128, FMT, TC_CPS> s{A, lda, B, ldb, M, N, K, out, ldo, alpha};
+    int splits, capmin;
+    cn_schedule(M, N, K, splits, capmin);
+    const int tuned = tuned_cn_splits(M, N, K, FMT);
+    if (tuned > 0) splits = std::max(tuned, capmin);
     return tc_launch<128, FMT>(s, M, N, K, splits, "tc_zgemm_cn", st);
 }
 
@@ -415,5 +441,65 @@ extern "C" jdft_status jdft_device_status(void* stream) {
         JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)));
         return set_error((jdft_status)v, "a bounded device-side wait gave up (tensor-core product skipped)");
     }
+    return JDFT_OK;
+}
+
+extern "C" jdft_status jdft_autotune_gemm(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                                          jdft_prec prec, int* splits, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(M >= 1 && N >= 1 && K >= 1 && A && B && lda >= K && ldb >= K, "bad arguments");
+    if (splits) *splits = 0;
+    if (prec != JDFT_TF32X3 && prec != JDFT_BF16X3) return JDFT_OK;  // only the tensor-core products have schedules
+    const int fmt = prec == JDFT_BF16X3 ? 1 : 0;
+    const bool bf16 = fmt == 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N <= 32) return JDFT_OK;  // the 32-column schedule is fixed
+    int dflt, capmin;
+    cn_schedule(M, N, K, dflt, capmin);
+    const int nck = (K + TC_CPS - 1) / TC_CPS;
+    std::vector<int> cand;
+    for (int f : {50, 75, 100, 150, 200}) {
+        const int c = std::max(capmin, std::min(nck, dflt * f / 100));
+        if (c >= 1 && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+    }
+    double2* out = nullptr;
+    JDFT_CUDA_TRY(cudaMalloc(&out, (size_t)M * N * sizeof(double2)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const auto key = std::make_tuple(M, N, K, fmt);
+    float best = 1e30f;
+    int best_c = dflt;
+    jdft_status s = JDFT_OK;
+    for (int c : cand) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cn[key] = c;
+        }
+        // one untimed call, then three timed ones (the accumulated values are not used)
+        s = tc_zgemm_cn(M, N, K, (const float2*)A, lda, (const float2*)B, ldb, out, N, 1.0, bf16, st);
+        if (s != JDFT_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && s == JDFT_OK; ++r)
+            s = tc_zgemm_cn(M, N, K, (const float2*)A, lda, (const float2*)B, ldb, out, N, 1.0, bf16, st);
+        cudaEventRecord(e1, st);
+        if (s != JDFT_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cn[key] = best_c;
+    }
+    if (s != JDFT_OK) return s;
+    if (splits) *splits = best_c;
     return JDFT_OK;
 }

@@ -93,6 +93,8 @@ _SIGS = {
     "jdft_batch_launch": [_vp, _vp],
     "jdft_batch_destroy": [_vp],
     "jdft_autotune_chunk": [_vp, _i, _vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _vp],
+    "jdft_autotune_gemm": [_i, _i, _i, _vp, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp],
+    "jdft_autotune": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -416,6 +418,30 @@ def jdft_autotune_chunk(basis, ik, C, HC, prec="fp64", stream=None) -> int:
     _call("jdft_autotune_chunk", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), ctypes.byref(out),
           _stream(stream))
     return out.value
+
+
+def jdft_autotune_gemm(A, B, prec="bf16x3", stream=None) -> int:
+    """Tune and keep the split-K schedule of A^dag B (band-major complex64 blocks A: M x K, B: N x K)."""
+    p, lda, M = _block(A, prec, "A")
+    q, ldb, N = _block(B, prec, "B")
+    K = A.shape[1]
+    out = ctypes.c_int()
+    _call("jdft_autotune_gemm", M, N, K, p, lda, q, ldb, _prec(prec), ctypes.byref(out), _stream(stream))
+    return out.value
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("chunk_mb", ctypes.c_int), ("splits_subspace", ctypes.c_int), ("splits_projector", ctypes.c_int)]
+
+
+def jdft_autotune(basis, ik, C, HC, prec="bf16x3", stream=None) -> dict:
+    """Tune the FFT-chain chunk budget and the GEMM schedules of this block (overwrites HC)."""
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, _ = _block(HC, prec, "HC")
+    r = TuneReport()
+    _call("jdft_autotune", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), ctypes.c_void_p(ctypes.addressof(r)),
+          _stream(stream))
+    return {"chunk_mb": r.chunk_mb, "splits_subspace": r.splits_subspace, "splits_projector": r.splits_projector}
 
 
 class Batch:

@@ -87,3 +87,35 @@ def test_autotune_chunk_keeps_results():
     jdft.jdft_apply_H(b, 0, C, H1, "fp32")
     torch.cuda.synchronize()
     assert torch.allclose(H0, H1, rtol=1e-5, atol=1e-6 * H0.abs().max().item())
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_autotune_schedules_keep_results(prec):
+    """jdft_autotune on a 150-band block of the 40^3 cell: the chosen chunk
+    budget and split-K schedules are valid, and H C and C^dag H C computed
+    with them still match the oracle."""
+    from oracle import planewave as pw
+    from paper_1708_03621_gb300 import jdft
+    from synth import WORKLOADS
+    w = WORKLOADS["mid"]
+    b = _cell(w)
+    nb = 150
+    C = _block(b, w, 0, nb, 7, prec)
+    rep = jdft.jdft_autotune(b, 0, C, torch.empty_like(C), prec)
+    assert rep["chunk_mb"] in (16, 32, 64, 96, 128, 256)
+    assert rep["splits_subspace"] >= 1 and rep["splits_projector"] >= 1
+    HC = torch.empty_like(C)
+    jdft.jdft_apply_H(b, 0, C, HC, prec)
+    CHC = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    jdft.jdft_subspace(b, 0, C, HC, CHC, None, prec)
+    ob = pw.Basis.build(w.R, w.S, w.kfrac[0], w.ecut)
+    atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+    V = pw.vloc_realspace(w.R, w.S, atoms)
+    P = pw.projectors(w.R, ob.kfrac, ob.iG, atoms)
+    Ch = C.cpu().numpy().astype(np.complex128)
+    ref = pw.apply_H(ob, V, Ch.T, P, pw.dmatrix(w.natoms)).T
+    got = HC.cpu().numpy().astype(np.complex128)
+    assert (np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() < 2e-5
+    chc_ref = Ch.conj() @ ref.T
+    assert np.max(np.abs(CHC.cpu().numpy() - chc_ref)) / np.max(np.abs(chc_ref)) < 2e-4
+    jdft.jdft_device_status()
