@@ -273,8 +273,9 @@ jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, in
 /* ---- schedule autotuning ------------------------------------------------ */
 
 /* Time jdft_apply_H on the caller's blocks for band-chunk budgets of
- * 16 ... 256 MB (the column buffer passed between the chain kernels; small
- * enough chunks stay in L2) and keep the fastest in the basis for later calls.
+ * 32 ... 1024 MB (the column buffer passed between the chain kernels; small
+ * chunks stay in L2, large ones make fewer launches; default 256 MB) and keep
+ * the fastest in the basis for later calls.
  * Overwrites HC.  *chunk_mb (host, may be NULL) receives the choice.
  * Synchronous; may grow the workspace. */
 jdft_status jdft_autotune_chunk(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,

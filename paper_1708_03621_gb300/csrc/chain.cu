@@ -517,15 +517,17 @@ static int chunk_bands(const ChainGeom& g, size_t elem, int nb, size_t budget) {
     return std::max(1, std::min(nb, c));
 }
 
-// Column-buffer bytes per chunk of bands: small enough that one chunk's
-// intermediate stays in the 126 MB L2 between the three kernels.  The
-// environment variable JDFT_CHUNK_MB overrides it (read on every call), then
-// a value the autotuner stored in the basis, then 64 MB.
+// Column-buffer bytes per chunk of bands.  The environment variable
+// JDFT_CHUNK_MB overrides it (read on every call), then a value the
+// autotuner stored in the basis, then 256 MB: measured on the 128^3,
+// 256-band block, two chunks of 131 bands beat eight L2-sized ones (64 MB),
+// since fewer, larger launches balance the persistent plane kernel better than
+// L2 residency of the column buffer saves.
 size_t chunk_budget(const jdft_basis_s* b) {
     const char* e = getenv("JDFT_CHUNK_MB");
     long long mb = e ? atoll(e) : 0;
     if (mb <= 0 && b) mb = b->chunk_mb;
-    return (size_t)(mb > 0 ? mb : 64) << 20;
+    return (size_t)(mb > 0 ? mb : 256) << 20;
 }
 
 template <typename T>
@@ -815,7 +817,7 @@ extern "C" jdft_status jdft_autotune_chunk(jdft_basis_t b, int ik, const void* C
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
     if (!b->have_V) return set_error(JDFT_ERR_ARG, "no potential set");
     cudaStream_t st = (cudaStream_t)stream;
-    const int cand[] = {16, 32, 64, 96, 128, 256};
+    const int cand[] = {32, 64, 128, 256, 512, 1024};
     cudaEvent_t e0, e1;
     JDFT_CUDA_TRY(cudaEventCreate(&e0));
     JDFT_CUDA_TRY(cudaEventCreate(&e1));

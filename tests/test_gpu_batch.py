@@ -82,7 +82,7 @@ def test_autotune_chunk_keeps_results():
     H0 = torch.empty_like(C)
     jdft.jdft_apply_H(b, 0, C, H0, "fp32")
     mb = jdft.jdft_autotune_chunk(b, 0, C, torch.empty_like(C), "fp32")
-    assert mb in (16, 32, 64, 96, 128, 256)
+    assert mb in (32, 64, 128, 256, 512, 1024)
     H1 = torch.empty_like(C)
     jdft.jdft_apply_H(b, 0, C, H1, "fp32")
     torch.cuda.synchronize()
@@ -102,7 +102,7 @@ def test_autotune_schedules_keep_results(prec):
     nb = 150
     C = _block(b, w, 0, nb, 7, prec)
     rep = jdft.jdft_autotune(b, 0, C, torch.empty_like(C), prec)
-    assert rep["chunk_mb"] in (16, 32, 64, 96, 128, 256)
+    assert rep["chunk_mb"] in (32, 64, 128, 256, 512, 1024)
     assert rep["splits_subspace"] >= 1 and rep["splits_projector"] >= 1
     HC = torch.empty_like(C)
     jdft.jdft_apply_H(b, 0, C, HC, prec)
