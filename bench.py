@@ -309,11 +309,12 @@ def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
 
 
 # DRAM bytes (read + write) per band of the dominant kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum of a 34-band launch on
-# the 128^3 workload; profiles/plane_apply_density_fast_128cubed_bf16x3.md).
-# ncu replays with cold caches, so this is an upper bound on the warm traffic.
-# Only valid for the kernel version it was taken on: set to None when it changes.
-TRAFFIC_PER_BAND = {"plane_apply_density_fast": (91.659776e6 + 27.659264e6) / 34}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum of a 64-band launch on
+# the 128^3 workload, --nbands 64; profiles/plane_apply_density_fast_128cubed_bf16x3.md),
+# scaled by the bands a launch processes.  ncu replays with cold caches, so
+# this bounds the warm traffic from above.  Only valid for the kernel version
+# it was taken on: set to None when the kernel changes.
+TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150325760 + 87282944) / 64}
 
 
 def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:
