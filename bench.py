@@ -513,6 +513,21 @@ def cg_measurements(prec: str, device, log=lambda *_: None) -> dict:
     w = WORKLOADS["small"]
     b = learned.build_cell(w, device)
     C0 = torch.tensor(learned.start_block(b, w), device=device)
+    # configuration 1's H C throughput (16 bands, 48^3): FP64 and the mixed precision
+    stream = torch.cuda.current_stream()
+    for pr, ct in (("fp64", torch.complex128), (prec, torch.complex64)):
+        Cx = C0.to(ct)
+        Hx = torch.empty_like(Cx)
+        for _ in range(5):
+            jdft.jdft_apply_H(b, 0, Cx, Hx, pr)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 200
+        a0.record(stream)
+        for _ in range(reps):
+            jdft.jdft_apply_H(b, 0, Cx, Hx, pr)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        out[f"small_apply_H_{pr}_band_applies_per_s"] = round(w.nbands * reps / (a0.elapsed_time(a1) / 1e3), 1)
     C = C0.clone()
     ref = jdft.jdft_minimize_bands(b, 0, C, tol=1e-10, max_iter=5000, precond="teter", prec="fp64")
     E_ref = ref["energy"]

@@ -19,6 +19,9 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <vector>
+#include <mutex>
+#include <map>
 #include <cstdlib>
 #include <type_traits>
 
@@ -623,6 +626,23 @@ static jdft_status run_cluster(int n, const double2* U, float2* W, int* status, 
     return check_launch("chol_cluster");
 }
 
+// A second stream per device for the inverse rows (created once, non-blocking).
+static cudaStream_t side_stream() {
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    cudaStream_t& s = streams[dev];
+    if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+    return s;
+}
+
+// The factorisation runs on `st`; the inverse rows run on a side stream,
+// row i as soon as factor step i has its diagonal tile (L_ij, j < i, and
+// X_jj, j <= i, are final then), so they fill the SMs the one-block diagonal
+// kernels leave idle.  The side stream forks from `st` after the set-up and
+// joins it before W is written (also under stream capture).
 template <typename S, typename T>
 static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W, int* status, cudaStream_t st) {
     const int nb = (n + CB - 1) / CB;
@@ -636,6 +656,20 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W
         Trace tr_("chol_init", st);
         chol_init_kernel<S><<<g, 256, 0, st>>>(n, N, U, L, X, Sa, dg, status);
     }
+    cudaStream_t sb = nb > 1 ? side_stream() : nullptr;
+    std::vector<cudaEvent_t> ev;
+    if (sb) {
+        ev.resize(nb + 1, nullptr);
+        for (auto& e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                for (auto& f : ev)
+                    if (f) cudaEventDestroy(f);
+                ev.clear();
+                sb = nullptr;
+                break;
+            }
+    }
+    cudaStream_t si = sb ? sb : st;  // stream of the inverse rows
     for (int k = 0; k < nb; ++k) {
         {
             Trace tr_("chol_diag", st);
@@ -643,6 +677,21 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W
                 chol_diag64_kernel<<<1, CT, 0, st>>>(N, k, L, X, dg, status);
             else
                 chol_diag_kernel<S><<<1, CT, 0, st>>>(N, k, L, X, dg, status);
+        }
+        if (k >= 1) {
+            // inverse row k: needs L rows <= k (panels 0 .. k-1 are done) and X_jj, j <= k
+            if (sb) {
+                JDFT_CUDA_TRY(cudaEventRecord(ev[k], st));
+                JDFT_CUDA_TRY(cudaStreamWaitEvent(sb, ev[k], 0));
+            }
+            {
+                Trace tr_("chol_inv_accum", si);
+                inv_accum_kernel<S><<<dim3(k * (k + 1) / 2, 4), CT, 0, si>>>(N, k, L, X, Sa);
+            }
+            {
+                Trace tr_("chol_inv_finish", si);
+                inv_finish_kernel<S><<<dim3(k, 4), CT, 0, si>>>(N, k, X, Sa);
+            }
         }
         const int m = nb - k - 1;
         if (m > 0) {
@@ -656,16 +705,14 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W
             }
         }
     }
-    for (int i = 1; i < nb; ++i) {
-        {
-            Trace tr_("chol_inv_accum", st);
-            inv_accum_kernel<S><<<dim3(i * (i + 1) / 2, 4), CT, 0, st>>>(N, i, L, X, Sa);
-        }
-        {
-            Trace tr_("chol_inv_finish", st);
-            inv_finish_kernel<S><<<dim3(i, 4), CT, 0, st>>>(N, i, X, Sa);
-        }
+    jdft_status s = check_launch("blocked_cholesky_winv");
+    if (sb) {
+        // join: W needs every inverse row
+        cudaEventRecord(ev[nb], sb);
+        cudaStreamWaitEvent(st, ev[nb], 0);
+        for (auto& e : ev) cudaEventDestroy(e);
     }
+    if (s != JDFT_OK) return s;
     {
         Trace tr_("chol_out", st);
         chol_out_kernel<S, T><<<g, 256, 0, st>>>(n, N, X, W);

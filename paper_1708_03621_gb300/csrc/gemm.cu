@@ -174,6 +174,12 @@ __global__ void dmul_kernel(int nproj, int nb, int w, const int* __restrict__ Dc
     }
 }
 
+bool gemm_nn_inplace_ok(jdft_prec prec, int N) {
+    if (prec == JDFT_BF16X3) return N <= 256;
+    if (prec == JDFT_TF32X3) return N <= 128;
+    return false;  // the CUDA-core products tile N in 16-column blocks
+}
+
 size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem) {
     if (nproj == 0) return 0;
     const size_t a = ((size_t)nproj * nb * sizeof(double2) + 255) / 256 * 256;

@@ -35,6 +35,13 @@ template <typename T>
 jdft_status gemm_nn_acc(jdft_prec prec, int M, int N, int K, const c_t<T>* A, int lda, const c_t<T>* Bm, int ldb,
                         c_t<T>* out, int ldo, cudaStream_t st, bool accumulate = true);
 
+// Whether gemm_nn_acc(prec, M, N, K, A, ...) may write its output over A
+// (out == A, same leading dimension, K == N): true when one block computes
+// all N output columns of its 128 rows (tensor-core products with N <= 256
+// for BF16 operands, N <= 128 otherwise), since a block reads those rows of A
+// for every k before its epilogue writes them and no other block touches them.
+bool gemm_nn_inplace_ok(jdft_prec prec, int N);
+
 // Workspace bytes the nonlocal term needs for nb bands.
 size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem);
 

@@ -631,8 +631,14 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
     if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega, st)))
         return s;
     if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
-    JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
-    if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st, false))) return s;
+    if (gemm_nn_inplace_ok(prec, nb)) {
+        // C <- C W in place: each block reads its rows of C for every band before writing them
+        if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, (const c_t<T>*)C, ldc, W, nb, (c_t<T>*)C, ldc, st, false)))
+            return s;
+    } else {
+        JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
+        if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st, false))) return s;
+    }
     int hs = 0;
     JDFT_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
