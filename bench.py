@@ -206,6 +206,8 @@ class Problem:
         # the project's autotuner picks the chain's chunk budget and the GEMM
         # split-K schedules for this block before anything is timed
         self.tune = jdft.jdft_autotune(self.basis, 0, self.C, self.HC, prec) if prec != "fp64" else None
+        # device status word of the asynchronous orthonormalisation, checked after each timed loop
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
 
     def buffers(self):
         """A second set of the step's device buffers (the double-buffered end-to-end loop)."""
@@ -225,7 +227,15 @@ class Problem:
         b["n"].zero_()
         j.jdft_apply_H_density(self.basis, 0, b["C"], b["HC"], self.f, b["n"], self.prec, stream)
         j.jdft_subspace(self.basis, 0, b["C"], b["HC"], b["CHC"], b["COC"], self.prec, stream)
-        j.jdft_orthonormalize(self.basis, 0, b["C"], self.prec, stream)
+        # no host wait per step: a failure lands in self.status (see check_status)
+        j.jdft_orthonormalize_async(self.basis, 0, b["C"], self.status, self.prec, stream)
+
+    def check_status(self):
+        """Raise if any orthonormalisation since set-up met linearly dependent bands."""
+        import torch
+        torch.cuda.synchronize()
+        if int(self.status.item()) != 0:
+            raise RuntimeError(f"orthonormalisation failed (status {int(self.status.item())})")
 
     def io_bytes(self):
         e = self.C.element_size()
@@ -356,6 +366,7 @@ def run_ours(args, world, rank, local, pg):
     jdft.jdft_profile_enable(False)
     prof = jdft.jdft_profile_read()
     clk = clocks.stop()
+    p.check_status()
     ms = e0.elapsed_time(e1)
     ms_max, units = job_totals(pg, ms, p.nb * args.steps)
     value = units / (ms_max / 1e3)
@@ -419,6 +430,7 @@ def run_ours(args, world, rank, local, pg):
             COC_host.copy_(sets[k]["COC"], non_blocking=True)
     torch.cuda.synchronize()
     e2e_s, e2e_units = job_totals(pg, time.perf_counter() - t0, p.nb * e2e_steps)
+    p.check_status()
     e2e = {"value": round(e2e_units / e2e_s, 1), "unit": UNIT, "h2d_bytes_per_step": Bi,
            "d2h_bytes_per_step": Bo, "steps": e2e_steps,
            "pipeline": "double-buffered: each step's input copy (pinned host -> device) and output copy "
@@ -441,6 +453,7 @@ def run_ours(args, world, rank, local, pg):
             q.step()
         a1.record(stream)
         torch.cuda.synchronize()
+        q.check_status()
         t64 = a0.elapsed_time(a1)
         fp64 = {"value": round(q.nb * k64 / (t64 / 1e3), 1), "ms_per_step": round(t64 / k64, 3), "steps": k64,
                 "mixed_errors_vs_fp64": precision_errors(q)}

@@ -192,6 +192,15 @@ jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, co
 jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,
                                 void* stream);
 
+/* jdft_orthonormalize without the wait: the same work is queued on `stream`
+ * and the factorisation's outcome is merged into the caller's device word
+ * *status (max of the old value and JDFT_ERR_NOT_POSDEF on linearly dependent
+ * bands, else unchanged), so a pipeline of steps can check once for all of
+ * them.  Returns argument and launch errors only.  The paper has no such
+ * call. */
+jdft_status jdft_orthonormalize_async(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,
+                                      int* status, void* stream);
+
 /* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
  * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,
  * nb doubles.  Synchronous. */

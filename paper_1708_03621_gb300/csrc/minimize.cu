@@ -608,9 +608,16 @@ extern "C" {
 }  // extern "C"
 
 namespace jdft {
+// *dst = max(*dst, *src): a sticky status word for the asynchronous form.
+__global__ void status_merge_kernel(const int* __restrict__ src, int* __restrict__ dst) {
+    if (threadIdx.x == 0 && *src > *dst) *dst = *src;
+}
+
+// sticky == nullptr: synchronous, the factorisation's status is returned;
+// otherwise the status is merged into the device word *sticky and nothing waits.
 template <typename T>
 static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc, int nb, jdft_prec prec,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, int* sticky = nullptr) {
     const int npw = b->ks[ik].npw;
     const int m = nb + (nb & 1);
     const size_t sm = ((size_t)nb * nb * sizeof(double2) + 255) / 256 * 256;
@@ -639,6 +646,13 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
         JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
         if ((s = gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st, false))) return s;
     }
+    if (sticky) {
+        {
+            Trace tr_("status_merge", st);
+            status_merge_kernel<<<1, 32, 0, st>>>(status, sticky);
+        }
+        return check_launch("status_merge");
+    }
     int hs = 0;
     JDFT_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
@@ -658,6 +672,18 @@ jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb
     cudaStream_t st = (cudaStream_t)stream;
     return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st)
                              : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st);
+}
+
+jdft_status jdft_orthonormalize_async(jdft_basis_t b, int ik, void* C, int ldc, int nb, jdft_prec prec,
+                                      int* status, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b && C && status, "null argument");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
+    JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st, status)
+                             : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st, status);
 }
 
 jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream) {

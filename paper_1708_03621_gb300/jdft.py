@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libjdft.so")
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_TIMEOUT",
           5: "ERR_NOT_POSDEF", 6: "ERR_NOT_CONVERGED", 7: "ERR_UNSUPPORTED"}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 
 class JdftError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "jdft_batch_launch": [_vp, _vp],
     "jdft_batch_destroy": [_vp],
     "jdft_autotune_chunk": [_vp, _i, _vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _vp],
+    "jdft_orthonormalize_async": [_vp, _i, _vp, _i, _i, _i, _vp, _vp],
     "jdft_autotune_gemm": [_i, _i, _i, _vp, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp],
     "jdft_autotune": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
     "jdft_profile_enable": [_i],
@@ -310,6 +312,12 @@ def jdft_orthonormalize(basis, ik, C, prec="fp64", stream=None):
     """C <- C L^{-dag}, Omega C^dag C = L L^dag (complex128 block for fp64, complex64 otherwise)."""
     p, ld, nb = _block(C, prec, "C")
     _call("jdft_orthonormalize", basis.handle, ik, p, ld, nb, _prec(prec), _stream(stream))
+
+
+def jdft_orthonormalize_async(basis, ik, C, status, prec="fp64", stream=None):
+    """jdft_orthonormalize without the wait; failures are merged into the device int32 tensor `status`."""
+    p, ld, nb = _block(C, prec, "C")
+    _call("jdft_orthonormalize_async", basis.handle, ik, p, ld, nb, _prec(prec), _ptr(status), _stream(stream))
 
 
 def jdft_subspace_eigs(A, eigs, stream=None):

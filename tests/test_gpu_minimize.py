@@ -107,6 +107,33 @@ def test_orthonormalize_fp32_factorisation_rejects_dependent_bands(cluster, monk
         jdft.jdft_orthonormalize(g.basis, 0, torch.tensor(C.astype(np.complex64), device="cuda"), "fp32")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_orthonormalize_async_matches_and_status_is_sticky(prec):
+    """The asynchronous form gives the synchronous one's block (up to the order
+    of the FP64 atomic split-K sums of C^dag C) and merges failures into a
+    device word that a later good call does not clear."""
+    from paper_1708_03621_gb300 import jdft
+    w, o, g = systems("mid")
+    ct = np.complex128 if prec == "fp64" else np.complex64
+    C = o.coeffs(70, seed=41)
+    A = torch.tensor(C.astype(ct), device="cuda")
+    B = A.clone()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    jdft.jdft_orthonormalize(g.basis, 0, A, prec)
+    jdft.jdft_orthonormalize_async(g.basis, 0, B, st, prec)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    a, b = A.cpu().numpy().astype(np.complex128), B.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(a - b)) < (1e-12 if prec == "fp64" else 1e-5) * np.max(np.abs(a))
+    D = o.coeffs(40)
+    D[39] = D[0]
+    Dd = torch.tensor(D.astype(ct), device="cuda")
+    jdft.jdft_orthonormalize_async(g.basis, 0, Dd, st, prec)
+    jdft.jdft_orthonormalize_async(g.basis, 0, B, st, prec)   # a good call afterwards
+    torch.cuda.synchronize()
+    assert int(st.item()) == jdft.STATUS_CODES["ERR_NOT_POSDEF"]
+
+
 @pytest.mark.parametrize("precond", ["teter", "identity"])
 def test_minimize_tiny_reaches_dense_eigenvalues(precond):
     from paper_1708_03621_gb300 import jdft
