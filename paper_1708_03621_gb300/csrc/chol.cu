@@ -12,9 +12,10 @@
 // Working precision S: FP64 for every block precision (W is rounded to the
 // block type at the end); FP32 for FP32 blocks only on request
 // (JDFT_CHOL_FP32=1).  FP64 units are scarce on this GPU (about two FP64 FMAs
-// per clock per SM), so the tile products are split into 16 x 16 output
-// quadrants on separate blocks, and the diagonal tile takes one block barrier
-// per column with each reciprocal taken once.
+// per clock per SM), so the FP64 work is spread over many blocks (the panel in
+// 4-row slices, the trailing update in 8 x 8 output blocks), every complex
+// multiply-add is 4 fused multiply-adds, and the diagonal tile factors and
+// inverts in one loop over its columns.
 // The matrix is padded to a multiple of 32 with identity rows.
 #include <cooperative_groups.h>
 
@@ -45,6 +46,31 @@ size_t chol_work_elems(int n) {
 template <typename S> struct PivotFloor;
 template <> struct PivotFloor<double> { static constexpr double v = 1e-13; };
 template <> struct PivotFloor<float> { static constexpr float v = 2e-4f; };
+
+// Complex multiply-adds as two fused multiply-adds per part (4 instructions
+// instead of the 6 of a product followed by an add).
+__device__ __forceinline__ double fm(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <typename V> __device__ __forceinline__ V cmac_conj(V acc, V p, V q) {  // acc + p conj(q)
+    acc.x = fm(p.x, q.x, fm(p.y, q.y, acc.x));
+    acc.y = fm(p.y, q.x, fm(-p.x, q.y, acc.y));
+    return acc;
+}
+template <typename V> __device__ __forceinline__ V cmac(V acc, V p, V q) {  // acc + p q
+    acc.x = fm(p.x, q.x, fm(-p.y, q.y, acc.x));
+    acc.y = fm(p.x, q.y, fm(p.y, q.x, acc.y));
+    return acc;
+}
+template <typename V> __device__ __forceinline__ V cmsub_conj(V acc, V p, V q) {  // acc - p conj(q)
+    acc.x = fm(-p.x, q.x, fm(-p.y, q.y, acc.x));
+    acc.y = fm(-p.y, q.x, fm(p.x, q.y, acc.y));
+    return acc;
+}
+template <typename V> __device__ __forceinline__ V cmsub(V acc, V p, V q) {  // acc - p q
+    acc.x = fm(-p.x, q.x, fm(p.y, q.y, acc.x));
+    acc.y = fm(-p.x, q.y, fm(-p.y, q.x, acc.y));
+    return acc;
+}
 
 // L = pad(U) (both triangles copied; only the lower is used), identity on the
 // pad; X = S = 0; dg = the diagonal of U.
@@ -165,19 +191,25 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 
 // FP64 diagonal tile.  FP64 warp instructions occupy the SM's FP64 units for
 // the same time whatever the number of active lanes, so the work is packed
-// into full warps:
-//  * factor: step j updates the active pairs (i, m), j < m <= i, read from a
-//    table of the 528 lower-triangle pairs ordered by m descending (the
-//    active pairs of step j are its first (31 - j)(32 - j) / 2 entries);
-//  * inverse X = L^{-1} by right-looking elimination: once row j of X is
-//    final, every row i > j subtracts L_ij times it, over the (i, c) pairs
-//    c <= j < i (5 456 complex MACs in all, in full warps).
+// into full warps, and the factor and the inverse X = L^{-1} share one loop
+// over the columns j:
+//  A: column j of L (l_ij = a_ij / L_jj, i > j) and row j of X (scaled by
+//     1 / L_jj; its entries c <= j are then final) are formed;
+//  B: the factor's trailing pairs (i, m), j < m <= i, lose l_ij conj(l_mj),
+//     and the inverse's pairs (i, c), c <= j < i, lose l_ij x_jc: one pass
+//     over both sets, 4 fused multiply-adds per pair.  The factor pairs come
+//     from a table of the 528 lower-triangle pairs ordered by m ascending, so
+//     the active ones are its last (31 - j)(32 - j) / 2 entries and the first
+//     of them is (j + 1, j + 1): thread 0 updates it first and then takes the
+//     next pivot while the others carry on.
+// Two barriers per column (64 in all).
 __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* __restrict__ L,
                                                          double2* __restrict__ X, const double* __restrict__ dg,
                                                          int* status) {
+    constexpr int NPAIR = CB * (CB + 1) / 2;
     __shared__ double2 a[CB][CB + 1];
     __shared__ double2 x[CB][CB + 1];
-    __shared__ unsigned short pr[CB * (CB + 1) / 2];
+    __shared__ unsigned short pr[NPAIR];
     __shared__ double rp[CB], pv[CB], fl[CB];
     __shared__ int bad;
     const int r0 = k * CB, tid = threadIdx.x;
@@ -186,11 +218,10 @@ __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* 
         a[i][j] = L[(size_t)(r0 + i) * N + r0 + j];
         x[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
-    // pair table: m descending, then i ascending; entry = i << 8 | m
+    // pair table: m ascending, then i ascending; entry = i << 8 | m
     if (tid < CB) {
-        const int m = CB - 1 - tid;
-        int off = 0;
-        for (int mm = CB - 1; mm > m; --mm) off += CB - mm;
+        const int m = tid;
+        const int off = m * CB - m * (m - 1) / 2;  // pairs in the columns before m
         for (int i = m; i < CB; ++i) pr[off + i - m] = (unsigned short)(i << 8 | m);
         fl[tid] = PivotFloor<double>::v * dg[r0 + tid];
     }
@@ -205,77 +236,77 @@ __global__ void __launch_bounds__(CT) chol_diag64_kernel(int N, int k, double2* 
     };
     if (tid == 0) pivot(0);
     __syncthreads();
-    for (int j = 0; j < CB - 1; ++j) {
-        const int cnt = (CB - 1 - j) * (CB - j) / 2;  // pairs with m > j
-        const double rd = rp[j] * rp[j];
-        for (int e = tid; e < cnt; e += CT) {
-            const int i = pr[e] >> 8, m = pr[e] & 0xff;
-            a[i][m] = csub(a[i][m], cmulc(cscale(a[i][j], rd), a[m][j]));
-            if (i == j + 1 && m == j + 1) pivot(j + 1);
+    for (int j = 0; j < CB; ++j) {
+        const double r = rp[j];
+        if (tid < CB) {
+            if (tid > j) a[tid][j] = cscale(a[tid][j], r);
+        } else if (tid < 2 * CB) {
+            const int c = tid - CB;
+            if (c <= j) x[j][c] = cscale(x[j][c], r);
+        }
+        __syncthreads();
+        const int nf = (CB - 1 - j) * (CB - j) / 2;  // factor pairs
+        const int w = j + 1, nx = (CB - 1 - j) * w;  // inverse pairs (i, c): w per row
+        const int base = NPAIR - nf;
+        // f / w for f < 256 by a float reciprocal: the error stays far below 0.5 / w
+        const float rw = 1.0f / (float)w;
+        for (int e = tid; e < nf + nx; e += CT) {
+            if (e < nf) {
+                const int p = pr[base + e], i = p >> 8, m = p & 0xff;
+                a[i][m] = cmsub_conj(a[i][m], a[i][j], a[m][j]);
+                if (e == 0) pivot(j + 1);
+            } else {
+                const int f = e - nf;
+                const int q = (int)(((float)f + 0.5f) * rw);
+                const int i = j + 1 + q, c = f - q * w;
+                x[i][c] = cmsub(x[i][c], a[i][j], x[j][c]);
+            }
         }
         __syncthreads();
     }
     for (int e = tid; e < CB * CB; e += CT) {
         const int r = e / CB, c = e % CB;
         double2 v = make_double2(0.0, 0.0);
-        if (r > c) v = cscale(a[r][c], rp[c]);
+        if (r > c) v = a[r][c];
         else if (r == c) v = make_double2(pv[r], 0.0);
-        a[r][c] = v;
         L[(size_t)(r0 + r) * N + r0 + c] = v;
-    }
-    __syncthreads();
-    // X = L^{-1}: x starts as the identity; at step j row j is scaled by 1/L_jj
-    // (its entries c <= j are final) and rows i > j lose L_ij times it
-    for (int j = 0; j < CB; ++j) {
-        if (tid <= j) x[j][tid] = cscale(x[j][tid], rp[j]);
-        __syncthreads();
-        const int w = j + 1, cnt = (CB - 1 - j) * w;  // pairs (i, c), i > j, c <= j
-        for (int e = tid; e < cnt; e += CT) {
-            const int i = j + 1 + e / w, c = e % w;
-            x[i][c] = csub(x[i][c], cmul(a[i][j], x[j][c]));
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < CB * CB; e += CT) {
-        const int i = e / CB, j = e % CB;
-        X[(size_t)(r0 + i) * N + r0 + j] = x[i][j];
+        X[(size_t)(r0 + r) * N + r0 + c] = x[r][c];
     }
     if (tid == 0 && bad) *status = JDFT_ERR_NOT_POSDEF;
 }
 
 // Panel: L_ik = A_ik X_kk^dag for tile rows i > k (blockIdx.x = i - k - 1),
-// rows [16 h, 16 h + 16) of the tile for blockIdx.y = h (a block overwrites
-// only the rows it read).
+// rows [4 h, 4 h + 4) of the tile for blockIdx.y = h (a block overwrites only
+// the rows it read; eight blocks share a tile row's FP64 work).
+constexpr int PR = 4;  // panel rows per block
 template <typename S>
 __global__ void __launch_bounds__(CT) chol_panel_kernel(int N, int k, c_t<S>* __restrict__ L,
                                                         const c_t<S>* __restrict__ X) {
     using V = c_t<S>;
-    __shared__ V a[CQ][CB + 1];
+    __shared__ V a[PR][CB + 1];
     __shared__ V xk[CB][CB + 1];
     const int i = k + 1 + blockIdx.x, h = blockIdx.y;
-    const int ri = i * CB + h * CQ, rk = k * CB;
+    const int ri = i * CB + h * PR, rk = k * CB;
     for (int e = threadIdx.x; e < CB * CB; e += CT) {
         const int r = e / CB, c = e % CB;
-        if (r < CQ) a[r][c] = L[(size_t)(ri + r) * N + rk + c];
+        if (r < PR) a[r][c] = L[(size_t)(ri + r) * N + rk + c];
         xk[r][c] = X[(size_t)(rk + r) * N + rk + c];
     }
     __syncthreads();
     // out[r][c] = sum_{m <= c} a[r][m] conj(xk[c][m])  (xk lower triangular).
-    // Warp w takes columns c = w + 8 q; its lanes are 16 rows x 2 halves of the
-    // m range (equal lengths, so no lane idles through a longer one), and a
-    // shuffle adds the halves.
-    {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = lane & 15, hf = lane >> 4;
-        for (int c = warp; c < CB; c += CT / 32) {
-            const int mid = (c + 2) / 2;
-            const int mlo = hf ? mid : 0, mhi = hf ? c + 1 : mid;
-            V sum = mk<S>(S(0), S(0));
-            for (int m = mlo; m < mhi; ++m) sum = cadd(sum, cmulc(a[r][m], xk[c][m]));
-            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, 16);
-            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, 16);
-            if (hf == 0) L[(size_t)(ri + r) * N + rk + c] = sum;
+    // Warp w takes columns c = w + 8 q; lane (r, s) = (lane / 8, lane % 8)
+    // sums m = s, s + 8, ... and three shuffles add the 8 partial sums.
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane >> 3, sg = lane & 7;
+    for (int c = warp; c < CB; c += CT / 32) {
+        V sum = mk<S>(S(0), S(0));
+        for (int m = sg; m <= c; m += 8) sum = cmac_conj(sum, a[r][m], xk[c][m]);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
         }
+        if (sg == 0) L[(size_t)(ri + r) * N + rk + c] = sum;
     }
 }
 
@@ -297,28 +328,44 @@ __device__ __forceinline__ void tri_pair(int p, int& i, int& j) {
     j = p - ii * (ii + 1) / 2;
 }
 
-// Trailing update: A_ij -= L_ik L_jk^dag for i >= j > k; blockIdx.x enumerates the pairs.
+// Trailing update: A_ij -= L_ik L_jk^dag for i >= j > k; blockIdx.x
+// enumerates the tile pairs, blockIdx.y = 4 br + bc the 8 x 8 output block
+// (br, bc) of the tile (blocks above the diagonal of a diagonal tile return at
+// once).  Warp w takes output row w of the block; lane (c, s) = (lane % 8,
+// lane / 8) sums m = s, s + 4, ... and two shuffles add the 4 partial sums, so
+// a tile pair's FP64 work is spread over 16 blocks.
+constexpr int UB = 8;  // update output block edge
 template <typename S>
 __global__ void __launch_bounds__(CT) chol_update_kernel(int N, int k, c_t<S>* __restrict__ L) {
     using V = c_t<S>;
-    __shared__ V li[CQ][CB + 1];
-    __shared__ V lj[CQ][CB + 1];
+    __shared__ V li[UB][CB + 1];
+    __shared__ V lj[UB][CB + 1];
     int ii, jj;
     tri_pair(blockIdx.x, ii, jj);
     const int i = k + 1 + ii, j = k + 1 + jj;
-    const Quad q;
+    const int br = (int)(blockIdx.y >> 2) * UB, bc = (int)(blockIdx.y & 3) * UB;
+    if (i == j && bc > br) return;  // the whole block: upper part of a diagonal tile
     const int rk = k * CB;
-    for (int e = threadIdx.x; e < CQ * CB; e += CT) {
-        const int r = e / CB, c = e % CB;
-        li[r][c] = L[(size_t)(i * CB + q.qr + r) * N + rk + c];
-        lj[r][c] = L[(size_t)(j * CB + q.qc + r) * N + rk + c];
+    {
+        const int r = threadIdx.x / CB, c = threadIdx.x % CB;  // UB x CB = CT elements
+        li[r][c] = L[(size_t)(i * CB + br + r) * N + rk + c];
+        lj[r][c] = L[(size_t)(j * CB + bc + r) * N + rk + c];
     }
     __syncthreads();
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = lane & 7, sg = lane >> 3;
     V s = mk<S>(S(0), S(0));
-#pragma unroll 8
-    for (int m = 0; m < CB; ++m) s = cadd(s, cmulc(li[q.r][m], lj[q.c][m]));
-    V* dst = &L[(size_t)(i * CB + q.qr + q.r) * N + j * CB + q.qc + q.c];
-    *dst = csub(*dst, s);
+#pragma unroll
+    for (int m = sg; m < CB; m += 4) s = cmac_conj(s, li[r][m], lj[c][m]);
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    if (sg == 0) {
+        V* dst = &L[(size_t)(i * CB + br + r) * N + j * CB + bc + c];
+        *dst = csub(*dst, s);
+    }
 }
 
 // Inverse, tile row i: S_ik += L_ij X_jk for every k <= j < i (blockIdx.x enumerates the (j, k) pairs).
@@ -340,7 +387,7 @@ __global__ void __launch_bounds__(CT) inv_accum_kernel(int N, int i, const c_t<S
     __syncthreads();
     V s = mk<S>(S(0), S(0));
 #pragma unroll 8
-    for (int m = 0; m < CB; ++m) s = cadd(s, cmul(l[q.r][m], x[m][q.c]));
+    for (int m = 0; m < CB; ++m) s = cmac(s, l[q.r][m], x[m][q.c]);
     V* dst = &Sa[(size_t)(i * CB + q.qr + q.r) * N + k * CB + q.qc + q.c];
     atomicAdd(&dst->x, s.x);
     atomicAdd(&dst->y, s.y);
@@ -364,7 +411,7 @@ __global__ void __launch_bounds__(CT) inv_finish_kernel(int N, int i, c_t<S>* __
     __syncthreads();
     V s = mk<S>(S(0), S(0));
     const int rr = q.qr + q.r;  // row within the tile; X_ii is lower triangular
-    for (int m = 0; m <= rr; ++m) s = cadd(s, cmul(d[q.r][m], s_[m][q.c]));
+    for (int m = 0; m <= rr; ++m) s = cmac(s, d[q.r][m], s_[m][q.c]);
     X[(size_t)(i * CB + rr) * N + k * CB + q.qc + q.c] = mk<S>(-s.x, -s.y);
 }
 
@@ -697,11 +744,11 @@ static jdft_status run_blocked(int n, const double2* U, double2* work, c_t<T>* W
         if (m > 0) {
             {
                 Trace tr_("chol_panel", st);
-                chol_panel_kernel<S><<<dim3(m, CB / CQ), CT, 0, st>>>(N, k, L, X);
+                chol_panel_kernel<S><<<dim3(m, CB / PR), CT, 0, st>>>(N, k, L, X);
             }
             {
                 Trace tr_("chol_update", st);
-                chol_update_kernel<S><<<dim3(m * (m + 1) / 2, 4), CT, 0, st>>>(N, k, L);
+                chol_update_kernel<S><<<dim3(m * (m + 1) / 2, (CB / UB) * (CB / UB)), CT, 0, st>>>(N, k, L);
             }
         }
     }
