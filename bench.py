@@ -227,8 +227,10 @@ class Problem:
         b["n"].zero_()
         j.jdft_apply_H_density(self.basis, 0, b["C"], b["HC"], self.f, b["n"], self.prec, stream)
         j.jdft_subspace(self.basis, 0, b["C"], b["HC"], b["CHC"], b["COC"], self.prec, stream)
-        # no host wait per step: a failure lands in self.status (see check_status)
-        j.jdft_orthonormalize_async(self.basis, 0, b["C"], self.status, self.prec, stream)
+        # the overlap C^dag O C just formed is the orthonormalisation's U (one
+        # overlap per iteration); no host wait per step: a failure lands in
+        # self.status (see check_status)
+        j.jdft_orthonormalize_async(self.basis, 0, b["C"], self.status, self.prec, stream, U=b["COC"])
 
     def check_status(self):
         """Raise if any orthonormalisation since set-up met linearly dependent bands."""

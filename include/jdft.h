@@ -196,10 +196,14 @@ jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, in
  * and the factorisation's outcome is merged into the caller's device word
  * *status (max of the old value and JDFT_ERR_NOT_POSDEF on linearly dependent
  * bands, else unchanged), so a pipeline of steps can check once for all of
- * them.  Returns argument and launch errors only.  The paper has no such
- * call. */
-jdft_status jdft_orthonormalize_async(jdft_basis_t basis, int ik, void* C, int ldc, int nb, jdft_prec prec,
-                                      int* status, void* stream);
+ * them.  U: NULL, or the overlap C^dag O C of this very block (device,
+ * nb x nb row-major complex128, e.g. the COC output of jdft_subspace for the
+ * same C), which is then read instead of recomputed: one iteration of the
+ * minimiser forms the overlap once and uses it for both the subspace matrices
+ * and the orthonormalisation (Sec. 2.1).  Returns argument and launch errors
+ * only.  The paper has no such call. */
+jdft_status jdft_orthonormalize_async(jdft_basis_t basis, int ik, void* C, int ldc, int nb, const void* U,
+                                      jdft_prec prec, int* status, void* stream);
 
 /* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
  * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,

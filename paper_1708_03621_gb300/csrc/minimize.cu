@@ -617,7 +617,7 @@ __global__ void status_merge_kernel(const int* __restrict__ src, int* __restrict
 // otherwise the status is merged into the device word *sticky and nothing waits.
 template <typename T>
 static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc, int nb, jdft_prec prec,
-                                       cudaStream_t st, int* sticky = nullptr) {
+                                       cudaStream_t st, int* sticky = nullptr, const double2* Ugiven = nullptr) {
     const int npw = b->ks[ik].npw;
     const int m = nb + (nb & 1);
     const size_t sm = ((size_t)nb * nb * sizeof(double2) + 255) / 256 * 256;
@@ -634,9 +634,13 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
     c_t<T>* tmp = (c_t<T>*)(q + sm + wbytes + lab);
     int* status = (int*)(q + sm + wbytes + lab + blk);
     JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
-    JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)nb * nb * sizeof(double2), st));
-    if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega, st)))
-        return s;
+    if (Ugiven) {
+        U = const_cast<double2*>(Ugiven);  // read only
+    } else {
+        JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)nb * nb * sizeof(double2), st));
+        if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega, st)))
+            return s;
+    }
     if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
     if (gemm_nn_inplace_ok(prec, nb)) {
         // C <- C W in place: each block reads its rows of C for every band before writing them
@@ -674,16 +678,17 @@ jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb
                              : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st);
 }
 
-jdft_status jdft_orthonormalize_async(jdft_basis_t b, int ik, void* C, int ldc, int nb, jdft_prec prec,
-                                      int* status, void* stream) {
+jdft_status jdft_orthonormalize_async(jdft_basis_t b, int ik, void* C, int ldc, int nb, const void* U,
+                                      jdft_prec prec, int* status, void* stream) {
     clear_error();
     JDFT_CHECK_ARG(b && C && status, "null argument");
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
     JDFT_CHECK_ARG(nb >= 1 && ldc >= b->ks[ik].npw, "bad block shape");
     JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
     cudaStream_t st = (cudaStream_t)stream;
-    return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st, status)
-                             : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st, status);
+    const double2* Ug = (const double2*)U;
+    return prec == JDFT_FP64 ? orthonormalize_impl<double>(b, ik, C, ldc, nb, prec, st, status, Ug)
+                             : orthonormalize_impl<float>(b, ik, C, ldc, nb, prec, st, status, Ug);
 }
 
 jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream) {

@@ -94,7 +94,7 @@ _SIGS = {
     "jdft_batch_launch": [_vp, _vp],
     "jdft_batch_destroy": [_vp],
     "jdft_autotune_chunk": [_vp, _i, _vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _vp],
-    "jdft_orthonormalize_async": [_vp, _i, _vp, _i, _i, _i, _vp, _vp],
+    "jdft_orthonormalize_async": [_vp, _i, _vp, _i, _i, _vp, _i, _vp, _vp],
     "jdft_autotune_gemm": [_i, _i, _i, _vp, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp],
     "jdft_autotune": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
     "jdft_profile_enable": [_i],
@@ -314,10 +314,18 @@ def jdft_orthonormalize(basis, ik, C, prec="fp64", stream=None):
     _call("jdft_orthonormalize", basis.handle, ik, p, ld, nb, _prec(prec), _stream(stream))
 
 
-def jdft_orthonormalize_async(basis, ik, C, status, prec="fp64", stream=None):
-    """jdft_orthonormalize without the wait; failures are merged into the device int32 tensor `status`."""
+def jdft_orthonormalize_async(basis, ik, C, status, prec="fp64", stream=None, U=None):
+    """jdft_orthonormalize without the wait; failures are merged into the device int32 tensor `status`.
+
+    U: None, or the complex128 (nb, nb) CUDA tensor C^dag O C of this block
+    (the COC output of jdft_subspace), read instead of recomputed."""
+    import torch
     p, ld, nb = _block(C, prec, "C")
-    _call("jdft_orthonormalize_async", basis.handle, ik, p, ld, nb, _prec(prec), _ptr(status), _stream(stream))
+    if U is not None:
+        assert U.is_cuda and U.dtype == torch.complex128 and tuple(U.shape) == (nb, nb) and U.is_contiguous(), \
+            "U must be a contiguous complex128 (nb, nb) CUDA tensor"
+    _call("jdft_orthonormalize_async", basis.handle, ik, p, ld, nb, _ptr(U) if U is not None else None,
+          _prec(prec), _ptr(status), _stream(stream))
 
 
 def jdft_subspace_eigs(A, eigs, stream=None):

@@ -39,7 +39,7 @@ def test_null_arguments_rejected():
     assert L.jdft_density(None, 0, None, 0, None, 1, None, 0, None) == 1
     assert L.jdft_apply_H_density(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
     assert L.jdft_autotune(None, 0, None, 0, None, 0, 1, 3, None, None) == 1
-    assert L.jdft_orthonormalize_async(None, 0, None, 1, 1, 0, None, None) == 1
+    assert L.jdft_orthonormalize_async(None, 0, None, 1, 1, None, 0, None, None) == 1
     assert L.jdft_autotune_gemm(0, 1, 1, None, 1, None, 1, 3, None, None) == 1
     assert L.jdft_subspace(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
     assert L.jdft_basis_npw(None, 0, None) == 1

@@ -134,6 +134,30 @@ def test_orthonormalize_async_matches_and_status_is_sticky(prec):
     assert int(st.item()) == jdft.STATUS_CODES["ERR_NOT_POSDEF"]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_orthonormalize_with_given_overlap(prec):
+    """U = the COC output of jdft_subspace for the same block gives the block
+    that recomputing the overlap gives, and C^dag O C = 1 afterwards."""
+    from paper_1708_03621_gb300 import jdft
+    w, o, g = systems("mid")
+    ct = np.complex128 if prec == "fp64" else np.complex64
+    C = o.coeffs(70, seed=43)
+    A = torch.tensor(C.astype(ct), device="cuda")
+    B = A.clone()
+    nb = A.shape[0]
+    COC = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    jdft.jdft_subspace(g.basis, 0, B, None, None, COC, prec)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    jdft.jdft_orthonormalize(g.basis, 0, A, prec)
+    jdft.jdft_orthonormalize_async(g.basis, 0, B, st, prec, U=COC)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    a, b = A.cpu().numpy().astype(np.complex128), B.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(a - b)) < (1e-12 if prec == "fp64" else 1e-5) * np.max(np.abs(a))
+    Q = b.T
+    assert np.allclose(o.basis.Omega * Q.conj().T @ Q, np.eye(nb), atol=1e-12 if prec == "fp64" else 2e-5)
+
+
 @pytest.mark.parametrize("precond", ["teter", "identity"])
 def test_minimize_tiny_reaches_dense_eigenvalues(precond):
     from paper_1708_03621_gb300 import jdft
