@@ -325,8 +325,8 @@ def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
 # the 128^3 workload, --nbands 64; profiles/plane_apply_density_fast_128cubed_bf16x3.md),
 # scaled by the bands a launch processes.  ncu replays with cold caches, so
 # this bounds the warm traffic from above.  Only valid for the kernel version
-# it was taken on: set to None when the kernel changes.
-TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150325760 + 87282944) / 64}
+# it was taken on: drop the entry when the kernel changes.
+TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150333184 + 87319296) / 64}
 
 
 def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:

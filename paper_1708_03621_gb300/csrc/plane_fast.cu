@@ -34,44 +34,87 @@ __device__ __forceinline__ int wrapf(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Elements of warp-private scratch: LPW padded lines of the longer axis.
-template <int N0, int E0, int N1, int E1>
-__host__ __device__ constexpr int warp_scratch() {
-    return (32 / (N0 / E0)) * padded_line(N0) > (32 / (N1 / E1)) * padded_line(N1)
-               ? (32 / (N0 / E0)) * padded_line(N0)
-               : (32 / (N1 / E1)) * padded_line(N1);
-}
+// Shared-memory layout of the register-FFT kernels.  A warp's 8-byte shared
+// access is served in two halves of 16 lanes and a 16-byte access in four
+// quarters of 8 lanes; lanes of one group that hit different addresses in the
+// same bank slot (16 eight-byte or 8 sixteen-byte slots per 128 bytes) cost
+// one wavefront each.  The constants below are the ones with the fewest such
+// conflicts over every shared access of these kernels, counted access by
+// access (plane_layout.py beside this package prints them); the 128^3 FP32
+// plane pass has none.
+//
+// Lanes: a line of N values is split over TL = N / E lanes and a warp serves
+// LPW = 32 / TL lines; lane l takes position l / LPW of line l % LPW, so a
+// half-warp covers several lines at once and several consecutive rows or
+// columns of the plane array.
+template <int N, int E>
+struct Lanes {
+    static constexpr int TL = N / E, LPW = 32 / TL;
+    static __device__ __forceinline__ int line(int lane) { return lane % LPW; }
+    static __device__ __forceinline__ int pos(int lane) { return lane / LPW; }
+};
 
-// Row stride of the plane array A (elements): N1 + pad, with the smallest pad
-// for which both warp access patterns spread evenly over the bank slots
-// (16 eight-byte slots per 128 bytes for float2, 8 sixteen-byte slots for
-// double2): LPW1 rows x TL1 consecutive positions in the row passes, TL0
-// consecutive rows x LPW0 consecutive columns in the column pass.
+// Elements between the LPW scratch lines of one warp (each line needs
+// padded_line(N)).
+template <typename T, int N>
+struct ScratchSpacing;
+#define JDFT_SCRATCH_SPACING(T, N, SP)                                                      \
+    template <>                                                                             \
+    struct ScratchSpacing<T, N> {                                                           \
+        static constexpr int value = SP;                                                    \
+        static_assert(SP >= padded_line(N), "scratch lines of one warp must not overlap"); \
+    };
+JDFT_SCRATCH_SPACING(float, 12, 13)
+JDFT_SCRATCH_SPACING(float, 16, 17)
+JDFT_SCRATCH_SPACING(float, 40, 43)
+JDFT_SCRATCH_SPACING(float, 48, 54)
+JDFT_SCRATCH_SPACING(float, 64, 68)
+JDFT_SCRATCH_SPACING(float, 80, 86)
+JDFT_SCRATCH_SPACING(float, 128, 140)
+JDFT_SCRATCH_SPACING(float, 256, 280)
+JDFT_SCRATCH_SPACING(double, 12, 13)
+JDFT_SCRATCH_SPACING(double, 16, 17)
+JDFT_SCRATCH_SPACING(double, 40, 43)
+JDFT_SCRATCH_SPACING(double, 48, 51)
+JDFT_SCRATCH_SPACING(double, 64, 70)
+JDFT_SCRATCH_SPACING(double, 80, 85)
+JDFT_SCRATCH_SPACING(double, 128, 138)
+JDFT_SCRATCH_SPACING(double, 256, 276)
+#undef JDFT_SCRATCH_SPACING
+
+// Row stride (elements) of the plane array A of an S0 x S1 plane.
+template <typename T, int N0, int N1>
+struct PlaneStride;
+#define JDFT_PLANE_STRIDE(T, N0, N1, LS)    \
+    template <>                             \
+    struct PlaneStride<T, N0, N1> {         \
+        static constexpr int value = LS;    \
+        static_assert(LS > N1, "row pad"); \
+    };
+JDFT_PLANE_STRIDE(float, 12, 12, 13)
+JDFT_PLANE_STRIDE(float, 16, 12, 13)
+JDFT_PLANE_STRIDE(float, 40, 40, 41)
+JDFT_PLANE_STRIDE(float, 48, 48, 50)
+JDFT_PLANE_STRIDE(float, 64, 64, 68)
+JDFT_PLANE_STRIDE(float, 80, 80, 82)
+JDFT_PLANE_STRIDE(float, 128, 128, 132)
+JDFT_PLANE_STRIDE(float, 256, 128, 130)
+JDFT_PLANE_STRIDE(double, 12, 12, 13)
+JDFT_PLANE_STRIDE(double, 16, 12, 13)
+JDFT_PLANE_STRIDE(double, 40, 40, 41)
+JDFT_PLANE_STRIDE(double, 48, 48, 49)
+JDFT_PLANE_STRIDE(double, 64, 64, 66)
+JDFT_PLANE_STRIDE(double, 80, 80, 81)
+JDFT_PLANE_STRIDE(double, 128, 128, 130)
+JDFT_PLANE_STRIDE(double, 256, 128, 130)
+#undef JDFT_PLANE_STRIDE
+
+// Elements of warp-private scratch: the LPW lines of the axis that needs more.
 template <typename T, int N0, int E0, int N1, int E1>
-__host__ __device__ constexpr int a_stride() {
-    constexpr int SLOTS = 128 / (int)sizeof(c_t<T>);
-    constexpr int TL0 = N0 / E0, TL1 = N1 / E1;
-    int best = 1, bestc = 1 << 30;
-    for (int pad = 1; pad <= SLOTS; ++pad) {
-        const int st = (N1 + pad) % SLOTS;
-        int c1[16] = {}, c2[16] = {};
-        int m1 = 0, m2 = 0;
-        for (int l = 0; l < 32 / TL1; ++l)
-            for (int t = 0; t < TL1; ++t) {
-                const int a = (l * st + t) % SLOTS;
-                if (++c1[a] > m1) m1 = c1[a];
-            }
-        for (int l = 0; l < 32 / TL0; ++l)
-            for (int t = 0; t < TL0; ++t) {
-                const int b = (t * st + l) % SLOTS;
-                if (++c2[b] > m2) m2 = c2[b];
-            }
-        if (m1 + m2 < bestc) {
-            bestc = m1 + m2;
-            best = pad;
-        }
-    }
-    return N1 + best;
+__host__ __device__ constexpr int warp_scratch() {
+    return Lanes<N0, E0>::LPW * ScratchSpacing<T, N0>::value > Lanes<N1, E1>::LPW * ScratchSpacing<T, N1>::value
+               ? Lanes<N0, E0>::LPW * ScratchSpacing<T, N0>::value
+               : Lanes<N1, E1>::LPW * ScratchSpacing<T, N1>::value;
 }
 
 // Phase 1 / 3 helpers -------------------------------------------------------
@@ -79,9 +122,10 @@ template <typename T, int N1, int E1, class R1, int NW = kFastWarps>
 __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<T>* __restrict__ plane, c_t<T>* A,
                                                   int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
     using F = LineFFT<T, N1, E1, +1, R1>;
-    constexpr int TL = N1 / E1, LPW = 32 / TL;
-    const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = wscr + liw * padded_line(N1);
+    using LN = Lanes<N1, E1>;
+    constexpr int LPW = LN::LPW;
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    c_t<T>* scr = wscr + liw * ScratchSpacing<T, N1>::value;
     for (int base = warp * LPW; base < g.nrows; base += NW * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
@@ -109,9 +153,10 @@ template <typename T, int N1, int E1, class R1, int NW = kFastWarps>
 __device__ __forceinline__ void rows_forward_fast(const ChainGeom& g, c_t<T>* __restrict__ plane, const c_t<T>* A,
                                                   int lsA, c_t<T>* wscr, const c_t<T>* W1, int warp, int lane) {
     using F = LineFFT<T, N1, E1, -1, R1>;
-    constexpr int TL = N1 / E1, LPW = 32 / TL;
-    const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = wscr + liw * padded_line(N1);
+    using LN = Lanes<N1, E1>;
+    constexpr int LPW = LN::LPW;
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    c_t<T>* scr = wscr + liw * ScratchSpacing<T, N1>::value;
     for (int base = warp * LPW; base < g.nrows; base += NW * LPW) {
         const int r = base + liw;
         const bool act = r < g.nrows;
@@ -152,8 +197,8 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
                                                                         const c_t<T>* __restrict__ tw0,
                                                                         const c_t<T>* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int lsA = a_stride<T, N0, E0, N1, E1>();
-    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();  // per-warp scratch (LPW padded lines)
+    constexpr int lsA = PlaneStride<T, N0, N1>::value;
+    constexpr int SCR = warp_scratch<T, N0, E0, N1, E1>();  // per-warp scratch (LPW lines)
     c_t<T>* W0 = reinterpret_cast<c_t<T>*>(smem_raw);
     c_t<T>* W1 = W0 + N0;
     c_t<T>* scr_all = W1 + N1;
@@ -171,9 +216,10 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
 
     {
         using FI = LineFFT<T, N0, E0, +1, R0>;
-        constexpr int TL = N0 / E0, LPW = 32 / TL;
-        const int liw = lane / TL, t = lane % TL;
-        c_t<T>* scr = wscr + liw * padded_line(N0);
+        using LN = Lanes<N0, E0>;
+        constexpr int LPW = LN::LPW;
+        const int liw = LN::line(lane), t = LN::pos(lane);
+        c_t<T>* scr = wscr + liw * ScratchSpacing<T, N0>::value;
         for (int base = warp * LPW; base < N1; base += kFastWarps * LPW) {
             const int j1 = base + liw;
             const bool act = j1 < N1;
@@ -210,9 +256,10 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
                                                                           const float2* __restrict__ tw0,
                                                                           const float2* __restrict__ tw1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int lsA = a_stride<float, N0, E0, N1, E1>();
-    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
-    constexpr int TL = N0 / E0, LPW = 32 / TL;
+    constexpr int lsA = PlaneStride<float, N0, N1>::value;
+    constexpr int SCR = warp_scratch<float, N0, E0, N1, E1>();
+    using LN = Lanes<N0, E0>;
+    constexpr int LPW = LN::LPW;
     constexpr int ROUNDS = (N1 + NW * LPW - 1) / (NW * LPW);
     float2* W0 = reinterpret_cast<float2*>(smem_raw);
     float2* W1 = W0 + N0;
@@ -225,7 +272,7 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
     __syncthreads();
     const int j2 = blockIdx.x;
     const int bA = blockIdx.y * bands_per_block, bB = min(nb, bA + bands_per_block);
-    const int liw = lane / TL, t = lane % TL;
+    const int liw = LN::line(lane), t = LN::pos(lane);
     float acc[ROUNDS][E0];
 #pragma unroll
     for (int k = 0; k < ROUNDS; ++k)
@@ -240,7 +287,8 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * NW * LPW;
             float2 v[E0];
-            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t, wscr + liw * padded_line(N0), W0);
+            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t,
+                                                   wscr + liw * ScratchSpacing<float, N0>::value, W0);
 #pragma unroll
             for (int e = 0; e < E0; ++e) acc[k][e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
         }
@@ -279,9 +327,10 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
     static_assert(E0 == 16, "the tensor-memory sums take 16 values per lane and round");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t tslot;
-    constexpr int lsA = a_stride<float, N0, E0, N1, E1>();
-    constexpr int SCR = warp_scratch<N0, E0, N1, E1>();
-    constexpr int TL = N0 / E0, LPW = 32 / TL;
+    constexpr int lsA = PlaneStride<float, N0, N1>::value;
+    constexpr int SCR = warp_scratch<float, N0, E0, N1, E1>();
+    using LN = Lanes<N0, E0>;
+    constexpr int LPW = LN::LPW;
     constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
     static_assert(ROUNDS * 16 <= 64, "at most 64 sums per lane");
     using FI = LineFFT<float, N0, E0, +1, R0>;
@@ -290,9 +339,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
     float2* scr_all = W1 + N1;
     float2* A = scr_all + kFastWarps * SCR;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int liw = lane / TL, t = lane % TL;
+    const int liw = LN::line(lane), t = LN::pos(lane);
     float2* wscr = scr_all + warp * SCR;
-    float2* scr = wscr + liw * padded_line(N0);
+    float2* scr = wscr + liw * ScratchSpacing<float, N0>::value;
     for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = tw0[i];
     for (int i = threadIdx.x; i < N1; i += blockDim.x) W1[i] = tw1[i];
     if (warp == 0) tc::tmem_alloc(&tslot, 128);
@@ -385,11 +434,12 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainG
                                                                           const c_t<T>* __restrict__ tw2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using F = LineFFT<T, N2, E2, +1, R2>;
-    constexpr int TL = N2 / E2, LPW = 32 / TL;
+    using LN = Lanes<N2, E2>;
+    constexpr int LPW = LN::LPW;
     c_t<T>* W = reinterpret_cast<c_t<T>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = W + N2 + (warp * LPW + liw) * padded_line(N2);
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    c_t<T>* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<T, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
     const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
@@ -425,11 +475,12 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainG
                                                                           const c_t<T>* __restrict__ tw2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using F = LineFFT<T, N2, E2, -1, R2>;
-    constexpr int TL = N2 / E2, LPW = 32 / TL;
+    using LN = Lanes<N2, E2>;
+    constexpr int LPW = LN::LPW;
     c_t<T>* W = reinterpret_cast<c_t<T>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int liw = lane / TL, t = lane % TL;
-    c_t<T>* scr = W + N2 + (warp * LPW + liw) * padded_line(N2);
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    c_t<T>* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<T, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
     const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
@@ -479,8 +530,10 @@ constexpr size_t kFastMaxSmem = 220 * 1024;
 template <int N0, int N1>
 static size_t fast_smem(const ChainGeom& g, size_t elem, int nw = kFastWarps) {
     constexpr int E0 = FastCfg<N0>::E, E1 = FastCfg<N1>::E;
-    const int lsA = elem == sizeof(double2) ? a_stride<double, N0, E0, N1, E1>() : a_stride<float, N0, E0, N1, E1>();
-    return ((size_t)N0 + N1 + (size_t)nw * warp_scratch<N0, E0, N1, E1>() + (size_t)g.nrows * lsA) * elem;
+    const bool dbl = elem == sizeof(double2);
+    const int lsA = dbl ? PlaneStride<double, N0, N1>::value : PlaneStride<float, N0, N1>::value;
+    const int scr = dbl ? warp_scratch<double, N0, E0, N1, E1>() : warp_scratch<float, N0, E0, N1, E1>();
+    return ((size_t)N0 + N1 + (size_t)nw * scr + (size_t)g.nrows * lsA) * elem;
 }
 
 // Warps of a density block: enough that the per-lane accumulators of the
@@ -538,10 +591,10 @@ static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, c
     return check_launch("plane_density_fast");
 }
 
-template <int N2>
-static size_t zpass_fast_smem(size_t elem) {
-    constexpr int TL = N2 / FastCfg<N2>::E, LPW = 32 / TL;
-    return ((size_t)N2 + (size_t)kFastWarps * LPW * padded_line(N2)) * elem;
+template <typename T, int N2>
+static size_t zpass_fast_smem() {
+    constexpr int LPW = Lanes<N2, FastCfg<N2>::E>::LPW;
+    return ((size_t)N2 + (size_t)kFastWarps * LPW * ScratchSpacing<T, N2>::value) * sizeof(c_t<T>);
 }
 
 template <int N2>
@@ -555,7 +608,7 @@ static jdft_status zinv_fast_impl(const ChainGeom& g, const c_t<T>* C, int ldc, 
                                   const c_t<T>* tw2, cudaStream_t st) {
     using C2 = FastCfg<N2>;
     auto kern = zpass_inverse_fast_kernel<T, N2, C2::E, typename C2::R>;
-    const size_t smem = zpass_fast_smem<N2>(sizeof(c_t<T>));
+    const size_t smem = zpass_fast_smem<T, N2>();
     cudaError_t e = set_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_inverse_fast: ") + cudaGetErrorString(e));
     {
@@ -571,7 +624,7 @@ static jdft_status zfwd_fast_impl(const ChainGeom& g, const c_t<T>* colbuf, cons
                                   cudaStream_t st) {
     using C2 = FastCfg<N2>;
     auto kern = zpass_forward_fast_kernel<T, N2, C2::E, typename C2::R, MODE>;
-    const size_t smem = zpass_fast_smem<N2>(sizeof(c_t<T>));
+    const size_t smem = zpass_fast_smem<T, N2>();
     cudaError_t e = set_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_forward_fast: ") + cudaGetErrorString(e));
     {
