@@ -326,7 +326,7 @@ def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
 # scaled by the bands a launch processes.  ncu replays with cold caches, so
 # this bounds the warm traffic from above.  Only valid for the kernel version
 # it was taken on: drop the entry when the kernel changes.
-TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150333184 + 87319296) / 64}
+TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150346496 + 87341568) / 64}
 
 
 def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:

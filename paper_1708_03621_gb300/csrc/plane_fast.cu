@@ -29,9 +29,16 @@ namespace jdft {
 constexpr int kFastThreads = 256;
 constexpr int kFastWarps = kFastThreads / 32;
 
-__device__ __forceinline__ int wrapf(int i, int n) {
-    int r = i % n;
-    return r < 0 ? r + n : r;
+// i mod N in [0, N) for either sign of i: one bit mask when N is a power of
+// two (two's complement), else a remainder and a correction.
+template <int N>
+__device__ __forceinline__ int wrapn(int i) {
+    if constexpr ((N & (N - 1)) == 0) {
+        return i & (N - 1);
+    } else {
+        const int r = i % N;
+        return r < 0 ? r + N : r;
+    }
 }
 
 // Shared-memory layout of the register-FFT kernels.  A warp's 8-byte shared
@@ -138,7 +145,7 @@ __device__ __forceinline__ void rows_inverse_fast(const ChainGeom& g, const c_t<
         c_t<T> v[E1];
 #pragma unroll
         for (int e = 0; e < E1; ++e) {
-            const int off = wrapf(F::in_index(t, e) - lo, N1);
+            const int off = wrapn<N1>(F::in_index(t, e) - lo);
             v[e] = (off < cnt) ? plane[cs + off] : mk<T>(T(0), T(0));
         }
         F::run(v, t, scr, W1);
@@ -170,7 +177,7 @@ __device__ __forceinline__ void rows_forward_fast(const ChainGeom& g, c_t<T>* __
             const int lo = g.row_i1lo[r];
 #pragma unroll
             for (int e = 0; e < E1; ++e) {
-                const int off = wrapf(F::out_index(t, e) - lo, N1);
+                const int off = wrapn<N1>(F::out_index(t, e) - lo);
                 if (off < cnt) plane[cs + off] = v[e];
             }
         }
@@ -184,7 +191,7 @@ __device__ __forceinline__ void column_inverse_fast(const ChainGeom& g, const c_
     using F = LineFFT<T, N0, E0, +1, R0>;
 #pragma unroll
     for (int e = 0; e < E0; ++e) {
-        const int r = wrapf(F::in_index(t, e) - g.i0min, N0);
+        const int r = wrapn<N0>(F::in_index(t, e) - g.i0min);
         v[e] = (act && r < g.nrows) ? A[r * lsA + j1] : mk<T>(T(0), T(0));
     }
     F::run(v, t, scr, W0);
@@ -220,9 +227,11 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
         constexpr int LPW = LN::LPW;
         const int liw = LN::line(lane), t = LN::pos(lane);
         c_t<T>* scr = wscr + liw * ScratchSpacing<T, N0>::value;
+        // every lane has a column when the rounds tile the plane exactly
+        constexpr bool kAllCols = N1 % (kFastWarps * LPW) == 0;
         for (int base = warp * LPW; base < N1; base += kFastWarps * LPW) {
             const int j1 = base + liw;
-            const bool act = j1 < N1;
+            const bool act = kAllCols || j1 < N1;
             c_t<T> v[E0];
             column_inverse_fast<T, N0, E0, R0>(g, A, lsA, j1, act, v, t, scr, W0);
             const T* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(kFastThreads) plane_apply_fast_kernel(ChainGeo
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E0; ++e) {
-                    const int r = wrapf(FI::in_index(t, e) - g.i0min, N0);
+                    const int r = wrapn<N0>(FI::in_index(t, e) - g.i0min);
                     if (r < g.nrows) A[r * lsA + j1] = v[e];
                 }
             }
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
     using LN = Lanes<N0, E0>;
     constexpr int LPW = LN::LPW;
     constexpr int ROUNDS = (N1 + NW * LPW - 1) / (NW * LPW);
+    constexpr bool kAllCols = N1 % (NW * LPW) == 0;  // every lane has a column in every round
     float2* W0 = reinterpret_cast<float2*>(smem_raw);
     float2* W1 = W0 + N0;
     float2* scr_all = W1 + N1;
@@ -287,7 +297,7 @@ __global__ void __launch_bounds__(32 * NW) plane_density_fast_kernel(ChainGeom g
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * NW * LPW;
             float2 v[E0];
-            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, j1 < N1, v, t,
+            column_inverse_fast<float, N0, E0, R0>(g, A, lsA, j1, kAllCols || j1 < N1, v, t,
                                                    wscr + liw * ScratchSpacing<float, N0>::value, W0);
 #pragma unroll
             for (int e = 0; e < E0; ++e) acc[k][e] += fb * (v[e].x * v[e].x + v[e].y * v[e].y);
@@ -332,6 +342,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
     using LN = Lanes<N0, E0>;
     constexpr int LPW = LN::LPW;
     constexpr int ROUNDS = (N1 + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+    constexpr bool kAllCols = N1 % (kFastWarps * LPW) == 0;  // every lane has a column in every round
     static_assert(ROUNDS * 16 <= 64, "at most 64 sums per lane");
     using FI = LineFFT<float, N0, E0, +1, R0>;
     float2* W0 = reinterpret_cast<float2*>(smem_raw);
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
 #pragma unroll 1
         for (int k = 0; k < ROUNDS; ++k) {
             const int j1 = warp * LPW + liw + k * kFastWarps * LPW;
-            const bool act = j1 < N1;
+            const bool act = kAllCols || j1 < N1;
             // this round's sums are fetched while the column transform runs
             uint32_t sr[16];
             tc::tmem_ld16_issue(tb + 16 * k, sr);
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E0; ++e) {
-                    const int r = wrapf(FI::in_index(t, e) - g.i0min, N0);
+                    const int r = wrapn<N0>(FI::in_index(t, e) - g.i0min);
                     if (r < g.nrows) A[r * lsA + j1] = v[e];
                 }
             }
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainG
     c_t<T> v[E2];
 #pragma unroll
     for (int e = 0; e < E2; ++e) {
-        const int off = wrapf(F::in_index(t, e) - z0, N2);
+        const int off = wrapn<N2>(F::in_index(t, e) - z0);
         v[e] = off < cnt ? Cb[off] : mk<T>(T(0), T(0));
     }
     F::run(v, t, scr, W);
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainG
         const int z0 = g.pw_z[q0];
 #pragma unroll
         for (int e = 0; e < E2; ++e) {
-            const int off = wrapf(F::out_index(t, e) - z0, N2);
+            const int off = wrapn<N2>(F::out_index(t, e) - z0);
             if (off < cnt) {
                 const int q = q0 + off;
                 c_t<T> r;
