@@ -58,7 +58,7 @@ typedef enum {
     JDFT_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
     JDFT_ERR_NOT_POSDEF = 5,   /* overlap matrix not positive definite */
     JDFT_ERR_NOT_CONVERGED = 6,/* minimiser hit its iteration limit */
-    JDFT_ERR_UNSUPPORTED = 7   /* valid request this build does not handle */
+    JDFT_ERR_UNSUPPORTED = 7   /* valid request the library does not handle */
 } jdft_status;
 
 typedef enum {
@@ -352,10 +352,10 @@ jdft_status jdft_batch_destroy(jdft_batch_t batch);
 
 /* Same result as jdft_apply_H (same arguments, layouts and precisions), but the
  * call allocates no device memory.  The paper has no counterpart: this exists
- * for callers that cannot let the library call cudaMalloc -- code running under
- * CUDA stream capture (an allocation is not capturable), applications that own
- * a fixed device-memory budget or pool, and latency-critical loops where a
- * synchronising allocation is unacceptable.
+ * for callers that cannot let the library call cudaMalloc -- applications that
+ * own a fixed device-memory budget or a pool allocator that must account for
+ * every device byte, and latency-critical loops where a synchronising
+ * allocation is unacceptable.
  *
  * The intermediate column buffer and the projector products live in one static
  * 32 MiB device array inside libjdft.so, which every GPU that loads the library

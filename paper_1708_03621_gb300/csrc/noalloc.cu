@@ -2,10 +2,9 @@
 //
 // jdft_apply_H keeps its intermediate column buffer in a basis-owned workspace
 // that grows with cudaMalloc on first use.  Some callers cannot allow that:
-// code running inside CUDA stream capture (cudaMalloc is not capturable and
-// would invalidate the capture), callers with a fixed memory budget or their
-// own pool allocator that must see every device byte the process uses, and
-// real-time loops where a synchronising allocation is not acceptable.  This
+// callers with a fixed memory budget or their own pool allocator that must see
+// every device byte the process uses, and real-time loops where a
+// synchronising allocation is not acceptable.  This
 // entry point instead uses one fixed scratch array compiled into the library
 // as a file-scope __device__ variable: every GPU that loads the library holds
 // it (kNoAllocScratchBytes) until the process exits, and the call itself

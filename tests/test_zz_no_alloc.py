@@ -1,7 +1,7 @@
 """jdft_apply_H_noalloc against jdft_apply_H, through the C ABI (GPU).
 
 The no-allocation entry point serves callers that cannot let the library call
-cudaMalloc (stream capture, fixed memory budgets, latency-critical loops); it
+cudaMalloc (fixed memory budgets or pool allocators, latency-critical loops); it
 keeps its intermediates in a static 32 MiB device array instead.  Its results
 must equal those of the allocating entry point within the parity tolerances,
 on two calls in a row (the static array keeps the previous call's contents,
