@@ -215,3 +215,45 @@ def test_rayleigh_ritz_bounds_exact_eigenvalues():
     Cx = X[:, :3] / np.sqrt(basis.Omega)
     CHCx, COCx = pw.subspace(basis, Cx, pw.apply_H(basis, V, Cx, P, D))
     assert np.allclose(np.sort(np.linalg.eigvalsh(CHCx)), ex[:3], atol=1e-12)
+
+
+def test_single_cosine_spectrum_is_union_of_tridiagonal_chains():
+    """V = 2 V0 cos(b_1 . r) couples only plane waves that differ by b_1, so H
+    splits into one chain per line of the sphere along b_1: a tridiagonal
+    (Mathieu-type) matrix with diagonal 1/2 |k+G|^2 and off-diagonal V0.
+    LAPACK's tridiagonal eigensolver on those chains, with the kinetic
+    energies written out for this orthorhombic cell, fixes the whole spectrum;
+    the oracle's dense H and its band minimiser (through the FFT apply_H) must
+    reproduce it."""
+    from scipy.linalg import eigh_tridiagonal
+
+    from oracle import minimize as mn
+
+    L = np.array([6.0, 6.5, 5.5])
+    S = (12, 13, 11)
+    kfrac = np.array([0.1, 0.2, 0.3])
+    basis = pw.Basis.build(np.diag(L), S, kfrac, 4.0)
+    b1 = 2 * np.pi / L[1] * np.array([0.0, 1.0, 0.0])
+    V0 = 0.37
+    V = 2 * V0 * np.cos(pw.grid_points(np.diag(L), S) @ b1)
+    T = 0.5 * np.sum((2 * np.pi * (basis.iG + kfrac) / L) ** 2, 1)
+    chains = {}
+    for g, (i0, i1, i2) in enumerate(basis.iG):
+        chains.setdefault((i0, i2), []).append((i1, g))
+    eigs = []
+    for members in chains.values():
+        members.sort()
+        i1 = [m[0] for m in members]
+        assert i1 == list(range(i1[0], i1[0] + len(i1)))  # a line through a ball is one run
+        d = T[[m[1] for m in members]]
+        eigs.extend(eigh_tridiagonal(d, np.full(len(d) - 1, V0), eigvals_only=True) if len(d) > 1 else d)
+    eigs = np.sort(eigs)
+    assert len(eigs) == basis.npw
+    dense = np.linalg.eigvalsh(pw.dense_H(basis, V) / basis.Omega)
+    assert np.max(np.abs(dense - eigs)) < 1e-12
+    nb = 6
+    assert eigs[nb] - eigs[nb - 1] > 1e-2
+    res = mn.minimize_bands(basis, lambda X: pw.apply_H(basis, V, X), rand_block(basis, nb, 11),
+                            precond=mn.precond_teter, tol=1e-10, max_iter=1000)
+    assert res.converged
+    assert np.max(np.abs(np.sort(res.eigs) - eigs[:nb])) < 1e-12
