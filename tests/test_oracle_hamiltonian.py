@@ -5,7 +5,8 @@ paper's algebraic formulation (Sec. 2.1); the Hamiltonian they build is the
 Kohn-Sham one of the plane-wave method (Sec. 2), with the nonlocal projector
 term of the pseudopotentials (Sec. 2.2).  Pins: plane-wave closed forms, the
 adjoint relations, the free-electron spectrum, the analytic matrix elements of
-a single-cosine potential, a rank-one secular equation for a single
+a single-cosine potential and its spectrum as a union of tridiagonal chains
+(LAPACK), a rank-one secular equation for a single
 projector, Hermiticity, the k -> -k and grid-translation symmetries of the
 spectrum, a brute-force dense Hamiltonian built from a direct O(N^2) DFT, and
 direct real-space sums for the density.
