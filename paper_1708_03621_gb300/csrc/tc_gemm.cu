@@ -159,6 +159,11 @@ struct StageCN {
             atomicAdd(&out[(size_t)m * ldo + n].y, alpha * (double)im);
         }
     }
+    // columns n .. n + 15 of row m
+    __device__ __forceinline__ void emit16(int m, int n, const float* re, const float* im) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) emit(m, n + j, re[j], im[j]);
+    }
 };
 
 // out[n][m] += sum_i A[i][m] Bm[i][n]  (A: K rows of length M; Bm row-major K x N); one writer per element.
@@ -205,12 +210,23 @@ struct StageNN {
             put_split<FMT, CPS>(buf, L::BI_HI, L::BI_LO, row, 2 * k, b.y, b.x);
         }
     }
-    __device__ __forceinline__ void emit(int m, int n, float re, float im) const {
-        if (m < M && n < N) {
-            float2 v = accumulate ? out[(size_t)n * ldo + m] : make_float2(0.f, 0.f);
-            v.x += re;
-            v.y += im;
-            out[(size_t)n * ldo + m] = v;
+    // columns n .. n + 15 of row m.  The 16 old values (accumulate) are all
+    // loaded before the first store: the addresses are distinct and this thread
+    // is their only writer, but the compiler cannot see that through ldo, and a
+    // load-add-store per column would wait out 16 global latencies in turn.
+    __device__ __forceinline__ void emit16(int m, int n, const float* re, const float* im) const {
+        if (m >= M) return;
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            v[j] = (accumulate && n + j < N) ? out[(size_t)(n + j) * ldo + m] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (n + j < N) {
+                v[j].x += re[j];
+                v[j].y += im[j];
+                out[(size_t)(n + j) * ldo + m] = v[j];
+            }
         }
     }
 };
@@ -317,8 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
             float re[16], im[16];
             tc::tmem_ld16(lane_base + col, re);
             tc::tmem_ld16(lane_base + NT + col, im);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) s.emit(m0 + row, n0 + col + j, re[j], im[j]);
+            s.emit16(m0 + row, n0 + col, re, im);
         }
     }
     tc::tc_fence_before_sync();
