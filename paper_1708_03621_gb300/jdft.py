@@ -321,9 +321,9 @@ def jdft_orthonormalize_async(basis, ik, C, status, prec="fp64", stream=None, U=
     (the COC output of jdft_subspace), read instead of recomputed."""
     import torch
     p, ld, nb = _block(C, prec, "C")
-    if U is not None:
-        assert U.is_cuda and U.dtype == torch.complex128 and tuple(U.shape) == (nb, nb) and U.is_contiguous(), \
-            "U must be a contiguous complex128 (nb, nb) CUDA tensor"
+    if U is not None and not (U.is_cuda and U.dtype == torch.complex128 and tuple(U.shape) == (nb, nb)
+                              and U.is_contiguous()):
+        raise ValueError("U must be a contiguous complex128 (nb, nb) CUDA tensor")
     _call("jdft_orthonormalize_async", basis.handle, ik, p, ld, nb, _ptr(U) if U is not None else None,
           _prec(prec), _ptr(status), _stream(stream))
 
