@@ -273,8 +273,9 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
         by = (p.npw + S2 * ncols) * e + (p.npw * e if name == "zpass_forward" else 0)
         return fl * per_launch_bands, by * per_launch_bands
     if name == "zgemm_cn":
-        # per step: P^dag C (nproj x nb), C^dag HC, C^dag C and the orthonormaliser's C^dag C (nb x nb), over npw
-        per_step = [(p.nproj, p.nb), (p.nb, p.nb), (p.nb, p.nb), (p.nb, p.nb)]
+        # per step: P^dag C (nproj x nb), C^dag HC and C^dag C (nb x nb), over npw (the orthonormaliser
+        # reuses the subspace step's C^dag O C)
+        per_step = [(p.nproj, p.nb), (p.nb, p.nb), (p.nb, p.nb)]
         fl = sum(8.0 * M * N * p.npw for M, N in per_step) / len(per_step)
         by = sum((M + N) * p.npw * e for M, N in per_step) / len(per_step)
         return fl, by
