@@ -8,8 +8,9 @@ adjoint relations, the free-electron spectrum, the analytic matrix elements of
 a single-cosine potential and its spectrum as a union of tridiagonal chains
 (LAPACK), a rank-one secular equation for a single
 projector, Hermiticity, the k -> -k and grid-translation symmetries of the
-spectrum, a brute-force dense Hamiltonian built from a direct O(N^2) DFT, and
-direct real-space sums for the density.
+spectrum, a brute-force dense Hamiltonian built from a direct O(N^2) DFT,
+direct real-space sums for the density, and the Loewdin orthonormalisation's
+closed forms and minimal-distance property.
 """
 import numpy as np
 import pytest
@@ -258,3 +259,26 @@ def test_single_cosine_spectrum_is_union_of_tridiagonal_chains():
                             precond=mn.precond_teter, tol=1e-10, max_iter=1000)
     assert res.converged
     assert np.max(np.abs(np.sort(res.eigs) - eigs[:nb])) < 1e-12
+
+
+def test_lowdin_closed_forms_and_minimal_distance():
+    """Loewdin orthonormalisation C (C^dag O C)^{-1/2}, O = Omega: one column is
+    just normalised; mutually orthogonal columns are each normalised; in
+    general the result is O-orthonormal, C^dag O C_L is Hermitian positive
+    definite (C_L = C times a positive matrix), and no other O-orthonormal basis
+    of the same span (C_L W, W unitary) is closer to C."""
+    Om = 3.7
+    x = rng.standard_normal((40, 1)) + 1j * rng.standard_normal((40, 1))
+    assert np.allclose(pw.lowdin(x, Om), x / np.sqrt(Om * np.vdot(x, x).real), atol=1e-14)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 3)) + 1j * rng.standard_normal((40, 3)))
+    D = Q * np.array([0.3, 2.0, 5.0])
+    assert np.allclose(pw.lowdin(D, Om), Q / np.sqrt(Om), atol=1e-13)
+    C = rng.standard_normal((40, 4)) + 1j * rng.standard_normal((40, 4))
+    L = pw.lowdin(C, Om)
+    assert np.allclose(Om * L.conj().T @ L, np.eye(4), atol=1e-13)
+    G = Om * C.conj().T @ L
+    assert np.allclose(G, G.conj().T, atol=1e-12) and np.all(np.linalg.eigvalsh(G) > 0)
+    d0 = np.linalg.norm(L - C)
+    for _ in range(20):
+        W, _ = np.linalg.qr(rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)))
+        assert np.linalg.norm(L @ W - C) >= d0 - 1e-12
