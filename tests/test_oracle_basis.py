@@ -28,6 +28,17 @@ def test_reciprocal_definition():
     assert np.allclose(R.T @ B, 2 * np.pi * np.eye(3), atol=1e-13)
 
 
+def test_cell_volume_triple_product():
+    # Omega = |a0 . (a1 x a2)| (columns of R), and the reciprocal cell holds (2 pi)^3 / Omega
+    R = skew_cell()
+    a0, a1, a2 = R[:, 0], R[:, 1], R[:, 2]
+    om = abs(a0 @ np.cross(a1, a2))
+    assert np.isclose(pw.cell_volume(R), om, rtol=1e-14)
+    B = pw.reciprocal(R)
+    assert np.isclose(abs(B[:, 0] @ np.cross(B[:, 1], B[:, 2])), (2 * np.pi) ** 3 / om, rtol=1e-13)
+    assert np.isclose(pw.cell_volume(np.diag([6.0, 6.5, 5.5])), 6.0 * 6.5 * 5.5, rtol=1e-15)
+
+
 def test_sphere_bounding_box_misses_nothing():
     R = skew_cell()
     k = np.array([0.3, -0.2, 0.45])
