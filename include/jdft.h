@@ -93,18 +93,22 @@ typedef struct {
 jdft_status jdft_basis_create(const jdft_cell_desc* desc, jdft_basis_t* out);
 jdft_status jdft_basis_destroy(jdft_basis_t basis);
 
-/* Number of plane waves at k-point ik. */
+/* Number of plane waves at k-point ik (the plane-wave basis, Sec. 2).  npw: host output. */
 jdft_status jdft_basis_npw(jdft_basis_t basis, int ik, int* npw);
 
-/* Sphere of k-point ik: iG (host, npw x 3, int32, row per plane wave, in basis order). */
+/* Sphere of k-point ik (the plane-wave basis, Sec. 2): iG (host, npw x 3, int32, row per
+ * plane wave, in basis order; the caller owns it). */
 jdft_status jdft_basis_gvectors(jdft_basis_t basis, int ik, int32_t* iG);
 
-/* Scalars: Omega (bohr^3), N, number of (i0,i1) disk columns at ik (host outputs; any may be NULL). */
+/* Scalars of the cell and grid (GridInfo, Sec. 2.1): Omega (bohr^3), N, number of (i0,i1) disk
+ * columns at ik (host outputs; any may be NULL). */
 jdft_status jdft_basis_info(jdft_basis_t basis, int ik, double* omega, int64_t* nbox, int* ncols);
 
 /* ---- potential and projectors ----------------------------------------- */
 
-/* Copy the local potential V(r_j) (device, N doubles, j2 fastest) into the basis. */
+/* Copy the local potential V(r_j) (device, N doubles, j2 fastest, borrowed for the call) into
+ * the basis: the real-space scalar field that the Hamiltonian multiplies pointwise (Sec. 2.1,
+ * Listing 1's field products).  JDFT_ERR_ARG on a null pointer. */
 jdft_status jdft_set_potential(jdft_basis_t basis, const double* V, void* stream);
 
 /* Copy the nonlocal projectors of k-point ik into the basis:
@@ -117,13 +121,16 @@ jdft_status jdft_set_potential(jdft_basis_t basis, const double* V, void* stream
 jdft_status jdft_set_projectors(jdft_basis_t basis, int ik, const void* P, int nproj,
                                 const double* D, void* stream);
 
-/* Synthetic local potential on the box: V(r) = -depth sum_a sum_T exp(-|r - R_a - T|^2 / 2 width^2),
+/* Synthetic local potential on the box (the paper has no counterpart: it stands in for the
+ * pseudopotential data of the paper's workloads, Sec. 3, Listing 2):
+ * V(r) = -depth sum_a sum_T exp(-|r - R_a - T|^2 / 2 width^2),
  * summed over every lattice image that comes within 10 bohr of the cell.
  * atoms: host, natoms x 3 Cartesian (bohr).  V_out: device, N doubles. */
 jdft_status jdft_gaussian_potential(jdft_basis_t basis, int natoms, const double* atoms,
                                     double depth, double width, double* V_out, void* stream);
 
-/* Synthetic projectors at k-point ik: 4 per atom (s, p_x, p_y, p_z), column 4a + l,
+/* Synthetic projectors at k-point ik (the paper has no counterpart: they stand in for the
+ * pseudopotential projectors of SpeciesInfo, Sec. 2.1): 4 per atom (s, p_x, p_y, p_z), column 4a + l,
  * P_{G,(a,l)} = F_l(k+G) exp(-i (k+G).R_a) with F_l the Fourier transform of the
  * unit-norm Gaussian-type function beta_s = N_s exp(-r^2/2 sigma^2),
  * beta_p = N_p x_l exp(-r^2/2 sigma^2).  atoms: host natoms x 3.
@@ -133,31 +140,36 @@ jdft_status jdft_gaussian_projectors(jdft_basis_t basis, int ik, int natoms, con
 
 /* ---- algebraic operators (Sec. 2.1) ------------------------------------ */
 
-/* psi = I C: nb bands, C band-major (ldc), psi device nb x N complex. */
+/* psi = I C (Sec. 2.1): nb bands, C band-major (ldc), psi device nb x N complex. */
 jdft_status jdft_op_I(jdft_basis_t basis, int ik, const void* C, int ldc, void* psi, int nb,
                       jdft_prec prec, void* stream);
-/* C = J psi (sphere part of the normalised forward transform). */
+/* C = J psi (Sec. 2.1; sphere part of the normalised forward transform). */
 jdft_status jdft_op_J(jdft_basis_t basis, int ik, const void* psi, void* C, int ldc, int nb,
                       jdft_prec prec, void* stream);
-/* C = Idag psi = N J psi. */
+/* C = Idag psi = N J psi (Sec. 2.1). */
 jdft_status jdft_op_Idag(jdft_basis_t basis, int ik, const void* psi, void* C, int ldc, int nb,
                          jdft_prec prec, void* stream);
-/* psi = Jdag C = I C / N. */
+/* psi = Jdag C = I C / N (Sec. 2.1). */
 jdft_status jdft_op_Jdag(jdft_basis_t basis, int ik, const void* C, int ldc, void* psi, int nb,
                          jdft_prec prec, void* stream);
-/* OC = O C = Omega C. */
+/* OC = O C = Omega C (Sec. 2.1; O is diagonal in the plane-wave basis). */
 jdft_status jdft_op_O(jdft_basis_t basis, int ik, const void* C, int ldc, void* OC, int ldoc,
                       int nb, jdft_prec prec, void* stream);
 
 /* ---- the hot path ------------------------------------------------------ */
 
-/* HC = H C for nb bands at k-point ik (kinetic + local + nonlocal terms).
- * C and HC must not overlap.  Scatter -> inverse 3-D FFT -> x V -> forward
- * 3-D FFT -> gather, plus kinetic and projector terms. */
+/* HC = H C for nb bands at k-point ik (kinetic + local + nonlocal terms): the
+ * Kohn-Sham Hamiltonian composed from the operators of Sec. 2.1 (I, the
+ * pointwise product with V, J, O) and the pseudopotential projectors of
+ * SpeciesInfo (Sec. 2.1, 2.2).  C and HC must not overlap.  Scatter -> inverse
+ * 3-D FFT -> x V -> forward 3-D FFT -> gather, plus kinetic and projector
+ * terms.  Uses (and may grow) the basis workspace.  JDFT_ERR_ARG on null or
+ * misaligned blocks, ldc/ldhc < npw, or no potential set. */
 jdft_status jdft_apply_H(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
                          int nb, jdft_prec prec, void* stream);
 
-/* n_r[j] += w_ik sum_b f[b] |(I C_b)_j|^2.  f: device, nb doubles.  n_r: device, N doubles. */
+/* n_r[j] += w_ik sum_b f[b] |(I C_b)_j|^2: the electron density of ElecVars (Sec. 2.1).
+ * f: device, nb doubles.  n_r: device, N doubles, accumulated (the caller zeroes it). */
 jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, const double* f,
                          int nb, double* n_r, jdft_prec prec, void* stream);
 
@@ -171,8 +183,10 @@ jdft_status jdft_density(jdft_basis_t basis, int ik, const void* C, int ldc, con
 jdft_status jdft_apply_H_density(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc,
                                  int nb, const double* f, double* n_r, jdft_prec prec, void* stream);
 
-/* CHC = C^dag (HC), COC = C^dag O C = Omega C^dag C: device complex128 nb x nb, row-major,
- * both triangles written.  Either output may be NULL to skip it. */
+/* CHC = C^dag (HC), COC = C^dag O C = Omega C^dag C: the subspace matrices of a
+ * ColumnBundle for the variational minimiser (Sec. 2.1, Minimize).  Device
+ * complex128 nb x nb, row-major, both triangles written, accumulated in FP64.
+ * Either output may be NULL to skip it. */
 jdft_status jdft_subspace(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
                           int ldhc, int nb, void* CHC, void* COC, jdft_prec prec, void* stream);
 
@@ -207,10 +221,13 @@ jdft_status jdft_orthonormalize_async(jdft_basis_t basis, int ik, void* C, int l
 
 /* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
  * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,
- * nb doubles.  Synchronous. */
+ * nb doubles.  Synchronous.  The subspace diagonalisation that gives the band
+ * energies from C^dag H C in the minimiser (Sec. 2.1, Minimize). */
 jdft_status jdft_subspace_eigs(int nb, const void* A, double* eigs, void* stream);
 
-/* Learned per-coefficient preconditioner: a 3 -> 64 -> 64 -> 1 network, SiLU
+/* Learned per-coefficient preconditioner for the band minimiser (the paper
+ * has no counterpart; it stands in for the Teter preconditioner, Teter, Payne
+ * & Allan, PRB 40, 12255 (1989)): a 3 -> 64 -> 64 -> 1 network, SiLU
  * hidden activations, softplus output (so K > 0).  Parameters, 4481 floats in
  * this order: W1 (64x3 row-major), b1 (64), W2 (64x64), b2 (64), W3 (64), b3 (1).
  * Features per coefficient G of band b: x = (1/2)|k+G|^2 / T_b,
@@ -283,7 +300,7 @@ jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, in
                                 const jdft_min_opts* opts, double* eigs, jdft_min_report* report,
                                 void* stream);
 
-/* ---- schedule autotuning ------------------------------------------------ */
+/* ---- schedule autotuning (the paper has no counterpart) ------------------ */
 
 /* Time jdft_apply_H on the caller's blocks for band-chunk budgets of
  * 32 ... 1024 MB (the column buffer passed between the chain kernels; small
@@ -318,7 +335,9 @@ typedef struct {
 jdft_status jdft_autotune(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
                           jdft_prec prec, jdft_tune_report* report, void* stream);
 
-/* ---- batches in one CUDA graph -------------------------------------------- */
+/* ---- batches in one CUDA graph ------------------------------------------ */
+/* The paper distributes k-points over MPI processes (Sec. 3); here a batch of
+ * k-points or of independent cells runs from one graph launch on one GPU. */
 
 /* One Hamiltonian application of a batch: H C for nb bands of k-point ik of
  * `basis` (arguments as for jdft_apply_H; device buffers owned by the caller). */
@@ -373,7 +392,7 @@ jdft_status jdft_batch_destroy(jdft_batch_t batch);
 jdft_status jdft_apply_H_noalloc(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC,
                                  int ldhc, int nb, jdft_prec prec, void* stream);
 
-/* ---- diagnostics and tracing ------------------------------------------- */
+/* ---- diagnostics and tracing (the paper has no counterpart) ------------ */
 
 /* Turn per-kernel timing on (1) or off (0).  While on, every kernel launch of
  * the library is bracketed by two CUDA events recorded on its stream. */
@@ -389,7 +408,8 @@ jdft_status jdft_profile_read(char* buf, int buflen);
  * clear the record.  JDFT_OK otherwise. */
 jdft_status jdft_device_status(void* stream);
 
-/* Number of kernels the library has launched in this process (all calls). */
+/* Number of kernels the library has launched in this process (all calls).
+ * Diagnostics calls have no counterpart in the paper. */
 long long jdft_launch_count(void);
 
 
