@@ -69,3 +69,34 @@ def test_bad_cell_descriptions_rejected():
     desc.R[4] = 0.0
     assert L.jdft_basis_create(ctypes.byref(desc), ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_more_null_and_size_arguments_rejected():
+    """Every entry point checks its handle, pointers and sizes before any CUDA call."""
+    L = jdft.lib()
+    E = 1  # JDFT_ERR_ARG
+    assert L.jdft_basis_gvectors(None, 0, None) == E
+    assert L.jdft_basis_info(None, 0, None, None, None) == E
+    assert L.jdft_set_potential(None, None, None) == E
+    assert L.jdft_set_projectors(None, 0, None, 0, None, None) == E
+    assert L.jdft_gaussian_potential(None, 1, None, 4.0, 1.0, None, None) == E
+    assert L.jdft_gaussian_projectors(None, 0, 1, None, 1.0, None, None) == E
+    for op in ("jdft_op_I", "jdft_op_Jdag"):
+        assert getattr(L, op)(None, 0, None, 0, None, 1, 0, None) == E
+    for op in ("jdft_op_J", "jdft_op_Idag"):
+        assert getattr(L, op)(None, 0, None, None, 0, 1, 0, None) == E
+    assert L.jdft_op_O(None, 0, None, 0, None, 0, 1, 0, None) == E
+    assert L.jdft_apply_H_noalloc(None, 0, None, 0, None, 0, 1, 0, None) == E
+    assert L.jdft_orthonormalize(None, 0, None, 1, 1, 0, None) == E
+    assert L.jdft_subspace_eigs(0, None, None, None) == E
+    assert L.jdft_minimize_bands(None, 0, None, 1, 1, None, None, None, None) == E
+    assert L.jdft_autotune_chunk(None, 0, None, 0, None, 0, 1, 0, None, None) == E
+    assert L.jdft_mlp_create(None, None) == E
+    assert L.jdft_mlp_forward(None, 1, None, None, None) == E
+    assert L.jdft_mlp_loss_grad(None, 1, None, None, None, None) == E
+    assert L.jdft_mlp_adam_step(None, None, 1e-3, None) == E
+    assert L.jdft_batch_create(0, None, None) == E
+    assert L.jdft_batch_launch(None, None) == E
+    buf = ctypes.create_string_buffer(1)
+    assert L.jdft_profile_read(buf, 0) == E
+    assert L.jdft_last_error() != b""
