@@ -408,6 +408,25 @@ jdft_status jdft_profile_read(char* buf, int buflen);
  * clear the record.  JDFT_OK otherwise. */
 jdft_status jdft_device_status(void* stream);
 
+/* Limit, in seconds, of each device-side wait of the tensor-core products on
+ * the current device (default 2 s; kernels launched after the call use it).
+ * A wait that runs out records JDFT_ERR_TIMEOUT for jdft_device_status, stops
+ * issuing products, waits (under a fixed 2 s limit of its own) for the products
+ * it already committed, and frees its tensor memory; the product's output is
+ * then incomplete.  0 makes every such product give up at its first wait,
+ * which tests of the failure path use.  JDFT_ERR_ARG outside [0, 60].  The
+ * paper has no counterpart. */
+jdft_status jdft_set_wait_limit(double seconds);
+
+/* Measured FP32 arithmetic peak of the current device, in TFLOP/s: chains of
+ * scalar fused multiply-adds (*ffma_tflops) and of packed two-wide ones
+ * (*ffma2_tflops) on every SM, timed with CUDA events on `stream` (best of
+ * three after one untimed launch); *sms receives the device's SM count.  All
+ * three outputs are host pointers.  Synchronous, about 0.1 s.  This is the
+ * denominator of the FFT kernels' arithmetic roofline; the paper has no
+ * counterpart. */
+jdft_status jdft_measure_fp32_peak(double* ffma_tflops, double* ffma2_tflops, int* sms, void* stream);
+
 /* Number of kernels the library has launched in this process (all calls).
  * Diagnostics calls have no counterpart in the paper. */
 long long jdft_launch_count(void);

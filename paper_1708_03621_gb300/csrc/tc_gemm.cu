@@ -17,8 +17,11 @@
 // mbarrier; two stages let the staging of chunk c+1 overlap the products of
 // chunk c.  Accumulators (Re at columns [0, NT), Im at [NT, 2 NT)) stay in
 // tensor memory until the epilogue reads them with tcgen05.ld.  Every wait is
-// bounded; a wait that gives up records JDFT_ERR_TIMEOUT in a device flag
-// (read by jdft_device_status), skips the epilogue and frees its tensor memory.
+// bounded by a run-time limit (g_tc_wait_ns, set by jdft_set_wait_limit).  A
+// wait that gives up records JDFT_ERR_TIMEOUT in a device flag (read by
+// jdft_device_status) and stops issuing products; the block then waits, under
+// a fixed limit of its own, for the products it has already committed, skips
+// the epilogue and only then frees its tensor memory.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,7 +40,10 @@ constexpr int TC_M = 128;
 constexpr int TC_CPS = 16;          // complex K elements per stage
 constexpr int TC_THREADS = 512;
 constexpr int TC_WARPS = TC_THREADS / 32;
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;
+// Limit of one wait for a batch of products (run-time, per device; 2 s by
+// default), and the fixed limit of the drain after a wait gave up.
+__device__ unsigned long long g_tc_wait_ns = 2000000000ull;
+constexpr unsigned long long TC_DRAIN_NS = 2000000000ull;
 
 __device__ int g_tc_status = 0;
 
@@ -255,6 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     const int c0 = blockIdx.z * chunks_per_split;
     const int c1 = min(nchunks, c0 + chunks_per_split);
     constexpr uint32_t idesc = tc::instr_desc(F::IDESC_FMT, TC_M, NT);
+    const unsigned long long wait_ns = g_tc_wait_ns;
     int ok = 1;
     int it = 0;
     // two register sets: the loads of chunk c + 2 are issued right after the
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
     auto step = [&](typename S::Regs& regs, char* buf, uint64_t* bar) -> bool {
         if (it >= 2) {
             // the products issued from this buffer two chunks ago must be done before restaging it
-            const int w = tc::mbar_wait_bounded(bar, (uint32_t)(((it - 2) >> 1) & 1), TC_WAIT_LIMIT) ? 1 : 0;
+            const int w = tc::mbar_wait_ns(bar, (uint32_t)(((it - 2) >> 1) & 1), wait_ns) ? 1 : 0;
             ok = __syncthreads_and(w);
             if (!ok) return false;
         }
@@ -314,12 +321,18 @@ __global__ void __launch_bounds__(TC_THREADS) tc_zgemm_kernel(S s, int nchunks, 
         if (c0 + it >= c1) break;
         if (!step(regs1, stage_buf[1], &mbar[1])) break;
     }
-    const int n = it;
+    const int n = it;  // batches committed
     if (ok && n > 0) {
         // the last commit completes after every earlier product of this thread
-        const int w = tc::mbar_wait_bounded(&mbar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), TC_WAIT_LIMIT) ? 1
-                                                                                                              : 0;
+        const int w = tc::mbar_wait_ns(&mbar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), wait_ns) ? 1 : 0;
         ok = __syncthreads_and(w);
+    }
+    if (!ok && n > 0) {
+        // a wait gave up: nothing more is issued, but committed products may
+        // still run and write this block's tensor memory (and read its
+        // stages), so wait for the last of them before freeing anything
+        tc::mbar_wait_ns(&mbar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), TC_DRAIN_NS);
+        __syncthreads();
     }
     tc::tc_fence_after_sync();
     if (ok && n > 0) {
@@ -456,6 +469,14 @@ extern "C" jdft_status jdft_device_status(void* stream) {
         JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)));
         return set_error((jdft_status)v, "a bounded device-side wait gave up (tensor-core product skipped)");
     }
+    return JDFT_OK;
+}
+
+extern "C" jdft_status jdft_set_wait_limit(double seconds) {
+    clear_error();
+    JDFT_CHECK_ARG(seconds >= 0.0 && seconds <= 60.0, "wait limit must be in [0, 60] s");
+    const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+    JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_wait_ns, &ns, sizeof(ns)));
     return JDFT_OK;
 }
 

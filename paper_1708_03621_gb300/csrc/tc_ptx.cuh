@@ -30,10 +30,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the phase did not complete within `limit` tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i)
+// The GPU's global nanosecond timer.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: true once the phase with the given parity has completed;
+// false if limit_ns nanoseconds pass first.  A limit of 0 gives up without
+// trying (the failure path's tests rely on that).
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns == 0) return false;
+    const uint64_t t0 = globaltimer_ns();
+    do {
         if (mbar_try_wait(bar, parity)) return true;
+    } while (globaltimer_ns() - t0 < limit_ns);
     return false;
 }
 

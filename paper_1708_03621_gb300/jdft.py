@@ -90,6 +90,8 @@ _SIGS = {
     "jdft_mlp_adam_step": [_vp, _vp, ctypes.c_float, _vp],
     "jdft_mlp_rows": [_vp, _i, _vp, _vp, _i, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
     "jdft_device_status": [_vp],
+    "jdft_set_wait_limit": [_d],
+    "jdft_measure_fp32_peak": [ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i), _vp],
     "jdft_batch_create": [_i, ctypes.POINTER(ApplyItem), ctypes.POINTER(_vp)],
     "jdft_batch_launch": [_vp, _vp],
     "jdft_batch_destroy": [_vp],
@@ -495,6 +497,18 @@ class Batch:
 def jdft_device_status(stream=None) -> None:
     """Raise JdftError(ERR_TIMEOUT) if a bounded device-side wait gave up."""
     _call("jdft_device_status", _stream(stream))
+
+
+def jdft_set_wait_limit(seconds: float) -> None:
+    """Limit of the tensor-core products' device-side waits on the current device."""
+    _call("jdft_set_wait_limit", ctypes.c_double(seconds))
+
+
+def jdft_measure_fp32_peak(stream=None) -> dict:
+    """Measured FP32 peak of the current device (scalar and packed FMA chains), TFLOP/s."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _call("jdft_measure_fp32_peak", ctypes.byref(a), ctypes.byref(b), ctypes.byref(n), _stream(stream))
+    return {"ffma_tflops": a.value, "ffma2_tflops": b.value, "sms": n.value}
 
 
 def jdft_launch_count() -> int:

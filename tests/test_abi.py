@@ -44,6 +44,10 @@ def test_null_arguments_rejected():
     assert L.jdft_subspace(None, 0, None, 0, None, 0, 1, None, None, 0, None) == 1
     assert L.jdft_basis_npw(None, 0, None) == 1
     assert L.jdft_basis_destroy(None) == 0
+    # the device-side wait limit is checked before any CUDA call
+    assert L.jdft_set_wait_limit(ctypes.c_double(-1.0)) == 1
+    assert L.jdft_set_wait_limit(ctypes.c_double(61.0)) == 1
+    assert L.jdft_measure_fp32_peak(None, None, None, None) == 1
 
 
 def test_bad_cell_descriptions_rejected():

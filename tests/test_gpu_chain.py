@@ -237,6 +237,50 @@ def test_large_sampled_bands(prec):
     jdft.jdft_device_status()
 
 
+_large_ref = {}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_large_autotuned_all_bands_occupied(prec):
+    """The benchmark's launch configuration: jdft_autotune on the 256-band
+    128^3 block (chunk budget: all bands in one chain launch; tuned split-K),
+    then the fused jdft_apply_H_density with every band occupied (f_b from 2
+    down to 0.5).  The whole density is compared with the oracle's
+    n = sum_b f_b |I C_b|^2 over all 256 bands (about a minute of FP64 host
+    work, in batches of 16 bands), and H C on eight sampled bands."""
+    w = workload("large")
+    if "o" not in _large_ref:
+        _large_ref["o"] = OracleSystem(w)
+    o = _large_ref["o"]
+    g = GpuSystem(w, o.atoms)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs()
+    nb = C.shape[0]
+    f = np.linspace(2.0, 0.5, nb)
+    if "n" not in _large_ref:
+        n = np.zeros(g.N)
+        for b0 in range(0, nb, 16):
+            n += pw.density(o.basis, C[b0:b0 + 16].T, f[b0:b0 + 16])
+        _large_ref["n"] = n
+        sample = [0, 37, 74, 111, 148, 185, 222, 255]
+        _large_ref["sample"] = sample
+        _large_ref["HC"] = o.apply_H(C[sample])
+    nref, sample, HCref = _large_ref["n"], _large_ref["sample"], _large_ref["HC"]
+    Cd = to_dev(C, prec)
+    HC = torch.empty_like(Cd)
+    tune = jdft.jdft_autotune(g.basis, 0, Cd, HC, prec)
+    assert tune["chunk_mb"] > 0
+    n = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    jdft.jdft_apply_H_density(g.basis, 0, Cd, HC, torch.tensor(f, device="cuda"), n, prec)
+    got_n = n.cpu().numpy()
+    assert np.max(np.abs(got_n - nref)) / np.max(np.abs(nref)) < TOL[prec]
+    # the integral of n is sum_b f_b times each band's norm Omega sum |C_b|^2
+    norms = o.basis.Omega * np.sum(np.abs(C) ** 2, axis=1)
+    assert np.isclose(o.basis.Omega / g.N * got_n.sum(), np.sum(f * norms), rtol=TOL[prec])
+    assert band_rel_err(host(HC)[sample], HCref) < TOL[prec]
+    jdft.jdft_device_status()
+
+
 def test_edge_cases():
     w, o, g = systems("tiny_cubic")
     from paper_1708_03621_gb300 import jdft

@@ -1,0 +1,48 @@
+"""Failure detection on the device, without a GPU fault (GPU).
+
+The tensor-core products wait on shared-memory barriers for their batches of
+products.  Every such wait is bounded by a run-time limit
+(jdft_set_wait_limit).  With the limit at 0 every wait gives up at once: the
+product must stop issuing, wait for what it already committed, free its
+tensor memory, return, and leave JDFT_ERR_TIMEOUT for jdft_device_status.  The
+context must stay usable: the next call, with the default limit back, gives
+the normal result and a clean status.
+"""
+import numpy as np
+import pytest
+
+from tests.systems import GpuSystem, OracleSystem, band_rel_err, workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_wait_limit_runs_out_and_context_survives(prec):
+    from paper_1708_03621_gb300 import jdft
+    w = workload("mid")
+    o = OracleSystem(w)
+    g = GpuSystem(w, o.atoms)
+    C = o.coeffs()
+    Cd = torch.tensor(C.astype(np.complex64), device="cuda")
+    ref = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, ref, prec)
+    jdft.jdft_device_status()
+    out = torch.zeros_like(Cd)
+    jdft.jdft_set_wait_limit(0.0)
+    try:
+        # the projector products P^dag C and P (D P^dag C) both give up
+        jdft.jdft_apply_H(g.basis, 0, Cd, out, prec)
+        with pytest.raises(jdft.JdftError) as err:
+            jdft.jdft_device_status()
+        assert err.value.status == jdft.STATUS_CODES["ERR_TIMEOUT"]
+    finally:
+        jdft.jdft_set_wait_limit(2.0)
+    # the status was cleared by the read; the same call now completes normally
+    jdft.jdft_device_status()
+    jdft.jdft_apply_H(g.basis, 0, Cd, out, prec)
+    jdft.jdft_device_status()
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.complex128)
+    assert band_rel_err(got, ref.cpu().numpy().astype(np.complex128)) < 1e-6
+    assert band_rel_err(got, o.apply_H(C)) < 2e-5

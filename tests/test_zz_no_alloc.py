@@ -14,7 +14,11 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5}
+# the tensor-core modes: both entry points run the nonlocal products with
+# different tile and split-K schedules (one scratch-sized chunk of bands at a
+# time here, the whole block in jdft_apply_H), so they agree to the split's
+# accuracy rather than bit for bit
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 2e-5}
 
 
 def _system(name):
@@ -39,7 +43,7 @@ def _rel(a, b):
     return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
 
 
-@pytest.mark.parametrize("name,prec", [("mid", "fp64"), ("mid", "fp32"), ("large", "fp64"), ("large", "fp32")])
+@pytest.mark.parametrize("name,prec", [(n, p) for n in ("mid", "large") for p in ("fp64", "fp32", "tf32x3", "bf16x3")])
 def test_noalloc_matches_apply_H_twice(name, prec):
     from paper_1708_03621_gb300 import jdft
     w, b, C = _system(name)
