@@ -36,8 +36,6 @@ if ROOT not in sys.path:
 
 METRIC = "Hψ band-applies/s & time to |ΔE|<1e-6 Ha: mixed+learned vs FP64, 1 GB300"
 UNIT = "band-applies/s"
-FP32_LANES_PER_SM = 128
-SMS = 152
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -259,11 +257,12 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
     l2 = math.log2
     if name in ("tc_zgemm_cn", "tc_zgemm_nn"):
         return kernel_work(p, name[3:], launches, nb)
-    if name in ("plane_apply", "plane_apply_fast", "plane_apply_density_fast"):
-        # the fused kernel does the same transforms; its density adds the n(r) update
+    if name in ("plane_apply", "plane_apply_fast", "plane_apply_pair", "plane_apply_density_fast",
+                "plane_apply_density_pair"):
+        # the fused kernels do the same transforms; their density adds the n(r) update
         fl = 5 * S2 * (2 * nrows * S1 * l2(S1) + 2 * S1 * S0 * l2(S0))
         by = 2 * S2 * ncols * e
-        extra = p.N * 16 if name == "plane_apply_density_fast" else 0
+        extra = p.N * 16 if "density" in name else 0
         return fl * per_launch_bands, by * per_launch_bands + p.N * (8 if e == 16 else 4) + extra
     if name in ("plane_density", "plane_density_fast"):
         fl = 5 * S2 * (nrows * S1 * l2(S1) + S1 * S0 * l2(S0))
@@ -287,14 +286,16 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
     return 0.0, 0.0
 
 
-def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
+def roofline_of(k: dict, prec: str, peaks: dict, fp32: dict) -> dict:
     """The roofline that bounds one kernel, with its peak and where that comes from.
 
-    FFT and CUDA-core GEMM kernels: FP32 (or FP64) issue rate; tensor-core
-    GEMMs: TF32 dense rate = measured BF16 burst x (1.1 / 2.25), the nominal
-    TF32/BF16 ratio, against algorithmic 8MNK flops (the 3-term split issues 3x
-    that, so 1/3 is that kernel's ceiling; BF16 pieces: the measured BF16
-    rate itself); everything else: HBM copy bandwidth.
+    FFT and CUDA-core GEMM kernels: the FP32 arithmetic peak measured on this
+    GPU by jdft_measure_fp32_peak (the larger of the scalar and the packed FMA
+    chains), or the nominal FP64 rate for FP64 blocks; tensor-core GEMMs: the
+    measured BF16 burst (BF16x3 pieces), or TF32 = that x (1.1 / 2.25), the
+    nominal TF32/BF16 ratio, against algorithmic 8MNK flops (the 3-term split
+    issues 3x that, so 1/3 is that kernel's ceiling); everything else: HBM
+    copy bandwidth.
     """
     name = k["name"]
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -309,31 +310,50 @@ def roofline_of(k: dict, prec: str, peaks: dict) -> dict:
         return {"bound": "tensor", "achieved": k["achieved_tflops"], "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round((k["achieved_tflops"] or 0) / peak, 4), "split_passes": 3, "peak_source": how}
     if name.startswith("plane_") or name.startswith("zgemm") or name.startswith("zpass"):
-        alu = fp_peak_tflops(prec, 2070.0)
+        if prec == "fp64":
+            alu, how = FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
+        else:
+            alu = max(fp32["ffma_tflops"], fp32["ffma2_tflops"])
+            how = (f"measured FP32 peak (of measured): FMA chains on all {fp32['sms']} SMs, scalar "
+                   f"{fp32['ffma_tflops']:.1f} / packed {fp32['ffma2_tflops']:.1f} TFLOP/s, the larger")
         r_alu = (k["achieved_tflops"] or 0) / alu
         r_hbm = (k["achieved_gbs"] or 0) / hbm
         if r_alu >= r_hbm:
             return {"bound": "alu", "achieved": k["achieved_tflops"], "peak": round(alu, 2), "unit": "TFLOP/s",
-                    "frac": round(r_alu, 4),
-                    "peak_source": ("FP32 lanes 128/SM x 152 SMs x 2 x 2070 MHz" if prec != "fp64"
-                                    else "FP64 nominal 1.25 TFLOP/s")}
+                    "frac": round(r_alu, 4), "peak_source": how}
     return {"bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
             "frac": round((k["achieved_gbs"] or 0) / hbm, 4), "peak_source": src_hbm}
 
 
-# DRAM bytes (read + write) per band of the dominant kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum of a 64-band launch on
-# the 128^3 workload, --nbands 64; profiles/plane_apply_density_fast_128cubed_bf16x3.md),
-# scaled by the bands a launch processes.  ncu replays with cold caches, so
-# this bounds the warm traffic from above.  Only valid for the kernel version
-# it was taken on: drop the entry when the kernel changes.
-TRAFFIC_PER_BAND = {"plane_apply_density_fast": (150346496 + 87341568) / 64}
+# DRAM bytes (read + write) per band of a kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one 64-band launch on the
+# 128^3 workload, --nbands 64), scaled by the bands a launch processes.  ncu
+# replays with cold caches, so this bounds the warm traffic from above.  Each
+# entry holds the SHA-256 of the kernel's source files at capture time; when
+# the sources differ, the figure no longer describes the kernel and the bench
+# reports null.
+TRAFFIC_SOURCES = {"plane_apply_density_pair": ["csrc/plane_pair.cu", "csrc/fft_pair.cuh", "csrc/fft_reg.cuh",
+                                                "csrc/chain.cuh", "csrc/common.cuh", "csrc/tc_ptx.cuh"]}
+TRAFFIC_PER_BAND = {}
 
 
-def fp_peak_tflops(prec: str, sm_max_mhz: float) -> float:
-    if prec == "fp64":
-        return FP64_NOMINAL_TFLOPS
-    return SMS * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+def sources_sha(name: str) -> str | None:
+    import hashlib
+    files = TRAFFIC_SOURCES.get(name)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1708_03621_gb300", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_band(name: str) -> float | None:
+    ent = TRAFFIC_PER_BAND.get(name)
+    if ent is None or sources_sha(name) != ent[1]:
+        return None
+    return ent[0]
 
 
 def run_ours(args, world, rank, local, pg):
@@ -342,6 +362,7 @@ def run_ours(args, world, rank, local, pg):
     from paper_1708_03621_gb300 import jdft
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    fp32 = jdft.jdft_measure_fp32_peak()  # the FFT kernels' arithmetic roofline, on this GPU
     p = Problem(args.workload, args.prec, dev, args.nbands)
     tune = p.tune
     stream = torch.cuda.current_stream()
@@ -375,7 +396,6 @@ def run_ours(args, world, rank, local, pg):
     value = units / (ms_max / 1e3)
 
     # ---- per-kernel roofline from the live events ----
-    sm_max = clk.get("sm_max_mhz") or 2070.0
     kernels = []
     for name, (n, kms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
         per_step_launches = n / args.steps
@@ -388,11 +408,11 @@ def run_ours(args, world, rank, local, pg):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     for k in kernels:
-        k["roofline"] = roofline_of(k, args.prec, peaks)
+        k["roofline"] = roofline_of(k, args.prec, peaks, fp32)
     top = kernels[0]
     roof = dict(top["roofline"])
     roof["kernel"] = top["name"]
-    tpb = TRAFFIC_PER_BAND.get(top["name"]) if args.workload == "large" else None
+    tpb = traffic_per_band(top["name"]) if args.workload == "large" else None
     # per launch, like `achieved`: bytes per band x the bands one launch processes on average
     roof["traffic"] = round(tpb * p.nb * args.steps / top["launches"]) if tpb else None
 

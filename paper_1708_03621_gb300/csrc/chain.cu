@@ -382,8 +382,10 @@ jdft_status launch_zpass_forward(const ChainGeom& g, const c_t<T>* colbuf, const
 template <typename T>
 jdft_status launch_plane_apply(const ChainGeom& g, c_t<T>* colbuf, const T* Vp, int nb, const c_t<T>* tw_base,
                                cudaStream_t st) {
-    // register-FFT kernel for the shapes it is compiled for, else the generic one
-    const jdft_status fs = launch_plane_apply_fast<T>(g, colbuf, Vp, nb, tw_base, st);
+    // band-pair or register-FFT kernel for the shapes they are compiled for, else the generic one
+    jdft_status fs = JDFT_ERR_UNSUPPORTED;
+    if constexpr (std::is_same<T, float>::value) fs = launch_plane_apply_pair(g, colbuf, Vp, nb, tw_base, st);
+    if (fs == JDFT_ERR_UNSUPPORTED) fs = launch_plane_apply_fast<T>(g, colbuf, Vp, nb, tw_base, st);
     if (fs != JDFT_ERR_UNSUPPORTED) return fs;
     PlaneSmem sm = plane_layout(g, sizeof(c_t<T>), g.S1, 0, 16);
     const size_t smem = plane_bytes(g, sm, sizeof(c_t<T>));
@@ -635,9 +637,13 @@ static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, i
         c_t<T>* Hc = (c_t<T>*)HC + (size_t)b0 * ldhc;
         if ((s = launch_zpass_inverse<T>(g, Cc, ldc, colbuf, n, twiddles<T>(b), st))) return s;
         jdft_status fs = JDFT_ERR_UNSUPPORTED;
-        if constexpr (std::is_same<T, float>::value)
-            fs = launch_plane_apply_density_fast(g, colbuf, potential<float>(b), n, f + b0, wk, n_r, twiddles<float>(b),
+        if constexpr (std::is_same<T, float>::value) {
+            fs = launch_plane_apply_density_pair(g, colbuf, potential<float>(b), n, f + b0, wk, n_r, twiddles<float>(b),
                                                  st);
+            if (fs == JDFT_ERR_UNSUPPORTED)
+                fs = launch_plane_apply_density_fast(g, colbuf, potential<float>(b), n, f + b0, wk, n_r,
+                                                     twiddles<float>(b), st);
+        }
         if (fs == JDFT_ERR_UNSUPPORTED) {
             if ((s = launch_plane_density<T>(g, colbuf, f + b0, wk, n_r, n, twiddles<T>(b), st))) return s;
             if ((s = launch_plane_apply<T>(g, colbuf, potential<T>(b), n, twiddles<T>(b), st))) return s;

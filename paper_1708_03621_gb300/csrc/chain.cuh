@@ -70,6 +70,14 @@ jdft_status launch_plane_density_fast(const ChainGeom& g, const float2* colbuf, 
 jdft_status launch_plane_apply_density_fast(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                             const double* f, double w, double* n_r, const float2* tw_base,
                                             cudaStream_t st);
+// The same for two bands at a time with packed FP32 arithmetic (plane_pair.cu;
+// JDFT_ERR_UNSUPPORTED, without launching, for shapes it is not compiled for).
+jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
+                                            const double* f, double w, double* n_r, const float2* tw_base,
+                                            cudaStream_t st);
+// The plane pass alone, two bands at a time (same contract as launch_plane_apply).
+jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
+                                    const float2* tw_base, cudaStream_t st);
 // Register-FFT z passes for the lengths S2 they are compiled for (same
 // contract as launch_zpass_*, tw2 = the length-S2 twiddle table); they return
 // JDFT_ERR_UNSUPPORTED (without launching) for other lengths.

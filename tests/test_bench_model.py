@@ -72,3 +72,20 @@ def test_tensor_products(bench):
     q = _problem(nb=64, nproj=256)
     fl, _ = bench.kernel_work(q, "tc_zgemm_cn", 3, 64)
     assert fl == pytest.approx(8.0 * 62759 * (256 * 64 + 64 * 64 + 64 * 64) / 3)
+
+
+def test_band_pair_kernels_use_the_same_work(bench):
+    """The band-pair plane kernels do the transforms of the one-band ones."""
+    p = _problem()
+    assert bench.kernel_work(p, "plane_apply_density_pair", 1, 2) == bench.kernel_work(p, "plane_apply_density_fast",
+                                                                                        1, 2)
+    assert bench.kernel_work(p, "plane_apply_pair", 1, 2) == bench.kernel_work(p, "plane_apply_fast", 1, 2)
+
+
+def test_traffic_figure_is_dropped_when_the_kernel_changes(bench, monkeypatch):
+    name = "plane_apply_density_pair"
+    sha = bench.sources_sha(name)
+    monkeypatch.setitem(bench.TRAFFIC_PER_BAND, name, (3.7e6, sha))
+    assert bench.traffic_per_band(name) == 3.7e6
+    monkeypatch.setitem(bench.TRAFFIC_PER_BAND, name, (3.7e6, "0" * 16))
+    assert bench.traffic_per_band(name) is None
