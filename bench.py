@@ -217,18 +217,16 @@ class Problem:
         return {"C": self.C, "HC": self.HC, "n": self.n, "CHC": self.CHC, "COC": self.COC}
 
     def step(self, stream=None, b=None):
-        """Rows a1-a9: H C and the density (one fused call), C^dag H C and
-        C^dag O C, Cholesky orthonormalisation (on buffer set b, default the
-        problem's own)."""
+        """Rows a1-a9 in one library call (on buffer set b, default the
+        problem's own): C^dag O C of the input block, its FP64 Cholesky
+        factorisation on the basis's side stream while H C and the density
+        run, C^dag H C, then the orthonormalisation C <- C L^-dag.  No host
+        wait per step: a failure lands in self.status (see check_status)."""
         j = self.jdft
         b = b or self.own_buffers()
         b["n"].zero_()
-        j.jdft_apply_H_density(self.basis, 0, b["C"], b["HC"], self.f, b["n"], self.prec, stream)
-        j.jdft_subspace(self.basis, 0, b["C"], b["HC"], b["CHC"], b["COC"], self.prec, stream)
-        # the overlap C^dag O C just formed is the orthonormalisation's U (one
-        # overlap per iteration); no host wait per step: a failure lands in
-        # self.status (see check_status)
-        j.jdft_orthonormalize_async(self.basis, 0, b["C"], self.status, self.prec, stream, U=b["COC"])
+        j.jdft_hamiltonian_step(self.basis, 0, b["C"], b["HC"], self.f, b["n"], b["CHC"], b["COC"], self.status,
+                                self.prec, stream)
 
     def check_status(self):
         """Raise if any orthonormalisation since set-up met linearly dependent bands."""

@@ -219,6 +219,28 @@ jdft_status jdft_orthonormalize(jdft_basis_t basis, int ik, void* C, int ldc, in
 jdft_status jdft_orthonormalize_async(jdft_basis_t basis, int ik, void* C, int ldc, int nb, const void* U,
                                       jdft_prec prec, int* status, void* stream);
 
+/* One pass of the hot path over a band block, rows a1-a9 of the method (Sec.
+ * 2.1: each iteration of the band minimiser, Minimize, applies H to the
+ * block, forms the subspace matrices and keeps the block O-orthonormal; the
+ * density is that of ElecVars):
+ *   HC = H C, n_r += w_k sum_b f_b |psi_b|^2, COC = C^dag O C, CHC = C^dag H C,
+ * and with orthonormalize != 0 then C <- C L^{-dag}, where COC = L L^dag is
+ * factored in FP64.  Arguments, layouts and precisions as jdft_apply_H_density
+ * and jdft_subspace (C, HC: band-major blocks of nb rows, leading dimensions
+ * ldc, ldhc >= npw; f: device nb FP64; n_r: device box, accumulated; CHC, COC:
+ * device nb x nb complex128, overwritten).  Differences from the separate
+ * calls: COC is formed from the input block first, and its factorisation runs
+ * on a second stream owned by the basis while H C is applied (a few SMs are
+ * left to it), joining `stream` before C is rotated; the BF16x3 products
+ * share one BF16 split of C.  status: device int (required with
+ * orthonormalize), raised to JDFT_ERR_NOT_POSDEF if the overlap is not
+ * positive definite; it is never cleared.  Asynchronous on `stream`; grows the
+ * basis workspaces (synchronously) on first use.  Returns argument and launch
+ * errors.  Calls for the same basis must not overlap on the GPU. */
+jdft_status jdft_hamiltonian_step(jdft_basis_t basis, int ik, void* C, int ldc, void* HC, int ldhc, int nb,
+                                  const double* f, double* n_r, void* CHC, void* COC, int orthonormalize,
+                                  int* status, jdft_prec prec, void* stream);
+
 /* Eigenvalues (ascending) of a Hermitian nb x nb matrix A (device complex128,
  * row-major), by cyclic Jacobi rotations in FP64 on the GPU; eigs: device,
  * nb doubles.  Synchronous.  The subspace diagonalisation that gives the band

@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "gemm.cuh"
 #include "profile.cuh"
 
 namespace jdft {
@@ -43,19 +44,21 @@ cudaError_t set_smem_attr(const void* func, size_t smem) {
     return e;
 }
 
-jdft_status ensure_workspace(jdft_basis_s* b, size_t bytes) {
-    if (b->work.bytes >= bytes) return JDFT_OK;
-    if (b->work.ptr) {
+jdft_status ensure_ws(Workspace& w, size_t bytes) {
+    if (w.bytes >= bytes) return JDFT_OK;
+    if (w.ptr) {
         JDFT_CUDA_TRY(cudaDeviceSynchronize());
-        JDFT_CUDA_TRY(cudaFree(b->work.ptr));
-        b->work.ptr = nullptr;
-        b->work.bytes = 0;
+        JDFT_CUDA_TRY(cudaFree(w.ptr));
+        w.ptr = nullptr;
+        w.bytes = 0;
     }
     size_t want = std::max(bytes, (size_t)1 << 20);
-    JDFT_CUDA_TRY(cudaMalloc(&b->work.ptr, want));
-    b->work.bytes = want;
+    JDFT_CUDA_TRY(cudaMalloc(&w.ptr, want));
+    w.bytes = want;
     return JDFT_OK;
 }
+
+jdft_status ensure_workspace(jdft_basis_s* b, size_t bytes) { return ensure_ws(b->work, bytes); }
 
 // Radices for a length n = 2^a 3^b 5^c: eights first, then a four or two,
 // then threes and fives (fewest passes for the lengths in use).
@@ -93,7 +96,7 @@ template <typename T> static jdft_status upload(T** dst, const std::vector<T>& s
 static void free_sphere(KSphere& s) {
     cudaFree(s.col_start); cudaFree(s.col_slot01); cudaFree(s.row_col_start); cudaFree(s.row_i1lo);
     cudaFree(s.pw_col); cudaFree(s.pw_z); cudaFree(s.kin); cudaFree(s.kvec); cudaFree(s.kin32);
-    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
+    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
     s = KSphere();
 }
 
@@ -342,6 +345,13 @@ jdft_status jdft_basis_destroy(jdft_basis_t b) {
     cudaSetDevice(b->device);
     for (auto& s : b->ks) free_sphere(s);
     cudaFree(b->tw64); cudaFree(b->tw32); cudaFree(b->V); cudaFree(b->V32); cudaFree(b->work.ptr);
+    if (b->side) {
+        cudaStreamSynchronize(b->side);
+        cudaStreamDestroy(b->side);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    cudaFree(b->fwork.ptr);
     cudaSetDevice(prev);
     delete b;
     return JDFT_OK;
@@ -397,8 +407,8 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     KSphere& s = b->ks[ik];
     if (s.P) {
         JDFT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
-        s.P = s.P32 = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
+        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
+        s.P = s.P32 = s.Psplit = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
     }
     s.nproj = nproj;
     if (nproj == 0) return JDFT_OK;
@@ -443,7 +453,11 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
         Trace tr_("to_complex64", st);
         to_complex64<<<grid_for((int64_t)n, 256), 256, 0, st>>>((const double2*)s.P, (float2*)s.P32, (int64_t)n);
     }
-    return check_launch("to_complex64");
+    jdft_status r = check_launch("to_complex64");
+    if (r != JDFT_OK) return r;
+    // BF16 planes of the projectors for the split-operand products
+    JDFT_CUDA_TRY(cudaMalloc(&s.Psplit, tcx_split_bytes(nproj, s.npw)));
+    return tcx_split((const float2*)s.P32, s.npw, nproj, s.npw, s.Psplit, st);
 }
 
 jdft_status jdft_gaussian_potential(jdft_basis_t b, int natoms, const double* atoms, double depth, double width,

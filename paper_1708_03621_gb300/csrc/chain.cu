@@ -595,7 +595,7 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
     const KSphere& sp = b->ks[ik];
     const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
-    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>));
+    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, true);
     jdft_status s = ensure_workspace(b, colbytes + nlbytes);
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -611,7 +611,7 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
             return s;
     }
     if (sp.nproj > 0)
-        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st);
+        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st, true);
     return JDFT_OK;
 }
 
@@ -619,13 +619,25 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
 // fused plane kernel where it exists (else density, then the H plane pass, on
 // the same column buffer), one z pass out; the nonlocal term after.
 template <typename T>
-static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
-                                       const double* f, double* n_r, jdft_prec prec, cudaStream_t st) {
+static size_t apply_H_density_bytes(const jdft_basis_s* b, int ik, int nb, jdft_prec prec, bool split_c) {
     const ChainGeom g = make_geom(b, ik);
     const KSphere& sp = b->ks[ik];
     const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
-    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>));
+    return colbytes + nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, split_c);
+}
+
+// Csplit: the BF16 planes of C (tcx_split) when the caller has them, so the
+// projection reads them instead of splitting C again.
+template <typename T>
+static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                       const double* f, double* n_r, jdft_prec prec, cudaStream_t st,
+                                       const void* Csplit = nullptr) {
+    const ChainGeom g = make_geom(b, ik);
+    const KSphere& sp = b->ks[ik];
+    const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
+    const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
+    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, !Csplit);
     jdft_status s = ensure_workspace(b, colbytes + nlbytes);
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -655,8 +667,21 @@ static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, i
             return s;
     }
     if (sp.nproj > 0)
-        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st);
+        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st, !Csplit,
+                                      Csplit);
     return JDFT_OK;
+}
+
+size_t apply_H_density_workspace(const jdft_basis_s* b, int ik, int nb, jdft_prec prec, bool split_c) {
+    return is_fp64(prec) ? apply_H_density_bytes<double>(b, ik, nb, prec, split_c)
+                         : apply_H_density_bytes<float>(b, ik, nb, prec, split_c);
+}
+
+jdft_status apply_H_density_with_split(jdft_basis_s* b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                       const double* f, double* n_r, jdft_prec prec, cudaStream_t st,
+                                       const void* Csplit) {
+    return is_fp64(prec) ? run_apply_H_density<double>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, prec, st, Csplit)
+                         : run_apply_H_density<float>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, prec, st, Csplit);
 }
 
 template <typename T>

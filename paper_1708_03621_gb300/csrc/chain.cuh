@@ -18,6 +18,7 @@ struct ChainGeom {
     const int* pw_col;         // npw
     const int* pw_z;           // npw
     FftPlan p0, p1, p2;
+    int reserve_sms;           // SMs the persistent plane kernels leave free
 };
 
 inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
@@ -29,6 +30,7 @@ inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
     g.row_i1lo = s.row_i1lo;
     g.pw_col = s.pw_col; g.pw_z = s.pw_z;
     g.p0 = b->plan[0]; g.p1 = b->plan[1]; g.p2 = b->plan[2];
+    g.reserve_sms = b->reserve_sms;
     return g;
 }
 
@@ -78,6 +80,12 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
 // The plane pass alone, two bands at a time (same contract as launch_plane_apply).
 jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                     const float2* tw_base, cudaStream_t st);
+// Workspace bytes of apply_H_density_with_split, and H C plus the density
+// with an optional caller-made BF16 split of C for the projection (chain.cu).
+size_t apply_H_density_workspace(const jdft_basis_s* b, int ik, int nb, jdft_prec prec, bool split_c);
+jdft_status apply_H_density_with_split(jdft_basis_s* b, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
+                                       const double* f, double* n_r, jdft_prec prec, cudaStream_t st,
+                                       const void* Csplit);
 // Register-FFT z passes for the lengths S2 they are compiled for (same
 // contract as launch_zpass_*, tw2 = the length-S2 twiddle table); they return
 // JDFT_ERR_UNSUPPORTED (without launching) for other lengths.

@@ -105,6 +105,7 @@ struct KSphere {
     int nproj = 0;
     void* P = nullptr;          // complex128 npw x nproj column-major
     void* P32 = nullptr;        // complex64 copy
+    void* Psplit = nullptr;     // BF16 planes of P32 for the BF16x3 products (Re hi, Re lo, Im hi, Im lo)
     double* D = nullptr;        // nproj x nproj
     // D as ELL rows: Dw entries per row (the widest row's nonzero count),
     // columns and values, padded with column 0 and value 0
@@ -142,10 +143,19 @@ struct jdft_basis_s {
     bool have_V = false;
     int device = 0;
     int chunk_mb = 0;         // band-chunk budget chosen by jdft_autotune_chunk (0 = default)
+    int reserve_sms = 0;      // SMs the persistent plane kernels leave free (work on a side stream)
     jdft::Workspace work;
+    // jdft_hamiltonian_step: the overlap factorisation's own scratch (it runs
+    // on a side stream while the chain uses `work`), the side stream and its
+    // fork / join events (created on first use)
+    jdft::Workspace fwork;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace jdft {
 // Grows the basis workspace to at least `bytes` (synchronous cudaMalloc).
 jdft_status ensure_workspace(jdft_basis_s* b, size_t bytes);
+// The same for any library-owned workspace of the basis.
+jdft_status ensure_ws(Workspace& w, size_t bytes);
 }  // namespace jdft

@@ -5,6 +5,8 @@
 // plane-wave basis).
 #include <algorithm>
 
+#include <type_traits>
+
 #include "gemm.cuh"
 #include "profile.cuh"
 
@@ -180,11 +182,12 @@ bool gemm_nn_inplace_ok(jdft_prec prec, int N) {
     return false;  // the CUDA-core products tile N in 16-column blocks
 }
 
-size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem) {
+size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw, jdft_prec prec, bool split_c) {
     if (nproj == 0) return 0;
     const size_t a = ((size_t)nproj * nb * sizeof(double2) + 255) / 256 * 256;
     const size_t b = ((size_t)nproj * nb * elem + 255) / 256 * 256;
-    return a + b;
+    const size_t c = split_c && tcx_eligible(prec, nproj, nb) ? (tcx_split_bytes(nb, npw) + 255) / 256 * 256 : 0;
+    return a + b + c;
 }
 
 template <typename T>
@@ -194,13 +197,25 @@ template <> const float2* proj_ptr<float>(const KSphere& sp) { return (const flo
 
 template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
-                                jdft_prec prec, void* work, cudaStream_t st) {
+                                jdft_prec prec, void* work, cudaStream_t st, bool split_c, const void* Csplit) {
     if (sp.nproj == 0 || nb == 0) return JDFT_OK;
     double2* Bc = (double2*)work;
-    c_t<T>* Bd = (c_t<T>*)((char*)work + ((size_t)sp.nproj * nb * sizeof(double2) + 255) / 256 * 256);
+    const size_t abytes = ((size_t)sp.nproj * nb * sizeof(double2) + 255) / 256 * 256;
+    const size_t bbytes = ((size_t)sp.nproj * nb * sizeof(c_t<T>) + 255) / 256 * 256;
+    c_t<T>* Bd = (c_t<T>*)((char*)work + abytes);
     JDFT_CUDA_TRY(cudaMemsetAsync(Bc, 0, (size_t)sp.nproj * nb * sizeof(double2), st));
-    jdft_status s = gemm_cn<T>(prec, sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0,
-                               st);
+    jdft_status s;
+    if (std::is_same<T, float>::value && (split_c || Csplit) && sp.Psplit && tcx_eligible(prec, sp.nproj, nb)) {
+        const void* Cs = Csplit;
+        if (!Cs) {
+            void* own = (char*)work + abytes + bbytes;
+            if ((s = tcx_split((const float2*)C, ldc, nb, sp.npw, own, st))) return s;
+            Cs = own;
+        }
+        s = tcx_cn(sp.nproj, nb, sp.npw, sp.Psplit, Cs, Bc, nb, 1.0, st);
+    } else {
+        s = gemm_cn<T>(prec, sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0, st);
+    }
     if (s != JDFT_OK) return s;
     {
         Trace tr_("dmul", st);
@@ -245,9 +260,9 @@ template jdft_status zgemm_nn_acc<double>(int, int, int, const double2*, int, co
 template jdft_status zgemm_nn_acc<float>(int, int, int, const float2*, int, const float2*, int, float2*, int,
                                          cudaStream_t, bool);
 template jdft_status nonlocal_accumulate<double>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,
-                                                 cudaStream_t);
+                                                 cudaStream_t, bool, const void*);
 template jdft_status nonlocal_accumulate<float>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,
-                                                cudaStream_t);
+                                                cudaStream_t, bool, const void*);
 
 }  // namespace jdft
 
@@ -267,6 +282,24 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
     JDFT_CHECK_ARG(((uintptr_t)CHC % 16) == 0 && ((uintptr_t)COC % 16) == 0, "outputs must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     jdft_status s = JDFT_OK;
+    if (prec == JDFT_BF16X3 && tcx_eligible(prec, nb, nb)) {
+        // split C (and HC) once into BF16 planes in the basis workspace; both
+        // products read the split C
+        const size_t cb = (tcx_split_bytes(nb, npw) + 255) / 256 * 256;
+        if ((s = ensure_workspace(b, CHC ? 2 * cb : cb))) return s;
+        char* ws = (char*)b->work.ptr;
+        if ((s = tcx_split((const float2*)C, ldc, nb, npw, ws, st))) return s;
+        if (CHC) {
+            if ((s = tcx_split((const float2*)HC, ldhc, nb, npw, ws + cb, st))) return s;
+            JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
+            if ((s = tcx_cn(nb, nb, npw, ws, ws + cb, (double2*)CHC, nb, 1.0, st))) return s;
+        }
+        if (COC) {
+            JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
+            if ((s = tcx_cn(nb, nb, npw, ws, ws, (double2*)COC, nb, b->omega, st))) return s;
+        }
+        return JDFT_OK;
+    }
     if (CHC) {
         JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
         s = (prec == JDFT_FP64)

@@ -26,6 +26,19 @@ jdft_status tc_zgemm_cn(int M, int N, int K, const float2* A, int lda, const flo
 jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const float2* Bm, int ldb, float2* out,
                             int ldo, bool bf16, cudaStream_t st, bool accumulate = true);
 
+// BF16x3 products from operands split once into BF16 planes (tc_gemm.cu).
+// A split block of `rows` rows of K complex values holds four planes of
+// rows x tcx_ldk(K) BF16 values: Re hi, Re lo, Im hi, Im lo (x = hi + lo).
+size_t tcx_split_bytes(int rows, int K);
+// Whether tcx_cn serves this product (BF16x3, both dimensions above 32).
+bool tcx_eligible(jdft_prec prec, int M, int N);
+// Split rows of X (complex64, row stride ld) into planes (16-byte aligned, tcx_split_bytes).
+jdft_status tcx_split(const float2* X, int ld, int rows, int K, void* planes, cudaStream_t st);
+// out[m * ldo + n] += alpha sum_k conj(A[m][k]) B[n][k] from the split blocks
+// of A (M rows) and B (N rows); FP64 atomics, so out must be zeroed first.
+jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
+                   cudaStream_t st);
+
 // Precision dispatch: JDFT_TF32X3 and JDFT_BF16X3 run the tensor-core
 // versions (T = float only), the other precisions the CUDA-core ones.
 template <typename T>
@@ -42,12 +55,20 @@ jdft_status gemm_nn_acc(jdft_prec prec, int M, int N, int K, const c_t<T>* A, in
 // for every k before its epilogue writes them and no other block touches them.
 bool gemm_nn_inplace_ok(jdft_prec prec, int N);
 
-// Workspace bytes the nonlocal term needs for nb bands.
-size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem);
+// Workspace bytes the nonlocal term needs for nb bands (with split_c, room
+// for the split copy of C that the BF16x3 projection P^dag C reads).
+size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw = 0, jdft_prec prec = JDFT_FP64,
+                                bool split_c = false);
 
 // HC += P D P^dag C for the sphere's projectors (no-op when nproj == 0).
+// split_c: take the projection from split operands (tcx_cn) when it is
+// eligible, splitting C in the workspace, which must then hold
+// nonlocal_workspace_bytes(..., true).
+// Csplit: the caller's BF16 planes of C (tcx_split), used instead of a split
+// of its own when the projection is eligible.
 template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
-                                jdft_prec prec, void* work, cudaStream_t st);
+                                jdft_prec prec, void* work, cudaStream_t st, bool split_c = false,
+                                const void* Csplit = nullptr);
 
 }  // namespace jdft

@@ -613,6 +613,10 @@ __global__ void status_merge_kernel(const int* __restrict__ src, int* __restrict
     if (threadIdx.x == 0 && *src > *dst) *dst = *src;
 }
 
+// SMs the plane kernels leave to the overlap factorisation running beside them
+// in jdft_hamiltonian_step (its kernels are small and latency-bound).
+constexpr int kStepReserveSms = 4;
+
 // sticky == nullptr: synchronous, the factorisation's status is returned;
 // otherwise the status is merged into the device word *sticky and nothing waits.
 template <typename T>
@@ -624,8 +628,11 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
     const size_t wbytes = ((size_t)nb * nb * sizeof(c_t<T>) + 255) / 256 * 256;
     const size_t lab = ((std::max(2 * (size_t)m * m, chol_work_elems(nb)) * sizeof(double2)) + 255) / 256 * 256;
     const size_t blk = ((size_t)nb * ldc * sizeof(c_t<T>) + 255) / 256 * 256;
-    // the basis workspace (grown once) holds U, W, the factorisation scratch, a copy of C and a status word
-    jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256);
+    const bool split = !Ugiven && std::is_same<T, float>::value && tcx_eligible(prec, nb, nb);
+    const size_t spl = split ? (tcx_split_bytes(nb, npw) + 255) / 256 * 256 : 0;
+    // the basis workspace (grown once) holds U, W, the factorisation scratch, a copy of C, a status
+    // word and, for the split-operand overlap, the BF16 planes of C
+    jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256 + spl);
     if (s != JDFT_OK) return s;
     char* q = (char*)b->work.ptr;
     double2* U = (double2*)q;
@@ -638,8 +645,15 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
         U = const_cast<double2*>(Ugiven);  // read only
     } else {
         JDFT_CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)nb * nb * sizeof(double2), st));
-        if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega, st)))
+        if (split) {
+            // the same split-operand product jdft_subspace forms C^dag O C with
+            void* planes = q + sm + wbytes + lab + blk + 256;
+            if ((s = tcx_split((const float2*)C, ldc, nb, npw, planes, st))) return s;
+            if ((s = tcx_cn(nb, nb, npw, planes, planes, U, nb, b->omega, st))) return s;
+        } else if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega,
+                                   st))) {
             return s;
+        }
     }
     if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
     if (gemm_nn_inplace_ok(prec, nb)) {
@@ -665,7 +679,127 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
 }
 }  // namespace jdft
 
+namespace jdft {
+
+static size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Side stream and fork / join events of a basis (created on first use).
+static jdft_status step_streams(jdft_basis_s* b) {
+    if (!b->side) {
+        JDFT_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        JDFT_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+        JDFT_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    }
+    return JDFT_OK;
+}
+
+// W = L^{-dag} of U = L L^dag (FP64 factorisation), in the basis's factor
+// workspace (not the chain's), with its outcome merged into *sticky.
+template <typename T>
+static jdft_status overlap_factor(jdft_basis_s* b, const double2* U, int nb, int* sticky, cudaStream_t st,
+                                  c_t<T>** W_out) {
+    const int m = nb + (nb & 1);
+    const size_t wbytes = r256((size_t)nb * nb * sizeof(c_t<T>));
+    const size_t lab = r256(std::max(2 * (size_t)m * m, chol_work_elems(nb)) * sizeof(double2));
+    jdft_status s = ensure_ws(b->fwork, wbytes + lab + 256);
+    if (s != JDFT_OK) return s;
+    char* q = (char*)b->fwork.ptr;
+    c_t<T>* W = (c_t<T>*)q;
+    double2* work = (double2*)(q + wbytes);
+    int* status = (int*)(q + wbytes + lab);
+    JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+    if ((s = small_cholesky_winv(nb, U, work, W, std::is_same<T, double>::value, status, st))) return s;
+    {
+        Trace tr_("status_merge", st);
+        status_merge_kernel<<<1, 32, 0, st>>>(status, sticky);
+    }
+    *W_out = W;
+    return check_launch("status_merge");
+}
+
+// One pass of the hot path over a band block: C^dag O C from the input block;
+// its FP64 factorisation on the basis's side stream (leaving reserve SMs free
+// of the persistent plane kernel) while H C and n(r) run; C^dag H C; then
+// C <- C L^{-dag} once the factor has joined.  Split-operand products share
+// one BF16 split of C (and one of H C).
+template <typename T>
+static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int ldc, void* HC, int ldhc, int nb,
+                                         const double* f, double* n_r, double2* CHC, double2* COC, bool ortho,
+                                         int* sticky, jdft_prec prec, cudaStream_t st) {
+    const int npw = b->ks[ik].npw;
+    const bool split = std::is_same<T, float>::value && tcx_eligible(prec, nb, nb);
+    const size_t chain = r256(apply_H_density_workspace(b, ik, nb, prec, !split));
+    const size_t cs = split ? r256(tcx_split_bytes(nb, npw)) : 0;
+    const bool inplace = gemm_nn_inplace_ok(prec, nb);
+    const size_t tmpb = inplace ? 0 : r256((size_t)nb * ldc * sizeof(c_t<T>));
+    // layout: chain region, planes of C, planes of H C; the copy of C that a
+    // rotation out of place needs reuses the start once the rest is done
+    jdft_status s = ensure_workspace(b, std::max(chain + 2 * cs, tmpb));
+    if (s != JDFT_OK) return s;
+    char* ws = (char*)b->work.ptr;
+    void* Cs = ws + chain;
+    void* HCs = ws + chain + cs;
+    const c_t<T>* Cc = (const c_t<T>*)C;
+    JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
+    if (split) {
+        if ((s = tcx_split((const float2*)C, ldc, nb, npw, Cs, st))) return s;
+        if ((s = tcx_cn(nb, nb, npw, Cs, Cs, COC, nb, b->omega, st))) return s;
+    } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, Cc, ldc, COC, nb, b->omega, st))) {
+        return s;
+    }
+    c_t<T>* W = nullptr;
+    if (ortho) {
+        if ((s = step_streams(b))) return s;
+        JDFT_CUDA_TRY(cudaEventRecord(b->ev_fork, st));
+        JDFT_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        if ((s = overlap_factor<T>(b, COC, nb, sticky, b->side, &W))) return s;
+        JDFT_CUDA_TRY(cudaEventRecord(b->ev_join, b->side));
+        b->reserve_sms = kStepReserveSms;
+    }
+    s = apply_H_density_with_split(b, ik, C, ldc, HC, ldhc, nb, f, n_r, prec, st, split ? Cs : nullptr);
+    b->reserve_sms = 0;
+    if (s != JDFT_OK) return s;
+    JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
+    if (split) {
+        if ((s = tcx_split((const float2*)HC, ldhc, nb, npw, HCs, st))) return s;
+        if ((s = tcx_cn(nb, nb, npw, Cs, HCs, CHC, nb, 1.0, st))) return s;
+    } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, (const c_t<T>*)HC, ldhc, CHC, nb, 1.0, st))) {
+        return s;
+    }
+    if (!ortho) return JDFT_OK;
+    JDFT_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_join, 0));
+    if (inplace) return gemm_nn_acc<T>(prec, npw, nb, nb, Cc, ldc, W, nb, (c_t<T>*)C, ldc, st, false);
+    c_t<T>* tmp = (c_t<T>*)ws;
+    JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));
+    return gemm_nn_acc<T>(prec, npw, nb, nb, tmp, ldc, W, nb, (c_t<T>*)C, ldc, st, false);
+}
+}  // namespace jdft
+
 extern "C" {
+
+jdft_status jdft_hamiltonian_step(jdft_basis_t b, int ik, void* C, int ldc, void* HC, int ldhc, int nb,
+                                  const double* f, double* n_r, void* CHC, void* COC, int orthonormalize,
+                                  int* status, jdft_prec prec, void* stream) {
+    clear_error();
+    JDFT_CHECK_ARG(b, "null basis");
+    JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
+    JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
+    JDFT_CHECK_ARG(nb >= 1, "nb must be >= 1");
+    const int npw = b->ks[ik].npw;
+    const uintptr_t align = prec == JDFT_FP64 ? 16 : 8;
+    JDFT_CHECK_ARG(C && HC && f && n_r && CHC && COC, "null block, occupation, density or subspace pointer");
+    JDFT_CHECK_ARG(ldc >= npw && ldhc >= npw, "leading dimension < npw");
+    JDFT_CHECK_ARG((uintptr_t)C % align == 0 && (uintptr_t)HC % align == 0, "C or HC not aligned to its complex type");
+    JDFT_CHECK_ARG((uintptr_t)CHC % 16 == 0 && (uintptr_t)COC % 16 == 0, "subspace outputs must be 16-byte aligned");
+    JDFT_CHECK_ARG(!orthonormalize || status, "orthonormalize needs a status word");
+    if (!b->have_V) return set_error(JDFT_ERR_ARG, "no potential set (call jdft_set_potential first)");
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == JDFT_FP64
+               ? hamiltonian_step_impl<double>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, (double2*)CHC, (double2*)COC,
+                                               orthonormalize != 0, status, prec, st)
+               : hamiltonian_step_impl<float>(b, ik, C, ldc, HC, ldhc, nb, f, n_r, (double2*)CHC, (double2*)COC,
+                                              orthonormalize != 0, status, prec, st);
+}
 
 jdft_status jdft_orthonormalize(jdft_basis_t b, int ik, void* C, int ldc, int nb, jdft_prec prec, void* stream) {
     clear_error();

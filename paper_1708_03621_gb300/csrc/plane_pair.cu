@@ -323,7 +323,7 @@ static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, sms) * resident);
+    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, sms - g.reserve_sms) * resident);
     {
         Trace tr_(name, st);
         kern<<<grid, 32 * kPairWarps, smem, st>>>(g, colbuf, Vp, nb, f, w, n_r, tw_base + g.p0.tw_offset,

@@ -22,11 +22,14 @@
 // jdft_device_status) and stops issuing products; the block then waits, under
 // a fixed limit of its own, for the products it has already committed, skips
 // the epilogue and only then frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -457,6 +460,335 @@ jdft_status tc_zgemm_nn_acc(int M, int N, int K, const float2* A, int lda, const
 
 }  // namespace jdft
 
+namespace jdft {
+
+// ===========================================================================
+// C^dag B products from operands split once into BF16 planes, staged by bulk
+// asynchronous copies (TMA).
+//
+// A complex block X (rows of K values, FP32) is stored split into four planes
+// of BF16 values: Re hi, Re lo, Im hi, Im lo, with x = hi + lo for
+// hi = bf16(x), lo = bf16(x - hi).  The split copy is ordered by chunks of 16
+// K: for each chunk, the four planes, each holding all rows (padded to a
+// multiple of 128 with zeros; K padded to a multiple of 16 with zeros) in the
+// no-swizzle K-major layout of the tensor cores (8-row x 8-value core
+// matrices of 128 contiguous bytes; the two core matrices of a row group
+// along K 128 bytes apart, row groups 256 bytes apart).  The rows a block
+// needs from one plane of one chunk are then one contiguous copy.
+//
+// For out[m][n] += alpha sum_k conj(A[m][k]) B[n][k]:
+//   Re = Ar.Br + Ai.Bi,  Im = Ar.Bi - Ai.Br,
+// each real product as hi.hi + hi.lo + lo.hi (FP32 accumulation in tensor
+// memory), the minus through the instruction descriptor's negate-A bit: 12
+// MMAs of 128 x NT x 16 per 16 complex K.
+//
+// One block of 128 threads computes a 128 x NT tile over a range of K (split-K
+// partial sums meet in FP64 with atomics): thread 0 issues the copies of a
+// 4-stage ring, thread 32 waits for a stage, issues its MMAs and commits them
+// to the stage's "empty" barrier, and after the last stage to the accumulator
+// barrier, which all four warps wait for before reading tensor memory (warp
+// w: rows 32 w .. 32 w + 31).  The epilogue passes each warp's 32 x 16 slices
+// through shared memory, so that one atomic instruction covers 16 consecutive
+// outputs of two rows.  Every wait is bounded by the run-time limit; a wait
+// that gives up records JDFT_ERR_TIMEOUT, and the block waits (under the fixed
+// drain limit) for the copies and products it already issued before freeing
+// its tensor memory.
+// ===========================================================================
+
+constexpr int TCX_M = 128;
+constexpr int TCX_KC = 16;  // complex K per stage: one instruction's K
+constexpr int TCX_STAGES = 4;
+constexpr int TCX_THREADS = 128;
+constexpr int TCX_PLANE = TCX_M * TCX_KC * 2;  // bytes of 128 rows x 16 K of one plane
+
+__host__ __device__ constexpr int tcx_rows_pad(int rows) { return (rows + TCX_M - 1) / TCX_M * TCX_M; }
+__host__ __device__ constexpr int tcx_chunks(int K) { return (K + TCX_KC - 1) / TCX_KC; }
+
+template <int NT>
+struct TcxLayout {
+    static constexpr int A_PL = TCX_PLANE;                 // bytes of one A plane in a stage
+    static constexpr int B_PL = (NT / TCX_M) * TCX_PLANE;  // bytes of one B plane in a stage
+    static constexpr int A_BYTES = 4 * A_PL;
+    static constexpr int STAGE = 4 * A_PL + 4 * B_PL;
+    static constexpr int BAR_OFF = TCX_STAGES * STAGE;
+    static constexpr int SMEM = BAR_OFF + 256 + 1024;  // barriers, flags; 1 KB to align the ring
+    static constexpr uint32_t NCOLS = 2 * NT <= 256 ? 256 : 512;
+    static_assert(NT % TCX_M == 0, "B blocks are whole 128-row blocks");
+};
+
+// Element offset of (row r, k) of plane p in a split block of rp (padded) rows.
+__device__ __forceinline__ size_t tcx_offset(int r, int k, int p, int rp) {
+    const int kc = k >> 4, kk = k & 15;
+    return ((size_t)(kc * 4 + p) * rp + (r & ~7)) * TCX_KC + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
+}
+
+// One thread per 16-byte row of a core matrix: 8 consecutive K values of one
+// row (64 contiguous input bytes), their hi and lo parts of Re and Im written
+// as one 16-byte store per plane.  Consecutive threads take consecutive rows
+// of a row group, then the second K half, then the next row group, so a
+// warp's stores to each plane are 512 contiguous bytes.
+__global__ void split_planes_kernel(const float2* __restrict__ X, int ld, int rows, int K, int rows_pad, int nkc,
+                                    __nv_bfloat16* __restrict__ out) {
+    const int per_chunk = rows_pad * 2;  // 16-byte units per plane of one chunk
+    const int64_t total = (int64_t)per_chunk * nkc;
+    const size_t P = (size_t)rows_pad * TCX_KC;  // elements between planes of one chunk
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kc = (int)(i / per_chunk), u = (int)(i - (int64_t)kc * per_chunk);
+        const int r8 = u & 7, h = (u >> 3) & 1, g = u >> 4;
+        const int r = g * 8 + r8, k0 = kc * TCX_KC + h * 8;
+        float2 v[8];
+        const float2* src = X + (size_t)r * ld + k0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (r < rows && k0 + j < K) ? src[j] : make_float2(0.f, 0.f);
+        uint32_t w[4][4];  // plane, 32-bit word (two BF16 values)
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            const __nv_bfloat16 hx0 = __float2bfloat16_rn(v[j].x), hx1 = __float2bfloat16_rn(v[j + 1].x);
+            const __nv_bfloat16 hy0 = __float2bfloat16_rn(v[j].y), hy1 = __float2bfloat16_rn(v[j + 1].y);
+            const __nv_bfloat162 hx = __halves2bfloat162(hx0, hx1), hy = __halves2bfloat162(hy0, hy1);
+            const __nv_bfloat162 lx = __halves2bfloat162(__float2bfloat16_rn(v[j].x - __bfloat162float(hx0)),
+                                                         __float2bfloat16_rn(v[j + 1].x - __bfloat162float(hx1)));
+            const __nv_bfloat162 ly = __halves2bfloat162(__float2bfloat16_rn(v[j].y - __bfloat162float(hy0)),
+                                                         __float2bfloat16_rn(v[j + 1].y - __bfloat162float(hy1)));
+            w[0][j / 2] = *reinterpret_cast<const uint32_t*>(&hx);
+            w[1][j / 2] = *reinterpret_cast<const uint32_t*>(&lx);
+            w[2][j / 2] = *reinterpret_cast<const uint32_t*>(&hy);
+            w[3][j / 2] = *reinterpret_cast<const uint32_t*>(&ly);
+        }
+        const size_t o = tcx_offset(r, k0, 0, rows_pad);
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            *reinterpret_cast<uint4*>(out + o + p * P) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
+                 : "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(TCX_THREADS, 1)
+    tcx_cn_kernel(const char* __restrict__ As, const char* __restrict__ Bs, int M, int N, int nkc, int cps,
+                  double2* __restrict__ out, int ldo, double alpha) {
+    // rows of the split blocks (padded to 128)
+    const int rpA = (M + TCX_M - 1) / TCX_M * TCX_M, rpB = (N + TCX_M - 1) / TCX_M * TCX_M;
+    using L = TcxLayout<NT>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+    uint64_t* empty = full + TCX_STAGES;
+    uint64_t* accbar = empty + TCX_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accbar + 1);
+    volatile int* flags = reinterpret_cast<volatile int*>(tslot + 1);  // 0: failed, 1: stages loaded, 2: committed
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TCX_M, n0 = blockIdx.y * NT;
+    // B rows this block copies (the last column block may hold fewer than NT)
+    const uint32_t bbytes = (uint32_t)min(NT, rpB - n0) * TCX_KC * 2;
+    const int c0 = blockIdx.z * cps;
+    const int nit = max(0, min(nkc, c0 + cps) - c0);
+    if (tid == 0) {
+        for (int s = 0; s < TCX_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accbar, 1);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 2) tc::tmem_alloc(tslot, L::NCOLS);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const unsigned long long wait_ns = g_tc_wait_ns;
+    if (tid == 0) {
+        // producer: a stage is refilled once the products that read it are done
+        int it = 0;
+        for (; it < nit; ++it) {
+            const int s = it % TCX_STAGES;
+            const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+            if (!tc::mbar_wait_ns(&empty[s], par ^ 1u, wait_ns)) {
+                flags[0] = 1;
+                break;
+            }
+            unsigned char* st = smem + s * L::STAGE;
+            const int kc = c0 + it;
+            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(4 * L::A_PL) + 4 * bbytes);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                bulk_load(st + p * L::A_PL, As + ((size_t)(kc * 4 + p) * rpA + m0) * (TCX_KC * 2), L::A_PL, &full[s]);
+                bulk_load(st + L::A_BYTES + p * L::B_PL, Bs + ((size_t)(kc * 4 + p) * rpB + n0) * (TCX_KC * 2), bbytes,
+                          &full[s]);
+            }
+        }
+        flags[1] = it;
+    } else if (tid == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc::instr_desc(1u, TCX_M, NT);
+        constexpr uint32_t idesc_neg = idesc | (1u << 13);  // negate A
+        int it = 0;
+        for (; it < nit; ++it) {
+            const int s = it % TCX_STAGES;
+            const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+            if (!tc::mbar_wait_ns(&full[s], par, wait_ns)) {
+                flags[0] = 1;
+                break;
+            }
+            tc::tc_fence_after_sync();
+            const uint32_t base = tc::smem_addr(smem + s * L::STAGE);
+            uint64_t a[4], b[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                a[p] = tc::smem_desc(base + p * L::A_PL, 128, 256);
+                b[p] = tc::smem_desc(base + L::A_BYTES + p * L::B_PL, 128, 256);
+            }
+            const uint32_t acc = it > 0 ? 1u : 0u;
+            const uint32_t re = tmem, im = tmem + NT;
+            // planes: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo
+            tc::mma_bf16(re, a[0], b[0], idesc, acc);
+            tc::mma_bf16(re, a[0], b[1], idesc, 1u);
+            tc::mma_bf16(re, a[1], b[0], idesc, 1u);
+            tc::mma_bf16(re, a[2], b[2], idesc, 1u);
+            tc::mma_bf16(re, a[2], b[3], idesc, 1u);
+            tc::mma_bf16(re, a[3], b[2], idesc, 1u);
+            tc::mma_bf16(im, a[0], b[2], idesc, acc);
+            tc::mma_bf16(im, a[0], b[3], idesc, 1u);
+            tc::mma_bf16(im, a[1], b[2], idesc, 1u);
+            tc::mma_bf16(im, a[2], b[0], idesc_neg, 1u);
+            tc::mma_bf16(im, a[2], b[1], idesc_neg, 1u);
+            tc::mma_bf16(im, a[3], b[0], idesc_neg, 1u);
+            tc::mma_commit(&empty[s]);
+        }
+        flags[2] = it;
+        if (it == nit && nit > 0) tc::mma_commit(accbar);
+    }
+    __syncthreads();
+    const int loaded = flags[1], committed = flags[2];
+    int ok = flags[0] == 0 && nit > 0;
+    if (ok) {
+        const int w = tc::mbar_wait_ns(accbar, 0u, wait_ns) ? 1 : 0;
+        ok = __syncthreads_and(w);
+    }
+    if (!ok && nit > 0) {
+        // drain before freeing anything: copies issued but never consumed, and
+        // the last committed batch of products (batches complete in order)
+        if (tid == 0) {
+            for (int it = committed; it < loaded; ++it)
+                tc::mbar_wait_ns(&full[it % TCX_STAGES], (uint32_t)((it / TCX_STAGES) & 1), TC_DRAIN_NS);
+            if (committed > 0)
+                tc::mbar_wait_ns(&empty[(committed - 1) % TCX_STAGES], (uint32_t)(((committed - 1) / TCX_STAGES) & 1),
+                                 TC_DRAIN_NS);
+            if (committed == nit) tc::mbar_wait_ns(accbar, 0u, TC_DRAIN_NS);
+        }
+        __syncthreads();
+    }
+    tc::tc_fence_after_sync();
+    if (ok) {
+        // each warp: its 32 rows in slices of 16 columns, transposed through
+        // shared memory (the ring is free now) so that lanes 0-15 and 16-31
+        // add to 16 consecutive outputs of one row each
+        float2* T = reinterpret_cast<float2*>(smem) + warp * (32 * 17);
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const int c = lane & 15, rh = lane >> 4;
+#pragma unroll 1
+        for (int col = 0; col < NT && n0 + col < N; col += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(lane_base + col, re);
+            tc::tmem_ld16(lane_base + NT + col, im);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) T[lane * 17 + j] = make_float2(re[j], im[j]);
+            __syncwarp();
+            const int n = n0 + col + c;
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const int r = 2 * i + rh;
+                const int m = m0 + warp * 32 + r;
+                const float2 v = T[r * 17 + c];
+                if (m < M && n < N) {
+                    atomicAdd(&out[(size_t)m * ldo + n].x, alpha * (double)v.x);
+                    atomicAdd(&out[(size_t)m * ldo + n].y, alpha * (double)v.y);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 2) tc::tmem_dealloc(tmem, L::NCOLS);
+    if (!ok && nit > 0 && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
+}
+
+size_t tcx_split_bytes(int rows, int K) { return (size_t)tcx_rows_pad(rows) * tcx_chunks(K) * 4 * TCX_KC * 2; }
+
+bool tcx_eligible(jdft_prec prec, int M, int N) { return prec == JDFT_BF16X3 && M > 32 && N > 32; }
+
+jdft_status tcx_split(const float2* X, int ld, int rows, int K, void* planes, cudaStream_t st) {
+    if (rows == 0 || K == 0) return JDFT_OK;
+    const int nkc = tcx_chunks(K), rp = tcx_rows_pad(rows);
+    const int64_t total = (int64_t)rp * 2 * nkc;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    {
+        Trace tr_("split_planes", st);
+        split_planes_kernel<<<grid, 256, 0, st>>>(X, ld, rows, K, rp, nkc, (__nv_bfloat16*)planes);
+    }
+    return check_launch("split_planes");
+}
+
+// Split-K counts of tcx_cn chosen by jdft_autotune_gemm, per (M, N, K).
+namespace {
+std::map<std::tuple<int, int, int>, int> g_tune_tcx;
+}  // namespace
+
+static int tuned_tcx_splits(int M, int N, int K) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_tcx.find(std::make_tuple(M, N, K));
+    return it == g_tune_tcx.end() ? 0 : it->second;
+}
+
+jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
+                   cudaStream_t st) {
+    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    const bool wide = N > 128;
+    const int NT = wide ? 256 : 128;
+    const int nkc = tcx_chunks(K);
+    const int tiles = ((M + TCX_M - 1) / TCX_M) * ((N + NT - 1) / NT);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one wave of blocks, and at most 4096 complex K accumulated per block
+    const int capmin = (nkc + 4096 / TCX_KC - 1) / (4096 / TCX_KC);
+    int splits = std::max(capmin, std::min(nkc, std::max(1, sms / tiles)));
+    const int tuned = tuned_tcx_splits(M, N, K);
+    if (tuned > 0) splits = std::max(capmin, std::min(nkc, tuned));
+    const int cps = (nkc + splits - 1) / splits;
+    splits = (nkc + cps - 1) / cps;
+    dim3 grid((M + TCX_M - 1) / TCX_M, (N + NT - 1) / NT, splits);
+    if (wide) {
+        auto kern = tcx_cn_kernel<256>;
+        cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<256>::SMEM);
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
+        Trace tr_("tcx_cn", st);
+        kern<<<grid, TCX_THREADS, TcxLayout<256>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
+                                                               cps, out, ldo, alpha);
+    } else {
+        auto kern = tcx_cn_kernel<128>;
+        cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<128>::SMEM);
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
+        Trace tr_("tcx_cn", st);
+        kern<<<grid, TCX_THREADS, TcxLayout<128>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
+                                                               cps, out, ldo, alpha);
+    }
+    return check_launch("tcx_cn");
+}
+
+}  // namespace jdft
+
 using namespace jdft;
 
 extern "C" jdft_status jdft_device_status(void* stream) {
@@ -480,6 +812,68 @@ extern "C" jdft_status jdft_set_wait_limit(double seconds) {
     return JDFT_OK;
 }
 
+namespace jdft {
+// Time tcx_cn on split copies of A and B for split-K counts around one wave
+// of blocks and keep the fastest for (M, N, K).
+static jdft_status autotune_tcx(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, int* splits,
+                                cudaStream_t st) {
+    const size_t sa = (tcx_split_bytes(M, K) + 255) / 256 * 256, sb = (tcx_split_bytes(N, K) + 255) / 256 * 256;
+    char* mem = nullptr;
+    JDFT_CUDA_TRY(cudaMalloc(&mem, sa + sb + (size_t)M * N * sizeof(double2)));
+    double2* out = (double2*)(mem + sa + sb);
+    jdft_status s = tcx_split(A, lda, M, K, mem, st);
+    if (s == JDFT_OK) s = tcx_split(B, ldb, N, K, mem + sa, st);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int NT = N > 128 ? 256 : 128;
+    const int tiles = ((M + TCX_M - 1) / TCX_M) * ((N + NT - 1) / NT);
+    const int wave = std::max(1, sms / tiles);
+    std::vector<int> cand;
+    for (int f : {25, 50, 75, 100, 150, 200}) {
+        const int c = std::max(1, wave * f / 100);
+        if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const auto key = std::make_tuple(M, N, K);
+    float best = 1e30f;
+    int best_c = wave;
+    for (int c : cand) {
+        if (s != JDFT_OK) break;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_tcx[key] = c;
+        }
+        // one untimed call, then three timed ones (the accumulated values are not used)
+        s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && s == JDFT_OK; ++r) s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st);
+        cudaEventRecord(e1, st);
+        if (s != JDFT_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(mem);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_tcx[key] = best_c;
+    }
+    if (s != JDFT_OK) return s;
+    if (splits) *splits = best_c;
+    return JDFT_OK;
+}
+}  // namespace jdft
+
 extern "C" jdft_status jdft_autotune_gemm(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                                           jdft_prec prec, int* splits, void* stream) {
     clear_error();
@@ -489,6 +883,7 @@ extern "C" jdft_status jdft_autotune_gemm(int M, int N, int K, const void* A, in
     const int fmt = prec == JDFT_BF16X3 ? 1 : 0;
     const bool bf16 = fmt == 1;
     cudaStream_t st = (cudaStream_t)stream;
+    if (tcx_eligible(prec, M, N)) return autotune_tcx(M, N, K, (const float2*)A, lda, (const float2*)B, ldb, splits, st);
     if (N <= 32) return JDFT_OK;  // the 32-column schedule is fixed
     int dflt, capmin;
     cn_schedule(M, N, K, dflt, capmin);

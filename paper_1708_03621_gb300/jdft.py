@@ -91,6 +91,7 @@ _SIGS = {
     "jdft_mlp_rows": [_vp, _i, _vp, _vp, _i, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_int64), _vp],
     "jdft_device_status": [_vp],
     "jdft_set_wait_limit": [_d],
+    "jdft_hamiltonian_step": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp],
     "jdft_measure_fp32_peak": [ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i), _vp],
     "jdft_batch_create": [_i, ctypes.POINTER(ApplyItem), ctypes.POINTER(_vp)],
     "jdft_batch_launch": [_vp, _vp],
@@ -328,6 +329,18 @@ def jdft_orthonormalize_async(basis, ik, C, status, prec="fp64", stream=None, U=
         raise ValueError("U must be a contiguous complex128 (nb, nb) CUDA tensor")
     _call("jdft_orthonormalize_async", basis.handle, ik, p, ld, nb, _ptr(U) if U is not None else None,
           _prec(prec), _ptr(status), _stream(stream))
+
+
+def jdft_hamiltonian_step(basis, ik, C, HC, f, n_r, CHC, COC, status=None, prec="bf16x3", stream=None):
+    """One pass of the hot path: HC = H C, n_r += density, COC = C^dag O C, CHC = C^dag H C,
+    and C <- C L^{-dag} (COC = L L^dag) when a device int32 status word is given."""
+    p, ld, nb = _block(C, prec, "C")
+    q, ldh, nbh = _block(HC, prec, "HC")
+    if nbh != nb:
+        raise ValueError("C and HC must have the same number of bands")
+    _call("jdft_hamiltonian_step", basis.handle, ik, p, ld, q, ldh, nb, _ptr(f), _ptr(n_r), _ptr(CHC), _ptr(COC),
+          1 if status is not None else 0, _ptr(status) if status is not None else None, _prec(prec),
+          _stream(stream))
 
 
 def jdft_subspace_eigs(A, eigs, stream=None):

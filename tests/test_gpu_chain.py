@@ -345,3 +345,46 @@ def test_generic_plane_kernels_match_oracle(name, prec, monkeypatch):
     jdft.jdft_density(g.basis, 0, Cd, torch.tensor(f, device="cuda"), n, prec)
     ref = pw.density(o.basis, C.T, f, weight=w.weights()[0])
     assert np.max(np.abs(n.cpu().numpy() - ref)) / np.max(ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("name,prec", [("mid", "fp64"), ("mid", "bf16x3"), ("large", "bf16x3"), ("large", "fp32")])
+def test_hamiltonian_step_equals_separate_calls(name, prec):
+    """jdft_hamiltonian_step (rows a1-a9 in one call, the overlap factored on a
+    side stream while H is applied) against jdft_apply_H_density,
+    jdft_subspace and jdft_orthonormalize_async on the same block, and its
+    H C against the oracle on sampled bands."""
+    w = workload(name)
+    o = OracleSystem(w) if name != "large" else _large_ref.setdefault("o", OracleSystem(w))
+    g = GpuSystem(w, o.atoms)
+    from paper_1708_03621_gb300 import jdft
+    C = o.coeffs(40, seed=31) if name == "mid" else o.coeffs()
+    nb = C.shape[0]
+    f = torch.tensor(np.linspace(2.0, 0.5, nb), device="cuda")
+    # separate calls
+    C1 = to_dev(C, prec)
+    H1 = torch.empty_like(C1)
+    n1 = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    S1 = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    O1 = torch.empty_like(S1)
+    st1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    jdft.jdft_apply_H_density(g.basis, 0, C1, H1, f, n1, prec)
+    jdft.jdft_subspace(g.basis, 0, C1, H1, S1, O1, prec)
+    jdft.jdft_orthonormalize_async(g.basis, 0, C1, st1, prec, U=O1)
+    # one call
+    C2 = to_dev(C, prec)
+    H2 = torch.empty_like(C2)
+    n2 = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+    S2 = torch.empty_like(S1)
+    O2 = torch.empty_like(S1)
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    jdft.jdft_hamiltonian_step(g.basis, 0, C2, H2, f, n2, S2, O2, st2, prec)
+    torch.cuda.synchronize()
+    assert int(st1.item()) == 0 and int(st2.item()) == 0
+    assert rel_max(host(H2), host(H1)) < SAME[prec]
+    assert np.max(np.abs(n2.cpu().numpy() - n1.cpu().numpy())) < SAME[prec] * np.max(np.abs(n1.cpu().numpy()))
+    assert rel_max(S2.cpu().numpy(), S1.cpu().numpy()) < SAME[prec]
+    assert rel_max(O2.cpu().numpy(), O1.cpu().numpy()) < SAME[prec]
+    assert rel_max(host(C2), host(C1)) < (1e-12 if prec == "fp64" else 1e-5)
+    sample = [0, nb // 2, nb - 1]
+    assert band_rel_err(host(H2)[sample], o.apply_H(C[sample])) < TOL[prec]
+    jdft.jdft_device_status()

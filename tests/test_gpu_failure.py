@@ -46,3 +46,35 @@ def test_wait_limit_runs_out_and_context_survives(prec):
     got = out.cpu().numpy().astype(np.complex128)
     assert band_rel_err(got, ref.cpu().numpy().astype(np.complex128)) < 1e-6
     assert band_rel_err(got, o.apply_H(C)) < 2e-5
+
+
+def test_wait_limit_runs_out_in_split_operand_products():
+    """The same for the BF16x3 subspace products that read split operands
+    through the TMA-fed pipeline (40 bands: both dimensions above 32)."""
+    from paper_1708_03621_gb300 import jdft
+    w = workload("mid")
+    o = OracleSystem(w)
+    g = GpuSystem(w, o.atoms)
+    C = o.coeffs(40, seed=8)
+    Cd = torch.tensor(C.astype(np.complex64), device="cuda")
+    HC = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, HC, "bf16x3")
+    nb = C.shape[0]
+    ref = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
+    jdft.jdft_subspace(g.basis, 0, Cd, HC, ref, None, "bf16x3")
+    jdft.jdft_device_status()
+    got = torch.zeros_like(ref)
+    jdft.jdft_set_wait_limit(0.0)
+    try:
+        jdft.jdft_subspace(g.basis, 0, Cd, HC, got, None, "bf16x3")
+        with pytest.raises(jdft.JdftError) as err:
+            jdft.jdft_device_status()
+        assert err.value.status == jdft.STATUS_CODES["ERR_TIMEOUT"]
+    finally:
+        jdft.jdft_set_wait_limit(2.0)
+    jdft.jdft_subspace(g.basis, 0, Cd, HC, got, None, "bf16x3")
+    jdft.jdft_device_status()
+    a, b = got.cpu().numpy(), ref.cpu().numpy()
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-6
+    HCo = o.apply_H(C)
+    assert np.max(np.abs(a - C.conj() @ HCo.T)) / np.max(np.abs(b)) < 2e-5
