@@ -309,6 +309,9 @@ typedef struct {
     double energy;          /* f tr(C^dag H C) at exit (Ha) */
     double residual;        /* the stopping residual at exit (Ha) */
     double seconds;         /* wall time of the call */
+    int precond_fallback;   /* 1: the learned preconditioner failed a check (a non-finite or non-descent
+                               direction, no energy decrease along it, or 40 iterations without progress)
+                               and Teter's took over for the rest of the call */
 } jdft_min_report;
 
 /* Preconditioned all-band conjugate-gradient minimisation of E = f tr(C^dag H C)

@@ -486,6 +486,14 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
     bool have_prev = false;
     double best = 1e300;
     int stall = 0;
+    // the learned preconditioner, while it passes its checks; Teter's after a failure
+    auto use_mlp = [&]() { return o.precond == JDFT_PRECOND_MLP && !rep->precond_fallback; };
+    double mlp_best = 1e300;
+    int mlp_stall = 0;
+    auto fall_back = [&]() {
+        rep->precond_fallback = 1;
+        have_prev = false;  // restart the conjugate directions
+    };
     for (int it = 0;; ++it) {
         // gradient and residual
         if ((s = axpby<T>(npw, nb, 1.0, M.HC, ld, 0.0, nullptr, 0, M.G, ld, st))) return s;
@@ -501,6 +509,10 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
             if (res < 0.7 * best) { best = res; stall = 0; }
             else if (++stall >= 8) return JDFT_OK;
         }
+        if (use_mlp()) {
+            if (res < 0.7 * mlp_best) { mlp_best = res; mlp_stall = 0; }
+            else if (++mlp_stall >= 40) fall_back();  // no progress with the network's directions
+        }
         if (it >= max_iter || rep->iterations >= o.max_iter)
             return set_error(JDFT_ERR_NOT_CONVERGED, "band minimiser reached its iteration limit");
         rep->iterations++;
@@ -510,7 +522,7 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
             band_kinetic_kernel<T><<<nb, 256, 0, st>>>(npw, M.C, ld, M.kin, M.omega, M.Tb);
         }
         if ((s = check_launch("band_kinetic"))) return s;
-        if (o.precond == JDFT_PRECOND_MLP) {
+        if (use_mlp()) {
             if ((s = mlp_precondition<T>(o.mlp, npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, M.Hs, M.bf, st))) return s;
         } else {
             Trace tr_("precond_teter", st);
@@ -523,6 +535,12 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
         if ((s = dot<T>(npw, nb, M.G, ld, M.KG, ld, M.scal + S_GKG, st))) return s;
         if (have_prev && (s = dot<T>(npw, nb, M.G, ld, M.KGp, ld, M.scal + S_GKGP, st))) return s;
         if ((s = M.read_scal(h, 4))) return s;
+        if (use_mlp() && !(std::isfinite(h[S_GKG]) && h[S_GKG] > 0.0)) {
+            // K G must be finite with G.(K G) > 0 (a positive preconditioner)
+            fall_back();
+            --rep->iterations;
+            continue;
+        }
         double beta = 0.0;
         if (have_prev && gkgp_prev != 0.0) beta = std::max(0.0, (h[S_GKG] - h[S_GKGP]) / gkgp_prev);
         const double gkg = h[S_GKG];
@@ -548,10 +566,21 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
         }
         const double a1 = 2.0 * h[S_A1];
         const double a2 = h[S_DHD] - h[S_HSDOD];
+        if (use_mlp() && !(std::isfinite(a1) && std::isfinite(a2) && a1 < 0.0)) {
+            fall_back();  // not a finite descent direction even after the restart
+            --rep->iterations;
+            continue;
+        }
         double lam = (a2 > 0.0) ? -a1 / (2.0 * a2) : 1.0;
-        // rounding level of the energy: 64 ulp in FP64; 16 ulp of FP32 when the blocks are FP32
-        const double noise = (std::is_same<T, double>::value ? 64.0 * 2.220446049250313e-16
-                                                             : 16.0 * 1.1920928955078125e-7) * std::fabs(E);
+        // error level of the computed energy: 64 ulp in FP64; with FP32 blocks,
+        // 16 FP32 ulp for CUDA-core products, and for the 3-product tensor-core
+        // splits their accuracy, 2e-5 relative (the FP32 accumulation of the
+        // split products over long K; a tighter rule stops the cheap phase as
+        // soon as the true decrease per step falls below it)
+        const double rel = std::is_same<T, double>::value ? 64.0 * 2.220446049250313e-16
+                           : (M.prec == JDFT_TF32X3 || M.prec == JDFT_BF16X3) ? 2e-5
+                                                                             : 16.0 * 1.1920928955078125e-7;
+        const double noise = rel * std::fabs(E);
         bool accepted = false;
         for (int tries = 0; tries < 30; ++tries) {
             if ((s = axpby<T>(npw, nb, 1.0, M.C, ld, lam, M.d, ld, M.Y, ld, st))) return s;
@@ -567,6 +596,12 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
             if ((s = M.read_scal(h, 8))) return s;
             if (M.f * h[S_TRN] <= E + noise) { accepted = true; break; }
             lam *= 0.5;
+        }
+        if (!accepted && use_mlp()) {
+            // no lower energy along the network's direction: Teter's from here on
+            fall_back();
+            --rep->iterations;
+            continue;
         }
         if (!accepted) { *res_out = res; return JDFT_OK; }  // no lower energy along d: stationary to rounding
         std::swap(M.C, M.Cn);

@@ -45,7 +45,8 @@ class MinOpts(ctypes.Structure):
 
 class MinReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("mixed_iterations", ctypes.c_int), ("converged", ctypes.c_int),
-                ("energy", ctypes.c_double), ("residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("energy", ctypes.c_double), ("residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("precond_fallback", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
