@@ -88,6 +88,32 @@ __host__ __device__ __forceinline__ f2x p_fma(f2x a, f2x b, f2x c) {
 }
 __host__ __device__ __forceinline__ f2x p_zero() { return p_pack(0.f, 0.f); }
 
+// Constant pairs of the butterflies, kept in the constant bank so that no
+// register holds them and no instruction builds them (device code); the host
+// versions serve CPU checks.
+enum PairConst { PC_C1, PC_S1, PC_H, PC_MC1, PC_MS1, PC_MH, PC_MHALF, PC_R3, PC_MR3, PC_COUNT };
+static __constant__ unsigned long long kPairConst[PC_COUNT] = {
+    0x3f6c835e3f6c835eull,  // cos(pi/8)
+    0x3ec3ef153ec3ef15ull,  // sin(pi/8)
+    0x3f3504f33f3504f3ull,  // 1/sqrt(2)
+    0xbf6c835ebf6c835eull,  // -cos(pi/8)
+    0xbec3ef15bec3ef15ull,  // -sin(pi/8)
+    0xbf3504f3bf3504f3ull,  // -1/sqrt(2)
+    0xbf000000bf000000ull,  // -1/2
+    0x3f5db3d73f5db3d7ull,  // sqrt(3)/2
+    0xbf5db3d7bf5db3d7ull,  // -sqrt(3)/2
+};
+__host__ __device__ __forceinline__ f2x pconst(int i) {
+#ifdef __CUDA_ARCH__
+    return f2x{kPairConst[i]};
+#else
+    const float v[PC_COUNT] = {0.92387953251128675613f, 0.38268343236508977173f, 0.70710678118654752440f,
+                               -0.92387953251128675613f, -0.38268343236508977173f, -0.70710678118654752440f,
+                               -0.5f, 0.86602540378443864676f, -0.86602540378443864676f};
+    return p_dup(v[i]);
+#endif
+}
+
 // The same complex entry of two bands.
 struct cpair {
     f2x x, y;
@@ -144,12 +170,11 @@ __host__ __device__ __forceinline__ void pdft4(cpair* v) {
 
 template <int SIGN>
 __host__ __device__ __forceinline__ void pdft3(cpair* v) {
-    const float h = 0.86602540378443864676f;  // sqrt(3)/2
     const cpair t1 = cp_add(v[1], v[2]), d = cp_sub(v[1], v[2]);
-    const cpair m = {p_fma(t1.x, p_dup(-0.5f), v[0].x), p_fma(t1.y, p_dup(-0.5f), v[0].y)};
+    const cpair m = {p_fma(t1.x, pconst(PC_MHALF), v[0].x), p_fma(t1.y, pconst(PC_MHALF), v[0].y)};
     v[0] = cp_add(v[0], t1);
-    // t2 = SIGN i h d = (-SIGN h d.y, SIGN h d.x)
-    const f2x ph = p_dup(SIGN * h), mh = p_dup(-SIGN * h);
+    // t2 = SIGN i h d = (-SIGN h d.y, SIGN h d.x), h = sqrt(3)/2
+    const f2x ph = pconst(SIGN > 0 ? PC_R3 : PC_MR3), mh = pconst(SIGN > 0 ? PC_MR3 : PC_R3);
     v[1] = {p_fma(d.y, mh, m.x), p_fma(d.x, ph, m.y)};
     v[2] = {p_fma(d.y, ph, m.x), p_fma(d.x, mh, m.y)};
 }
@@ -160,8 +185,7 @@ __host__ __device__ __forceinline__ void pdft8(cpair* v) {
     cpair o[4] = {v[1], v[3], v[5], v[7]};
     pdft4<SIGN>(e);
     pdft4<SIGN>(o);
-    const float r = 0.70710678118654752440f;  // 1/sqrt(2)
-    const f2x pr = p_dup(r), mr = p_dup(-r);
+    const f2x pr = pconst(PC_H), mr = pconst(PC_MH);  // +-1/sqrt(2)
     v[0] = cp_add(e[0], o[0]);
     v[4] = cp_sub(e[0], o[0]);
     // W8^1 o1 = r (o1.x - SIGN o1.y, o1.y + SIGN o1.x)
@@ -192,9 +216,6 @@ __host__ __device__ __forceinline__ void pdft8(cpair* v) {
 template <int SIGN>
 __host__ __device__ __forceinline__ void pdft16(cpair* v) {
     // 16 = 4 x 4: DFT4 over n2 (stride 4), twiddle W16^{n1 k1}, DFT4 over n1.
-    const float c1 = 0.92387953251128675613f;  // cos(pi/8)
-    const float s1 = 0.38268343236508977173f;  // sin(pi/8)
-    const float h = 0.70710678118654752440f;   // cos(pi/4)
     cpair a[4][4];
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) {
@@ -203,24 +224,28 @@ __host__ __device__ __forceinline__ void pdft16(cpair* v) {
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) a[n1][k1] = w[k1];
     }
-    // x exp(SIGN 2 pi i e / 16) for e = n1 k1 in {1, 2, 3, 4, 6, 9}
+    // x exp(SIGN 2 pi i e / 16) for e = n1 k1 in {1, 2, 3, 4, 6, 9}: (x.x c - x.y s, x.x s + x.y c)
+    // with (c, s) = (C1, S1), (H, H), (S1, C1), (0, 1), (-H, H), (-C1, -S1) and s negated for SIGN < 0
     auto tw = [&](cpair x, int e) -> cpair {
-        float c, s;
+        int c, s, ms;
         switch (e) {
-            case 1: c = c1; s = s1; break;
-            case 2: c = h; s = h; break;
-            case 3: c = s1; s = c1; break;
+            case 1: c = PC_C1; s = PC_S1; ms = PC_MS1; break;
+            case 2: c = PC_H; s = PC_H; ms = PC_MH; break;
+            case 3: c = PC_S1; s = PC_C1; ms = PC_MC1; break;
             case 4: {
                 // SIGN i x = (-SIGN x.y, SIGN x.x)
                 const f2x nx = p_sub(p_zero(), SIGN > 0 ? x.y : x.x);
                 return SIGN > 0 ? cpair{nx, x.x} : cpair{x.y, nx};
             }
-            case 6: c = -h; s = h; break;
-            default: c = -c1; s = -s1; break;  // e = 9
+            case 6: c = PC_MH; s = PC_H; ms = PC_MH; break;
+            default: c = PC_MC1; s = PC_MS1; ms = PC_S1; break;  // e = 9
         }
-        s = SIGN > 0 ? s : -s;
-        // (x.x c - x.y s, x.x s + x.y c)
-        return {p_fma(x.y, p_dup(-s), p_mul(x.x, p_dup(c))), p_fma(x.x, p_dup(s), p_mul(x.y, p_dup(c)))};
+        if (SIGN < 0) {
+            const int t = s;
+            s = ms;
+            ms = t;
+        }
+        return {p_fma(x.y, pconst(ms), p_mul(x.x, pconst(c))), p_fma(x.x, pconst(s), p_mul(x.y, pconst(c)))};
     };
 #pragma unroll
     for (int n1 = 1; n1 < 4; ++n1)

@@ -89,3 +89,10 @@ def test_traffic_figure_is_dropped_when_the_kernel_changes(bench, monkeypatch):
     assert bench.traffic_per_band(name) == 3.7e6
     monkeypatch.setitem(bench.TRAFFIC_PER_BAND, name, (3.7e6, "0" * 16))
     assert bench.traffic_per_band(name) is None
+
+
+def test_split_operand_products_and_split_pass(bench):
+    p = _problem(nb=256, nproj=256)
+    assert bench.kernel_work(p, "tcx_cn", 3, 256) == bench.kernel_work(p, "tc_zgemm_cn", 3, 256)
+    fl, by = bench.kernel_work(p, "split_planes", 2, 256)
+    assert fl == 0.0 and by == pytest.approx(16.0 * 256 * 62759)
