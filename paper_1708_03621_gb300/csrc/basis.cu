@@ -160,6 +160,8 @@ static jdft_status build_sphere(jdft_basis_s* b, int ik) {
     col_start.push_back(s.npw);
     s.i0min = mn[0];
     s.nrows = mx[0] - mn[0] + 1;
+    s.i1min = mn[1];
+    s.i1max = mx[1];
     // First column of each row r (i0 = i0min + r): columns are sorted by i0.
     std::vector<int> row_col_start(s.nrows + 1);
     for (int r = 0; r <= s.nrows; ++r)

@@ -11,6 +11,7 @@ namespace jdft {
 struct ChainGeom {
     int S0, S1, S2;
     int npw, ncols, nrows, i0min;
+    int i1min, i1max;          // range of i1 over the sphere
     const int* col_start;      // ncols + 1
     const int* col_slot01;     // ncols: (row << 16) | (i1 mod S1)
     const int* row_col_start;  // nrows + 1
@@ -26,6 +27,7 @@ inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
     ChainGeom g;
     g.S0 = b->S[0]; g.S1 = b->S[1]; g.S2 = b->S[2];
     g.npw = s.npw; g.ncols = s.ncols; g.nrows = s.nrows; g.i0min = s.i0min;
+    g.i1min = s.i1min; g.i1max = s.i1max;
     g.col_start = s.col_start; g.col_slot01 = s.col_slot01; g.row_col_start = s.row_col_start;
     g.row_i1lo = s.row_i1lo;
     g.pw_col = s.pw_col; g.pw_z = s.pw_z;

@@ -89,6 +89,7 @@ struct KSphere {
     int ncols = 0;          // number of distinct (i0, i1) columns
     int nrows = 0;          // i0 range covered by the columns: i0min .. i0min + nrows - 1
     int i0min = 0;
+    int i1min = 0, i1max = 0;   // range of i1 over the sphere
     // device arrays
     int* col_start = nullptr;   // ncols + 1: first sphere index of each column (prefix sums)
     int* col_slot01 = nullptr;  // ncols: packed (row r = i0 - i0min) << 16 | (i1 mod S1)

@@ -213,16 +213,35 @@ __host__ __device__ __forceinline__ void pdft8(cpair* v) {
     }
 }
 
-template <int SIGN>
+// PIN: the inputs v[4] .. v[11] are zero (a line whose nonzero values lie in
+// the central quarter of the box on either side of the origin); the first
+// layer's 4-point DFTs then have two inputs each.  POUT: only the outputs
+// v[0..3] and v[12..15] are wanted; the last layer computes only those and
+// leaves the others undefined.
+template <int SIGN, bool PIN = false, bool POUT = false>
 __host__ __device__ __forceinline__ void pdft16(cpair* v) {
     // 16 = 4 x 4: DFT4 over n2 (stride 4), twiddle W16^{n1 k1}, DFT4 over n1.
     cpair a[4][4];
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) {
-        cpair w[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
-        pdft4<SIGN>(w);
+        if constexpr (PIN) {
+            // out[k] = w0 + w3 (SIGN i)^{3k}: w0 + w3, w0 - SIGN i w3, w0 - w3, w0 + SIGN i w3
+            const cpair w0 = v[n1], w3 = v[n1 + 12];
+            a[n1][0] = cp_add(w0, w3);
+            a[n1][2] = cp_sub(w0, w3);
+            if constexpr (SIGN > 0) {
+                a[n1][1] = {p_add(w0.x, w3.y), p_sub(w0.y, w3.x)};
+                a[n1][3] = {p_sub(w0.x, w3.y), p_add(w0.y, w3.x)};
+            } else {
+                a[n1][1] = {p_sub(w0.x, w3.y), p_add(w0.y, w3.x)};
+                a[n1][3] = {p_add(w0.x, w3.y), p_sub(w0.y, w3.x)};
+            }
+        } else {
+            cpair w[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+            pdft4<SIGN>(w);
 #pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) a[n1][k1] = w[k1];
+            for (int k1 = 0; k1 < 4; ++k1) a[n1][k1] = w[k1];
+        }
     }
     // x exp(SIGN 2 pi i e / 16) for e = n1 k1 in {1, 2, 3, 4, 6, 9}: (x.x c - x.y s, x.x s + x.y c)
     // with (c, s) = (C1, S1), (H, H), (S1, C1), (0, 1), (-H, H), (-C1, -S1) and s negated for SIGN < 0
@@ -253,20 +272,29 @@ __host__ __device__ __forceinline__ void pdft16(cpair* v) {
         for (int k1 = 1; k1 < 4; ++k1) a[n1][k1] = tw(a[n1][k1], n1 * k1);
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        cpair w[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
-        pdft4<SIGN>(w);
+        if constexpr (POUT) {
+            // outputs k2 = 0 and 3 of the 4-point DFT over n1
+            const cpair y0 = cp_add(a[0][k1], a[2][k1]), y1 = cp_sub(a[0][k1], a[2][k1]);
+            const cpair y2 = cp_add(a[1][k1], a[3][k1]), d = cp_sub(a[1][k1], a[3][k1]);
+            v[k1] = cp_add(y0, y2);
+            v[k1 + 12] = SIGN > 0 ? cpair{p_add(y1.x, d.y), p_sub(y1.y, d.x)} : cpair{p_sub(y1.x, d.y), p_add(y1.y, d.x)};
+        } else {
+            cpair w[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+            pdft4<SIGN>(w);
 #pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = w[k2];
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = w[k2];
+        }
     }
 }
 
-template <int SIGN, int R>
+template <int SIGN, int R, bool PIN = false, bool POUT = false>
 __host__ __device__ __forceinline__ void pdft_r(cpair* v) {
+    static_assert(R == 16 || !(PIN || POUT), "pruned butterflies exist for radix 16 only");
     if constexpr (R == 2) pdft2<SIGN>(v);
     else if constexpr (R == 3) pdft3<SIGN>(v);
     else if constexpr (R == 4) pdft4<SIGN>(v);
     else if constexpr (R == 8) pdft8<SIGN>(v);
-    else if constexpr (R == 16) pdft16<SIGN>(v);
+    else if constexpr (R == 16) pdft16<SIGN, PIN, POUT>(v);
     else static_assert(R == 2 || R == 3 || R == 4 || R == 8 || R == 16, "radix not available for band pairs");
 }
 
@@ -286,7 +314,7 @@ __device__ __forceinline__ void pstage_twiddles(tw2* w, int b, const float4* __r
     }
 }
 
-template <int N, int TL, int E, int SIGN, int NS, int R>
+template <int N, int TL, int E, int SIGN, int NS, int R, bool PIN = false>
 __device__ __forceinline__ void pstage_compute(cpair* v, int t, const float4* __restrict__ W) {
     constexpr int NB = E / R;
 #pragma unroll
@@ -299,16 +327,16 @@ __device__ __forceinline__ void pstage_compute(cpair* v, int t, const float4* __
 #pragma unroll
             for (int r = 1; r < R; ++r) v[u * R + r] = cp_twiddle<SIGN>(v[u * R + r], w[r]);
         }
-        pdft_r<SIGN, R>(v + u * R);
+        pdft_r<SIGN, R, PIN, false>(v + u * R);
     }
 }
 
-template <int N, int TL, int E, int SIGN2, int NS, int R>
+template <int N, int TL, int E, int SIGN2, int NS, int R, bool POUT = false>
 __device__ __forceinline__ void pstage_adjoint(cpair* v, int t, const float4* __restrict__ W) {
     constexpr int NB = E / R;
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
-        pdft_r<SIGN2, R>(v + u * R);
+        pdft_r<SIGN2, R, false, POUT>(v + u * R);
         const int j = t + TL * u;
         const int k = j % NS;
         if (NS > 1 && k != 0) {
@@ -339,48 +367,59 @@ __device__ __forceinline__ void pexchange(cpair* v, float2* scr, Dst dst, Src sr
     for (int i = 0; i < E; ++i) v[i].y = *reinterpret_cast<const f2x*>(scr + padx(src(i)));
 }
 
-template <int N, int TL, int E, int SIGN, int NS, int R, int... Rest>
+// PRUNE: the first stage (NS = 1) takes the pruned radix-16 butterflies
+// (inputs outside the window are zero in run, outputs outside it unwanted in
+// the adjoint).
+template <int N, int TL, int E, int SIGN, int NS, bool PRUNE, int R, int... Rest>
 struct PStageRunner {
     static __device__ __forceinline__ void run(cpair* v, int t, float2* scr, const float4* __restrict__ W) {
-        pstage_compute<N, TL, E, SIGN, NS, R>(v, t, W);
+        pstage_compute<N, TL, E, SIGN, NS, R, PRUNE && NS == 1>(v, t, W);
         if constexpr (sizeof...(Rest) > 0) {
             constexpr int Rn = FirstRadix<Rest...>::value;
             pexchange<E>(
                 v, scr, [&](int i) { return stage_out_index<TL, NS, R>(t, i / R, i % R); },
                 [&](int i) { return t + TL * (i / Rn) + (i % Rn) * (N / Rn); });
-            PStageRunner<N, TL, E, SIGN, NS * R, Rest...>::run(v, t, scr, W);
+            PStageRunner<N, TL, E, SIGN, NS * R, false, Rest...>::run(v, t, scr, W);
         }
     }
 };
 
-template <int N, int TL, int E, int SIGN2, int NS, int R, int... Rest>
+template <int N, int TL, int E, int SIGN2, int NS, bool PRUNE, int R, int... Rest>
 struct PAdjRunner {
     static __device__ __forceinline__ void run(cpair* v, int t, float2* scr, const float4* __restrict__ W) {
         if constexpr (sizeof...(Rest) > 0) {
-            PAdjRunner<N, TL, E, SIGN2, NS * R, Rest...>::run(v, t, scr, W);
+            PAdjRunner<N, TL, E, SIGN2, NS * R, false, Rest...>::run(v, t, scr, W);
             constexpr int Rn = FirstRadix<Rest...>::value;
             pexchange<E>(
                 v, scr, [&](int i) { return t + TL * (i / Rn) + (i % Rn) * (N / Rn); },
                 [&](int i) { return stage_out_index<TL, NS, R>(t, i / R, i % R); });
         }
-        pstage_adjoint<N, TL, E, SIGN2, NS, R>(v, t, W);
+        pstage_adjoint<N, TL, E, SIGN2, NS, R, PRUNE && NS == 1>(v, t, W);
     }
 };
 
-template <int N, int E, int SIGN, class RadList>
+template <int N, int E, int SIGN, class RadList, bool WIN = false>
 struct LineFFTP;
 
 // Same lane layout and index maps as LineFFT<T, N, E, SIGN, Rad<R0, R...>>.
-template <int N, int E, int SIGN, int R0, int... R>
-struct LineFFTP<N, E, SIGN, Rad<R0, R...>> {
+// WIN: the line's nonzero inputs of run() (and the wanted outputs of
+// run_adjoint()) lie at positions -N/4 .. N/4 - 1 (mod N); with a first
+// radix of 16 and E = 16, lane t holds positions t + (N/16) e, so that is
+// e in 0..3 and 12..15 for every lane, and the first stage's butterflies are
+// pruned to them.
+template <int N, int E, int SIGN, int R0, int... R, bool WIN>
+struct LineFFTP<N, E, SIGN, Rad<R0, R...>, WIN> {
     static constexpr int TL = N / E;
     static_assert(RadInfo<R0, R...>::prod == N, "radices must multiply to N");
     static_assert(E % RadInfo<R0, R...>::lcm == 0, "E must be a multiple of every radix");
+    static_assert(!WIN || (R0 == 16 && E == 16), "the window pruning needs a first radix of 16 and E = 16");
+    // whether value e of a lane can lie in the window
+    static __host__ __device__ constexpr bool in_window(int e) { return !WIN || e < 4 || e >= 12; }
     static __device__ __forceinline__ void run(cpair* v, int t, float2* scr, const float4* __restrict__ W) {
-        PStageRunner<N, TL, E, SIGN, 1, R0, R...>::run(v, t, scr, W);
+        PStageRunner<N, TL, E, SIGN, 1, WIN, R0, R...>::run(v, t, scr, W);
     }
     static __device__ __forceinline__ void run_adjoint(cpair* v, int t, float2* scr, const float4* __restrict__ W) {
-        PAdjRunner<N, TL, E, -SIGN, 1, R0, R...>::run(v, t, scr, W);
+        PAdjRunner<N, TL, E, -SIGN, 1, WIN, R0, R...>::run(v, t, scr, W);
     }
     static __device__ __forceinline__ int in_index(int t, int e) {
         return first_in_index<N, TL, R0>(t, e / R0, e % R0);

@@ -79,11 +79,11 @@ __device__ __forceinline__ cpair ld_pair(const ulonglong2* p) {
 __device__ __forceinline__ void st_pair(ulonglong2* p, cpair v) { *p = make_ulonglong2(v.x.v, v.y.v); }
 
 // Rows pass, inverse: row r of both bands' disk values -> A[r][.].
-template <int N1, int E1, class R1, int NW>
+template <int N1, int E1, class R1, int NW, bool WIN>
 __device__ __forceinline__ void prows_inverse(const ChainGeom& g, const float2* __restrict__ p0,
                                               const float2* __restrict__ p1, ulonglong2* A, int lsA, float2* wscr,
                                               const float4* W1, int warp, int lane) {
-    using F = LineFFTP<N1, E1, +1, R1>;
+    using F = LineFFTP<N1, E1, +1, R1, WIN>;
     using LN = PLanes<N1, E1>;
     constexpr int LPW = LN::LPW;
     const int liw = LN::line(lane), t = LN::pos(lane);
@@ -101,7 +101,7 @@ __device__ __forceinline__ void prows_inverse(const ChainGeom& g, const float2* 
 #pragma unroll
         for (int e = 0; e < E1; ++e) {
             const int off = pwrap<N1>(F::in_index(t, e) - lo);
-            if (off < cnt) {
+            if (F::in_window(e) && off < cnt) {
                 const float2 a = p0[cs + off], b = p1[cs + off];
                 v[e] = {p_pack(a.x, b.x), p_pack(a.y, b.y)};
             } else {
@@ -116,12 +116,14 @@ __device__ __forceinline__ void prows_inverse(const ChainGeom& g, const float2* 
     }
 }
 
-// Rows pass, forward: A[r][.] -> both bands' disk values of row r.
-template <int N1, int E1, class R1, int NW>
+// Rows pass, forward: A[r][.] -> both bands' disk values of row r.  The
+// transform runs as the adjoint of the inverse flow graph, so that with WIN
+// its last stage is the pruned one.
+template <int N1, int E1, class R1, int NW, bool WIN>
 __device__ __forceinline__ void prows_forward(const ChainGeom& g, float2* __restrict__ p0, float2* __restrict__ p1,
                                               bool have1, const ulonglong2* A, int lsA, float2* wscr,
                                               const float4* W1, int warp, int lane) {
-    using F = LineFFTP<N1, E1, -1, R1>;
+    using F = LineFFTP<N1, E1, +1, R1, WIN>;
     using LN = PLanes<N1, E1>;
     constexpr int LPW = LN::LPW;
     const int liw = LN::line(lane), t = LN::pos(lane);
@@ -131,16 +133,16 @@ __device__ __forceinline__ void prows_forward(const ChainGeom& g, float2* __rest
         const bool act = r < g.nrows;
         cpair v[E1];
 #pragma unroll
-        for (int e = 0; e < E1; ++e) v[e] = act ? ld_pair(A + r * lsA + F::in_index(t, e)) : cp_zero();
-        F::run(v, t, scr, W1);
+        for (int e = 0; e < E1; ++e) v[e] = act ? ld_pair(A + r * lsA + F::out_index(t, e)) : cp_zero();
+        F::run_adjoint(v, t, scr, W1);
         if (act) {
             const int cs = g.row_col_start[r];
             const int cnt = g.row_col_start[r + 1] - cs;
             const int lo = g.row_i1lo[r];
 #pragma unroll
             for (int e = 0; e < E1; ++e) {
-                const int off = pwrap<N1>(F::out_index(t, e) - lo);
-                if (off < cnt) {
+                const int off = pwrap<N1>(F::in_index(t, e) - lo);
+                if (F::in_window(e) && off < cnt) {
                     float x0, x1, y0, y1;
                     p_unpack(v[e].x, x0, x1);
                     p_unpack(v[e].y, y0, y1);
@@ -170,13 +172,16 @@ struct PairPlane {
     }
 };
 
-// DENS = false: the plane pass alone (no density, no tensor memory).
-template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS>
+// DENS = false: the plane pass alone (no density, no tensor memory).  WIN:
+// the sphere lies in the central quarter of the box along axes 0 and 1
+// (LineFFTP's window), so the transforms prune their first-stage butterflies
+// and the loads and stores outside it are skipped.
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN>
 __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
     ChainGeom g, float2* __restrict__ colbuf, const float* __restrict__ Vp, int nb, const double* __restrict__ f,
     double w, double* __restrict__ n_r, const float2* __restrict__ tw0, const float2* __restrict__ tw1) {
     using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
-    using FI = LineFFTP<N0, E0, +1, R0>;
+    using FI = LineFFTP<N0, E0, +1, R0, WIN>;
     using LN = PLanes<N0, E0>;
     constexpr int LPW = LN::LPW, ROUNDS = PP::ROUNDS, lsA = PP::lsA;
     constexpr bool kAllCols = N1 % (NW * LPW) == 0;
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
         float2* plane0 = colbuf + colbuf_index(g, b0, j2, 0);
         // a missing second band reads the first band's values and is never written
         float2* plane1 = have1 ? colbuf + colbuf_index(g, b0 + 1, j2, 0) : plane0;
-        prows_inverse<N1, E1, R1, NW>(g, plane0, plane1, A, lsA, wscr, W1, warp, lane);
+        prows_inverse<N1, E1, R1, NW, WIN>(g, plane0, plane1, A, lsA, wscr, W1, warp, lane);
         __syncthreads();
         const f2x fb = DENS ? p_pack((float)f[b0], have1 ? (float)f[b0 + 1] : 0.f) : p_zero();
         // rolled: copies of the two column transforms would overflow the instruction cache
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
 #pragma unroll
             for (int e = 0; e < E0; ++e) {
                 const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
-                v[e] = (act && r < g.nrows) ? ld_pair(A + r * lsA + j1) : cp_zero();
+                v[e] = (FI::in_window(e) && act && r < g.nrows) ? ld_pair(A + r * lsA + j1) : cp_zero();
             }
             FI::run(v, t, scr, W0);
             if constexpr (DENS) {
@@ -274,13 +279,13 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
 #pragma unroll
                 for (int e = 0; e < E0; ++e) {
                     const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
-                    if (r < g.nrows) st_pair(A + r * lsA + j1, v[e]);
+                    if (FI::in_window(e) && r < g.nrows) st_pair(A + r * lsA + j1, v[e]);
                 }
             }
         }
         if constexpr (DENS) tc::tmem_wait_st();
         __syncthreads();
-        prows_forward<N1, E1, R1, NW>(g, plane0, plane1, have1, A, lsA, wscr, W1, warp, lane);
+        prows_forward<N1, E1, R1, NW, WIN>(g, plane0, plane1, have1, A, lsA, wscr, W1, warp, lane);
         __syncthreads();
     }
     if (DENS && cur >= 0) flush(cur);
@@ -288,6 +293,9 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
     __syncthreads();
     if (DENS && warp == 0) tc::tmem_dealloc(tslot, PP::TM_COLS);
 }
+
+template <class R> struct FirstRadix16 { static constexpr bool value = false; };
+template <int... R> struct FirstRadix16<Rad<16, R...>> { static constexpr bool value = true; };
 
 template <int N> struct PairCfg;
 template <> struct PairCfg<12> { static constexpr int E = 12; using R = Rad<4, 3>; };
@@ -301,7 +309,19 @@ static bool pair_disabled() {
     return e && e[0] == '0';
 }
 
-template <int N0, int N1, bool DENS>
+// Whether the sphere lies in LineFFTP's window along axes 0 and 1: signed
+// indices -S/4 .. S/4 - 1 (and the axis transforms are radix-16 first with
+// 16 values a lane).
+template <int N0, int N1>
+static bool pair_window(const ChainGeom& g) {
+    using C0 = PairCfg<N0>;
+    using C1 = PairCfg<N1>;
+    if (!(C0::E == 16 && C1::E == 16 && FirstRadix16<typename C0::R>::value && FirstRadix16<typename C1::R>::value))
+        return false;
+    return g.i0min >= -N0 / 4 && g.i0min + g.nrows - 1 <= N0 / 4 - 1 && g.i1min >= -N1 / 4 && g.i1max <= N1 / 4 - 1;
+}
+
+template <int N0, int N1, bool DENS, bool WIN>
 static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp, int nb, const double* f, double w,
                              double* n_r, const float2* tw_base, cudaStream_t st) {
     using C0 = PairCfg<N0>;
@@ -310,7 +330,8 @@ static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp
     const char* name = DENS ? "plane_apply_density_pair" : "plane_apply_pair";
     const size_t smem = PP::smem(g.nrows);
     if (smem > 227 * 1024) return JDFT_ERR_UNSUPPORTED;
-    auto kern = plane_apply_density_pair_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps, DENS>;
+    auto kern =
+        plane_apply_density_pair_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps, DENS, WIN>;
     cudaError_t e = set_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
     const int64_t items = (int64_t)g.S2 * ((nb + 1) / 2);
@@ -336,8 +357,10 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
                                             const double* f, double w, double* n_r, const float2* tw_base,
                                             cudaStream_t st) {
     if (pair_disabled()) return JDFT_ERR_UNSUPPORTED;
-    if (g.S0 == 128 && g.S1 == 128) return pair_impl<128, 128, true>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
-    if (g.S0 == 16 && g.S1 == 12) return pair_impl<16, 12, true>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
+    if (g.S0 == 128 && g.S1 == 128)
+        return pair_window<128, 128>(g) ? pair_impl<128, 128, true, true>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st)
+                                        : pair_impl<128, 128, true, false>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
+    if (g.S0 == 16 && g.S1 == 12) return pair_impl<16, 12, true, false>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
     return JDFT_ERR_UNSUPPORTED;
 }
 
@@ -345,9 +368,11 @@ jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const fl
                                     const float2* tw_base, cudaStream_t st) {
     if (pair_disabled()) return JDFT_ERR_UNSUPPORTED;
     if (g.S0 == 128 && g.S1 == 128)
-        return pair_impl<128, 128, false>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st);
+        return pair_window<128, 128>(g)
+                   ? pair_impl<128, 128, false, true>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st)
+                   : pair_impl<128, 128, false, false>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st);
     if (g.S0 == 16 && g.S1 == 12)
-        return pair_impl<16, 12, false>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st);
+        return pair_impl<16, 12, false, false>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st);
     return JDFT_ERR_UNSUPPORTED;
 }
 
