@@ -96,7 +96,8 @@ template <typename T> static jdft_status upload(T** dst, const std::vector<T>& s
 static void free_sphere(KSphere& s) {
     cudaFree(s.col_start); cudaFree(s.col_slot01); cudaFree(s.row_col_start); cudaFree(s.row_i1lo);
     cudaFree(s.pw_col); cudaFree(s.pw_z); cudaFree(s.kin); cudaFree(s.kvec); cudaFree(s.kin32);
-    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
+    cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.Psplit_t); cudaFree(s.D); cudaFree(s.Dcol);
+    cudaFree(s.Dval);
     s = KSphere();
 }
 
@@ -409,8 +410,9 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     KSphere& s = b->ks[ik];
     if (s.P) {
         JDFT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.D); cudaFree(s.Dcol); cudaFree(s.Dval);
-        s.P = s.P32 = s.Psplit = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
+        cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.Psplit_t); cudaFree(s.D); cudaFree(s.Dcol);
+        cudaFree(s.Dval);
+        s.P = s.P32 = s.Psplit = s.Psplit_t = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
     }
     s.nproj = nproj;
     if (nproj == 0) return JDFT_OK;
@@ -459,7 +461,9 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
     if (r != JDFT_OK) return r;
     // BF16 planes of the projectors for the split-operand products
     JDFT_CUDA_TRY(cudaMalloc(&s.Psplit, tcx_split_bytes(nproj, s.npw)));
-    return tcx_split((const float2*)s.P32, s.npw, nproj, s.npw, s.Psplit, st);
+    if ((r = tcx_split((const float2*)s.P32, s.npw, nproj, s.npw, s.Psplit, st)) != JDFT_OK) return r;
+    JDFT_CUDA_TRY(cudaMalloc(&s.Psplit_t, tcx_split_bytes(s.npw, nproj)));
+    return tcx_split_t((const float2*)s.P32, s.npw, s.npw, nproj, s.Psplit_t, st);
 }
 
 jdft_status jdft_gaussian_potential(jdft_basis_t b, int natoms, const double* atoms, double depth, double width,

@@ -107,6 +107,7 @@ struct KSphere {
     void* P = nullptr;          // complex128 npw x nproj column-major
     void* P32 = nullptr;        // complex64 copy
     void* Psplit = nullptr;     // BF16 planes of P32 for the BF16x3 products (Re hi, Re lo, Im hi, Im lo)
+    void* Psplit_t = nullptr;   // the same of P32's transpose (rows = plane waves), for P X
     double* D = nullptr;        // nproj x nproj
     // D as ELL rows: Dw entries per row (the widest row's nonzero count),
     // columns and values, padded with column 0 and value 0

@@ -187,7 +187,9 @@ size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw, jdft_pr
     const size_t a = ((size_t)nproj * nb * sizeof(double2) + 255) / 256 * 256;
     const size_t b = ((size_t)nproj * nb * elem + 255) / 256 * 256;
     const size_t c = split_c && tcx_eligible(prec, nproj, nb) ? (tcx_split_bytes(nb, npw) + 255) / 256 * 256 : 0;
-    return a + b + c;
+    // the split of (D P^dag C)'s transpose for P (D P^dag C) on split operands
+    const size_t d = tcx_eligible(prec, nproj, nb) ? (tcx_split_bytes(nb, nproj) + 255) / 256 * 256 : 0;
+    return a + b + c + d;
 }
 
 template <typename T>
@@ -205,7 +207,11 @@ jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void*
     c_t<T>* Bd = (c_t<T>*)((char*)work + abytes);
     JDFT_CUDA_TRY(cudaMemsetAsync(Bc, 0, (size_t)sp.nproj * nb * sizeof(double2), st));
     jdft_status s;
-    if (std::is_same<T, float>::value && (split_c || Csplit) && sp.Psplit && tcx_eligible(prec, sp.nproj, nb)) {
+    const bool split_ops = std::is_same<T, float>::value && (split_c || Csplit) && sp.Psplit &&
+                           tcx_eligible(prec, sp.nproj, nb);
+    const size_t cbytes = split_c && tcx_eligible(prec, sp.nproj, nb)
+                              ? (tcx_split_bytes(nb, sp.npw) + 255) / 256 * 256 : 0;
+    if (split_ops) {
         const void* Cs = Csplit;
         if (!Cs) {
             void* own = (char*)work + abytes + bbytes;
@@ -223,6 +229,12 @@ jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void*
                                                                                         sp.Dval, Bc, Bd);
     }
     if ((s = check_launch("dmul"))) return s;
+    if (split_ops && sp.Psplit_t) {
+        // HC += P (D P^dag C): P's transposed split (made with the projectors) and that of D P^dag C
+        void* Bt = (char*)work + abytes + bbytes + cbytes;
+        if ((s = tcx_split_t((const float2*)Bd, nb, nb, sp.nproj, Bt, st))) return s;
+        return tcx_nn(sp.npw, nb, sp.nproj, sp.Psplit_t, Bt, (float2*)HC, ldhc, true, st);
+    }
     return gemm_nn_acc<T>(prec, sp.npw, nb, sp.nproj, proj_ptr<T>(sp), sp.npw, Bd, nb, (c_t<T>*)HC, ldhc, st);
 }
 

@@ -34,6 +34,15 @@ size_t tcx_split_bytes(int rows, int K);
 bool tcx_eligible(jdft_prec prec, int M, int N);
 // Split rows of X (complex64, row stride ld) into planes (16-byte aligned, tcx_split_bytes).
 jdft_status tcx_split(const float2* X, int ld, int rows, int K, void* planes, cudaStream_t st);
+// The split block of the transpose: row r, value k taken from X[k * ld + r]
+// (X: K rows of `rows` values), for operands contiguous along M or N.
+jdft_status tcx_split_t(const float2* X, int ld, int rows, int K, void* planes, cudaStream_t st);
+// out[n * ldo + m] (+)= sum_k A[m][k] B[n][k] (no conjugate) from split blocks
+// of A (M rows of K) and B (N rows of K); K up to a few hundred (one block
+// covers all of it); accumulate = false overwrites.  out may alias neither
+// split block but may be the block A was split from.
+jdft_status tcx_nn(int M, int N, int K, const void* Aplanes, const void* Bplanes, float2* out, int ldo,
+                   bool accumulate, cudaStream_t st);
 // out[m * ldo + n] += alpha sum_k conj(A[m][k]) B[n][k] from the split blocks
 // of A (M rows) and B (N rows); FP64 atomics, so out must be zeroed first.
 jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,

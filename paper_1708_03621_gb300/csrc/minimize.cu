@@ -769,7 +769,9 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     const size_t tmpb = inplace ? 0 : r256((size_t)nb * ldc * sizeof(c_t<T>));
     // layout: chain region, planes of C, planes of H C; the copy of C that a
     // rotation out of place needs reuses the start once the rest is done
-    jdft_status s = ensure_workspace(b, std::max(chain + 2 * cs, tmpb));
+    // the rotation's transposed splits of C and W reuse the start once the rest is done
+    const size_t rot = split ? r256(tcx_split_bytes(npw, nb)) + r256(tcx_split_bytes(nb, nb)) : 0;
+    jdft_status s = ensure_workspace(b, std::max(std::max(chain + 2 * cs, tmpb), rot));
     if (s != JDFT_OK) return s;
     char* ws = (char*)b->work.ptr;
     void* Cs = ws + chain;
@@ -803,6 +805,15 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     }
     if (!ortho) return JDFT_OK;
     JDFT_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_join, 0));
+    if (split) {
+        // C <- C W from split operands: C's transpose (its planes take the
+        // chain region, free now) and W's; the product writes C directly
+        void* Ct = ws;
+        void* Wt = ws + r256(tcx_split_bytes(npw, nb));
+        if ((s = tcx_split_t((const float2*)C, ldc, npw, nb, Ct, st))) return s;
+        if ((s = tcx_split_t((const float2*)W, nb, nb, nb, Wt, st))) return s;
+        return tcx_nn(npw, nb, nb, Ct, Wt, (float2*)C, ldc, false, st);
+    }
     if (inplace) return gemm_nn_acc<T>(prec, npw, nb, nb, Cc, ldc, W, nb, (c_t<T>*)C, ldc, st, false);
     c_t<T>* tmp = (c_t<T>*)ws;
     JDFT_CUDA_TRY(cudaMemcpyAsync(tmp, C, (size_t)nb * ldc * sizeof(c_t<T>), cudaMemcpyDeviceToDevice, st));

@@ -527,6 +527,10 @@ __device__ __forceinline__ size_t tcx_offset(int r, int k, int p, int rp) {
 // as one 16-byte store per plane.  Consecutive threads take consecutive rows
 // of a row group, then the second K half, then the next row group, so a
 // warp's stores to each plane are 512 contiguous bytes.
+// TRANS: the split block's row r, value k is X[k * ld + r] (the split of the
+// transpose, for the operands of the M-contiguous products); otherwise
+// X[r * ld + k].  Consecutive threads then read consecutive r: coalesced too.
+template <bool TRANS>
 __global__ void split_planes_kernel(const float2* __restrict__ X, int ld, int rows, int K, int rows_pad, int nkc,
                                     __nv_bfloat16* __restrict__ out) {
     const int per_chunk = rows_pad * 2;  // 16-byte units per plane of one chunk
@@ -537,9 +541,15 @@ __global__ void split_planes_kernel(const float2* __restrict__ X, int ld, int ro
         const int r8 = u & 7, h = (u >> 3) & 1, g = u >> 4;
         const int r = g * 8 + r8, k0 = kc * TCX_KC + h * 8;
         float2 v[8];
-        const float2* src = X + (size_t)r * ld + k0;
+        if constexpr (TRANS) {
+            const float2* src = X + (size_t)k0 * ld + r;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = (r < rows && k0 + j < K) ? src[j] : make_float2(0.f, 0.f);
+            for (int j = 0; j < 8; ++j) v[j] = (r < rows && k0 + j < K) ? src[(size_t)j * ld] : make_float2(0.f, 0.f);
+        } else {
+            const float2* src = X + (size_t)r * ld + k0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (r < rows && k0 + j < K) ? src[j] : make_float2(0.f, 0.f);
+        }
         uint32_t w[4][4];  // plane, 32-bit word (two BF16 values)
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
@@ -724,6 +734,178 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     if (!ok && nit > 0 && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
 }
 
+// out[n * ldo + m] (+)= sum_k A[m][k] B[n][k] from split blocks of A (M rows,
+// K values: the split of the transpose of an M-contiguous operand) and B (N
+// rows).  No conjugate: Re = Ar.Br - Ai.Bi, Im = Ar.Bi + Ai.Br.  One block
+// covers a 128 x NT tile over all of K (K is a projector or band count, a few
+// hundred at most), so the output is written once, without atomics: thread
+// (warp w, lane l) owns output row m = m0 + 32 w + l and writes it for every
+// column n, so a warp's stores to one band are 32 consecutive values.  Same
+// ring, roles, waits and drain as tcx_cn_kernel.
+template <int NT, bool ACC>
+__global__ void __launch_bounds__(TCX_THREADS, 1)
+    tcx_nn_kernel(const char* __restrict__ As, const char* __restrict__ Bs, int M, int N, int nkc,
+                  float2* __restrict__ out, int ldo) {
+    const int rpA = (M + TCX_M - 1) / TCX_M * TCX_M, rpB = (N + TCX_M - 1) / TCX_M * TCX_M;
+    using L = TcxLayout<NT>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+    uint64_t* empty = full + TCX_STAGES;
+    uint64_t* accbar = empty + TCX_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(accbar + 1);
+    volatile int* flags = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TCX_M, n0 = blockIdx.y * NT;
+    const uint32_t bbytes = (uint32_t)min(NT, rpB - n0) * TCX_KC * 2;
+    const int nit = nkc;
+    if (tid == 0) {
+        for (int s = 0; s < TCX_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accbar, 1);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 2) tc::tmem_alloc(tslot, L::NCOLS);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const unsigned long long wait_ns = g_tc_wait_ns;
+    if (tid == 0) {
+        int it = 0;
+        for (; it < nit; ++it) {
+            const int s = it % TCX_STAGES;
+            const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+            if (!tc::mbar_wait_ns(&empty[s], par ^ 1u, wait_ns)) {
+                flags[0] = 1;
+                break;
+            }
+            unsigned char* st = smem + s * L::STAGE;
+            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(4 * L::A_PL) + 4 * bbytes);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                bulk_load(st + p * L::A_PL, As + ((size_t)(it * 4 + p) * rpA + m0) * (TCX_KC * 2), L::A_PL, &full[s]);
+                bulk_load(st + L::A_BYTES + p * L::B_PL, Bs + ((size_t)(it * 4 + p) * rpB + n0) * (TCX_KC * 2), bbytes,
+                          &full[s]);
+            }
+        }
+        flags[1] = it;
+    } else if (tid == 32) {
+        constexpr uint32_t idesc = tc::instr_desc(1u, TCX_M, NT);
+        constexpr uint32_t idesc_neg = idesc | (1u << 13);  // negate A
+        int it = 0;
+        for (; it < nit; ++it) {
+            const int s = it % TCX_STAGES;
+            const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+            if (!tc::mbar_wait_ns(&full[s], par, wait_ns)) {
+                flags[0] = 1;
+                break;
+            }
+            tc::tc_fence_after_sync();
+            const uint32_t base = tc::smem_addr(smem + s * L::STAGE);
+            uint64_t a[4], b[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                a[p] = tc::smem_desc(base + p * L::A_PL, 128, 256);
+                b[p] = tc::smem_desc(base + L::A_BYTES + p * L::B_PL, 128, 256);
+            }
+            const uint32_t acc = it > 0 ? 1u : 0u;
+            const uint32_t re = tmem, im = tmem + NT;
+            // planes: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo
+            tc::mma_bf16(re, a[0], b[0], idesc, acc);
+            tc::mma_bf16(re, a[0], b[1], idesc, 1u);
+            tc::mma_bf16(re, a[1], b[0], idesc, 1u);
+            tc::mma_bf16(re, a[2], b[2], idesc_neg, 1u);
+            tc::mma_bf16(re, a[2], b[3], idesc_neg, 1u);
+            tc::mma_bf16(re, a[3], b[2], idesc_neg, 1u);
+            tc::mma_bf16(im, a[0], b[2], idesc, acc);
+            tc::mma_bf16(im, a[0], b[3], idesc, 1u);
+            tc::mma_bf16(im, a[1], b[2], idesc, 1u);
+            tc::mma_bf16(im, a[2], b[0], idesc, 1u);
+            tc::mma_bf16(im, a[2], b[1], idesc, 1u);
+            tc::mma_bf16(im, a[3], b[0], idesc, 1u);
+            tc::mma_commit(&empty[s]);
+        }
+        flags[2] = it;
+        if (it == nit && nit > 0) tc::mma_commit(accbar);
+    }
+    __syncthreads();
+    const int loaded = flags[1], committed = flags[2];
+    int ok = flags[0] == 0 && nit > 0;
+    if (ok) {
+        const int w = tc::mbar_wait_ns(accbar, 0u, wait_ns) ? 1 : 0;
+        ok = __syncthreads_and(w);
+    }
+    if (!ok && nit > 0) {
+        if (tid == 0) {
+            for (int it = committed; it < loaded; ++it)
+                tc::mbar_wait_ns(&full[it % TCX_STAGES], (uint32_t)((it / TCX_STAGES) & 1), TC_DRAIN_NS);
+            if (committed > 0)
+                tc::mbar_wait_ns(&empty[(committed - 1) % TCX_STAGES], (uint32_t)(((committed - 1) / TCX_STAGES) & 1),
+                                 TC_DRAIN_NS);
+            if (committed == nit) tc::mbar_wait_ns(accbar, 0u, TC_DRAIN_NS);
+        }
+        __syncthreads();
+    }
+    tc::tc_fence_after_sync();
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int col = 0; col < NT && n0 + col < N; col += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(lane_base + col, re);
+            tc::tmem_ld16(lane_base + NT + col, im);
+            if (m < M) {
+                float2 v[16];
+                // all old values first: one latency for the slice, not one per column
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = (ACC && n0 + col + j < N) ? out[(size_t)(n0 + col + j) * ldo + m] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + col + j < N) out[(size_t)(n0 + col + j) * ldo + m] = make_float2(v[j].x + re[j], v[j].y + im[j]);
+            }
+        }
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 2) tc::tmem_dealloc(tmem, L::NCOLS);
+    if (!ok && nit > 0 && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
+}
+
+template <int NT, bool ACC>
+static jdft_status launch_tcx_nn(int M, int N, int nkc, const void* Aplanes, const void* Bplanes, float2* out,
+                                 int ldo, cudaStream_t st) {
+    auto kern = tcx_nn_kernel<NT, ACC>;
+    cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<NT>::SMEM);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_nn: ") + cudaGetErrorString(e));
+    dim3 grid((M + TCX_M - 1) / TCX_M, (N + NT - 1) / NT);
+    {
+        Trace tr_("tcx_nn", st);
+        kern<<<grid, TCX_THREADS, TcxLayout<NT>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
+                                                              out, ldo);
+    }
+    return check_launch("tcx_nn");
+}
+
+jdft_status tcx_nn(int M, int N, int K, const void* Aplanes, const void* Bplanes, float2* out, int ldo,
+                   bool accumulate, cudaStream_t st) {
+    if (M == 0 || N == 0) return JDFT_OK;
+    const int nkc = tcx_chunks(K);
+    if (N > 128)
+        return accumulate ? launch_tcx_nn<256, true>(M, N, nkc, Aplanes, Bplanes, out, ldo, st)
+                          : launch_tcx_nn<256, false>(M, N, nkc, Aplanes, Bplanes, out, ldo, st);
+    return accumulate ? launch_tcx_nn<128, true>(M, N, nkc, Aplanes, Bplanes, out, ldo, st)
+                      : launch_tcx_nn<128, false>(M, N, nkc, Aplanes, Bplanes, out, ldo, st);
+}
+
 size_t tcx_split_bytes(int rows, int K) { return (size_t)tcx_rows_pad(rows) * tcx_chunks(K) * 4 * TCX_KC * 2; }
 
 bool tcx_eligible(jdft_prec prec, int M, int N) { return prec == JDFT_BF16X3 && M > 32 && N > 32; }
@@ -735,7 +917,19 @@ jdft_status tcx_split(const float2* X, int ld, int rows, int K, void* planes, cu
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     {
         Trace tr_("split_planes", st);
-        split_planes_kernel<<<grid, 256, 0, st>>>(X, ld, rows, K, rp, nkc, (__nv_bfloat16*)planes);
+        split_planes_kernel<false><<<grid, 256, 0, st>>>(X, ld, rows, K, rp, nkc, (__nv_bfloat16*)planes);
+    }
+    return check_launch("split_planes");
+}
+
+jdft_status tcx_split_t(const float2* X, int ld, int rows, int K, void* planes, cudaStream_t st) {
+    if (rows == 0 || K == 0) return JDFT_OK;
+    const int nkc = tcx_chunks(K), rp = tcx_rows_pad(rows);
+    const int64_t total = (int64_t)rp * 2 * nkc;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    {
+        Trace tr_("split_planes", st);
+        split_planes_kernel<true><<<grid, 256, 0, st>>>(X, ld, rows, K, rp, nkc, (__nv_bfloat16*)planes);
     }
     return check_launch("split_planes");
 }
