@@ -391,6 +391,12 @@ jdft_status jdft_batch_create(int n, const jdft_apply_item* items, jdft_batch_t*
 /* Replay every application of the batch on `stream` with one graph launch. */
 jdft_status jdft_batch_launch(jdft_batch_t batch, void* stream);
 jdft_status jdft_batch_destroy(jdft_batch_t batch);
+/* 1 if the batch runs its FFT chain k-batched: all items are k-points of one
+ * basis with FP32 blocks on a box the band-pair kernels serve (128 x 128
+ * planes), so each chain stage is one launch over all items (each item with
+ * its own sphere maps and a column buffer the batch owns); else 0 (one
+ * jdft_apply_H per item in the graph).  The paper has no counterpart. */
+int jdft_batch_is_kbatched(jdft_batch_t batch);
 
 /* ---- the Hamiltonian without device allocation --------------------------- */
 

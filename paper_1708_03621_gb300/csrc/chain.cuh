@@ -5,6 +5,8 @@
 #include "common.cuh"
 #include "fft.cuh"
 
+#include <vector>
+
 namespace jdft {
 
 // Everything a chain kernel needs to know about one sphere on one box.
@@ -82,6 +84,33 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
 // The plane pass alone, two bands at a time (same contract as launch_plane_apply).
 jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                     const float2* tw_base, cudaStream_t st);
+// One k-point (or cell on the same box) of a k-batched chain: its sphere
+// maps, blocks, column buffer and first plane-pass item (kbatch.cu).
+struct KJob {
+    ChainGeom g;
+    const float2* C;
+    int ldc;
+    float2* HC;
+    int ldhc;
+    float2* colbuf;    // nb x S2 x ncols
+    const float* kin;  // (1/2)|k+G|^2, FP32
+    int nb;
+    int64_t item0;     // first (plane, band pair) item of this job in the batch
+};
+// The band-pair plane pass (no density) over all jobs in one launch, for the
+// shapes the band-pair kernels are compiled for (JDFT_ERR_UNSUPPORTED
+// otherwise).  gs: the jobs' geometries on the host (the launch checks the
+// window on all of them); jobs: the same jobs on the device.
+bool plane_pair_batch_supported(const ChainGeom& g);
+jdft_status launch_plane_apply_pair_batch(const std::vector<ChainGeom>& gs, const KJob* jobs, int64_t items,
+                                          const float* Vp, const float2* tw_base, cudaStream_t st);
+// The z passes over all jobs (blockIdx.z = job), for the lengths the register
+// line FFTs are compiled for (JDFT_ERR_UNSUPPORTED otherwise).  max_ncols,
+// max_nb: the largest column and band counts over the jobs.
+jdft_status launch_zpass_inverse_batch(const ChainGeom& g, const KJob* jobs, int njobs, int max_ncols, int max_nb,
+                                       const float2* tw2, cudaStream_t st);
+jdft_status launch_zpass_forward_batch(const ChainGeom& g, const KJob* jobs, int njobs, int max_ncols, int max_nb,
+                                       float omega, float scale, const float2* tw2, cudaStream_t st);
 // Workspace bytes of apply_H_density_with_split, and H C plus the density
 // with an optional caller-made BF16 split of C for the projection (chain.cu).
 size_t apply_H_density_workspace(const jdft_basis_s* b, int ik, int nb, jdft_prec prec, bool split_c);

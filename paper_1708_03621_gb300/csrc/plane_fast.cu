@@ -525,6 +525,92 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainG
     }
 }
 
+// The z passes of a k-batched chain: blockIdx.z selects the job (k-point),
+// blockIdx.y the band, blockIdx.x the block of columns, as in the one-job
+// kernels; blocks beyond a job's columns or bands return at once.
+template <int N2, int E2, class R2>
+__global__ void __launch_bounds__(kFastThreads) zpass_inverse_batch_kernel(const KJob* __restrict__ jobs,
+                                                                           const float2* __restrict__ tw2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using F = LineFFT<float, N2, E2, +1, R2>;
+    using LN = Lanes<N2, E2>;
+    constexpr int LPW = LN::LPW;
+    const KJob& J = jobs[blockIdx.z];
+    const ChainGeom& g = J.g;
+    const int b = blockIdx.y;
+    if (b >= J.nb || (int)blockIdx.x * kFastWarps * LPW >= g.ncols) return;
+    float2* W = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    float2* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<float, N2>::value;
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
+    __syncthreads();
+    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const bool act = c < g.ncols;
+    int q0 = 0, cnt = 0, z0 = 0;
+    if (act) {
+        q0 = g.col_start[c];
+        cnt = g.col_start[c + 1] - q0;
+        z0 = g.pw_z[q0];
+    }
+    const float2* Cb = J.C + (size_t)b * J.ldc + q0;
+    float2 v[E2];
+#pragma unroll
+    for (int e = 0; e < E2; ++e) {
+        const int off = wrapn<N2>(F::in_index(t, e) - z0);
+        v[e] = off < cnt ? Cb[off] : make_float2(0.f, 0.f);
+    }
+    F::run(v, t, scr, W);
+    if (act) {
+#pragma unroll
+        for (int e = 0; e < E2; ++e) J.colbuf[colbuf_index(g, b, F::out_index(t, e), c)] = v[e];
+    }
+}
+
+// HC = omega (kin C + scale y) for every job.
+template <int N2, int E2, class R2>
+__global__ void __launch_bounds__(kFastThreads) zpass_forward_batch_kernel(const KJob* __restrict__ jobs, float omega,
+                                                                           float scale,
+                                                                           const float2* __restrict__ tw2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using F = LineFFT<float, N2, E2, -1, R2>;
+    using LN = Lanes<N2, E2>;
+    constexpr int LPW = LN::LPW;
+    const KJob& J = jobs[blockIdx.z];
+    const ChainGeom& g = J.g;
+    const int b = blockIdx.y;
+    if (b >= J.nb || (int)blockIdx.x * kFastWarps * LPW >= g.ncols) return;
+    float2* W = reinterpret_cast<float2*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    float2* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<float, N2>::value;
+    for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
+    __syncthreads();
+    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const bool act = c < g.ncols;
+    float2 v[E2];
+#pragma unroll
+    for (int e = 0; e < E2; ++e)
+        v[e] = act ? J.colbuf[colbuf_index(g, b, F::in_index(t, e), c)] : make_float2(0.f, 0.f);
+    F::run(v, t, scr, W);
+    if (act) {
+        const int q0 = g.col_start[c];
+        const int cnt = g.col_start[c + 1] - q0;
+        const int z0 = g.pw_z[q0];
+#pragma unroll
+        for (int e = 0; e < E2; ++e) {
+            const int off = wrapn<N2>(F::out_index(t, e) - z0);
+            if (off < cnt) {
+                const int q = q0 + off;
+                const float2 cq = J.C[(size_t)b * J.ldc + q];
+                const float kq = J.kin[q];
+                J.HC[(size_t)b * J.ldhc + q] =
+                    make_float2(omega * (kq * cq.x + scale * v[e].x), omega * (kq * cq.y + scale * v[e].y));
+            }
+        }
+    }
+}
+
 // Line shapes per compiled length: E values per lane and the radix list.
 template <int N> struct FastCfg;
 template <> struct FastCfg<12> { static constexpr int E = 12; using R = Rad<4, 3>; };
@@ -752,5 +838,45 @@ template jdft_status launch_plane_apply_fast<double>(const ChainGeom&, double2*,
                                                      cudaStream_t);
 template jdft_status launch_plane_apply_fast<float>(const ChainGeom&, float2*, const float*, int, const float2*,
                                                     cudaStream_t);
+
+jdft_status launch_zpass_inverse_batch(const ChainGeom& g, const KJob* jobs, int njobs, int max_ncols, int max_nb,
+                                       const float2* tw2, cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a)                                                                                             \
+    if (g.S2 == a) {                                                                                             \
+        using C2 = FastCfg<a>;                                                                                   \
+        auto kern = zpass_inverse_batch_kernel<a, C2::E, typename C2::R>;                                        \
+        const size_t smem = zpass_fast_smem<float, a>();                                                         \
+        cudaError_t e = set_smem_attr((const void*)kern, smem);                                                  \
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_inverse_batch: ") + cudaGetErrorString(e)); \
+        constexpr int CPB = kFastWarps * (32 / (a / C2::E));                                                     \
+        Trace tr_("zpass_inverse_batch", st);                                                                    \
+        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kFastThreads, smem, st>>>(jobs, tw2);           \
+        return check_launch("zpass_inverse_batch");                                                              \
+    }
+    JDFT_FAST_LENGTHS(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+jdft_status launch_zpass_forward_batch(const ChainGeom& g, const KJob* jobs, int njobs, int max_ncols, int max_nb,
+                                       float omega, float scale, const float2* tw2, cudaStream_t st) {
+    if (fast_disabled()) return JDFT_ERR_UNSUPPORTED;
+#define JDFT_CASE(a)                                                                                             \
+    if (g.S2 == a) {                                                                                             \
+        using C2 = FastCfg<a>;                                                                                   \
+        auto kern = zpass_forward_batch_kernel<a, C2::E, typename C2::R>;                                        \
+        const size_t smem = zpass_fast_smem<float, a>();                                                         \
+        cudaError_t e = set_smem_attr((const void*)kern, smem);                                                  \
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_forward_batch: ") + cudaGetErrorString(e)); \
+        constexpr int CPB = kFastWarps * (32 / (a / C2::E));                                                     \
+        Trace tr_("zpass_forward_batch", st);                                                                    \
+        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kFastThreads, smem, st>>>(jobs, omega, scale, tw2); \
+        return check_launch("zpass_forward_batch");                                                              \
+    }
+    JDFT_FAST_LENGTHS(JDFT_CASE)
+#undef JDFT_CASE
+    return JDFT_ERR_UNSUPPORTED;
+}
 
 }  // namespace jdft

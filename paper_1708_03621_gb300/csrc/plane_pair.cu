@@ -19,6 +19,7 @@
 // Listing 1 on temporaries, and the density of ElecVars, Sec. 2.1.)
 #include <algorithm>
 #include <cstdlib>
+#include <vector>
 
 #include "chain.cuh"
 #include "fft_pair.cuh"
@@ -172,6 +173,74 @@ struct PairPlane {
     }
 };
 
+// One (z-plane j2, band pair b0, b0 + 1) item of the plane pass: rows
+// inverse, columns (inverse, density sums, x V, forward), rows forward, with a
+// block barrier after each phase.  g: the item's sphere maps; colbuf: its
+// column buffer of nb bands.
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN>
+__device__ __forceinline__ void pair_item(const ChainGeom& g, float2* __restrict__ colbuf, int nb,
+                                          const double* __restrict__ f, const float* __restrict__ Vp, int j2, int b0,
+                                          const float4* W0, const float4* W1, float2* wscr, float2* scr,
+                                          ulonglong2* A, uint32_t tb, int warp, int lane) {
+    using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
+    using FI = LineFFTP<N0, E0, +1, R0, WIN>;
+    using LN = PLanes<N0, E0>;
+    constexpr int LPW = LN::LPW, ROUNDS = PP::ROUNDS, lsA = PP::lsA;
+    constexpr bool kAllCols = N1 % (NW * LPW) == 0;
+    const int liw = LN::line(lane), t = LN::pos(lane);
+    const bool have1 = b0 + 1 < nb;
+    float2* plane0 = colbuf + colbuf_index(g, b0, j2, 0);
+    // a missing second band reads the first band's values and is never written
+    float2* plane1 = have1 ? colbuf + colbuf_index(g, b0 + 1, j2, 0) : plane0;
+    prows_inverse<N1, E1, R1, NW, WIN>(g, plane0, plane1, A, lsA, wscr, W1, warp, lane);
+    __syncthreads();
+    const f2x fb = DENS ? p_pack((float)f[b0], have1 ? (float)f[b0 + 1] : 0.f) : p_zero();
+    // rolled: copies of the two column transforms would overflow the instruction cache
+#pragma unroll 1
+    for (int k = 0; k < ROUNDS; ++k) {
+        const int j1 = warp * LPW + liw + k * NW * LPW;
+        const bool act = kAllCols || j1 < N1;
+        // this round's sums are fetched while the column transform runs
+        uint32_t sr[16];
+        if constexpr (DENS) tc::tmem_ld16_issue(tb + 16 * k, sr);
+        cpair v[E0];
+#pragma unroll
+        for (int e = 0; e < E0; ++e) {
+            const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
+            v[e] = (FI::in_window(e) && act && r < g.nrows) ? ld_pair(A + r * lsA + j1) : cp_zero();
+        }
+        FI::run(v, t, scr, W0);
+        if constexpr (DENS) {
+            tc::tmem_wait_ld16(sr);
+            float acc[16];
+#pragma unroll
+            for (int e = 0; e < E0; ++e) {
+                // (f_0 |psi_0|^2, f_1 |psi_1|^2), folded into one sum
+                const f2x d = p_mul(p_fma(v[e].y, v[e].y, p_mul(v[e].x, v[e].x)), fb);
+                float d0, d1;
+                p_unpack(d, d0, d1);
+                acc[e] = __uint_as_float(sr[e]) + d0 + d1;
+            }
+            tc::tmem_st16(tb + 16 * k, acc);
+        }
+        const float* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
+#pragma unroll
+        for (int e = 0; e < E0; ++e) v[e] = act ? cp_scale(v[e], p_dup(Vq[FI::out_index(t, e)])) : cp_zero();
+        FI::run_adjoint(v, t, scr, W0);
+        if (act) {
+#pragma unroll
+            for (int e = 0; e < E0; ++e) {
+                const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
+                if (FI::in_window(e) && r < g.nrows) st_pair(A + r * lsA + j1, v[e]);
+            }
+        }
+    }
+    if constexpr (DENS) tc::tmem_wait_st();
+    __syncthreads();
+    prows_forward<N1, E1, R1, NW, WIN>(g, plane0, plane1, have1, A, lsA, wscr, W1, warp, lane);
+    __syncthreads();
+}
+
 // DENS = false: the plane pass alone (no density, no tensor memory).  WIN:
 // the sphere lies in the central quarter of the box along axes 0 and 1
 // (LineFFTP's window), so the transforms prune their first-stage butterflies
@@ -183,8 +252,7 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
     using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
     using FI = LineFFTP<N0, E0, +1, R0, WIN>;
     using LN = PLanes<N0, E0>;
-    constexpr int LPW = LN::LPW, ROUNDS = PP::ROUNDS, lsA = PP::lsA;
-    constexpr bool kAllCols = N1 % (NW * LPW) == 0;
+    constexpr int LPW = LN::LPW, ROUNDS = PP::ROUNDS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t tslot;
     float4* W0 = reinterpret_cast<float4*>(smem_raw);
@@ -230,68 +298,68 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
     int cur = -1;
     for (int64_t it = it0; it < it1; ++it) {
         const int j2 = (int)(it / np), p = (int)(it - (int64_t)j2 * np);
-        const int b0 = 2 * p;
-        const bool have1 = b0 + 1 < nb;
         if (DENS && j2 != cur) {
             if (cur >= 0) flush(cur);
             zero();
             cur = j2;
         }
-        float2* plane0 = colbuf + colbuf_index(g, b0, j2, 0);
-        // a missing second band reads the first band's values and is never written
-        float2* plane1 = have1 ? colbuf + colbuf_index(g, b0 + 1, j2, 0) : plane0;
-        prows_inverse<N1, E1, R1, NW, WIN>(g, plane0, plane1, A, lsA, wscr, W1, warp, lane);
-        __syncthreads();
-        const f2x fb = DENS ? p_pack((float)f[b0], have1 ? (float)f[b0 + 1] : 0.f) : p_zero();
-        // rolled: copies of the two column transforms would overflow the instruction cache
-#pragma unroll 1
-        for (int k = 0; k < ROUNDS; ++k) {
-            const int j1 = warp * LPW + liw + k * NW * LPW;
-            const bool act = kAllCols || j1 < N1;
-            // this round's sums are fetched while the column transform runs
-            uint32_t sr[16];
-            if constexpr (DENS) tc::tmem_ld16_issue(tb + 16 * k, sr);
-            cpair v[E0];
-#pragma unroll
-            for (int e = 0; e < E0; ++e) {
-                const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
-                v[e] = (FI::in_window(e) && act && r < g.nrows) ? ld_pair(A + r * lsA + j1) : cp_zero();
-            }
-            FI::run(v, t, scr, W0);
-            if constexpr (DENS) {
-                tc::tmem_wait_ld16(sr);
-                float acc[16];
-#pragma unroll
-                for (int e = 0; e < E0; ++e) {
-                    // (f_0 |psi_0|^2, f_1 |psi_1|^2), folded into one sum
-                    const f2x d = p_mul(p_fma(v[e].y, v[e].y, p_mul(v[e].x, v[e].x)), fb);
-                    float d0, d1;
-                    p_unpack(d, d0, d1);
-                    acc[e] = __uint_as_float(sr[e]) + d0 + d1;
-                }
-                tc::tmem_st16(tb + 16 * k, acc);
-            }
-            const float* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
-#pragma unroll
-            for (int e = 0; e < E0; ++e) v[e] = act ? cp_scale(v[e], p_dup(Vq[FI::out_index(t, e)])) : cp_zero();
-            FI::run_adjoint(v, t, scr, W0);
-            if (act) {
-#pragma unroll
-                for (int e = 0; e < E0; ++e) {
-                    const int r = pwrap<N0>(FI::in_index(t, e) - g.i0min);
-                    if (FI::in_window(e) && r < g.nrows) st_pair(A + r * lsA + j1, v[e]);
-                }
-            }
-        }
-        if constexpr (DENS) tc::tmem_wait_st();
-        __syncthreads();
-        prows_forward<N1, E1, R1, NW, WIN>(g, plane0, plane1, have1, A, lsA, wscr, W1, warp, lane);
-        __syncthreads();
+        pair_item<N0, E0, R0, N1, E1, R1, NW, DENS, WIN>(g, colbuf, nb, f, Vp, j2, 2 * p, W0, W1, wscr, scr, A, tb,
+                                                          warp, lane);
     }
     if (DENS && cur >= 0) flush(cur);
     tc::tc_fence_before_sync();
     __syncthreads();
     if (DENS && warp == 0) tc::tmem_dealloc(tslot, PP::TM_COLS);
+}
+
+// The plane pass (no density) over the items of several k-points (or cells
+// on the same box) in one persistent launch: the batch's item list is the
+// concatenation of each job's (plane, band pair) items, jobs[k].item0 its
+// first item.  A block takes a contiguous range of the list and copies the
+// current job's description to shared memory whenever its range crosses
+// into the next job.
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool WIN>
+__global__ void __launch_bounds__(32 * NW, 1) plane_apply_pair_batch_kernel(const KJob* __restrict__ jobs, int njobs,
+                                                                            int64_t items, const float* __restrict__ Vp,
+                                                                            const float2* __restrict__ tw0,
+                                                                            const float2* __restrict__ tw1) {
+    using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
+    using LN = PLanes<N0, E0>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KJob sj;
+    __shared__ int sk;
+    float4* W0 = reinterpret_cast<float4*>(smem_raw);
+    float4* W1 = W0 + N0;
+    float2* scr_all = reinterpret_cast<float2*>(W1 + N1);
+    ulonglong2* A = reinterpret_cast<ulonglong2*>(scr_all + NW * PP::SCR);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int liw = LN::line(lane);
+    float2* wscr = scr_all + warp * PP::SCR;
+    float2* scr = wscr + liw * PScratch<N0>::value;
+    for (int i = threadIdx.x; i < N0; i += blockDim.x) W0[i] = make_float4(tw0[i].x, tw0[i].x, tw0[i].y, tw0[i].y);
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) W1[i] = make_float4(tw1[i].x, tw1[i].x, tw1[i].y, tw1[i].y);
+    if (threadIdx.x == 0) sk = -1;
+    __syncthreads();
+    const int64_t it0 = items * blockIdx.x / gridDim.x, it1 = items * (blockIdx.x + 1) / gridDim.x;
+    int64_t next = -1;  // first item of the job after the current one (-1: no job loaded yet)
+    for (int64_t it = it0; it < it1; ++it) {
+        if (next < 0 || it >= next) {
+            // every thread is past the previous item's last barrier
+            if (threadIdx.x == 0) {
+                int k = sk < 0 ? 0 : sk;
+                while (k + 1 < njobs && jobs[k + 1].item0 <= it) ++k;
+                sk = k;
+                sj = jobs[k];
+            }
+            __syncthreads();
+            next = sk + 1 < njobs ? jobs[sk + 1].item0 : items;
+        }
+        const int64_t local = it - sj.item0;
+        const int np = (sj.nb + 1) / 2;
+        const int j2 = (int)(local / np), p = (int)(local - (int64_t)j2 * np);
+        pair_item<N0, E0, R0, N1, E1, R1, NW, false, WIN>(sj.g, sj.colbuf, sj.nb, nullptr, Vp, j2, 2 * p, W0, W1,
+                                                           wscr, scr, A, 0u, warp, lane);
+    }
 }
 
 template <class R> struct FirstRadix16 { static constexpr bool value = false; };
@@ -374,6 +442,52 @@ jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const fl
     if (g.S0 == 16 && g.S1 == 12)
         return pair_impl<16, 12, false, false>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st);
     return JDFT_ERR_UNSUPPORTED;
+}
+
+template <int N0, int N1, bool WIN>
+static jdft_status pair_batch_impl(const ChainGeom& g, const KJob* jobs, int njobs, int64_t items, int nrows_max,
+                                   const float* Vp, const float2* tw_base, cudaStream_t st) {
+    using C0 = PairCfg<N0>;
+    using C1 = PairCfg<N1>;
+    using PP = PairPlane<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps>;
+    const size_t smem = PP::smem(nrows_max);
+    if (smem > 227 * 1024) return JDFT_ERR_UNSUPPORTED;
+    auto kern = plane_apply_pair_batch_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps, WIN>;
+    cudaError_t e = set_smem_attr((const void*)kern, smem);
+    if (e != cudaSuccess)
+        return set_error(JDFT_ERR_CUDA, std::string("plane_apply_pair_batch: ") + cudaGetErrorString(e));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int resident = std::max(1, std::min((int)((228u * 1024u) / (smem + 1024u)), 2048 / (32 * kPairWarps)));
+    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, sms) * resident);
+    {
+        Trace tr_("plane_apply_pair_batch", st);
+        kern<<<grid, 32 * kPairWarps, smem, st>>>(jobs, njobs, items, Vp, tw_base + g.p0.tw_offset,
+                                                  tw_base + g.p1.tw_offset);
+    }
+    return check_launch("plane_apply_pair_batch");
+}
+
+bool plane_pair_batch_supported(const ChainGeom& g) {
+    return !pair_disabled() && ((g.S0 == 128 && g.S1 == 128) || (g.S0 == 16 && g.S1 == 12));
+}
+
+jdft_status launch_plane_apply_pair_batch(const std::vector<ChainGeom>& gs, const KJob* jobs, int64_t items,
+                                          const float* Vp, const float2* tw_base, cudaStream_t st) {
+    if (gs.empty() || !plane_pair_batch_supported(gs[0])) return JDFT_ERR_UNSUPPORTED;
+    const ChainGeom& g = gs[0];
+    int nrows_max = 0;
+    bool win = true;
+    for (const ChainGeom& x : gs) {
+        nrows_max = std::max(nrows_max, x.nrows);
+        if (g.S0 == 128) win = win && pair_window<128, 128>(x);
+    }
+    const int nj = (int)gs.size();
+    if (g.S0 == 128)
+        return win ? pair_batch_impl<128, 128, true>(g, jobs, nj, items, nrows_max, Vp, tw_base, st)
+                   : pair_batch_impl<128, 128, false>(g, jobs, nj, items, nrows_max, Vp, tw_base, st);
+    return pair_batch_impl<16, 12, false>(g, jobs, nj, items, nrows_max, Vp, tw_base, st);
 }
 
 }  // namespace jdft

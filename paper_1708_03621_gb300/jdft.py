@@ -105,7 +105,7 @@ _SIGS = {
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
 #: Every symbol include/jdft.h declares (the loader checks all are exported).
-EXPORTS = sorted(list(_SIGS) + ["jdft_last_error", "jdft_version", "jdft_launch_count"])
+EXPORTS = sorted(list(_SIGS) + ["jdft_last_error", "jdft_version", "jdft_launch_count", "jdft_batch_is_kbatched"])
 
 _lib = None
 
@@ -128,6 +128,8 @@ def lib() -> ctypes.CDLL:
         L.jdft_version.argtypes = []
         L.jdft_launch_count.restype = ctypes.c_longlong
         L.jdft_launch_count.argtypes = []
+        L.jdft_batch_is_kbatched.restype = ctypes.c_int
+        L.jdft_batch_is_kbatched.argtypes = [ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -492,6 +494,11 @@ class Batch:
         h = ctypes.c_void_p()
         _call("jdft_batch_create", len(items), arr, ctypes.byref(h))
         self.handle = h
+
+    @property
+    def kbatched(self) -> bool:
+        """Whether the chain runs one launch per stage over all items."""
+        return bool(lib().jdft_batch_is_kbatched(self.handle))
 
     def launch(self, stream=None):
         _call("jdft_batch_launch", self.handle, _stream(stream))

@@ -119,3 +119,45 @@ def test_autotune_schedules_keep_results(prec):
     chc_ref = Ch.conj() @ ref.T
     assert np.max(np.abs(CHC.cpu().numpy() - chc_ref)) / np.max(np.abs(chc_ref)) < 2e-4
     jdft.jdft_device_status()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_kbatched_kpoints_equal_individual_calls_and_oracle(prec):
+    """k-points of the 128^3 cell with uneven spheres and odd band counts run
+    as one k-batched chain (one launch per FFT stage over all of them, the
+    paper's k-point parallelism, Sec. 3, folded into one GPU launch): equal to
+    the individual jdft_apply_H calls, and to the oracle on sampled bands."""
+    from paper_1708_03621_gb300 import jdft
+    from tests.systems import OracleSystem
+    kpts = tuple(tuple(k) for k in random_kpoints(3, 41))
+    w = Workload("kbatch128", (20.0, 20.0, 20.0), 30.0, (128, 128, 128), kpts, 64, 9, 11, 12)
+    b = _cell(w)
+    nbs = [9, 6, 11]
+    items, refs = [], []
+    for ik, nb in enumerate(nbs):
+        C = _block(b, w, ik, nb, 300 + ik, prec)
+        items.append((b, ik, C, torch.empty_like(C), prec))
+        R = torch.empty_like(C)
+        jdft.jdft_apply_H(b, ik, C, R, prec)
+        refs.append(R)
+    torch.cuda.synchronize()
+    batch = jdft.Batch(items)
+    assert batch.kbatched
+    for it in items:
+        it[3].fill_(float("nan"))
+    batch.launch()
+    torch.cuda.synchronize()
+    for it, R in zip(items, refs):
+        got, ref = it[3].cpu().numpy(), R.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref)) < 1e-6 * np.max(np.abs(ref))
+    # the oracle on two bands of the second k-point
+    o = OracleSystem(w, ik=1)
+    C1 = items[1][2].cpu().numpy().astype(np.complex128)
+    sample = [0, nbs[1] - 1]
+    ref = o.apply_H(C1[sample])
+    got = items[1][3].cpu().numpy().astype(np.complex128)[sample]
+    err = np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1))
+    assert err < 2e-5
+    batch.close()
+    jdft.jdft_device_status()
