@@ -20,6 +20,7 @@
 #include "gemm.cuh"
 #include "minimize.cuh"
 #include "profile.cuh"
+#include "tc_ptx.cuh"
 
 namespace jdft {
 
@@ -50,35 +51,6 @@ __device__ __forceinline__ float dsiluf_(float z) {
 }
 __device__ __forceinline__ float softplusf_(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
 
-__device__ __forceinline__ void load_weights(const __nv_bfloat16* __restrict__ wb, float* w) {
-    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) w[i] = __bfloat162float(wb[i]);
-    __syncthreads();
-}
-
-// K for one feature triple (weights in shared memory as FP32 values of the BF16 parameters).
-__device__ __forceinline__ float mlp_eval(const float* w, float f0, float f1, float f2) {
-    float h1[HID];
-#pragma unroll
-    for (int i = 0; i < HID; ++i)
-        h1[i] = siluf_(w[OW1 + 3 * i] * f0 + w[OW1 + 3 * i + 1] * f1 + w[OW1 + 3 * i + 2] * f2 + w[OB1 + i]);
-    float z = w[OB3];
-    for (int j = 0; j < HID; ++j) {
-        float acc = w[OB2 + j];
-#pragma unroll
-        for (int i = 0; i < HID; ++i) acc += w[OW2 + HID * j + i] * h1[i];
-        z += w[OW3 + j] * siluf_(acc);
-    }
-    return softplusf_(z);
-}
-
-__global__ void __launch_bounds__(128) mlp_forward_kernel(int64_t rows, const float* __restrict__ feats,
-                                                          float* __restrict__ K, const __nv_bfloat16* __restrict__ wb) {
-    __shared__ float w[NPARAM];
-    load_weights(wb, w);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
-        K[r] = mlp_eval(w, feats[3 * r], feats[3 * r + 1], feats[3 * r + 2]);
-}
-
 // Per-band features: bf[2b] = 1/T_b, bf[2b+1] = log(1 + T_b), bf[2nb + b] = (h_b - min h)/T_b.
 __global__ void band_features_kernel(int nb, const double* __restrict__ Tb, const double2* __restrict__ Hs,
                                      float* __restrict__ bf) {
@@ -97,21 +69,193 @@ __global__ void band_features_kernel(int nb, const double* __restrict__ Tb, cons
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) mlp_precond_kernel(int npw, int nb, const c_t<T>* __restrict__ G, int ldg,
-                                                          c_t<T>* __restrict__ KG, int ldk,
-                                                          const double* __restrict__ kin,
-                                                          const float* __restrict__ bf,
-                                                          const __nv_bfloat16* __restrict__ wb) {
-    __shared__ float w[NPARAM];
-    load_weights(wb, w);
-    const int64_t total = (int64_t)npw * nb;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / npw, g = i - b * npw;
-        const float k = mlp_eval(w, (float)kin[g] * bf[2 * b], bf[2 * b + 1], bf[2 * nb + b]);
-        const c_t<T> v = G[b * ldg + g];
-        KG[b * ldk + g] = mk<T>((T)(k * v.x), (T)(k * v.y));
+// ---------------------------------------------------------------------------
+// Inference with the hidden layer on the tensor cores.  A block of 128
+// threads takes tiles of 128 rows (one row per thread and tensor-memory lane):
+// each thread forms its row's layer-1 activations h (FP32, SiLU) and writes
+// them as h = hi + mid + lo in BF16 (h to about 2^-24 relative, as in FP32)
+// into three 128 x 64 K-major tiles in shared memory; one thread issues the
+// hidden layer a2 = W2 h as 12 tcgen05.mma (M = 128, N = 64, K = 16 each:
+// each tile times the BF16 weights, FP32 accumulation in 64 tensor-memory
+// columns) and commits them to
+// an mbarrier; every thread then reads its row's 64 sums, adds b2, applies
+// SiLU, the output layer and softplus.  The wait is bounded; one that gives
+// up records JDFT_ERR_TIMEOUT (jdft_device_status) and stops the block after
+// waiting for the products already issued.
+// ---------------------------------------------------------------------------
+constexpr int MT = 128;                      // rows per tile = threads per block
+constexpr int MT_ATILE = MT * HID * 2;       // bytes of one BF16 activation tile (16 KB)
+constexpr int MT_BTILE = HID * HID * 2;      // bytes of the BF16 W2 tile (8 KB)
+constexpr unsigned long long MLP_WAIT_NS = 2000000000ull;
+__device__ int g_mlp_status = 0;
+
+// Byte offset of (row r, k) in a K-major tile of 64 values per row: 8-row x
+// 8-value core matrices of 128 bytes, K-adjacent ones 128 bytes apart, 8-row
+// groups 1024 bytes apart.
+__device__ __forceinline__ uint32_t mlp_core_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// MODE 0: K[r] for feature triples feats[3 r ..]; MODE 1: KG = K G for every
+// coefficient of an (npw x nb) block (features from kin and the band features).
+template <int MODE, typename T>
+__global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* __restrict__ feats,
+                                                    float* __restrict__ Kout, int npw, int nb,
+                                                    const c_t<T>* __restrict__ G, int ldg, c_t<T>* __restrict__ KG,
+                                                    int ldk, const double* __restrict__ kin,
+                                                    const float* __restrict__ bf,
+                                                    const __nv_bfloat16* __restrict__ wb) {
+    extern __shared__ __align__(1024) unsigned char sraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* Ahi = sm;
+    unsigned char* Amid = sm + MT_ATILE;
+    unsigned char* Alo = sm + 2 * MT_ATILE;
+    unsigned char* Bt = sm + 3 * MT_ATILE;
+    float* w = reinterpret_cast<float*>(Bt + MT_BTILE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(w + NPARAM + 3);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < NPARAM; i += MT) w[i] = __bfloat162float(wb[i]);
+    // W2 as the B operand: row j (output), K = i (input)
+    for (int e = tid; e < HID * HID / 2; e += MT) {
+        const int j = (2 * e) / HID, i = (2 * e) % HID;
+        *reinterpret_cast<__nv_bfloat162*>(Bt + mlp_core_off(j, i)) =
+            __halves2bfloat162(wb[OW2 + HID * j + i], wb[OW2 + HID * j + i + 1]);
     }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = tc::instr_desc(1u, MT, HID);
+    const int64_t tiles = (rows + MT - 1) / MT;
+    int ok = 1;
+    uint32_t phase = 0;
+    for (int64_t tl = blockIdx.x; tl < tiles && ok; tl += gridDim.x) {
+        const int64_t r = tl * MT + tid;
+        const bool act = r < rows;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        int64_t b = 0, gq = 0;
+        if (act) {
+            if constexpr (MODE == 0) {
+                f0 = feats[3 * r];
+                f1 = feats[3 * r + 1];
+                f2 = feats[3 * r + 2];
+            } else {
+                b = r / npw;
+                gq = r - b * npw;
+                f0 = (float)kin[gq] * bf[2 * b];
+                f1 = bf[2 * b + 1];
+                f2 = bf[2 * nb + b];
+            }
+        }
+        // layer 1 -> the hi / lo activation tiles, 8 values (16 bytes) at a time
+#pragma unroll 1
+        for (int k0 = 0; k0 < HID; k0 += 8) {
+            float h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = k0 + q;
+                h[q] = siluf_(w[OW1 + 3 * i] * f0 + w[OW1 + 3 * i + 1] * f1 + w[OW1 + 3 * i + 2] * f2 + w[OB1 + i]);
+            }
+            uint32_t hi[4], mid[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(h[q], h[q + 1]);
+                const float r0 = h[q] - __low2float(hh), r1 = h[q + 1] - __high2float(hh);
+                const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
+                hi[q / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+                mid[q / 2] = *reinterpret_cast<const uint32_t*>(&mm);
+                lo[q / 2] = bf2_bits(r0 - __low2float(mm), r1 - __high2float(mm));
+            }
+            const uint32_t o = mlp_core_off(tid, k0);
+            *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(Amid + o) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
+            *reinterpret_cast<uint4*>(Alo + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after_sync();
+            const uint32_t ah = tc::smem_addr(Ahi), am = tc::smem_addr(Amid), al = tc::smem_addr(Alo);
+            const uint32_t bb = tc::smem_addr(Bt);
+#pragma unroll
+            for (int s = 0; s < HID / 16; ++s) {
+                const uint64_t db = tc::smem_desc(bb + s * 256, 128, 1024);
+                tc::mma_bf16(tmem, tc::smem_desc(ah + s * 256, 128, 1024), db, idesc, s > 0 ? 1u : 0u);
+                tc::mma_bf16(tmem, tc::smem_desc(am + s * 256, 128, 1024), db, idesc, 1u);
+                tc::mma_bf16(tmem, tc::smem_desc(al + s * 256, 128, 1024), db, idesc, 1u);
+            }
+            tc::mma_commit(bar);
+        }
+        const int w_ok = tc::mbar_wait_ns(bar, phase, MLP_WAIT_NS) ? 1 : 0;
+        ok = __syncthreads_and(w_ok);
+        if (!ok) {
+            // the products may still run: wait for them (fixed limit) before leaving
+            tc::mbar_wait_ns(bar, phase, MLP_WAIT_NS);
+            if (tid == 0) atomicExch(&g_mlp_status, (int)JDFT_ERR_TIMEOUT);
+            break;
+        }
+        phase ^= 1u;
+        tc::tc_fence_after_sync();
+        float z = w[OB3];
+#pragma unroll 1
+        for (int c = 0; c < HID; c += 16) {
+            float acc[16];
+            tc::tmem_ld16(lane_base + c, acc);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) z += w[OW3 + c + q] * siluf_(acc[q] + w[OB2 + c + q]);
+        }
+        const float Kv = softplusf_(z);
+        if (act) {
+            if constexpr (MODE == 0) {
+                Kout[r] = Kv;
+            } else {
+                const c_t<T> v = G[b * ldg + gq];
+                KG[b * ldk + gq] = mk<T>((T)(Kv * v.x), (T)(Kv * v.y));
+            }
+        }
+        tc::tc_fence_before_sync();
+        __syncthreads();  // every lane's tensor-memory reads and tile reads are done before the next tile
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+constexpr size_t MLP_TC_SMEM = 1024 + 3 * MT_ATILE + MT_BTILE + (NPARAM + 3) * sizeof(float) + 64;
+
+// Persistent grid of the tensor-core inference kernel: two blocks per SM
+// (shared memory; their 64 tensor-memory columns each fit easily).
+static int mlp_tc_grid(int64_t rows) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (rows + MT - 1) / MT;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(1, sms) * 2));
+}
+
+jdft_status mlp_device_status() {
+    int v = 0;
+    JDFT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_mlp_status, sizeof(int)));
+    if (v != 0) {
+        const int zero = 0;
+        JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_mlp_status, &zero, sizeof(int)));
+        return set_error((jdft_status)v, "a bounded device-side wait gave up (preconditioner network)");
+    }
+    return JDFT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -342,9 +486,13 @@ jdft_status mlp_precondition(jdft_mlp_t mlp, int npw, int nb, const c_t<T>* G, i
     jdft_status s = check_launch("band_features");
     if (s != JDFT_OK) return s;
     {
+        auto kern = mlp_tc_kernel<1, T>;
+        cudaError_t e = set_smem_attr((const void*)kern, MLP_TC_SMEM);
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("mlp_precond: ") + cudaGetErrorString(e));
+        const int64_t rows = (int64_t)npw * nb;
         Trace tr_("mlp_precond", st);
-        mlp_precond_kernel<T><<<grid_rows((int64_t)npw * nb, 128), 128, 0, st>>>(npw, nb, G, ldg, KG, ldk, kin, bf,
-                                                                                mlp->wb);
+        kern<<<mlp_tc_grid(rows), MT, MLP_TC_SMEM, st>>>(rows, nullptr, nullptr, npw, nb, G, ldg, KG, ldk, kin, bf,
+                                                         mlp->wb);
     }
     return check_launch("mlp_precond");
 }
@@ -404,8 +552,12 @@ jdft_status jdft_mlp_forward(jdft_mlp_t m, int64_t rows, const float* feats, flo
     if (rows == 0) return JDFT_OK;
     cudaStream_t st = (cudaStream_t)stream;
     {
+        auto kern = mlp_tc_kernel<0, float>;
+        cudaError_t e = set_smem_attr((const void*)kern, MLP_TC_SMEM);
+        if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("mlp_forward: ") + cudaGetErrorString(e));
         Trace tr_("mlp_forward", st);
-        mlp_forward_kernel<<<grid_rows(rows, 128), 128, 0, st>>>(rows, feats, K, m->wb);
+        kern<<<mlp_tc_grid(rows), MT, MLP_TC_SMEM, st>>>(rows, feats, K, 0, 0, nullptr, 0, nullptr, 0, nullptr,
+                                                         nullptr, m->wb);
     }
     return check_launch("mlp_forward");
 }

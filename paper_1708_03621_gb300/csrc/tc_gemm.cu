@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "gemm.cuh"
+#include "minimize.cuh"
 #include "profile.cuh"
 #include "tc_ptx.cuh"
 
@@ -995,7 +996,7 @@ extern "C" jdft_status jdft_device_status(void* stream) {
         JDFT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int)));
         return set_error((jdft_status)v, "a bounded device-side wait gave up (tensor-core product skipped)");
     }
-    return JDFT_OK;
+    return mlp_device_status();
 }
 
 extern "C" jdft_status jdft_set_wait_limit(double seconds) {
