@@ -258,6 +258,15 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
     if name == "tcx_cn":
         # the same C^dag B products, from split operands (BF16 hi/lo planes: 8 bytes per complex value)
         return kernel_work(p, "zgemm_cn", launches, nb)
+    if name == "tcx_nn":
+        return kernel_work(p, "zgemm_nn", launches, nb)
+    if name == "tcx_reduce":
+        # the split-K partial tiles of one tcx_cn product (128 x 256 FP32 complex per block, one block
+        # per (tile, split): the autotuned split count) read once, the nb x nb FP64 output read and written
+        tune = getattr(p, "tune", None) or {}
+        splits = tune.get("splits_subspace") or 1
+        tiles = -(-p.nb // 128)
+        return 0.0, splits * tiles * 128 * 256 * 8.0 + 2 * p.nb * p.nb * 16.0
     if name == "split_planes":
         # one block of nb rows: FP32 complex read, four BF16 planes written (8 + 8 bytes per value)
         return 0.0, 16.0 * nb * p.npw
@@ -304,7 +313,7 @@ def roofline_of(k: dict, prec: str, peaks: dict, fp32: dict) -> dict:
     name = k["name"]
     hbm = peaks.get("hbm_gbs", 6800.0)
     src_hbm = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
-    if name.startswith("tc_zgemm") or name == "tcx_cn":
+    if name.startswith("tc_zgemm") or name in ("tcx_cn", "tcx_nn"):
         bf16 = peaks.get("bf16_tflops", 1900.0)
         src = "of measured" if "bf16_tflops" in peaks else "of fallback"
         if prec == "bf16x3":

@@ -80,7 +80,7 @@ static jdft_status kbatch_setup(jdft_batch_s* bt) {
         col_off.push_back(off);
         off += r256((size_t)it.nb * g.S2 * g.ncols * sizeof(float2));
         const KSphere& sp = b->ks[it.ik];
-        nl = std::max(nl, nonlocal_workspace_bytes(sp.nproj, it.nb, sizeof(float2), sp.npw, it.prec, true));
+        nl = std::max(nl, nonlocal_workspace_bytes(sp.nproj, it.nb, sizeof(float2), sp.npw, it.prec, true, true));
     }
     const size_t jobs_off = off;
     off += r256(bt->items.size() * sizeof(KJob));
@@ -130,7 +130,8 @@ static jdft_status run_kbatch(jdft_batch_s* bt, cudaStream_t st) {
         return s;
     for (const auto& it : bt->items) {
         const KSphere& sp = b->ks[it.ik];
-        if ((s = nonlocal_accumulate<float>(sp, it.C, it.ldc, it.HC, it.ldhc, it.nb, it.prec, bt->nlwork, st, true)))
+        if ((s = nonlocal_accumulate<float>(sp, it.C, it.ldc, it.HC, it.ldhc, it.nb, it.prec, bt->nlwork, st, true,
+                                            nullptr, true)))
             return s;
     }
     return JDFT_OK;

@@ -595,7 +595,7 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
     const KSphere& sp = b->ks[ik];
     const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
-    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, true);
+    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, true, true);
     jdft_status s = ensure_workspace(b, colbytes + nlbytes);
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -611,7 +611,8 @@ static jdft_status run_apply_H(jdft_basis_s* b, int ik, const void* C, int ldc, 
             return s;
     }
     if (sp.nproj > 0)
-        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st, true);
+        return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st, true, nullptr,
+                                      true);
     return JDFT_OK;
 }
 
@@ -624,7 +625,7 @@ static size_t apply_H_density_bytes(const jdft_basis_s* b, int ik, int nb, jdft_
     const KSphere& sp = b->ks[ik];
     const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
-    return colbytes + nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, split_c);
+    return colbytes + nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, split_c, true);
 }
 
 // Csplit: the BF16 planes of C (tcx_split) when the caller has them, so the
@@ -637,7 +638,7 @@ static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, i
     const KSphere& sp = b->ks[ik];
     const int nc = chunk_bands(g, sizeof(c_t<T>), nb, chunk_budget(b));
     const size_t colbytes = ((size_t)nc * g.S2 * g.ncols * sizeof(c_t<T>) + 255) / 256 * 256;
-    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, !Csplit);
+    const size_t nlbytes = nonlocal_workspace_bytes(sp.nproj, nb, sizeof(c_t<T>), sp.npw, prec, !Csplit, true);
     jdft_status s = ensure_workspace(b, colbytes + nlbytes);
     if (s != JDFT_OK) return s;
     c_t<T>* colbuf = (c_t<T>*)b->work.ptr;
@@ -668,7 +669,7 @@ static jdft_status run_apply_H_density(jdft_basis_s* b, int ik, const void* C, i
     }
     if (sp.nproj > 0)
         return nonlocal_accumulate<T>(sp, C, ldc, HC, ldhc, nb, prec, (char*)b->work.ptr + colbytes, st, !Csplit,
-                                      Csplit);
+                                      Csplit, true);
     return JDFT_OK;
 }
 

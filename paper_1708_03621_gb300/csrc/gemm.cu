@@ -182,14 +182,16 @@ bool gemm_nn_inplace_ok(jdft_prec prec, int N) {
     return false;  // the CUDA-core products tile N in 16-column blocks
 }
 
-size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw, jdft_prec prec, bool split_c) {
+size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw, jdft_prec prec, bool split_c,
+                                bool partials) {
     if (nproj == 0) return 0;
     const size_t a = ((size_t)nproj * nb * sizeof(double2) + 255) / 256 * 256;
     const size_t b = ((size_t)nproj * nb * elem + 255) / 256 * 256;
     const size_t c = split_c && tcx_eligible(prec, nproj, nb) ? (tcx_split_bytes(nb, npw) + 255) / 256 * 256 : 0;
     // the split of (D P^dag C)'s transpose for P (D P^dag C) on split operands
     const size_t d = tcx_eligible(prec, nproj, nb) ? (tcx_split_bytes(nb, nproj) + 255) / 256 * 256 : 0;
-    return a + b + c + d;
+    const size_t e = partials && tcx_eligible(prec, nproj, nb) ? tcx_cn_partial_bytes(nproj, nb, npw) : 0;
+    return a + b + c + d + e;
 }
 
 template <typename T>
@@ -199,7 +201,8 @@ template <> const float2* proj_ptr<float>(const KSphere& sp) { return (const flo
 
 template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
-                                jdft_prec prec, void* work, cudaStream_t st, bool split_c, const void* Csplit) {
+                                jdft_prec prec, void* work, cudaStream_t st, bool split_c, const void* Csplit,
+                                bool partials) {
     if (sp.nproj == 0 || nb == 0) return JDFT_OK;
     double2* Bc = (double2*)work;
     const size_t abytes = ((size_t)sp.nproj * nb * sizeof(double2) + 255) / 256 * 256;
@@ -218,7 +221,10 @@ jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void*
             if ((s = tcx_split((const float2*)C, ldc, nb, sp.npw, own, st))) return s;
             Cs = own;
         }
-        s = tcx_cn(sp.nproj, nb, sp.npw, sp.Psplit, Cs, Bc, nb, 1.0, st);
+        const size_t dbytes = (tcx_split_bytes(nb, sp.nproj) + 255) / 256 * 256;
+        void* part = partials ? (char*)work + abytes + bbytes + cbytes + dbytes : nullptr;
+        s = tcx_cn(sp.nproj, nb, sp.npw, sp.Psplit, Cs, Bc, nb, 1.0, st, part,
+                   partials ? tcx_cn_partial_bytes(sp.nproj, nb, sp.npw) : 0);
     } else {
         s = gemm_cn<T>(prec, sp.nproj, nb, sp.npw, proj_ptr<T>(sp), sp.npw, (const c_t<T>*)C, ldc, Bc, nb, 1.0, st);
     }
@@ -272,9 +278,9 @@ template jdft_status zgemm_nn_acc<double>(int, int, int, const double2*, int, co
 template jdft_status zgemm_nn_acc<float>(int, int, int, const float2*, int, const float2*, int, float2*, int,
                                          cudaStream_t, bool);
 template jdft_status nonlocal_accumulate<double>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,
-                                                 cudaStream_t, bool, const void*);
+                                                 cudaStream_t, bool, const void*, bool);
 template jdft_status nonlocal_accumulate<float>(const KSphere&, const void*, int, void*, int, int, jdft_prec, void*,
-                                                cudaStream_t, bool, const void*);
+                                                cudaStream_t, bool, const void*, bool);
 
 }  // namespace jdft
 
@@ -297,18 +303,21 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
     if (prec == JDFT_BF16X3 && tcx_eligible(prec, nb, nb)) {
         // split C (and HC) once into BF16 planes in the basis workspace; both
         // products read the split C
+        // (and room for the products' split-K partial tiles after them)
         const size_t cb = (tcx_split_bytes(nb, npw) + 255) / 256 * 256;
-        if ((s = ensure_workspace(b, CHC ? 2 * cb : cb))) return s;
+        const size_t pb = tcx_cn_partial_bytes(nb, nb, npw);
+        const size_t sb = CHC ? 2 * cb : cb;
+        if ((s = ensure_workspace(b, sb + pb))) return s;
         char* ws = (char*)b->work.ptr;
         if ((s = tcx_split((const float2*)C, ldc, nb, npw, ws, st))) return s;
         if (CHC) {
             if ((s = tcx_split((const float2*)HC, ldhc, nb, npw, ws + cb, st))) return s;
             JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
-            if ((s = tcx_cn(nb, nb, npw, ws, ws + cb, (double2*)CHC, nb, 1.0, st))) return s;
+            if ((s = tcx_cn(nb, nb, npw, ws, ws + cb, (double2*)CHC, nb, 1.0, st, ws + sb, pb))) return s;
         }
         if (COC) {
             JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
-            if ((s = tcx_cn(nb, nb, npw, ws, ws, (double2*)COC, nb, b->omega, st))) return s;
+            if ((s = tcx_cn(nb, nb, npw, ws, ws, (double2*)COC, nb, b->omega, st, ws + sb, pb))) return s;
         }
         return JDFT_OK;
     }

@@ -44,9 +44,15 @@ jdft_status tcx_split_t(const float2* X, int ld, int rows, int K, void* planes, 
 jdft_status tcx_nn(int M, int N, int K, const void* Aplanes, const void* Bplanes, float2* out, int ldo,
                    bool accumulate, cudaStream_t st);
 // out[m * ldo + n] += alpha sum_k conj(A[m][k]) B[n][k] from the split blocks
-// of A (M rows) and B (N rows); FP64 atomics, so out must be zeroed first.
+// of A (M rows) and B (N rows), split along K over one wave of blocks.  With
+// `partials` (partial_bytes >= tcx_cn_partial_bytes(M, N, K), 16-byte
+// aligned) the blocks' FP32 partial tiles are stored there and summed (with
+// compensated FP32 sums, in a fixed order) by a second kernel; without, they
+// are added to out with FP64 atomics.  Either way out accumulates, so zero it
+// first for a product.
+size_t tcx_cn_partial_bytes(int M, int N, int K);
 jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
-                   cudaStream_t st);
+                   cudaStream_t st, void* partials = nullptr, size_t partial_bytes = 0);
 
 // Precision dispatch: JDFT_TF32X3 and JDFT_BF16X3 run the tensor-core
 // versions (T = float only), the other precisions the CUDA-core ones.
@@ -65,9 +71,10 @@ jdft_status gemm_nn_acc(jdft_prec prec, int M, int N, int K, const c_t<T>* A, in
 bool gemm_nn_inplace_ok(jdft_prec prec, int N);
 
 // Workspace bytes the nonlocal term needs for nb bands (with split_c, room
-// for the split copy of C that the BF16x3 projection P^dag C reads).
+// for the split copy of C that the BF16x3 projection P^dag C reads; with
+// partials, room for that projection's split-K partial tiles).
 size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw = 0, jdft_prec prec = JDFT_FP64,
-                                bool split_c = false);
+                                bool split_c = false, bool partials = false);
 
 // HC += P D P^dag C for the sphere's projectors (no-op when nproj == 0).
 // split_c: take the projection from split operands (tcx_cn) when it is
@@ -75,9 +82,11 @@ size_t nonlocal_workspace_bytes(int nproj, int nb, size_t elem, int npw = 0, jdf
 // nonlocal_workspace_bytes(..., true).
 // Csplit: the caller's BF16 planes of C (tcx_split), used instead of a split
 // of its own when the projection is eligible.
+// partials: the workspace holds nonlocal_workspace_bytes(..., split_c, true)
+// and the projection's split-K partial tiles go there (no atomics).
 template <typename T>
 jdft_status nonlocal_accumulate(const KSphere& sp, const void* C, int ldc, void* HC, int ldhc, int nb,
                                 jdft_prec prec, void* work, cudaStream_t st, bool split_c = false,
-                                const void* Csplit = nullptr);
+                                const void* Csplit = nullptr, bool partials = false);
 
 }  // namespace jdft

@@ -665,9 +665,10 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
     const size_t blk = ((size_t)nb * ldc * sizeof(c_t<T>) + 255) / 256 * 256;
     const bool split = !Ugiven && std::is_same<T, float>::value && tcx_eligible(prec, nb, nb);
     const size_t spl = split ? (tcx_split_bytes(nb, npw) + 255) / 256 * 256 : 0;
+    const size_t pb = split ? tcx_cn_partial_bytes(nb, nb, npw) : 0;
     // the basis workspace (grown once) holds U, W, the factorisation scratch, a copy of C, a status
-    // word and, for the split-operand overlap, the BF16 planes of C
-    jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256 + spl);
+    // word and, for the split-operand overlap, the BF16 planes of C and the product's partial tiles
+    jdft_status s = ensure_workspace(b, sm + wbytes + lab + blk + 256 + spl + pb);
     if (s != JDFT_OK) return s;
     char* q = (char*)b->work.ptr;
     double2* U = (double2*)q;
@@ -684,7 +685,7 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
             // the same split-operand product jdft_subspace forms C^dag O C with
             void* planes = q + sm + wbytes + lab + blk + 256;
             if ((s = tcx_split((const float2*)C, ldc, nb, npw, planes, st))) return s;
-            if ((s = tcx_cn(nb, nb, npw, planes, planes, U, nb, b->omega, st))) return s;
+            if ((s = tcx_cn(nb, nb, npw, planes, planes, U, nb, b->omega, st, (char*)planes + spl, pb))) return s;
         } else if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega,
                                    st))) {
             return s;
@@ -771,16 +772,19 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     // rotation out of place needs reuses the start once the rest is done
     // the rotation's transposed splits of C and W reuse the start once the rest is done
     const size_t rot = split ? r256(tcx_split_bytes(npw, nb)) + r256(tcx_split_bytes(nb, nb)) : 0;
-    jdft_status s = ensure_workspace(b, std::max(std::max(chain + 2 * cs, tmpb), rot));
+    // the split-K partial tiles of C^dag O C and C^dag H C follow the planes
+    const size_t pb = split ? tcx_cn_partial_bytes(nb, nb, npw) : 0;
+    jdft_status s = ensure_workspace(b, std::max(std::max(chain + 2 * cs + pb, tmpb), rot));
     if (s != JDFT_OK) return s;
     char* ws = (char*)b->work.ptr;
     void* Cs = ws + chain;
     void* HCs = ws + chain + cs;
+    void* part = ws + chain + 2 * cs;
     const c_t<T>* Cc = (const c_t<T>*)C;
     JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
     if (split) {
         if ((s = tcx_split((const float2*)C, ldc, nb, npw, Cs, st))) return s;
-        if ((s = tcx_cn(nb, nb, npw, Cs, Cs, COC, nb, b->omega, st))) return s;
+        if ((s = tcx_cn(nb, nb, npw, Cs, Cs, COC, nb, b->omega, st, part, pb))) return s;
     } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, Cc, ldc, COC, nb, b->omega, st))) {
         return s;
     }
@@ -799,7 +803,7 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
     if (split) {
         if ((s = tcx_split((const float2*)HC, ldhc, nb, npw, HCs, st))) return s;
-        if ((s = tcx_cn(nb, nb, npw, Cs, HCs, CHC, nb, 1.0, st))) return s;
+        if ((s = tcx_cn(nb, nb, npw, Cs, HCs, CHC, nb, 1.0, st, part, pb))) return s;
     } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, (const c_t<T>*)HC, ldhc, CHC, nb, 1.0, st))) {
         return s;
     }

@@ -483,13 +483,17 @@ namespace jdft {
 // memory), the minus through the instruction descriptor's negate-A bit: 12
 // MMAs of 128 x NT x 16 per 16 complex K.
 //
-// One block of 128 threads computes a 128 x NT tile over a range of K (split-K
-// partial sums meet in FP64 with atomics): thread 0 issues the copies of a
-// 4-stage ring, thread 32 waits for a stage, issues its MMAs and commits them
-// to the stage's "empty" barrier, and after the last stage to the accumulator
-// barrier, which all four warps wait for before reading tensor memory (warp
-// w: rows 32 w .. 32 w + 31).  The epilogue passes each warp's 32 x 16 slices
-// through shared memory, so that one atomic instruction covers 16 consecutive
+// One block of 128 threads computes a 128 x NT tile over a range of K (split-K):
+// thread 0 issues the copies of a 4-stage ring, thread 32 waits for a stage,
+// issues its MMAs and commits them to the stage's "empty" barrier, and after
+// the last stage to the accumulator barrier, which all four warps wait for
+// before reading tensor memory (warp w: rows 32 w .. 32 w + 31).  The split-K
+// partial tiles meet in one of two ways.  With a partial buffer, each block
+// stores its FP32 tile (column-major, so a warp's store is 32 consecutive
+// rows) and tcx_reduce_kernel sums the tiles of every output with compensated
+// FP32 sums in a fixed order (deterministic; no atomics).  Without one, the epilogue adds the
+// tile to the output with FP64 atomics, each warp's 32 x 16 slices passed
+// through shared memory so that one atomic instruction covers 16 consecutive
 // outputs of two rows.  Every wait is bounded by the run-time limit; a wait
 // that gives up records JDFT_ERR_TIMEOUT, and the block waits (under the fixed
 // drain limit) for the copies and products it already issued before freeing
@@ -583,7 +587,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 template <int NT>
 __global__ void __launch_bounds__(TCX_THREADS, 1)
     tcx_cn_kernel(const char* __restrict__ As, const char* __restrict__ Bs, int M, int N, int nkc, int cps,
-                  double2* __restrict__ out, int ldo, double alpha) {
+                  double2* __restrict__ out, int ldo, double alpha, float2* __restrict__ part) {
     // rows of the split blocks (padded to 128)
     const int rpA = (M + TCX_M - 1) / TCX_M * TCX_M, rpB = (N + TCX_M - 1) / TCX_M * TCX_M;
     using L = TcxLayout<NT>;
@@ -700,7 +704,25 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
         __syncthreads();
     }
     tc::tc_fence_after_sync();
-    if (ok) {
+    if (ok && part) {
+        // the partial buffer is [tile][column pair][split][row], one 16-byte entry (Re, Im
+        // of column 2 j, Re, Im of column 2 j + 1) per row, so that the splits of a column
+        // pair are contiguous for the reduction
+        const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        float4* P = reinterpret_cast<float4*>(part) + (tile * (NT / 2) * gridDim.z + blockIdx.z) * TCX_M + warp * 32 +
+                    lane;
+        const size_t jstride = (size_t)gridDim.z * TCX_M;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int col = 0; col < NT && n0 + col < N; col += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(lane_base + col, re);
+            tc::tmem_ld16(lane_base + NT + col, im);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2)
+                P[(size_t)((col + j) / 2) * jstride] = make_float4(re[j], im[j], re[j + 1], im[j + 1]);
+        }
+    } else if (ok) {
         // each warp: its 32 rows in slices of 16 columns, transposed through
         // shared memory (the ring is free now) so that lanes 0-15 and 16-31
         // add to 16 consecutive outputs of one row each
@@ -733,6 +755,75 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     __syncthreads();
     if (warp == 2) tc::tmem_dealloc(tmem, L::NCOLS);
     if (!ok && nit > 0 && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
+}
+
+// Compensated FP32 summation (Knuth's TwoSum): s + c carries the running sum
+// of FP32 terms to twice the FP32 precision, with FP32 instructions only (the
+// FP64 rate of the SMs is a small fraction of the FP32 rate).
+struct Sum2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+};
+
+// out[m * ldo + n] += alpha sum_z (partial tile z of (m, n)) over the split-K
+// partial tiles of tcx_cn_kernel ([tile][column pair][split][row] of 16-byte
+// entries): block (column pair j of a tile, tile) with 128 x TCX_RZ
+// threads; thread (r, q) sums the splits z = q, q + TCX_RZ, ... of columns 2 j
+// and 2 j + 1 of row r with compensated FP32 sums, and the TCX_RZ sums of a
+// row are combined in q order, so the result does not depend on timing.  The
+// sums are formed to about 2^-44 of the sum of the terms' magnitudes, then
+// rounded to FP64.
+constexpr int TCX_RZ = 8;
+__global__ void __launch_bounds__(TCX_M* TCX_RZ)
+    tcx_reduce_kernel(const float4* __restrict__ part, int splits, int tiles_m, int NT, int M, int N,
+                      double2* __restrict__ out, int ldo, double alpha) {
+    __shared__ float4 sum[TCX_RZ][2][TCX_M];
+    const int r = threadIdx.x, q = threadIdx.y;
+    const int j = blockIdx.x, tile = blockIdx.y;
+    const size_t zstride = TCX_M;
+    const float4* p = part + ((size_t)tile * (NT / 2) + j) * (size_t)splits * TCX_M + r;
+    Sum2 s[4];  // Re, Im of column 2 j; Re, Im of column 2 j + 1
+    // eight loads in flight per thread, then their sums (absent splits add zeros)
+    for (int z0 = q; z0 < splits; z0 += 8 * TCX_RZ) {
+        float4 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int z = z0 + i * TCX_RZ;
+            v[i] = z < splits ? p[(size_t)z * zstride] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            s[0].add(v[i].x);
+            s[1].add(v[i].y);
+            s[2].add(v[i].z);
+            s[3].add(v[i].w);
+        }
+    }
+    sum[q][0][r] = make_float4(s[0].s, s[0].c, s[1].s, s[1].c);
+    sum[q][1][r] = make_float4(s[2].s, s[2].c, s[3].s, s[3].c);
+    __syncthreads();
+    // thread (r, 0) finishes column 2 j of row r, thread (r, 1) column 2 j + 1
+    if (q >= 2) return;
+    Sum2 x, y;
+#pragma unroll
+    for (int i = 0; i < TCX_RZ; ++i) {
+        const float4 u = sum[i][q][r];
+        x.add(u.x);
+        x.add(u.y);
+        y.add(u.z);
+        y.add(u.w);
+    }
+    const int m = (tile % tiles_m) * TCX_M + r, n = (tile / tiles_m) * NT + 2 * j + q;
+    if (m < M && n < N) {
+        double2* o = out + (size_t)m * ldo + n;
+        o->x += alpha * ((double)x.s + (double)x.c);
+        o->y += alpha * ((double)y.s + (double)y.c);
+    }
 }
 
 // out[n * ldo + m] (+)= sum_k A[m][k] B[n][k] from split blocks of A (M rows,
@@ -946,11 +1037,9 @@ static int tuned_tcx_splits(int M, int N, int K) {
     return it == g_tune_tcx.end() ? 0 : it->second;
 }
 
-jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
-                   cudaStream_t st) {
-    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
-    const bool wide = N > 128;
-    const int NT = wide ? 256 : 128;
+// Tile width, K chunks per split and split count tcx_cn launches with for (M, N, K).
+static void tcx_cn_config(int M, int N, int K, int& NT, int& cps, int& splits) {
+    NT = N > 128 ? 256 : 128;
     const int nkc = tcx_chunks(K);
     const int tiles = ((M + TCX_M - 1) / TCX_M) * ((N + NT - 1) / NT);
     int dev = 0, sms = 0;
@@ -958,28 +1047,54 @@ jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // one wave of blocks, and at most 4096 complex K accumulated per block
     const int capmin = (nkc + 4096 / TCX_KC - 1) / (4096 / TCX_KC);
-    int splits = std::max(capmin, std::min(nkc, std::max(1, sms / tiles)));
+    splits = std::max(capmin, std::min(nkc, std::max(1, sms / tiles)));
     const int tuned = tuned_tcx_splits(M, N, K);
     if (tuned > 0) splits = std::max(capmin, std::min(nkc, tuned));
-    const int cps = (nkc + splits - 1) / splits;
+    cps = (nkc + splits - 1) / splits;
     splits = (nkc + cps - 1) / cps;
-    dim3 grid((M + TCX_M - 1) / TCX_M, (N + NT - 1) / NT, splits);
+}
+
+size_t tcx_cn_partial_bytes(int M, int N, int K) {
+    if (M == 0 || N == 0 || K == 0) return 0;
+    int NT, cps, splits;
+    tcx_cn_config(M, N, K, NT, cps, splits);
+    const size_t tiles = (size_t)((M + TCX_M - 1) / TCX_M) * ((N + NT - 1) / NT);
+    return ((size_t)splits * tiles * TCX_M * NT * sizeof(float2) + 255) / 256 * 256;
+}
+
+jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
+                   cudaStream_t st, void* partials, size_t partial_bytes) {
+    if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    int NT, cps, splits;
+    tcx_cn_config(M, N, K, NT, cps, splits);
+    const bool wide = NT == 256;
+    const int nkc = tcx_chunks(K);
+    const int tiles_m = (M + TCX_M - 1) / TCX_M, tiles = tiles_m * ((N + NT - 1) / NT);
+    float2* part = partials && partial_bytes >= tcx_cn_partial_bytes(M, N, K) ? (float2*)partials : nullptr;
+    dim3 grid(tiles_m, (N + NT - 1) / NT, splits);
     if (wide) {
         auto kern = tcx_cn_kernel<256>;
         cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<256>::SMEM);
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
         Trace tr_("tcx_cn", st);
         kern<<<grid, TCX_THREADS, TcxLayout<256>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
-                                                               cps, out, ldo, alpha);
+                                                               cps, out, ldo, alpha, part);
     } else {
         auto kern = tcx_cn_kernel<128>;
         cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<128>::SMEM);
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
         Trace tr_("tcx_cn", st);
         kern<<<grid, TCX_THREADS, TcxLayout<128>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
-                                                               cps, out, ldo, alpha);
+                                                               cps, out, ldo, alpha, part);
     }
-    return check_launch("tcx_cn");
+    jdft_status s = check_launch("tcx_cn");
+    if (s != JDFT_OK || !part) return s;
+    {
+        Trace tr_("tcx_reduce", st);
+        tcx_reduce_kernel<<<dim3(NT / 2, tiles), dim3(TCX_M, TCX_RZ), 0, st>>>((const float4*)part, splits, tiles_m, NT,
+                                                                               M, N, out, ldo, alpha);
+    }
+    return check_launch("tcx_reduce");
 }
 
 }  // namespace jdft
@@ -1013,11 +1128,6 @@ namespace jdft {
 static jdft_status autotune_tcx(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, int* splits,
                                 cudaStream_t st) {
     const size_t sa = (tcx_split_bytes(M, K) + 255) / 256 * 256, sb = (tcx_split_bytes(N, K) + 255) / 256 * 256;
-    char* mem = nullptr;
-    JDFT_CUDA_TRY(cudaMalloc(&mem, sa + sb + (size_t)M * N * sizeof(double2)));
-    double2* out = (double2*)(mem + sa + sb);
-    jdft_status s = tcx_split(A, lda, M, K, mem, st);
-    if (s == JDFT_OK) s = tcx_split(B, ldb, N, K, mem + sa, st);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1029,6 +1139,18 @@ static jdft_status autotune_tcx(int M, int N, int K, const float2* A, int lda, c
         const int c = std::max(1, wave * f / 100);
         if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
     }
+    // the partial buffer of the largest candidate (the products are timed as
+    // the library runs them, with partial tiles and the reduction)
+    const int cmax = *std::max_element(cand.begin(), cand.end());
+    const size_t ob = ((size_t)M * N * sizeof(double2) + 255) / 256 * 256;
+    const size_t pb = ((size_t)std::max(cmax, tcx_chunks(K) / 256 + 1) * tiles * TCX_M * NT * sizeof(float2) + 255) /
+                      256 * 256;
+    char* mem = nullptr;
+    JDFT_CUDA_TRY(cudaMalloc(&mem, sa + sb + ob + pb));
+    double2* out = (double2*)(mem + sa + sb);
+    void* part = mem + sa + sb + ob;
+    jdft_status s = tcx_split(A, lda, M, K, mem, st);
+    if (s == JDFT_OK) s = tcx_split(B, ldb, N, K, mem + sa, st);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1042,9 +1164,9 @@ static jdft_status autotune_tcx(int M, int N, int K, const float2* A, int lda, c
             g_tune_tcx[key] = c;
         }
         // one untimed call, then three timed ones (the accumulated values are not used)
-        s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st);
+        s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st, part, pb);
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && s == JDFT_OK; ++r) s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st);
+        for (int r = 0; r < 3 && s == JDFT_OK; ++r) s = tcx_cn(M, N, K, mem, mem + sa, out, N, 1.0, st, part, pb);
         cudaEventRecord(e1, st);
         if (s != JDFT_OK) break;
         cudaEventSynchronize(e1);

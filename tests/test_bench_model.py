@@ -96,3 +96,12 @@ def test_split_operand_products_and_split_pass(bench):
     assert bench.kernel_work(p, "tcx_cn", 3, 256) == bench.kernel_work(p, "tc_zgemm_cn", 3, 256)
     fl, by = bench.kernel_work(p, "split_planes", 2, 256)
     assert fl == 0.0 and by == pytest.approx(16.0 * 256 * 62759)
+
+
+def test_split_operand_nn_and_reduction(bench):
+    p = _problem(nb=256, nproj=256)
+    assert bench.kernel_work(p, "tcx_nn", 2, 256) == bench.kernel_work(p, "tc_zgemm_nn", 2, 256)
+    # 76 splits x 2 tiles of 128 x 256 FP32 complex partials, the 256 x 256 FP64 output read and written
+    p.tune = {"splits_subspace": 76}
+    fl, by = bench.kernel_work(p, "tcx_reduce", 3, 256)
+    assert fl == 0.0 and by == pytest.approx(76 * 2 * 128 * 256 * 8 + 2 * 256 * 256 * 16)

@@ -237,6 +237,33 @@ def test_large_sampled_bands(prec):
     jdft.jdft_device_status()
 
 
+def test_split_operand_subspace_full_size_is_deterministic():
+    """C^dag O C and C^dag B on split operands at the benchmark's shape (256
+    bands, 62 759 plane waves, one wave of split-K blocks): the blocks' FP32
+    partial tiles are summed in a fixed order, so two calls agree to
+    the bit, and both agree with the complex128 product of the same FP32
+    inputs within the BF16x3 bound."""
+    from paper_1708_03621_gb300 import jdft
+    w = workload("large")
+    basis = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+    npw, nb = basis.npw(0), 256
+    rng = np.random.default_rng(1708)
+    C = ((rng.standard_normal((nb, npw)) + 1j * rng.standard_normal((nb, npw))) / np.sqrt(npw)).astype(np.complex64)
+    B = ((rng.standard_normal((nb, npw)) + 1j * rng.standard_normal((nb, npw))) / np.sqrt(npw)).astype(np.complex64)
+    Cd, Bd = torch.tensor(C, device="cuda"), torch.tensor(B, device="cuda")
+    out = [torch.empty((nb, nb), dtype=torch.complex128, device="cuda") for _ in range(4)]
+    jdft.jdft_subspace(basis, 0, Cd, Bd, out[0], out[1], "bf16x3")
+    jdft.jdft_subspace(basis, 0, Cd, Bd, out[2], out[3], "bf16x3")
+    got = [host(t) for t in out]
+    assert np.array_equal(got[0], got[2]) and np.array_equal(got[1], got[3])
+    C64 = C.astype(np.complex128)
+    ref_b = C64.conj() @ B.astype(np.complex128).T
+    ref_o = abs(np.linalg.det(np.asarray(w.R, dtype=np.float64))) * (C64.conj() @ C64.T)  # O = cell volume
+    assert rel_max(got[0], ref_b) < TOL["bf16x3"]
+    assert rel_max(got[1], ref_o) < TOL["bf16x3"]
+    jdft.jdft_device_status()
+
+
 _large_ref = {}
 
 
