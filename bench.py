@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library defaults instead of the autotuned chunk budget and split-K counts (profiling)")
     return ap.parse_args()
 
 
@@ -161,7 +163,7 @@ class Clocks:
 class Problem:
     """Device-resident inputs and outputs of one step, built through the C ABI."""
 
-    def __init__(self, wname: str, prec: str, device, nbands: int = 0):
+    def __init__(self, wname: str, prec: str, device, nbands: int = 0, autotune: bool = True):
         import torch
 
         from paper_1708_03621_gb300 import jdft
@@ -203,7 +205,8 @@ class Problem:
         self.ctype = ct
         # the project's autotuner picks the chain's chunk budget and the GEMM
         # split-K schedules for this block before anything is timed
-        self.tune = jdft.jdft_autotune(self.basis, 0, self.C, self.HC, prec) if prec != "fp64" else None
+        self.tune = (jdft.jdft_autotune(self.basis, 0, self.C, self.HC, prec)
+                     if prec != "fp64" and autotune else None)
         # device status word of the asynchronous orthonormalisation, checked after each timed loop
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
 
@@ -268,8 +271,11 @@ def kernel_work(p: Problem, name: str, launches: int, nb: int) -> tuple[float, f
         tiles = -(-p.nb // 128)
         return 0.0, splits * tiles * 128 * 256 * 8.0 + 2 * p.nb * p.nb * 16.0
     if name == "split_planes":
-        # one block of nb rows: FP32 complex read, four BF16 planes written (8 + 8 bytes per value)
-        return 0.0, 16.0 * nb * p.npw
+        # per step: C, H C (nb rows of npw), C's transpose (npw rows of nb), (D P^dag C)'s and W's
+        # transposes (nb rows of nproj, nb); FP32 complex read, four BF16 planes written (8 + 8
+        # bytes per value), averaged over the launches
+        vals = 3.0 * p.nb * p.npw + p.nb * p.nproj + p.nb * p.nb
+        return 0.0, 16.0 * vals / max(1, launches)
     if name in ("plane_apply", "plane_apply_fast", "plane_apply_pair", "plane_apply_density_fast",
                 "plane_apply_density_pair"):
         # the fused kernels do the same transforms; their density adds the n(r) update
@@ -347,7 +353,10 @@ def roofline_of(k: dict, prec: str, peaks: dict, fp32: dict) -> dict:
 # reports null.
 TRAFFIC_SOURCES = {"plane_apply_density_pair": ["csrc/plane_pair.cu", "csrc/fft_pair.cuh", "csrc/fft_reg.cuh",
                                                 "csrc/chain.cuh", "csrc/common.cuh", "csrc/tc_ptx.cuh"]}
-TRAFFIC_PER_BAND = {}
+TRAFFIC_PER_BAND = {
+    # 150 365 440 + 85 946 880 bytes over 64 bands (profiles/plane_apply_density_pair_128cubed_bf16x3.md)
+    "plane_apply_density_pair": (3.6924e6, "ab37b9a6e1d1d474"),
+}
 
 
 def sources_sha(name: str) -> str | None:
@@ -376,7 +385,7 @@ def run_ours(args, world, rank, local, pg):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     fp32 = jdft.jdft_measure_fp32_peak()  # the FFT kernels' arithmetic roofline, on this GPU
-    p = Problem(args.workload, args.prec, dev, args.nbands)
+    p = Problem(args.workload, args.prec, dev, args.nbands, autotune=not args.no_autotune)
     tune = p.tune
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):

@@ -28,6 +28,9 @@ namespace jdft {
 
 constexpr int kFastThreads = 256;
 constexpr int kFastWarps = kFastThreads / 32;
+// z passes: warps per block (LPW columns each)
+constexpr int kZWarps = 8;
+constexpr int kZThreads = 32 * kZWarps;
 
 // i mod N in [0, N) for either sign of i: one bit mask when N is a power of
 // two (two's complement), else a remainder and a correction.
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) plane_apply_density_fast_kern
 // (modulo S2), so a slot p holds sphere entry (p - z0) mod S2 when that is
 // below the column's count.
 template <typename T, int N2, int E2, class R2>
-__global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainGeom g, const c_t<T>* __restrict__ C,
+__global__ void __launch_bounds__(kZThreads) zpass_inverse_fast_kernel(ChainGeom g, const c_t<T>* __restrict__ C,
                                                                           int ldc, c_t<T>* __restrict__ colbuf,
                                                                           const c_t<T>* __restrict__ tw2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -453,7 +456,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainG
     c_t<T>* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<T, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
-    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int c = (blockIdx.x * kZWarps + warp) * LPW + liw;
     const int b = blockIdx.y;
     const bool act = c < g.ncols;
     int q0 = 0, cnt = 0, z0 = 0;
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_fast_kernel(ChainG
 
 // MODE 0: out = omega (kin C + scale y); MODE 1: out = scale y.
 template <typename T, int N2, int E2, class R2, int MODE>
-__global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainGeom g,
+__global__ void __launch_bounds__(kZThreads) zpass_forward_fast_kernel(ChainGeom g,
                                                                           const c_t<T>* __restrict__ colbuf,
                                                                           const c_t<T>* __restrict__ C, int ldc,
                                                                           c_t<T>* __restrict__ out, int ldo,
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainG
     c_t<T>* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<T, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
-    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int c = (blockIdx.x * kZWarps + warp) * LPW + liw;
     const int b = blockIdx.y;
     const bool act = c < g.ncols;
     c_t<T> v[E2];
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_fast_kernel(ChainG
 // blockIdx.y the band, blockIdx.x the block of columns, as in the one-job
 // kernels; blocks beyond a job's columns or bands return at once.
 template <int N2, int E2, class R2>
-__global__ void __launch_bounds__(kFastThreads) zpass_inverse_batch_kernel(const KJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kZThreads) zpass_inverse_batch_kernel(const KJob* __restrict__ jobs,
                                                                            const float2* __restrict__ tw2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using F = LineFFT<float, N2, E2, +1, R2>;
@@ -538,14 +541,14 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_batch_kernel(const
     const KJob& J = jobs[blockIdx.z];
     const ChainGeom& g = J.g;
     const int b = blockIdx.y;
-    if (b >= J.nb || (int)blockIdx.x * kFastWarps * LPW >= g.ncols) return;
+    if (b >= J.nb || (int)blockIdx.x * kZWarps * LPW >= g.ncols) return;
     float2* W = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int liw = LN::line(lane), t = LN::pos(lane);
     float2* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<float, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
-    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int c = (blockIdx.x * kZWarps + warp) * LPW + liw;
     const bool act = c < g.ncols;
     int q0 = 0, cnt = 0, z0 = 0;
     if (act) {
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(kFastThreads) zpass_inverse_batch_kernel(const
 
 // HC = omega (kin C + scale y) for every job.
 template <int N2, int E2, class R2>
-__global__ void __launch_bounds__(kFastThreads) zpass_forward_batch_kernel(const KJob* __restrict__ jobs, float omega,
+__global__ void __launch_bounds__(kZThreads) zpass_forward_batch_kernel(const KJob* __restrict__ jobs, float omega,
                                                                            float scale,
                                                                            const float2* __restrict__ tw2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -579,14 +582,14 @@ __global__ void __launch_bounds__(kFastThreads) zpass_forward_batch_kernel(const
     const KJob& J = jobs[blockIdx.z];
     const ChainGeom& g = J.g;
     const int b = blockIdx.y;
-    if (b >= J.nb || (int)blockIdx.x * kFastWarps * LPW >= g.ncols) return;
+    if (b >= J.nb || (int)blockIdx.x * kZWarps * LPW >= g.ncols) return;
     float2* W = reinterpret_cast<float2*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int liw = LN::line(lane), t = LN::pos(lane);
     float2* scr = W + N2 + (warp * LPW + liw) * ScratchSpacing<float, N2>::value;
     for (int i = threadIdx.x; i < N2; i += blockDim.x) W[i] = tw2[i];
     __syncthreads();
-    const int c = (blockIdx.x * kFastWarps + warp) * LPW + liw;
+    const int c = (blockIdx.x * kZWarps + warp) * LPW + liw;
     const bool act = c < g.ncols;
     float2 v[E2];
 #pragma unroll
@@ -691,13 +694,13 @@ static jdft_status density_fast_impl(const ChainGeom& g, const float2* colbuf, c
 template <typename T, int N2>
 static size_t zpass_fast_smem() {
     constexpr int LPW = Lanes<N2, FastCfg<N2>::E>::LPW;
-    return ((size_t)N2 + (size_t)kFastWarps * LPW * ScratchSpacing<T, N2>::value) * sizeof(c_t<T>);
+    return ((size_t)N2 + (size_t)kZWarps * LPW * ScratchSpacing<T, N2>::value) * sizeof(c_t<T>);
 }
 
 template <int N2>
 static int zpass_fast_blocks(const ChainGeom& g) {
     constexpr int TL = N2 / FastCfg<N2>::E, LPW = 32 / TL;
-    return (g.ncols + kFastWarps * LPW - 1) / (kFastWarps * LPW);
+    return (g.ncols + kZWarps * LPW - 1) / (kZWarps * LPW);
 }
 
 template <typename T, int N2>
@@ -710,7 +713,7 @@ static jdft_status zinv_fast_impl(const ChainGeom& g, const c_t<T>* C, int ldc, 
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_inverse_fast: ") + cudaGetErrorString(e));
     {
         Trace tr_("zpass_inverse", st);
-        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kFastThreads, smem, st>>>(g, C, ldc, colbuf, tw2);
+        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kZThreads, smem, st>>>(g, C, ldc, colbuf, tw2);
     }
     return check_launch("zpass_inverse_fast");
 }
@@ -726,7 +729,7 @@ static jdft_status zfwd_fast_impl(const ChainGeom& g, const c_t<T>* colbuf, cons
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_forward_fast: ") + cudaGetErrorString(e));
     {
         Trace tr_("zpass_forward", st);
-        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kFastThreads, smem, st>>>(g, colbuf, C, ldc, out, ldo, kin, omega,
+        kern<<<dim3(zpass_fast_blocks<N2>(g), nb), kZThreads, smem, st>>>(g, colbuf, C, ldc, out, ldo, kin, omega,
                                                                             scale, tw2);
     }
     return check_launch("zpass_forward_fast");
@@ -849,9 +852,9 @@ jdft_status launch_zpass_inverse_batch(const ChainGeom& g, const KJob* jobs, int
         const size_t smem = zpass_fast_smem<float, a>();                                                         \
         cudaError_t e = set_smem_attr((const void*)kern, smem);                                                  \
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_inverse_batch: ") + cudaGetErrorString(e)); \
-        constexpr int CPB = kFastWarps * (32 / (a / C2::E));                                                     \
+        constexpr int CPB = kZWarps * (32 / (a / C2::E));                                                     \
         Trace tr_("zpass_inverse_batch", st);                                                                    \
-        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kFastThreads, smem, st>>>(jobs, tw2);           \
+        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kZThreads, smem, st>>>(jobs, tw2);           \
         return check_launch("zpass_inverse_batch");                                                              \
     }
     JDFT_FAST_LENGTHS(JDFT_CASE)
@@ -869,9 +872,9 @@ jdft_status launch_zpass_forward_batch(const ChainGeom& g, const KJob* jobs, int
         const size_t smem = zpass_fast_smem<float, a>();                                                         \
         cudaError_t e = set_smem_attr((const void*)kern, smem);                                                  \
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("zpass_forward_batch: ") + cudaGetErrorString(e)); \
-        constexpr int CPB = kFastWarps * (32 / (a / C2::E));                                                     \
+        constexpr int CPB = kZWarps * (32 / (a / C2::E));                                                     \
         Trace tr_("zpass_forward_batch", st);                                                                    \
-        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kFastThreads, smem, st>>>(jobs, omega, scale, tw2); \
+        kern<<<dim3((max_ncols + CPB - 1) / CPB, max_nb, njobs), kZThreads, smem, st>>>(jobs, omega, scale, tw2); \
         return check_launch("zpass_forward_batch");                                                              \
     }
     JDFT_FAST_LENGTHS(JDFT_CASE)

@@ -869,6 +869,19 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     tc::tc_fence_after_sync();
     const uint32_t tmem = *tslot;
     const unsigned long long wait_ns = g_tc_wait_ns;
+    // accumulating: the old values of this thread's output row m, 64 columns at a
+    // time; the first 64 are requested now, so their latency passes during the products
+    const int m = m0 + warp * 32 + lane;
+    constexpr int OG = ACC ? 64 : 1;
+    float2 old[OG];
+    auto load_old = [&](int col0) {
+#pragma unroll
+        for (int j = 0; j < OG; ++j) {
+            const int n = n0 + col0 + j;
+            old[j] = (m < M && n < N) ? out[(size_t)n * ldo + m] : make_float2(0.f, 0.f);
+        }
+    };
+    if (ACC) load_old(0);
     if (tid == 0) {
         int it = 0;
         for (; it < nit; ++it) {
@@ -947,22 +960,40 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     }
     tc::tc_fence_after_sync();
     if (ok) {
-        const int m = m0 + warp * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        if constexpr (ACC) {
+            // groups of 64 columns: the group's old values were requested before its
+            // four slices (one latency per group, the first one hidden)
 #pragma unroll 1
-        for (int col = 0; col < NT && n0 + col < N; col += 16) {
-            float re[16], im[16];
-            tc::tmem_ld16(lane_base + col, re);
-            tc::tmem_ld16(lane_base + NT + col, im);
-            if (m < M) {
-                float2 v[16];
-                // all old values first: one latency for the slice, not one per column
+            for (int g = 0; g < NT && n0 + g < N; g += 64) {
+                if (g > 0) load_old(g);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    v[j] = (ACC && n0 + col + j < N) ? out[(size_t)(n0 + col + j) * ldo + m] : make_float2(0.f, 0.f);
+                for (int q = 0; q < 64; q += 16) {
+                    const int col = g + q;
+                    if (n0 + col >= N) break;
+                    float re[16], im[16];
+                    tc::tmem_ld16(lane_base + col, re);
+                    tc::tmem_ld16(lane_base + NT + col, im);
+                    if (m < M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (n0 + col + j < N) out[(size_t)(n0 + col + j) * ldo + m] = make_float2(v[j].x + re[j], v[j].y + im[j]);
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + col + j < N)
+                                out[(size_t)(n0 + col + j) * ldo + m] =
+                                    make_float2(old[q + j].x + re[j], old[q + j].y + im[j]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int col = 0; col < NT && n0 + col < N; col += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(lane_base + col, re);
+                tc::tmem_ld16(lane_base + NT + col, im);
+                if (m < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + col + j < N) out[(size_t)(n0 + col + j) * ldo + m] = make_float2(re[j], im[j]);
+                }
             }
         }
     }

@@ -54,21 +54,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-// ---- bulk tensor copies (TMA) ---------------------------------------------------
-// 3-D tiled load of the box at coordinates (c0, c1, c2) of the tensor map into
-// shared memory at dst; completion is reported to `bar` as transaction bytes.
-// c0 (the innermost coordinate) times the element size must be a multiple of
-// 16 bytes.
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int c0, int c1, int c2, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_map(const void* map) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
 // ---- proxies and tcgen05 ordering ----------------------------------------
 // Make this thread's generic-proxy shared-memory writes visible to the async proxy (tensor cores).
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -104,19 +89,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
     // base offset 0, absolute lbo mode 0, layout type 0 = no swizzle
-    return d;
-}
-
-// Shared-memory matrix descriptor for a K-major tile written by TMA with
-// 32-byte swizzling: rows of 32 bytes (16 BF16 values, one instruction's K),
-// 8-row groups 256 bytes apart.  The tile must start on a 256-byte boundary.
-__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;               // leading byte offset (unused with a one-atom K extent)
-    d |= (uint64_t)(256 >> 4) << 32;      // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;               // descriptor version for tcgen05
-    d |= (uint64_t)6 << 61;               // layout: 32-byte swizzle
     return d;
 }
 

@@ -94,8 +94,9 @@ def test_traffic_figure_is_dropped_when_the_kernel_changes(bench, monkeypatch):
 def test_split_operand_products_and_split_pass(bench):
     p = _problem(nb=256, nproj=256)
     assert bench.kernel_work(p, "tcx_cn", 3, 256) == bench.kernel_work(p, "tc_zgemm_cn", 3, 256)
-    fl, by = bench.kernel_work(p, "split_planes", 2, 256)
-    assert fl == 0.0 and by == pytest.approx(16.0 * 256 * 62759)
+    # five splits per step: C, H C, C's transpose (256 x 62 759 values each), two 256 x 256
+    fl, by = bench.kernel_work(p, "split_planes", 5, 256)
+    assert fl == 0.0 and by == pytest.approx(16.0 * (3 * 256 * 62759 + 2 * 256 * 256) / 5)
 
 
 def test_split_operand_nn_and_reduction(bench):
