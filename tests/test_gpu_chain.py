@@ -374,6 +374,38 @@ def test_generic_plane_kernels_match_oracle(name, prec, monkeypatch):
     assert np.max(np.abs(n.cpu().numpy() - ref)) / np.max(ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("name", ["tiny_ortho", "large"])
+def test_one_band_plane_kernels_match_band_pair_kernels(name, monkeypatch):
+    """FP32 blocks with the band-pair plane kernels switched off run the
+    one-band register-FFT kernels: same transforms, one band per lane, so the
+    same H C and density up to FP32 rounding order, and both match the oracle
+    (sampled bands on the 128^3 box)."""
+    w, o, g = systems(name) if name != "large" else (workload("large"), None, None)
+    from paper_1708_03621_gb300 import jdft
+    if name == "large":
+        o = _large_ref.setdefault("o", OracleSystem(w))
+        g = GpuSystem(w, o.atoms)
+    C = o.coeffs()
+    nb = C.shape[0]
+    f = torch.tensor(np.linspace(2.0, 0.5, nb), device="cuda")
+    Cd = to_dev(C, "fp32")
+    out = {}
+    for mode in ("pair", "one"):
+        if mode == "one":
+            monkeypatch.setenv("JDFT_PAIR_PLANE", "0")
+        HC = torch.empty_like(Cd)
+        n = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+        jdft.jdft_apply_H_density(g.basis, 0, Cd, HC, f, n, "fp32")
+        out[mode] = (host(HC), n.cpu().numpy())
+    assert rel_max(out["one"][0], out["pair"][0]) < SAME["fp32"] * 10
+    assert np.max(np.abs(out["one"][1] - out["pair"][1])) / np.max(np.abs(out["pair"][1])) < 1e-6
+    sample = [0, nb // 2, nb - 1] if name == "large" else list(range(nb))
+    ref = o.apply_H(C[sample])
+    for mode in out:
+        assert band_rel_err(out[mode][0][sample], ref) < TOL["fp32"]
+    jdft.jdft_device_status()
+
+
 @pytest.mark.parametrize("name,prec", [("mid", "fp64"), ("mid", "bf16x3"), ("large", "bf16x3"), ("large", "fp32")])
 def test_hamiltonian_step_equals_separate_calls(name, prec):
     """jdft_hamiltonian_step (rows a1-a9 in one call, the overlap factored on a
