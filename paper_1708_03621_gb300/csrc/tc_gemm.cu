@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1003,6 +1004,228 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     if (!ok && nit > 0 && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
 }
 
+// Persistent X.Y products for N > 128 (tcx_nn with 256-column tiles): one
+// block per SM walks a list of work items, so that the copies of an item's
+// first stages overlap the previous item's epilogue and every block finishes
+// at about the same time.  The list holds the r * P full tiles (128 rows x 256
+// columns; P blocks, r = floor(tiles / P)) and then, when N is a multiple of
+// 256, the remaining R tiles split into 2 R half tiles of 128 columns (else
+// they stay whole); block p takes items p, p + P, p + 2P ...
+// Roles: warps 0-3 drain tensor memory (warp w: rows 32 w .. 32 w + 31), warp
+// 4 issues the copies of the 4-stage ring, warp 5 the MMAs.  The MMA warp
+// starts an item once the four epilogue warps have released tensor memory
+// (barrier tfree, 4 arrivals); the epilogue starts once the item's products
+// have completed (barrier accfull).  Re accumulates at tensor-memory columns
+// [0, nt), Im at [256, 256 + nt).  Every wait is bounded; a role whose wait
+// gives up stops the others, and the block waits for its issued copies and
+// products (drain limit) before freeing tensor memory.
+constexpr int TCXP_THREADS = 192;
+
+struct TcxItem {
+    int m0, n0, nt;
+};
+
+// Tile t covers rows 128 (t / nblk) and columns 256 (t mod nblk) of the output.
+__device__ __forceinline__ bool tcxp_item(int j, int full_tiles, int halves, int nblk, TcxItem& item) {
+    const int idx = blockIdx.x + j * gridDim.x;
+    int t = idx, half = -1;
+    if (idx >= full_tiles) {
+        const int h = idx - full_tiles;
+        if (h >= halves) return false;
+        t = full_tiles + h / 2;
+        half = h & 1;
+    }
+    const int mt = t / nblk, nt = t - mt * nblk;
+    item = {mt * TCX_M, nt * 256 + (half > 0 ? 128 : 0), half < 0 ? 256 : 128};
+    return true;
+}
+
+__device__ __forceinline__ void tcxp_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(TCXP_THREADS, 1)
+    tcx_nn_persist_kernel(const char* __restrict__ As, const char* __restrict__ Bs, int M, int N, int nkc,
+                          float2* __restrict__ out, int ldo, int full_tiles, int halves) {
+    const int rpA = (M + TCX_M - 1) / TCX_M * TCX_M, rpB = (N + TCX_M - 1) / TCX_M * TCX_M;
+    const int nblk = (N + 255) / 256;
+    using L = TcxLayout<256>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+    uint64_t* empty = full + TCX_STAGES;
+    uint64_t* accfull = empty + TCX_STAGES;
+    uint64_t* tfree = accfull + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tfree + 1);
+    volatile int* flags = reinterpret_cast<volatile int*>(tslot + 1);  // 0: failed, 1: stages loaded, 2: committed
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < TCX_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accfull, 1);
+        tc::mbar_init(tfree, 4);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, L::NCOLS);
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const unsigned long long wait_ns = g_tc_wait_ns;
+    TcxItem item;
+    if (warp == 4) {
+        if (lane == 0) {
+            int it = 0;
+            for (int j = 0; !flags[0] && tcxp_item(j, full_tiles, halves, nblk, item); ++j) {
+                const uint32_t bbytes = (uint32_t)min(item.nt, rpB - item.n0) * TCX_KC * 2;
+                for (int k = 0; k < nkc; ++k) {
+                    const int s = it % TCX_STAGES;
+                    const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+                    if (!tc::mbar_wait_ns(&empty[s], par ^ 1u, wait_ns)) {
+                        flags[0] = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + s * L::STAGE;
+                    tc::mbar_arrive_expect_tx(&full[s], (uint32_t)(4 * L::A_PL) + 4 * bbytes);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        bulk_load(st + q * L::A_PL, As + ((size_t)(k * 4 + q) * rpA + item.m0) * (TCX_KC * 2), L::A_PL,
+                                  &full[s]);
+                        bulk_load(st + L::A_BYTES + q * L::B_PL,
+                                  Bs + ((size_t)(k * 4 + q) * rpB + item.n0) * (TCX_KC * 2), bbytes, &full[s]);
+                    }
+                    ++it;
+                }
+            }
+            flags[1] = it;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t id256 = tc::instr_desc(1u, TCX_M, 256), id128 = tc::instr_desc(1u, TCX_M, 128);
+            int it = 0;
+            for (int j = 0; !flags[0] && tcxp_item(j, full_tiles, halves, nblk, item); ++j) {
+                if (j > 0 && !tc::mbar_wait_ns(tfree, (uint32_t)((j - 1) & 1), wait_ns)) {
+                    flags[0] = 1;
+                    break;
+                }
+                tc::tc_fence_after_sync();
+                const uint32_t idesc = item.nt == 256 ? id256 : id128;
+                const uint32_t idesc_neg = idesc | (1u << 13);  // negate A
+                bool fail = false;
+                for (int k = 0; k < nkc; ++k) {
+                    const int s = it % TCX_STAGES;
+                    const uint32_t par = (uint32_t)((it / TCX_STAGES) & 1);
+                    if (!tc::mbar_wait_ns(&full[s], par, wait_ns)) {
+                        fail = true;
+                        break;
+                    }
+                    tc::tc_fence_after_sync();
+                    const uint32_t base = tc::smem_addr(smem + s * L::STAGE);
+                    uint64_t a[4], b[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        a[q] = tc::smem_desc(base + q * L::A_PL, 128, 256);
+                        b[q] = tc::smem_desc(base + L::A_BYTES + q * L::B_PL, 128, 256);
+                    }
+                    const uint32_t acc = k > 0 ? 1u : 0u;
+                    const uint32_t re = tmem, im = tmem + 256;
+                    // planes: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo
+                    tc::mma_bf16(re, a[0], b[0], idesc, acc);
+                    tc::mma_bf16(re, a[0], b[1], idesc, 1u);
+                    tc::mma_bf16(re, a[1], b[0], idesc, 1u);
+                    tc::mma_bf16(re, a[2], b[2], idesc_neg, 1u);
+                    tc::mma_bf16(re, a[2], b[3], idesc_neg, 1u);
+                    tc::mma_bf16(re, a[3], b[2], idesc_neg, 1u);
+                    tc::mma_bf16(im, a[0], b[2], idesc, acc);
+                    tc::mma_bf16(im, a[0], b[3], idesc, 1u);
+                    tc::mma_bf16(im, a[1], b[2], idesc, 1u);
+                    tc::mma_bf16(im, a[2], b[0], idesc, 1u);
+                    tc::mma_bf16(im, a[2], b[1], idesc, 1u);
+                    tc::mma_bf16(im, a[3], b[0], idesc, 1u);
+                    tc::mma_commit(&empty[s]);
+                    ++it;
+                }
+                if (fail) {
+                    flags[0] = 1;
+                    break;
+                }
+                tc::mma_commit(accfull);
+            }
+            flags[2] = it;
+        }
+    } else {
+        // epilogue: thread (warp w, lane l) owns output row m = m0 + 32 w + l of each item
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        constexpr int OG = ACC ? 64 : 1;
+        float2 old[OG];
+        for (int j = 0; tcxp_item(j, full_tiles, halves, nblk, item); ++j) {
+            const int m = item.m0 + warp * 32 + lane;
+            auto load_old = [&](int col0) {
+#pragma unroll
+                for (int q = 0; q < OG; ++q) {
+                    const int n = item.n0 + col0 + q;
+                    old[q] = (m < M && n < N) ? out[(size_t)n * ldo + m] : make_float2(0.f, 0.f);
+                }
+            };
+            if (ACC) load_old(0);  // requested while the item's products run
+            int ok = 0;
+            if (lane == 0) ok = tc::mbar_wait_ns(accfull, (uint32_t)(j & 1), wait_ns) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok || flags[0]) {
+                flags[0] = 1;
+                break;
+            }
+            tc::tc_fence_after_sync();
+#pragma unroll 1
+            for (int g = 0; g < item.nt && item.n0 + g < N; g += 64) {
+                if (ACC && g > 0) load_old(g);
+#pragma unroll
+                for (int q = 0; q < 64; q += 16) {
+                    const int col = g + q;
+                    if (item.n0 + col >= N) break;
+                    float re[16], im[16];
+                    tc::tmem_ld16(lane_base + col, re);
+                    tc::tmem_ld16(lane_base + 256 + col, im);
+                    if (m < M) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int n = item.n0 + col + i;
+                            if (n < N)
+                                out[(size_t)n * ldo + m] = ACC ? make_float2(old[q + i].x + re[i], old[q + i].y + im[i])
+                                                               : make_float2(re[i], im[i]);
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tcxp_arrive(tfree);
+        }
+    }
+    __syncthreads();
+    const bool failed = flags[0] != 0;
+    if (failed && tid == 0) {
+        // drain: copies issued but never consumed, and the last committed batch of products
+        const int loaded = flags[1], committed = flags[2];
+        for (int it = committed; it < loaded; ++it)
+            tc::mbar_wait_ns(&full[it % TCX_STAGES], (uint32_t)((it / TCX_STAGES) & 1), TC_DRAIN_NS);
+        if (committed > 0)
+            tc::mbar_wait_ns(&empty[(committed - 1) % TCX_STAGES], (uint32_t)(((committed - 1) / TCX_STAGES) & 1),
+                             TC_DRAIN_NS);
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::NCOLS);
+    if (failed && tid == 0) atomicExch(&g_tc_status, (int)JDFT_ERR_TIMEOUT);
+}
+
 template <int NT, bool ACC>
 static jdft_status launch_tcx_nn(int M, int N, int nkc, const void* Aplanes, const void* Bplanes, float2* out,
                                  int ldo, cudaStream_t st) {
@@ -1018,13 +1241,46 @@ static jdft_status launch_tcx_nn(int M, int N, int nkc, const void* Aplanes, con
     return check_launch("tcx_nn");
 }
 
+static bool getenv_zero(const char* name) {
+    const char* e = getenv(name);
+    return e && e[0] == '0';
+}
+
+template <bool ACC>
+static jdft_status launch_tcx_nn_persist(int M, int N, int nkc, const void* Aplanes, const void* Bplanes, float2* out,
+                                         int ldo, int blocks, int full_tiles, int halves, cudaStream_t st) {
+    auto kern = tcx_nn_persist_kernel<ACC>;
+    cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<256>::SMEM);
+    if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_nn: ") + cudaGetErrorString(e));
+    {
+        Trace tr_("tcx_nn", st);
+        kern<<<blocks, TCXP_THREADS, TcxLayout<256>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
+                                                                 out, ldo, full_tiles, halves);
+    }
+    return check_launch("tcx_nn");
+}
+
 jdft_status tcx_nn(int M, int N, int K, const void* Aplanes, const void* Bplanes, float2* out, int ldo,
                    bool accumulate, cudaStream_t st) {
     if (M == 0 || N == 0) return JDFT_OK;
     const int nkc = tcx_chunks(K);
-    if (N > 128)
+    if (N > 128) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int tiles = (M + TCX_M - 1) / TCX_M * ((N + 255) / 256);
+        if (tiles >= sms && !getenv_zero("JDFT_NN_PERSIST")) {
+            const bool split = N % 256 == 0;
+            const int full_tiles = split ? tiles / sms * sms : tiles;
+            const int halves = 2 * (tiles - full_tiles);
+            return accumulate ? launch_tcx_nn_persist<true>(M, N, nkc, Aplanes, Bplanes, out, ldo, sms, full_tiles,
+                                                            halves, st)
+                              : launch_tcx_nn_persist<false>(M, N, nkc, Aplanes, Bplanes, out, ldo, sms, full_tiles,
+                                                             halves, st);
+        }
         return accumulate ? launch_tcx_nn<256, true>(M, N, nkc, Aplanes, Bplanes, out, ldo, st)
                           : launch_tcx_nn<256, false>(M, N, nkc, Aplanes, Bplanes, out, ldo, st);
+    }
     return accumulate ? launch_tcx_nn<128, true>(M, N, nkc, Aplanes, Bplanes, out, ldo, st)
                       : launch_tcx_nn<128, false>(M, N, nkc, Aplanes, Bplanes, out, ldo, st);
 }

@@ -50,7 +50,8 @@ def test_wait_limit_runs_out_and_context_survives(prec):
 
 def test_wait_limit_runs_out_in_split_operand_products():
     """The same for the BF16x3 subspace products that read split operands
-    through the TMA-fed pipeline (40 bands: both dimensions above 32)."""
+    through the ring fed by bulk asynchronous copies (40 bands: both
+    dimensions above 32)."""
     from paper_1708_03621_gb300 import jdft
     w = workload("mid")
     o = OracleSystem(w)
@@ -78,3 +79,32 @@ def test_wait_limit_runs_out_in_split_operand_products():
     assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 1e-6
     HCo = o.apply_H(C)
     assert np.max(np.abs(a - C.conj() @ HCo.T)) / np.max(np.abs(b)) < 2e-5
+
+
+def test_wait_limit_runs_out_in_persistent_products():
+    """The same on the 128^3 block (62 759 plane waves, 256 bands), where
+    P (D P^dag C) runs as the persistent product with separate copy, MMA and
+    epilogue warps: every role gives up, the block drains and frees its
+    tensor memory, and the next call is exact again."""
+    from paper_1708_03621_gb300 import jdft
+    w = workload("large")
+    o = OracleSystem(w)
+    g = GpuSystem(w, o.atoms)
+    Cd = torch.tensor(o.coeffs().astype(np.complex64), device="cuda")
+    ref = torch.empty_like(Cd)
+    jdft.jdft_apply_H(g.basis, 0, Cd, ref, "bf16x3")
+    jdft.jdft_device_status()
+    out = torch.zeros_like(Cd)
+    jdft.jdft_set_wait_limit(0.0)
+    try:
+        jdft.jdft_apply_H(g.basis, 0, Cd, out, "bf16x3")
+        with pytest.raises(jdft.JdftError) as err:
+            jdft.jdft_device_status()
+        assert err.value.status == jdft.STATUS_CODES["ERR_TIMEOUT"]
+    finally:
+        jdft.jdft_set_wait_limit(2.0)
+    jdft.jdft_device_status()
+    jdft.jdft_apply_H(g.basis, 0, Cd, out, "bf16x3")
+    jdft.jdft_device_status()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
