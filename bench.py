@@ -594,6 +594,9 @@ def cg_measurements(prec: str, device, log=lambda *_: None) -> dict:
     per_it = max(1e-9, (wall[6] - wall[2]) / 4)
     out["large_iteration_ms"] = round(per_it * 1e3, 3)
     out["large_iteration_band_applies_per_s"] = round(w.nbands / per_it, 1)
+    wts = learned.load_weights()
+    net = jdft.Mlp(wts) if wts is not None else None
+    out["large_kernels"] = cg_kernel_shares(b, C0, prec, "mlp" if net is not None else "teter", net, iters=6)
     b.close()
     del C0, C
     w = WORKLOADS["small"]
@@ -772,10 +775,36 @@ def slab_measurements(prec: str, device) -> dict:
         del C
     out["cg_preconditioner"] = pc
     out["cg_iteration_ms"] = round(max(1e-9, (wall[4] - wall[2]) / 2) * 1e3, 3)
+    out["cg_kernels"] = cg_kernel_shares(b, C0, prec, pc, mlp, iters=4)
     del blocks
     b.close()
     torch.cuda.empty_cache()
     return out
+
+
+def cg_kernel_shares(b, C0, prec, precond, mlp, iters: int = 4, top: int = 10) -> dict:
+    """Per-kernel time of a few band-CG iterations (library tracing, CUDA
+    events around every launch): where an iteration's time goes, including
+    the preconditioner network's kernels when it is used."""
+    import torch
+
+    from paper_1708_03621_gb300 import jdft
+    C = C0.to(torch.complex128).clone()
+    torch.cuda.synchronize()
+    jdft.jdft_profile_read()
+    jdft.jdft_profile_enable(True)
+    t0 = time.perf_counter()
+    jdft.jdft_minimize_bands(b, 0, C, tol=1e-30, max_iter=iters, precond=precond, prec=prec, switch_tol=1e-30,
+                             check=False, mlp=mlp)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    jdft.jdft_profile_enable(False)
+    prof = jdft.jdft_profile_read()
+    del C
+    rows = sorted(prof.items(), key=lambda kv: -kv[1][1])[:top]
+    return {"iterations": iters, "preconditioner": precond, "wall_ms": round(wall * 1e3, 3),
+            "kernels": [{"name": n, "launches": c, "ms": round(ms, 3), "share_of_wall": round(ms / (wall * 1e3), 4)}
+                        for n, (c, ms) in rows]}
 
 
 def precision_errors(q) -> dict:

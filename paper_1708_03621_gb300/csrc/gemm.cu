@@ -317,7 +317,8 @@ extern "C" jdft_status jdft_subspace(jdft_basis_t b, int ik, const void* C, int 
         }
         if (COC) {
             JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
-            if ((s = tcx_cn(nb, nb, npw, ws, ws, (double2*)COC, nb, b->omega, st, ws + sb, pb))) return s;
+            if ((s = tcx_cn(nb, nb, npw, ws, ws, (double2*)COC, nb, b->omega, st, ws + sb, pb, true)))
+                return s;
         }
         return JDFT_OK;
     }

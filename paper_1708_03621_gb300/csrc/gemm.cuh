@@ -49,10 +49,13 @@ jdft_status tcx_nn(int M, int N, int K, const void* Aplanes, const void* Bplanes
 // aligned) the blocks' FP32 partial tiles are stored there and summed (with
 // compensated FP32 sums, in a fixed order) by a second kernel; without, they
 // are added to out with FP64 atomics.  Either way out accumulates, so zero it
-// first for a product.
+// first for a product.  hermitian (M == N, with partials): the product is
+// Hermitian by construction (C^dag O C, or C^dag H C with H C = H C exactly),
+// so only the upper-triangle 128 x 128 tiles are formed and the reduction
+// mirrors them; the partial tiles then need at most tcx_cn_partial_bytes.
 size_t tcx_cn_partial_bytes(int M, int N, int K);
 jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
-                   cudaStream_t st, void* partials = nullptr, size_t partial_bytes = 0);
+                   cudaStream_t st, void* partials = nullptr, size_t partial_bytes = 0, bool hermitian = false);
 
 // Precision dispatch: JDFT_TF32X3 and JDFT_BF16X3 run the tensor-core
 // versions (T = float only), the other precisions the CUDA-core ones.

@@ -685,7 +685,8 @@ static jdft_status orthonormalize_impl(jdft_basis_s* b, int ik, void* C, int ldc
             // the same split-operand product jdft_subspace forms C^dag O C with
             void* planes = q + sm + wbytes + lab + blk + 256;
             if ((s = tcx_split((const float2*)C, ldc, nb, npw, planes, st))) return s;
-            if ((s = tcx_cn(nb, nb, npw, planes, planes, U, nb, b->omega, st, (char*)planes + spl, pb))) return s;
+            if ((s = tcx_cn(nb, nb, npw, planes, planes, U, nb, b->omega, st, (char*)planes + spl, pb, true)))
+                return s;
         } else if ((s = gemm_cn<T>(prec, nb, nb, npw, (const c_t<T>*)C, ldc, (const c_t<T>*)C, ldc, U, nb, b->omega,
                                    st))) {
             return s;
@@ -784,7 +785,7 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     JDFT_CUDA_TRY(cudaMemsetAsync(COC, 0, (size_t)nb * nb * sizeof(double2), st));
     if (split) {
         if ((s = tcx_split((const float2*)C, ldc, nb, npw, Cs, st))) return s;
-        if ((s = tcx_cn(nb, nb, npw, Cs, Cs, COC, nb, b->omega, st, part, pb))) return s;
+        if ((s = tcx_cn(nb, nb, npw, Cs, Cs, COC, nb, b->omega, st, part, pb, true))) return s;
     } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, Cc, ldc, COC, nb, b->omega, st))) {
         return s;
     }
@@ -803,7 +804,8 @@ static jdft_status hamiltonian_step_impl(jdft_basis_s* b, int ik, void* C, int l
     JDFT_CUDA_TRY(cudaMemsetAsync(CHC, 0, (size_t)nb * nb * sizeof(double2), st));
     if (split) {
         if ((s = tcx_split((const float2*)HC, ldhc, nb, npw, HCs, st))) return s;
-        if ((s = tcx_cn(nb, nb, npw, Cs, HCs, CHC, nb, 1.0, st, part, pb))) return s;
+        // H C is this step's own H C, so C^dag H C is Hermitian up to rounding
+        if ((s = tcx_cn(nb, nb, npw, Cs, HCs, CHC, nb, 1.0, st, part, pb, true))) return s;
     } else if ((s = gemm_cn<T>(prec, nb, nb, npw, Cc, ldc, (const c_t<T>*)HC, ldhc, CHC, nb, 1.0, st))) {
         return s;
     }

@@ -585,10 +585,21 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+// Tile t of the upper triangle of an nt x nt grid of tiles, counted row by row
+// ((0, 0) .. (0, nt - 1), (1, 1) ..): its tile row tm and column tn >= tm.
+__host__ __device__ inline void tcx_upper_tile(int t, int nt, int& tm, int& tn) {
+    tm = 0;
+    while (t >= nt - tm) {
+        t -= nt - tm;
+        ++tm;
+    }
+    tn = tm + t;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(TCX_THREADS, 1)
     tcx_cn_kernel(const char* __restrict__ As, const char* __restrict__ Bs, int M, int N, int nkc, int cps,
-                  double2* __restrict__ out, int ldo, double alpha, float2* __restrict__ part) {
+                  double2* __restrict__ out, int ldo, double alpha, float2* __restrict__ part, int upper_nt) {
     // rows of the split blocks (padded to 128)
     const int rpA = (M + TCX_M - 1) / TCX_M * TCX_M, rpB = (N + TCX_M - 1) / TCX_M * TCX_M;
     using L = TcxLayout<NT>;
@@ -601,7 +612,11 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(accbar + 1);
     volatile int* flags = reinterpret_cast<volatile int*>(tslot + 1);  // 0: failed, 1: stages loaded, 2: committed
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TCX_M, n0 = blockIdx.y * NT;
+    // upper_nt > 0: the grid's x index runs over the upper-triangle tiles of an
+    // upper_nt x upper_nt tile grid (a Hermitian product's other tiles are its mirror)
+    int tm = blockIdx.x, tn = blockIdx.y;
+    if (upper_nt > 0) tcx_upper_tile(blockIdx.x, upper_nt, tm, tn);
+    const int m0 = tm * TCX_M, n0 = tn * NT;
     // B rows this block copies (the last column block may hold fewer than NT)
     const uint32_t bbytes = (uint32_t)min(NT, rpB - n0) * TCX_KC * 2;
     const int c0 = blockIdx.z * cps;
@@ -709,7 +724,7 @@ __global__ void __launch_bounds__(TCX_THREADS, 1)
         // the partial buffer is [tile][column pair][split][row], one 16-byte entry (Re, Im
         // of column 2 j, Re, Im of column 2 j + 1) per row, so that the splits of a column
         // pair are contiguous for the reduction
-        const size_t tile = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        const size_t tile = upper_nt > 0 ? (size_t)blockIdx.x : (size_t)blockIdx.y * gridDim.x + blockIdx.x;
         float4* P = reinterpret_cast<float4*>(part) + (tile * (NT / 2) * gridDim.z + blockIdx.z) * TCX_M + warp * 32 +
                     lane;
         const size_t jstride = (size_t)gridDim.z * TCX_M;
@@ -778,11 +793,13 @@ struct Sum2 {
 // and 2 j + 1 of row r with compensated FP32 sums, and the TCX_RZ sums of a
 // row are combined in q order, so the result does not depend on timing.  The
 // sums are formed to about 2^-44 of the sum of the terms' magnitudes, then
-// rounded to FP64.
+// rounded to FP64.  upper_nt > 0: the tiles are the upper triangle of an
+// upper_nt x upper_nt tile grid of a Hermitian product, and each off-diagonal
+// tile is also added, conjugated, at its mirror position.
 constexpr int TCX_RZ = 8;
 __global__ void __launch_bounds__(TCX_M* TCX_RZ)
     tcx_reduce_kernel(const float4* __restrict__ part, int splits, int tiles_m, int NT, int M, int N,
-                      double2* __restrict__ out, int ldo, double alpha) {
+                      double2* __restrict__ out, int ldo, double alpha, int upper_nt) {
     __shared__ float4 sum[TCX_RZ][2][TCX_M];
     const int r = threadIdx.x, q = threadIdx.y;
     const int j = blockIdx.x, tile = blockIdx.y;
@@ -819,11 +836,19 @@ __global__ void __launch_bounds__(TCX_M* TCX_RZ)
         y.add(u.z);
         y.add(u.w);
     }
-    const int m = (tile % tiles_m) * TCX_M + r, n = (tile / tiles_m) * NT + 2 * j + q;
+    int tm = tile % tiles_m, tn = tile / tiles_m;
+    if (upper_nt > 0) tcx_upper_tile(tile, upper_nt, tm, tn);
+    const int m = tm * TCX_M + r, n = tn * NT + 2 * j + q;
     if (m < M && n < N) {
+        const double re = alpha * ((double)x.s + (double)x.c), im = alpha * ((double)y.s + (double)y.c);
         double2* o = out + (size_t)m * ldo + n;
-        o->x += alpha * ((double)x.s + (double)x.c);
-        o->y += alpha * ((double)y.s + (double)y.c);
+        o->x += re;
+        o->y += im;
+        if (upper_nt > 0 && tm != tn) {
+            double2* t = out + (size_t)n * ldo + m;
+            t->x += re;
+            t->y -= im;
+        }
     }
 }
 
@@ -1350,8 +1375,39 @@ size_t tcx_cn_partial_bytes(int M, int N, int K) {
 }
 
 jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes, double2* out, int ldo, double alpha,
-                   cudaStream_t st, void* partials, size_t partial_bytes) {
+                   cudaStream_t st, void* partials, size_t partial_bytes, bool hermitian) {
     if (M == 0 || N == 0 || K == 0) return JDFT_OK;
+    if (hermitian && M == N && N > 128 && partials) {
+        // the upper-triangle 128 x 128 tiles only, each over a share of K; the
+        // reduction mirrors the off-diagonal ones
+        const int nt = (N + TCX_M - 1) / TCX_M, tiles = nt * (nt + 1) / 2;
+        const int nkc = tcx_chunks(K);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int capmin = (nkc + 4096 / TCX_KC - 1) / (4096 / TCX_KC);
+        int splits = std::max(capmin, std::min(nkc, std::max(1, sms / tiles)));
+        const int cps = (nkc + splits - 1) / splits;
+        splits = (nkc + cps - 1) / cps;
+        if ((size_t)splits * tiles * TCX_M * 128 * sizeof(float2) <= partial_bytes) {
+            auto kern = tcx_cn_kernel<128>;
+            cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<128>::SMEM);
+            if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
+            {
+                Trace tr_("tcx_cn", st);
+                kern<<<dim3(tiles, 1, splits), TCX_THREADS, TcxLayout<128>::SMEM, st>>>(
+                    (const char*)Aplanes, (const char*)Bplanes, M, N, nkc, cps, out, ldo, alpha, (float2*)partials, nt);
+            }
+            jdft_status s = check_launch("tcx_cn");
+            if (s != JDFT_OK) return s;
+            {
+                Trace tr_("tcx_reduce", st);
+                tcx_reduce_kernel<<<dim3(64, tiles), dim3(TCX_M, TCX_RZ), 0, st>>>(
+                    (const float4*)partials, splits, nt, 128, M, N, out, ldo, alpha, nt);
+            }
+            return check_launch("tcx_reduce");
+        }
+    }
     int NT, cps, splits;
     tcx_cn_config(M, N, K, NT, cps, splits);
     const bool wide = NT == 256;
@@ -1365,21 +1421,21 @@ jdft_status tcx_cn(int M, int N, int K, const void* Aplanes, const void* Bplanes
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
         Trace tr_("tcx_cn", st);
         kern<<<grid, TCX_THREADS, TcxLayout<256>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
-                                                               cps, out, ldo, alpha, part);
+                                                               cps, out, ldo, alpha, part, 0);
     } else {
         auto kern = tcx_cn_kernel<128>;
         cudaError_t e = set_smem_attr((const void*)kern, TcxLayout<128>::SMEM);
         if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string("tcx_cn: ") + cudaGetErrorString(e));
         Trace tr_("tcx_cn", st);
         kern<<<grid, TCX_THREADS, TcxLayout<128>::SMEM, st>>>((const char*)Aplanes, (const char*)Bplanes, M, N, nkc,
-                                                               cps, out, ldo, alpha, part);
+                                                               cps, out, ldo, alpha, part, 0);
     }
     jdft_status s = check_launch("tcx_cn");
     if (s != JDFT_OK || !part) return s;
     {
         Trace tr_("tcx_reduce", st);
         tcx_reduce_kernel<<<dim3(NT / 2, tiles), dim3(TCX_M, TCX_RZ), 0, st>>>((const float4*)part, splits, tiles_m, NT,
-                                                                               M, N, out, ldo, alpha);
+                                                                               M, N, out, ldo, alpha, 0);
     }
     return check_launch("tcx_reduce");
 }

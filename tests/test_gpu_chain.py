@@ -441,7 +441,16 @@ def test_hamiltonian_step_equals_separate_calls(name, prec):
     assert int(st1.item()) == 0 and int(st2.item()) == 0
     assert rel_max(host(H2), host(H1)) < SAME[prec]
     assert np.max(np.abs(n2.cpu().numpy() - n1.cpu().numpy())) < SAME[prec] * np.max(np.abs(n1.cpu().numpy()))
-    assert rel_max(S2.cpu().numpy(), S1.cpu().numpy()) < SAME[prec]
+    S1h, S2h = S1.cpu().numpy(), S2.cpu().numpy()
+    if prec == "bf16x3" and nb > 128:
+        # the step forms its Hermitian C^dag H C from the upper-triangle 128 x 128
+        # tiles (other split-K ranges) and mirrors the rest; jdft_subspace forms
+        # every tile of C^dag (H C) for any H C.  They agree to the products'
+        # accuracy (FP32 accumulation in tensor memory), and the mirror is exact.
+        assert rel_max(S2h, S1h) < TOL[prec]
+        assert np.array_equal(S2h[128:, :128], S2h[:128, 128:].conj().T)
+    else:
+        assert rel_max(S2h, S1h) < SAME[prec]
     assert rel_max(O2.cpu().numpy(), O1.cpu().numpy()) < SAME[prec]
     assert rel_max(host(C2), host(C1)) < (1e-12 if prec == "fp64" else 1e-5)
     sample = [0, nb // 2, nb - 1]
