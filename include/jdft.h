@@ -351,11 +351,15 @@ typedef struct {
     int chunk_mb;          /* band-chunk budget kept for the chain kernels */
     int splits_subspace;   /* split-K count kept for the nb x nb x npw products (0: no schedule) */
     int splits_projector;  /* the same for the nproj x nb x npw projection P^dag C (0: none) */
+    int plane_bands;       /* bands per plane-pass work item kept for FP32 blocks: 2 (band pairs,
+                              packed FP32) or 1; 0 when the box has no band-pair kernel */
 } jdft_tune_report;
 
 /* Autotune everything the Hamiltonian, density and subspace calls of this
- * block use: the band-chunk budget of the FFT chain (jdft_autotune_chunk) and
- * the split-K schedules of the block's subspace and projector products
+ * block use: the band-chunk budget of the FFT chain (jdft_autotune_chunk),
+ * the plane pass's work-item shape for FP32 blocks (one band or a band pair
+ * per (plane, item), where both are compiled; kept in the basis) and the
+ * split-K schedules of the block's subspace and projector products
  * (jdft_autotune_gemm).  Overwrites HC.  Synchronous; may grow the workspace. */
 jdft_status jdft_autotune(jdft_basis_t basis, int ik, const void* C, int ldc, void* HC, int ldhc, int nb,
                           jdft_prec prec, jdft_tune_report* report, void* stream);

@@ -883,11 +883,41 @@ extern "C" jdft_status jdft_autotune(jdft_basis_t b, int ik, const void* C, int 
     clear_error();
     JDFT_CHECK_ARG(b && C && HC && report && nb >= 1, "bad arguments");
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
-    *report = jdft_tune_report{0, 0, 0};
+    *report = jdft_tune_report{0, 0, 0, 0};
     int mb = 0;
     jdft_status s = jdft_autotune_chunk(b, ik, C, ldc, HC, ldhc, nb, prec, &mb, stream);
     if (s != JDFT_OK) return s;
     report->chunk_mb = mb;
+    b->plane_bands = 0;
+    if (!is_fp64(prec) && plane_pair_batch_supported(make_geom(b, ik))) {
+        // plane-pass work items of one band or of a band pair: time H C with each
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_n = 0;
+        for (int bands : {2, 1}) {
+            b->plane_bands = bands == 1 ? 1 : 0;
+            if ((s = jdft_apply_H(b, ik, C, ldc, HC, ldhc, nb, prec, stream))) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 2 && s == JDFT_OK; ++r) s = jdft_apply_H(b, ik, C, ldc, HC, ldhc, nb, prec, stream);
+            cudaEventRecord(e1, st);
+            if (s != JDFT_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_n = bands;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->plane_bands = best_n == 1 ? 1 : 0;
+        if (s != JDFT_OK) return s;
+        report->plane_bands = best_n;
+    }
     if (prec != JDFT_TF32X3 && prec != JDFT_BF16X3) return JDFT_OK;
     const KSphere& sp = b->ks[ik];
     if ((s = jdft_autotune_gemm(nb, nb, sp.npw, C, ldc, C, ldc, prec, &report->splits_subspace, stream))) return s;

@@ -22,6 +22,7 @@ struct ChainGeom {
     const int* pw_z;           // npw
     FftPlan p0, p1, p2;
     int reserve_sms;           // SMs the persistent plane kernels leave free
+    int one_band;              // 1: the one-band plane kernels even where band-pair ones exist
 };
 
 inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
@@ -35,6 +36,7 @@ inline ChainGeom make_geom(const jdft_basis_s* b, int ik) {
     g.pw_col = s.pw_col; g.pw_z = s.pw_z;
     g.p0 = b->plan[0]; g.p1 = b->plan[1]; g.p2 = b->plan[2];
     g.reserve_sms = b->reserve_sms;
+    g.one_band = b->plane_bands == 1 ? 1 : 0;
     return g;
 }
 

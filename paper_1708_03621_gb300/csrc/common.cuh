@@ -146,6 +146,7 @@ struct jdft_basis_s {
     int device = 0;
     int chunk_mb = 0;         // band-chunk budget chosen by jdft_autotune_chunk (0 = default)
     int reserve_sms = 0;      // SMs the persistent plane kernels leave free (work on a side stream)
+    int plane_bands = 0;      // bands per plane-pass item of FP32 blocks: 0 = 2 where compiled (autotuned), 1
     jdft::Workspace work;
     // jdft_hamiltonian_step: the overlap factorisation's own scratch (it runs
     // on a side stream while the chain uses `work`), the side stream and its

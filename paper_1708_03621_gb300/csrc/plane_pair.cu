@@ -424,7 +424,7 @@ static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp
 jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                             const double* f, double w, double* n_r, const float2* tw_base,
                                             cudaStream_t st) {
-    if (pair_disabled()) return JDFT_ERR_UNSUPPORTED;
+    if (pair_disabled() || g.one_band) return JDFT_ERR_UNSUPPORTED;
     if (g.S0 == 128 && g.S1 == 128)
         return pair_window<128, 128>(g) ? pair_impl<128, 128, true, true>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st)
                                         : pair_impl<128, 128, true, false>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
@@ -434,7 +434,7 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
 
 jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                     const float2* tw_base, cudaStream_t st) {
-    if (pair_disabled()) return JDFT_ERR_UNSUPPORTED;
+    if (pair_disabled() || g.one_band) return JDFT_ERR_UNSUPPORTED;
     if (g.S0 == 128 && g.S1 == 128)
         return pair_window<128, 128>(g)
                    ? pair_impl<128, 128, false, true>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st)
@@ -470,7 +470,7 @@ static jdft_status pair_batch_impl(const ChainGeom& g, const KJob* jobs, int njo
 }
 
 bool plane_pair_batch_supported(const ChainGeom& g) {
-    return !pair_disabled() && ((g.S0 == 128 && g.S1 == 128) || (g.S0 == 16 && g.S1 == 12));
+    return !pair_disabled() && !g.one_band && ((g.S0 == 128 && g.S1 == 128) || (g.S0 == 16 && g.S1 == 12));
 }
 
 jdft_status launch_plane_apply_pair_batch(const std::vector<ChainGeom>& gs, const KJob* jobs, int64_t items,

@@ -465,7 +465,8 @@ def jdft_autotune_gemm(A, B, prec="bf16x3", stream=None) -> int:
 
 
 class TuneReport(ctypes.Structure):
-    _fields_ = [("chunk_mb", ctypes.c_int), ("splits_subspace", ctypes.c_int), ("splits_projector", ctypes.c_int)]
+    _fields_ = [("chunk_mb", ctypes.c_int), ("splits_subspace", ctypes.c_int), ("splits_projector", ctypes.c_int),
+                ("plane_bands", ctypes.c_int)]
 
 
 def jdft_autotune(basis, ik, C, HC, prec="bf16x3", stream=None) -> dict:
@@ -475,7 +476,8 @@ def jdft_autotune(basis, ik, C, HC, prec="bf16x3", stream=None) -> dict:
     r = TuneReport()
     _call("jdft_autotune", basis.handle, ik, p, ld, q, ldh, nb, _prec(prec), ctypes.c_void_p(ctypes.addressof(r)),
           _stream(stream))
-    return {"chunk_mb": r.chunk_mb, "splits_subspace": r.splits_subspace, "splits_projector": r.splits_projector}
+    return {"chunk_mb": r.chunk_mb, "splits_subspace": r.splits_subspace, "splits_projector": r.splits_projector,
+            "plane_bands": r.plane_bands}
 
 
 class Batch:

@@ -104,6 +104,7 @@ def test_autotune_schedules_keep_results(prec):
     rep = jdft.jdft_autotune(b, 0, C, torch.empty_like(C), prec)
     assert rep["chunk_mb"] in (32, 64, 128, 256, 512, 1024)
     assert rep["splits_subspace"] >= 1 and rep["splits_projector"] >= 1
+    assert rep["plane_bands"] == 0  # 40^3 planes have no band-pair kernel
     HC = torch.empty_like(C)
     jdft.jdft_apply_H(b, 0, C, HC, prec)
     CHC = torch.empty((nb, nb), dtype=torch.complex128, device="cuda")
