@@ -354,8 +354,8 @@ def roofline_of(k: dict, prec: str, peaks: dict, fp32: dict) -> dict:
 TRAFFIC_SOURCES = {"plane_apply_density_pair": ["csrc/plane_pair.cu", "csrc/fft_pair.cuh", "csrc/fft_reg.cuh",
                                                 "csrc/chain.cuh", "csrc/common.cuh", "csrc/tc_ptx.cuh"]}
 TRAFFIC_PER_BAND = {
-    # 150 365 440 + 85 946 880 bytes over 64 bands (profiles/plane_apply_density_pair_128cubed_bf16x3.md)
-    "plane_apply_density_pair": (3.6924e6, "ab37b9a6e1d1d474"),
+    # 150 448 896 + 86 052 608 bytes over 64 bands (ncu capture of one 64-band launch)
+    "plane_apply_density_pair": (3.6953e6, "afc1031263dd9059"),
 }
 
 
