@@ -783,28 +783,41 @@ def slab_measurements(prec: str, device) -> dict:
 
 
 def cg_kernel_shares(b, C0, prec, precond, mlp, iters: int = 4, top: int = 10) -> dict:
-    """Per-kernel time of a few band-CG iterations (library tracing, CUDA
-    events around every launch): where an iteration's time goes, including
-    the preconditioner network's kernels when it is used."""
+    """Where a band-CG iteration's time goes, per kernel (library tracing, CUDA
+    events around every launch), the preconditioner network's kernels
+    included: two traced minimisations stopped after 2 and after 2 + iters
+    iterations, differenced, so that the set-up of each call and the FP64
+    phase's start (orthonormalisation and subspace products on the FP64 block,
+    run once per call) cancel."""
     import torch
 
     from paper_1708_03621_gb300 import jdft
-    C = C0.to(torch.complex128).clone()
-    torch.cuda.synchronize()
-    jdft.jdft_profile_read()
-    jdft.jdft_profile_enable(True)
-    t0 = time.perf_counter()
-    jdft.jdft_minimize_bands(b, 0, C, tol=1e-30, max_iter=iters, precond=precond, prec=prec, switch_tol=1e-30,
-                             check=False, mlp=mlp)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    jdft.jdft_profile_enable(False)
-    prof = jdft.jdft_profile_read()
-    del C
-    rows = sorted(prof.items(), key=lambda kv: -kv[1][1])[:top]
-    return {"iterations": iters, "preconditioner": precond, "wall_ms": round(wall * 1e3, 3),
-            "kernels": [{"name": n, "launches": c, "ms": round(ms, 3), "share_of_wall": round(ms / (wall * 1e3), 4)}
-                        for n, (c, ms) in rows]}
+    runs = {}
+    for k in (2, 2 + iters):
+        C = C0.to(torch.complex128).clone()
+        torch.cuda.synchronize()
+        jdft.jdft_profile_read()
+        jdft.jdft_profile_enable(True)
+        t0 = time.perf_counter()
+        jdft.jdft_minimize_bands(b, 0, C, tol=1e-30, max_iter=k, precond=precond, prec=prec, switch_tol=1e-30,
+                                 check=False, mlp=mlp)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        jdft.jdft_profile_enable(False)
+        runs[k] = (wall, jdft.jdft_profile_read())
+        del C
+    (wa, pa), (wb, pb) = runs[2], runs[2 + iters]
+    it_ms = max(1e-9, (wb - wa) / iters * 1e3)
+    rows = []
+    for name, (n, ms) in pb.items():
+        n0, ms0 = pa.get(name, (0, 0.0))
+        d = (ms - ms0) / iters
+        if d > 0:
+            rows.append({"name": name, "launches_per_iteration": round((n - n0) / iters, 2),
+                         "ms_per_iteration": round(d, 3), "share_of_iteration": round(d / it_ms, 4)})
+    rows.sort(key=lambda r: -r["ms_per_iteration"])
+    return {"iterations_differenced": iters, "preconditioner": precond, "iteration_ms": round(it_ms, 3),
+            "kernels": rows[:top]}
 
 
 def precision_errors(q) -> dict:

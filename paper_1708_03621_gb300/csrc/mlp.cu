@@ -45,6 +45,13 @@ __device__ __forceinline__ float sigmoidf_(float z) {
     return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
 }
 __device__ __forceinline__ float siluf_(float z) { return z * sigmoidf_(z); }
+// SiLU from the hardware exponential and an approximate quotient (a few ulp),
+// for inference: the network's output only shapes search directions, and 128
+// activations per coefficient make the IEEE forms the kernel's largest cost.
+__device__ __forceinline__ float siluf_fast_(float z) {
+    const float e = __expf(-fabsf(z));
+    return z * __fdividef(z >= 0.f ? 1.f : e, 1.f + e);
+}
 __device__ __forceinline__ float dsiluf_(float z) {
     const float s = sigmoidf_(z);
     return s * (1.f + z * (1.f - s));
@@ -103,6 +110,11 @@ __device__ __forceinline__ uint32_t bf2_bits(float a, float b) {
 
 // MODE 0: K[r] for feature triples feats[3 r ..]; MODE 1: KG = K G for every
 // coefficient of an (npw x nb) block (features from kin and the band features).
+// The inference kernel keeps W1, b1 ([0, OW2) of the parameters) and b2, W3, b3
+// ([OB2, NPARAM)) in shared memory as FP32, at these offsets.
+constexpr int MLP_WSMALL = OW2 + (NPARAM - OB2);
+constexpr int WS_OB2 = OW2, WS_OW3 = OW2 + (OW3 - OB2), WS_OB3 = OW2 + (OB3 - OB2);
+
 template <int MODE, typename T>
 __global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* __restrict__ feats,
                                                     float* __restrict__ Kout, int npw, int nb,
@@ -116,11 +128,13 @@ __global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* _
     unsigned char* Amid = sm + MT_ATILE;
     unsigned char* Alo = sm + 2 * MT_ATILE;
     unsigned char* Bt = sm + 3 * MT_ATILE;
+    // the CUDA-core layers' parameters: W1, b1, b2, W3, b3 (W2 is the B operand)
     float* w = reinterpret_cast<float*>(Bt + MT_BTILE);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(w + NPARAM + 3);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(w + MLP_WSMALL + 3);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < NPARAM; i += MT) w[i] = __bfloat162float(wb[i]);
+    for (int i = tid; i < MLP_WSMALL; i += MT)
+        w[i] = __bfloat162float(wb[i < OW2 ? i : i - OW2 + OB2]);  // [0, OW2) then [OB2, NPARAM)
     // W2 as the B operand: row j (output), K = i (input)
     for (int e = tid; e < HID * HID / 2; e += MT) {
         const int j = (2 * e) / HID, i = (2 * e) % HID;
@@ -167,7 +181,8 @@ __global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* _
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int i = k0 + q;
-                h[q] = siluf_(w[OW1 + 3 * i] * f0 + w[OW1 + 3 * i + 1] * f1 + w[OW1 + 3 * i + 2] * f2 + w[OB1 + i]);
+                h[q] = siluf_fast_(w[OW1 + 3 * i] * f0 + w[OW1 + 3 * i + 1] * f1 + w[OW1 + 3 * i + 2] * f2 +
+                                   w[OB1 + i]);
             }
             uint32_t hi[4], mid[4], lo[4];
 #pragma unroll
@@ -210,13 +225,13 @@ __global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* _
         }
         phase ^= 1u;
         tc::tc_fence_after_sync();
-        float z = w[OB3];
+        float z = w[WS_OB3];
 #pragma unroll 1
         for (int c = 0; c < HID; c += 16) {
             float acc[16];
             tc::tmem_ld16(lane_base + c, acc);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) z += w[OW3 + c + q] * siluf_(acc[q] + w[OB2 + c + q]);
+            for (int q = 0; q < 16; ++q) z += w[WS_OW3 + c + q] * siluf_fast_(acc[q] + w[WS_OB2 + c + q]);
         }
         const float Kv = softplusf_(z);
         if (act) {
@@ -235,7 +250,7 @@ __global__ void __launch_bounds__(MT) mlp_tc_kernel(int64_t rows, const float* _
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
-constexpr size_t MLP_TC_SMEM = 1024 + 3 * MT_ATILE + MT_BTILE + (NPARAM + 3) * sizeof(float) + 64;
+constexpr size_t MLP_TC_SMEM = 1024 + 3 * MT_ATILE + MT_BTILE + (MLP_WSMALL + 3) * sizeof(float) + 64;
 
 // Persistent grid of the tensor-core inference kernel: two blocks per SM
 // (shared memory; their 64 tensor-memory columns each fit easily).
@@ -244,7 +259,8 @@ static int mlp_tc_grid(int64_t rows) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (rows + MT - 1) / MT;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(1, sms) * 2));
+    // three blocks per SM: shared memory (about 59 KB each) and tensor memory (64 columns each) allow it
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(1, sms) * 3));
 }
 
 jdft_status mlp_device_status() {
