@@ -388,15 +388,25 @@ struct MinState {
     int* status;
     DevBuf mem;
     const double* kin;
+    // split-operand (BF16x3) products of FP32 blocks: the BF16 planes of one
+    // block (or of its transpose), of a second block, of the small matrix, and
+    // the split-K partial tiles
+    bool tcx = false;
+    char *sp1 = nullptr, *sp2 = nullptr, *spw = nullptr, *spp = nullptr;
+    size_t spp_bytes = 0;
 
     jdft_status alloc() {
         const size_t blk = (size_t)nb * ld * sizeof(c_t<T>);
         const size_t sm = (size_t)nb * nb * sizeof(double2);
         const int m = nb + (nb & 1);
         const size_t lab = std::max(2 * (size_t)m * m, chol_work_elems(nb)) * sizeof(double2);
+        tcx = std::is_same<T, float>::value && tcx_eligible(prec, nb, nb);
+        const size_t s1 = tcx ? std::max(tcx_split_bytes(nb, npw), tcx_split_bytes(npw, nb)) : 0;
+        const size_t s2 = tcx ? tcx_split_bytes(nb, npw) : 0, sw = tcx ? tcx_split_bytes(nb, nb) : 0;
+        spp_bytes = tcx ? tcx_cn_partial_bytes(nb, nb, npw) : 0;
         const size_t total = 12 * blk + 5 * sm + lab + 2 * (size_t)nb * nb * sizeof(c_t<T>) +
                              (size_t)nb * sizeof(double) + 64 * sizeof(double) + 64 + 3 * (size_t)nb * sizeof(float) +
-                             17 * 256;
+                             s1 + s2 + sw + spp_bytes + 21 * 256;
         JDFT_CUDA_TRY(cudaMalloc(&mem.p, total));
         char* q = (char*)mem.p;
         auto take = [&](size_t n) { char* r = q; q += (n + 255) / 256 * 256; return (void*)r; };
@@ -408,6 +418,12 @@ struct MinState {
         Bm = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>)); W = (c_t<T>*)take((size_t)nb * nb * sizeof(c_t<T>));
         Tb = (double*)take(nb * sizeof(double)); scal = (double*)take(64 * sizeof(double)); status = (int*)take(64);
         bf = (float*)take(3 * (size_t)nb * sizeof(float));
+        if (tcx) {
+            sp1 = (char*)take(s1);
+            sp2 = (char*)take(s2);
+            spw = (char*)take(sw);
+            spp = (char*)take(spp_bytes);
+        }
         JDFT_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
         return JDFT_OK;
     }
@@ -418,7 +434,21 @@ struct MinState {
     // out (nb x nb complex128) = alpha X^dag Y
     jdft_status cn(const c_t<T>* X, const c_t<T>* Yb, double2* out, double alpha) {
         JDFT_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)nb * nb * sizeof(double2), st));
+        if (tcx) {
+            // X^dag X is Hermitian: its upper tiles only
+            jdft_status s = tcx_split((const float2*)X, ld, nb, npw, sp1, st);
+            if (s == JDFT_OK && Yb != X) s = tcx_split((const float2*)Yb, ld, nb, npw, sp2, st);
+            if (s != JDFT_OK) return s;
+            return tcx_cn(nb, nb, npw, sp1, Yb != X ? sp2 : sp1, out, nb, alpha, st, spp, spp_bytes, Yb == X);
+        }
         return gemm_cn<T>(prec, nb, nb, npw, X, ld, Yb, ld, out, nb, alpha, st);
+    }
+    // Z (+)= X . S for a small block-type S, from split operands
+    jdft_status tcx_times(const c_t<T>* X, const c_t<T>* S, c_t<T>* Z, bool accumulate) {
+        jdft_status s = tcx_split_t((const float2*)X, ld, npw, nb, sp1, st);
+        if (s == JDFT_OK) s = tcx_split_t((const float2*)S, nb, nb, nb, spw, st);
+        if (s != JDFT_OK) return s;
+        return tcx_nn(npw, nb, nb, sp1, spw, (float2*)Z, ld, accumulate, st);
     }
     // Z += X . (alpha A)   (A small complex128)
     jdft_status nn_acc(const c_t<T>* X, const double2* A, double alpha, c_t<T>* Z) {
@@ -428,10 +458,12 @@ struct MinState {
         }
         jdft_status s = check_launch("small_scale");
         if (s != JDFT_OK) return s;
+        if (tcx) return tcx_times(X, Bm, Z, true);
         return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, Bm, nb, Z, ld, st);
     }
     // Z = X . W  (W already in block type)
     jdft_status rotate(const c_t<T>* X, c_t<T>* Z) {
+        if (tcx) return tcx_times(X, W, Z, false);
         return gemm_nn_acc<T>(prec, npw, nb, nb, X, ld, W, nb, Z, ld, st, false);
     }
     jdft_status hermitize(double2* A, double* tr) {
