@@ -32,36 +32,47 @@
 namespace jdft {
 
 // ---------------------------------------------------------------------------
-// Block kernels (a block is nb bands x npw, band-major, leading dimension ld)
+// Block kernels (a block is nb bands x npw, band-major, leading dimension ld).
+// Grid: x strides over the plane waves of a band, y over the bands, so no
+// thread divides an element index.  FP32 blocks compute in FP32 (the SMs'
+// FP64 rate is a small fraction of it), with compensated FP32 sums where a
+// reduction must keep FP64-like accuracy; FP64 blocks compute in FP64.
 // ---------------------------------------------------------------------------
+// s + c carries a running FP32 sum to twice the FP32 precision (Knuth's TwoSum).
+struct CompSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 template <typename T>
 __global__ void blk_axpby_kernel(int npw, int nb, double a, const c_t<T>* __restrict__ x, int ldx, double b,
                                  const c_t<T>* __restrict__ y, int ldy, c_t<T>* __restrict__ z, int ldz) {
-    const int64_t total = (int64_t)npw * nb;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bb = i / npw, g = i - bb * npw;
-        const c_t<T> u = x[bb * ldx + g];
-        c_t<T> r = mk<T>((T)(a * u.x), (T)(a * u.y));
-        if (y) {
-            const c_t<T> v = y[bb * ldy + g];
-            r.x += (T)(b * v.x);
-            r.y += (T)(b * v.y);
+    const T ar = (T)a, br = (T)b;
+    for (int bb = blockIdx.y; bb < nb; bb += gridDim.y) {
+        const c_t<T>* xb = x + (size_t)bb * ldx;
+        const c_t<T>* yb = y ? y + (size_t)bb * ldy : nullptr;
+        c_t<T>* zb = z + (size_t)bb * ldz;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+            const c_t<T> u = xb[g];
+            c_t<T> r = mk<T>(ar * u.x, ar * u.y);
+            if (yb) {
+                const c_t<T> v = yb[g];
+                r.x += br * v.x;
+                r.y += br * v.y;
+            }
+            zb[g] = r;
         }
-        z[bb * ldz + g] = r;
     }
 }
 
-// out[slot] += Re sum conj(x) y over the whole block (FP64 accumulation).
-template <typename T>
-__global__ void blk_dot_kernel(int npw, int nb, const c_t<T>* __restrict__ x, int ldx, const c_t<T>* __restrict__ y,
-                               int ldy, double* __restrict__ out) {
-    const int64_t total = (int64_t)npw * nb;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bb = i / npw, g = i - bb * npw;
-        const c_t<T> u = x[bb * ldx + g], v = y[bb * ldy + g];
-        acc += (double)u.x * (double)v.x + (double)u.y * (double)v.y;
-    }
+// Block sum of a per-thread double into *out (one FP64 atomic per block).
+__device__ __forceinline__ void block_sum_to(double acc, double* out) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -73,16 +84,42 @@ __global__ void blk_dot_kernel(int npw, int nb, const c_t<T>* __restrict__ x, in
     }
 }
 
+// out[slot] += Re sum conj(x) y over the whole block.
+template <typename T>
+__global__ void blk_dot_kernel(int npw, int nb, const c_t<T>* __restrict__ x, int ldx, const c_t<T>* __restrict__ y,
+                               int ldy, double* __restrict__ out) {
+    double acc = 0.0;
+    CompSum cs;
+    for (int bb = blockIdx.y; bb < nb; bb += gridDim.y) {
+        const c_t<T>* xb = x + (size_t)bb * ldx;
+        const c_t<T>* yb = y + (size_t)bb * ldy;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+            const c_t<T> u = xb[g], v = yb[g];
+            if constexpr (std::is_same<T, float>::value)
+                cs.add(fmaf(u.x, v.x, u.y * v.y));
+            else
+                acc += u.x * v.x + u.y * v.y;
+        }
+    }
+    if constexpr (std::is_same<T, float>::value) acc = cs.value();
+    block_sum_to(acc, out);
+}
+
 // Tb[b] = Omega sum_G kin[G] |C_Gb|^2 (one block per band).
 template <typename T>
 __global__ void band_kinetic_kernel(int npw, const c_t<T>* __restrict__ C, int ldc, const double* __restrict__ kin,
-                                    double omega, double* __restrict__ Tb) {
+                                    const float* __restrict__ kin32, double omega, double* __restrict__ Tb) {
     const int b = blockIdx.x;
     double acc = 0.0;
+    CompSum cs;
     for (int g = threadIdx.x; g < npw; g += blockDim.x) {
         const c_t<T> c = C[(size_t)b * ldc + g];
-        acc += kin[g] * ((double)c.x * c.x + (double)c.y * c.y);
+        if constexpr (std::is_same<T, float>::value)
+            cs.add(kin32[g] * fmaf(c.x, c.x, c.y * c.y));
+        else
+            acc += kin[g] * (c.x * c.x + c.y * c.y);
     }
+    if constexpr (std::is_same<T, float>::value) acc = cs.value();
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -94,22 +131,30 @@ __global__ void band_kinetic_kernel(int npw, const c_t<T>* __restrict__ C, int l
     }
 }
 
-// KG = K(x) G with x = kin / Tb (Teter) or K = 1 (identity).
+// KG = K(x) G with x = kin / Tb (Teter) or K = 1 (identity); in the block's precision.
 template <typename T>
 __global__ void precond_teter_kernel(int npw, int nb, const c_t<T>* __restrict__ G, int ldg, c_t<T>* __restrict__ KG,
-                                     int ldk, const double* __restrict__ kin, const double* __restrict__ Tb,
-                                     int identity) {
-    const int64_t total = (int64_t)npw * nb;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bb = i / npw, g = i - bb * npw;
-        double k = 1.0;
-        if (!identity) {
-            const double x = kin[g] / Tb[bb];
-            const double num = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
-            k = num / (num + 16.0 * x * x * x * x);
+                                     int ldk, const double* __restrict__ kin, const float* __restrict__ kin32,
+                                     const double* __restrict__ Tb, int identity) {
+    for (int bb = blockIdx.y; bb < nb; bb += gridDim.y) {
+        const T rT = (T)(1.0 / Tb[bb]);
+        const c_t<T>* gb = G + (size_t)bb * ldg;
+        c_t<T>* kb = KG + (size_t)bb * ldk;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npw; g += gridDim.x * blockDim.x) {
+            T k = (T)1;
+            if (!identity) {
+                T kg;
+                if constexpr (std::is_same<T, float>::value)
+                    kg = kin32[g];
+                else
+                    kg = kin[g];
+                const T xx = kg * rT;
+                const T num = (T)27 + xx * ((T)18 + xx * ((T)12 + (T)8 * xx));
+                k = num / (num + (T)16 * xx * xx * xx * xx);
+            }
+            const c_t<T> v = gb[g];
+            kb[g] = mk<T>(k * v.x, k * v.y);
         }
-        const c_t<T> v = G[bb * ldg + g];
-        KG[bb * ldk + g] = mk<T>((T)(k * v.x), (T)(k * v.y));
     }
 }
 
@@ -307,13 +352,20 @@ __global__ void jacobi_eig_kernel(int n, int m, double2* A, int sweeps, double* 
 }
 
 static int blocks_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8); }
+// Grid of the band-row kernels: about 8 blocks of 256 threads per SM, split
+// between the plane waves of a band (x) and the bands (y).
+static dim3 rows_grid(int npw, int nb) {
+    const int bx = std::max(1, std::min((npw + 255) / 256, 32));
+    const int by = std::max(1, std::min(nb, std::max(1, 152 * 8 / bx)));
+    return dim3(bx, by);
+}
 
 template <typename T>
 static jdft_status axpby(int npw, int nb, double a, const c_t<T>* x, int ldx, double b, const c_t<T>* y, int ldy,
                          c_t<T>* z, int ldz, cudaStream_t st) {
     {
         Trace tr_("blk_axpby", st);
-        blk_axpby_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, a, x, ldx, b, y, ldy, z, ldz);
+        blk_axpby_kernel<T><<<rows_grid(npw, nb), 256, 0, st>>>(npw, nb, a, x, ldx, b, y, ldy, z, ldz);
     }
     return check_launch("blk_axpby");
 }
@@ -324,7 +376,7 @@ static jdft_status dot(int npw, int nb, const c_t<T>* x, int ldx, const c_t<T>* 
     JDFT_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), st));
     {
         Trace tr_("blk_dot", st);
-        blk_dot_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(npw, nb, x, ldx, y, ldy, out);
+        blk_dot_kernel<T><<<rows_grid(npw, nb), 256, 0, st>>>(npw, nb, x, ldx, y, ldy, out);
     }
     return check_launch("blk_dot");
 }
@@ -388,6 +440,7 @@ struct MinState {
     int* status;
     DevBuf mem;
     const double* kin;
+    const float* kin32;
     // split-operand (BF16x3) products of FP32 blocks: the BF16 planes of one
     // block (or of its transpose), of a second block, of the small matrix, and
     // the split-K partial tiles
@@ -551,15 +604,15 @@ static jdft_status run_phase(MinState<T>& M, const jdft_min_opts& o, double stop
         // preconditioned gradient, projected
         {
             Trace tr_("band_kinetic", st);
-            band_kinetic_kernel<T><<<nb, 256, 0, st>>>(npw, M.C, ld, M.kin, M.omega, M.Tb);
+            band_kinetic_kernel<T><<<nb, 256, 0, st>>>(npw, M.C, ld, M.kin, M.kin32, M.omega, M.Tb);
         }
         if ((s = check_launch("band_kinetic"))) return s;
         if (use_mlp()) {
             if ((s = mlp_precondition<T>(o.mlp, npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, M.Hs, M.bf, st))) return s;
         } else {
             Trace tr_("precond_teter", st);
-            precond_teter_kernel<T><<<blocks_for((int64_t)npw * nb), 256, 0, st>>>(
-                npw, nb, M.G, ld, M.KG, ld, M.kin, M.Tb, o.precond == JDFT_PRECOND_IDENTITY);
+            precond_teter_kernel<T><<<rows_grid(npw, nb), 256, 0, st>>>(
+                npw, nb, M.G, ld, M.KG, ld, M.kin, M.kin32, M.Tb, o.precond == JDFT_PRECOND_IDENTITY);
         }
         if ((s = check_launch("precondition"))) return s;
         if ((s = M.project(M.KG))) return s;
@@ -651,7 +704,7 @@ template <typename T>
 static jdft_status setup_state(MinState<T>& M, jdft_basis_s* b, int ik, int nb, jdft_prec prec, double f,
                                cudaStream_t st) {
     M.b = b; M.ik = ik; M.nb = nb; M.npw = b->ks[ik].npw; M.ld = M.npw; M.prec = prec; M.st = st;
-    M.omega = b->omega; M.f = f; M.kin = b->ks[ik].kin;
+    M.omega = b->omega; M.f = f; M.kin = b->ks[ik].kin; M.kin32 = b->ks[ik].kin32;
     return M.alloc();
 }
 
