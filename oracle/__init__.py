@@ -12,4 +12,6 @@ Modules:
               apply_H, density, subspace, dense Hamiltonian
   minimize    band conjugate-gradient minimiser (Teter / MLP / identity)
   mlp         the FP64 reference of the per-coefficient preconditioner network
+  scf         Hartree potential, LDA exchange-correlation, Pulay mixing and the
+              self-consistent field loop around dense band solves
 """
