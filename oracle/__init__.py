@@ -14,4 +14,5 @@ Modules:
   mlp         the FP64 reference of the per-coefficient preconditioner network
   scf         Hartree potential, LDA exchange-correlation, Pulay mixing and the
               self-consistent field loop around dense band solves
+  pcm         the linear dielectric Poisson solve (hessian, CG, A_diel)
 """
