@@ -325,6 +325,156 @@ jdft_status jdft_minimize_bands(jdft_basis_t basis, int ik, void* C, int ldc, in
                                 const jdft_min_opts* opts, double* eigs, jdft_min_report* report,
                                 void* stream);
 
+/* ---- self-consistent field (Sec. 2.1: Coulomb, ExCorr, Pulay; Sec. 2.2) ---
+ * Real-space fields here are real FP64 boxes of N values (device, j2 fastest).
+ * The full-box transforms use a complex FP64 box of the basis (16 N bytes plus
+ * 1 MB of partial sums, grown synchronously on first use); calls on the same
+ * basis must not overlap on the GPU.  Energies go to device doubles, summed in
+ * a fixed order (deterministic). */
+
+/* Hartree potential of the density n (the periodic Coulomb kernel of class
+ * Coulomb, Sec. 2.1): with nt = J n over the whole box (frequencies folded to
+ * [-S/2, S/2) per axis, G = B iG),  V_H = I (4 pi nt(G) / |G|^2), the G = 0 term
+ * dropped (a uniform neutralising background).  vh: device N doubles, must not
+ * overlap n.  energy: device double or NULL; receives
+ * E_H = (Omega/2) sum_G 4 pi |nt(G)|^2 / |G|^2.  Asynchronous. */
+jdft_status jdft_hartree(jdft_basis_t basis, const double* n, double* vh, double* energy, void* stream);
+
+/* Local-density exchange-correlation (class ExCorr, Sec. 2.1; LDA among the
+ * semilocal functionals of Sec. 2.2), spin-unpolarised: Slater exchange plus
+ * the Perdew-Zunger 1981 fit (PRB 23, 5048) of the Ceperley-Alder correlation.
+ * Points with n <= 0 get e_xc = v_xc = 0.  vxc: device N doubles (NULL to skip;
+ * may be n itself); energy: device double or NULL, receives
+ * E_xc = (Omega/N) sum_j n_j e_xc(n_j).  Asynchronous. */
+jdft_status jdft_xc_lda(jdft_basis_t basis, const double* n, double* vxc, double* energy, void* stream);
+
+/* Kohn-Sham potential V_KS = V_ion + V_H[n] + v_xc[n] in one Hartree chain,
+ * the potential and exchange-correlation terms added in the last transform's
+ * epilogue.  vks: device N doubles, overlapping neither n nor vion.  energies:
+ * device double[2] or NULL, receives (E_H, E_xc) as jdft_hartree and
+ * jdft_xc_lda define them.  Asynchronous. */
+jdft_status jdft_ks_potential(jdft_basis_t basis, const double* n, const double* vion, double* vks,
+                              double* energies, void* stream);
+
+/* Pulay mixing of densities ("self-consistency by Pulay mixing", class Pulay,
+ * Sec. 2.1; P. Pulay, Chem. Phys. Lett. 73, 393 (1980)).  The mixer keeps the
+ * last `history` pairs (n_in^i, R^i = n_out^i - n_in^i) on the device (2 x history
+ * x n doubles, allocated by jdft_pulay_create).  A step stores the new pair,
+ * finds c minimising |sum_i c_i R^i| (plain sum over the box) subject to
+ * sum_i c_i = 1 from the bordered system [A 1; 1^T 0][c; lam] = [0; 1],
+ * A_ij = <R^i, R^j> (Gaussian elimination with partial pivoting in FP64 on the
+ * GPU; while a pivot falls below 1e-13 max |A_ii| the oldest pair is dropped),
+ * and writes n_next = sum_i c_i (n_in^i + alpha R^i). */
+typedef struct jdft_pulay_s* jdft_pulay_t;
+
+/* n: values per density (>= 1); history in [1, 16]; alpha in (0, 1].  Uses the
+ * current device.  JDFT_ERR_OOM if the history does not fit. */
+jdft_status jdft_pulay_create(int64_t n, int history, double alpha, jdft_pulay_t* out);
+jdft_status jdft_pulay_destroy(jdft_pulay_t mixer);
+/* Forget the stored pairs (the next step is plain linear mixing). */
+jdft_status jdft_pulay_reset(jdft_pulay_t mixer);
+/* One mixing step: n_in, n_out, n_next device n doubles; n_next may be n_in,
+ * not n_out.  Asynchronous on `stream`; steps of one mixer must be issued in
+ * order from one host thread. */
+jdft_status jdft_pulay_step(jdft_pulay_t mixer, const double* n_in, const double* n_out, double* n_next,
+                            void* stream);
+/* Number of pairs the last step combined (host int; waits for `stream`). */
+jdft_status jdft_pulay_used(jdft_pulay_t mixer, int* used, void* stream);
+
+typedef struct {
+    double tol_energy;      /* converged when |E - E_prev| < tol_energy (Ha; 0 = 1e-8) ... */
+    double tol_density;     /* ... and sqrt((Omega/N) sum_j (n_out - n_in)_j^2) < tol_density (0 = 1e-6) */
+    int max_iter;           /* SCF iterations (0 = 100) */
+    int history;            /* Pulay pairs kept (0 = 8, at most 16) */
+    double alpha;           /* Pulay mixing fraction (0 = 0.5) */
+    double band_tol;        /* band minimiser tolerance of every iteration (0 = 1e-9) */
+    int band_max_iter;      /* band minimiser iteration limit (0 = 1000) */
+    jdft_precond precond;   /* band minimiser preconditioner */
+    jdft_prec prec;         /* band minimiser precision schedule (JDFT_FP64 or a mixed mode) */
+    double occupation;      /* f per band (0 = 2) */
+    jdft_mlp_t mlp;         /* weights for JDFT_PRECOND_MLP, else NULL */
+} jdft_scf_opts;
+
+typedef struct {
+    int iterations;         /* SCF iterations taken */
+    int converged;
+    int band_iterations;    /* band CG iterations, all SCF iterations and k-points */
+    int band_unconverged;   /* band solves that stopped at band_max_iter */
+    double energy;          /* total energy E (Ha) of the last iteration */
+    double band_energy;     /* sum_k w_k f sum_b eps_kb */
+    double double_counting; /* -(Omega/N) sum_j n_out,j (V_H + v_xc)[n_in]_j */
+    double hartree;         /* E_H[n_out] */
+    double xc;              /* E_xc[n_out] */
+    double residual;        /* density residual of the last iteration */
+    double seconds;         /* wall time of the call */
+} jdft_scf_report;
+
+/* Self-consistent field loop at fixed occupations (Sec. 2.2: SCF by Pulay
+ * mixing, the alternative to total-energy minimisation).  The electrons see
+ * V_KS[n] = V_ion + V_H[n] + v_xc[n] (jdft_ks_potential); the basis's projectors
+ * stay as set.  C: host array of nk device pointers, one complex128 band-major
+ * block of nb bands per k-point (ldc >= npw of every k), in: starting guess,
+ * out: the orbitals of the last iteration (O-orthonormal).  vion: device N
+ * doubles.  The start density is that of the orthonormalised starting blocks.
+ * Each iteration: V_KS of the input density -> jdft_minimize_bands at every
+ * k-point (warm-started) -> output density n_out -> total energy
+ *   E = sum_k w_k f sum_b eps_kb - (Omega/N) sum_j n_out,j (V_H + v_xc)[n_in]_j
+ *       + E_H[n_out] + E_xc[n_out]
+ * -> convergence test (both tolerances, from the second iteration) -> Pulay step.
+ * n_r: device N doubles, receives n_out of the last iteration; eigs: device
+ * nk x nb doubles or NULL, the last band energies.  On return the basis holds
+ * V_KS of the last input density as its potential.  report: host.  Synchronous;
+ * allocates its working fields (4 N doubles), the mixer and the minimiser's
+ * blocks for the duration of the call.  JDFT_ERR_NOT_CONVERGED (outputs and
+ * report filled) if max_iter is reached. */
+jdft_status jdft_scf(jdft_basis_t basis, void* const* C, int ldc, int nb, const double* vion, double* n_r,
+                     double* eigs, const jdft_scf_opts* opts, jdft_scf_report* report, void* stream);
+
+/* ---- scalar fields and the linear dielectric (Sec. 2.1, Listing 1) --------
+ * A reciprocal-space field (ScalarFieldTilde) is a full complex128 box X(G) of
+ * N values (device, j2 fastest), slot iG mod S holding G = B iG with
+ * frequencies folded to [-S/2, S/2) per axis.  A real-space field
+ * (ScalarField) is a box of N values; these calls take it as complex128. */
+
+/* x = I X: x_j = sum_G X(G) exp(+i G.r_j) over the whole box (Sec. 2.1, I on
+ * scalar fields).  X and x may be the same buffer.  FP64.  Asynchronous. */
+jdft_status jdft_field_I(jdft_basis_t basis, const void* X, void* x, void* stream);
+/* X = J x: X(G) = (1/N) sum_j x_j exp(-i G.r_j) (Sec. 2.1, J on scalar fields).
+ * x and X may be the same buffer.  FP64.  Asynchronous. */
+jdft_status jdft_field_J(jdft_basis_t basis, const void* x, void* X, void* stream);
+
+/* The dielectric operator of the paper's LinearPCM example (Sec. 2.1,
+ * Eq. (Poisson), Listing 1's hessian):
+ *   out~ = -(1/4 pi) div J(eps * I(grad phi~)),  grad = i G_d, div = sum_d i G_d,
+ * Hermitian and positive semi-definite for eps > 0, zero on G = 0.  eps: device
+ * N doubles (real space); phi_t, out_t: device complex128 reciprocal-space boxes
+ * that must not overlap.  Uses the basis field workspace (three complex boxes
+ * and 1 MB, grown synchronously on first use).  Asynchronous. */
+jdft_status jdft_pcm_hessian(jdft_basis_t basis, const double* eps, const void* phi_t, void* out_t,
+                             void* stream);
+
+typedef struct {
+    int iterations;         /* CG iterations (one hessian each) */
+    int converged;
+    double residual;        /* |r| / |rho~| at exit (plain sums over the box, G != 0) */
+    double A_diel;          /* (1/2) Re sum_G conj(phi~ - 4 pi rho~ / G^2) Omega rho~ (Ha) */
+    double seconds;         /* wall time of the call */
+} jdft_pcm_report;
+
+/* Solve -4 pi rho = div(eps grad phi) for phi~ by preconditioned conjugate
+ * gradients on reciprocal-space fields (Sec. 2.1, class LinearSolvable; the
+ * paper's Listing 1 `solve(rhoTilde)`), then the solvation energy of
+ * Eq. (Adiel) (`getAdiel`).  The G = 0 term of rho~ is ignored (a neutral
+ * charge) and phi~(0) = 0.  Preconditioner: the Coulomb kernel 4 pi / G^2 (the
+ * exact inverse for eps = 1).  Start phi~ = 0; converged when
+ * |r| <= tol |rho~|.  eps: device N doubles (> 0); rho_t, phi_t: device
+ * complex128 boxes (phi_t overwritten, not overlapping rho_t).  report: host.
+ * Synchronous (one host read of the residual per iteration); uses the basis
+ * field workspace (six complex boxes and 1 MB).  JDFT_ERR_NOT_CONVERGED (phi_t
+ * and report filled) if max_iter is reached. */
+jdft_status jdft_pcm_solve(jdft_basis_t basis, const double* eps, const void* rho_t, void* phi_t, double tol,
+                           int max_iter, jdft_pcm_report* report, void* stream);
+
 /* ---- schedule autotuning (the paper has no counterpart) ------------------ */
 
 /* Time jdft_apply_H on the caller's blocks for band-chunk budgets of

@@ -355,6 +355,7 @@ jdft_status jdft_basis_destroy(jdft_basis_t b) {
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     cudaFree(b->fwork.ptr);
+    cudaFree(b->fieldwork.ptr);
     cudaSetDevice(prev);
     delete b;
     return JDFT_OK;

@@ -152,6 +152,9 @@ struct jdft_basis_s {
     // on a side stream while the chain uses `work`), the side stream and its
     // fork / join events (created on first use)
     jdft::Workspace fwork;
+    // full-box field transforms (Hartree, Kohn-Sham potential): a complex FP64
+    // box and per-block partial sums (grown on first use)
+    jdft::Workspace fieldwork;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };

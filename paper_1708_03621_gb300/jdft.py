@@ -54,6 +54,23 @@ class MinReport(ctypes.Structure):
 
 PRECOND = {"identity": 0, "teter": 1, "mlp": 2}
 
+
+class ScfOpts(ctypes.Structure):
+    _fields_ = [("tol_energy", ctypes.c_double), ("tol_density", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("history", ctypes.c_int), ("alpha", ctypes.c_double), ("band_tol", ctypes.c_double),
+                ("band_max_iter", ctypes.c_int), ("precond", ctypes.c_int), ("prec", ctypes.c_int),
+                ("occupation", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+
+
+class ScfReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("band_iterations", ctypes.c_int),
+                ("band_unconverged", ctypes.c_int), ("energy", ctypes.c_double), ("band_energy", ctypes.c_double),
+                ("double_counting", ctypes.c_double), ("hartree", ctypes.c_double), ("xc", ctypes.c_double),
+                ("residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 class ApplyItem(ctypes.Structure):
     _fields_ = [("basis", ctypes.c_void_p), ("ik", ctypes.c_int), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int),
                 ("HC", ctypes.c_void_p), ("ldhc", ctypes.c_int), ("nb", ctypes.c_int), ("prec", ctypes.c_int)]
@@ -101,6 +118,19 @@ _SIGS = {
     "jdft_orthonormalize_async": [_vp, _i, _vp, _i, _i, _vp, _i, _vp, _vp],
     "jdft_autotune_gemm": [_i, _i, _i, _vp, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp],
     "jdft_autotune": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp],
+    "jdft_hartree": [_vp, _vp, _vp, _vp, _vp],
+    "jdft_xc_lda": [_vp, _vp, _vp, _vp, _vp],
+    "jdft_ks_potential": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "jdft_pulay_create": [ctypes.c_int64, _i, _d, ctypes.POINTER(_vp)],
+    "jdft_pulay_destroy": [_vp],
+    "jdft_pulay_reset": [_vp],
+    "jdft_pulay_step": [_vp, _vp, _vp, _vp, _vp],
+    "jdft_pulay_used": [_vp, ctypes.POINTER(_i), _vp],
+    "jdft_scf": [_vp, _vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(ScfOpts), ctypes.POINTER(ScfReport), _vp],
+    "jdft_field_I": [_vp, _vp, _vp, _vp],
+    "jdft_field_J": [_vp, _vp, _vp, _vp],
+    "jdft_pcm_hessian": [_vp, _vp, _vp, _vp, _vp],
+    "jdft_pcm_solve": [_vp, _vp, _vp, _vp, _d, _i, _vp, _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -365,6 +395,143 @@ def jdft_minimize_bands(basis, ik, C, eigs=None, tol=1e-8, max_iter=1000, precon
     out["status"] = STATUS.get(st, st)
     if check and st != 0:
         raise JdftError(st, "jdft_minimize_bands", L.jdft_last_error().decode())
+    return out
+
+
+def _field(t, name, N=None):
+    """Pointer of a real FP64 box (a contiguous float64 CUDA tensor)."""
+    import torch
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if N is not None and t.numel() != N:
+        raise ValueError(f"{name} must hold {N} values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def jdft_hartree(basis, n, vh, energy=None, stream=None):
+    """vh = V_H[n]; energy (float64 CUDA tensor of 1, optional) = E_H."""
+    N = int(np.prod(basis.S))
+    _call("jdft_hartree", basis.handle, _field(n, "n", N), _field(vh, "vh", N),
+          _ptr(energy), _stream(stream))
+
+
+def jdft_xc_lda(basis, n, vxc=None, energy=None, stream=None):
+    """vxc = v_xc[n] (optional); energy (float64 CUDA tensor of 1, optional) = E_xc."""
+    N = int(np.prod(basis.S))
+    _call("jdft_xc_lda", basis.handle, _field(n, "n", N), None if vxc is None else _field(vxc, "vxc", N),
+          _ptr(energy), _stream(stream))
+
+
+def jdft_ks_potential(basis, n, vion, vks, energies=None, stream=None):
+    """vks = vion + V_H[n] + v_xc[n]; energies (float64 CUDA tensor of 2, optional) = (E_H, E_xc)."""
+    N = int(np.prod(basis.S))
+    _call("jdft_ks_potential", basis.handle, _field(n, "n", N), _field(vion, "vion", N), _field(vks, "vks", N),
+          _ptr(energies), _stream(stream))
+
+
+class Pulay:
+    """Owner of a jdft_pulay_t density mixer (see jdft_pulay_create)."""
+
+    def __init__(self, n: int, history: int = 8, alpha: float = 0.5):
+        h = ctypes.c_void_p()
+        _call("jdft_pulay_create", int(n), int(history), float(alpha), ctypes.byref(h))
+        self.handle = h
+        self.n = int(n)
+
+    def step(self, n_in, n_out, n_next, stream=None):
+        _call("jdft_pulay_step", self.handle, _field(n_in, "n_in", self.n), _field(n_out, "n_out", self.n),
+              _field(n_next, "n_next", self.n), _stream(stream))
+
+    def used(self, stream=None) -> int:
+        u = ctypes.c_int()
+        _call("jdft_pulay_used", self.handle, ctypes.byref(u), _stream(stream))
+        return u.value
+
+    def reset(self):
+        _call("jdft_pulay_reset", self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().jdft_pulay_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def jdft_scf(basis, C, vion, n_r, eigs=None, tol_energy=1e-8, tol_density=1e-6, max_iter=100, history=8,
+             alpha=0.5, band_tol=1e-9, band_max_iter=1000, precond="teter", prec="fp64", occupation=2.0,
+             mlp=None, stream=None, check=True) -> dict:
+    """SCF loop; C: list of nk complex128 (nb, ld) CUDA blocks (updated in place).  Returns the report."""
+    if len(C) != basis.nk:
+        raise ValueError("one coefficient block per k-point is required")
+    blocks = [_block(c, "fp64", f"C[{i}]") for i, c in enumerate(C)]
+    ld, nb = blocks[0][1], blocks[0][2]
+    if any(b[1] != ld or b[2] != nb for b in blocks):
+        raise ValueError("all blocks need the same band count and row stride (views of (nb, ld) storage with "
+                         "ld >= the largest npw)")
+    ptrs = (ctypes.c_void_p * len(C))(*[b[0].value for b in blocks])
+    N = int(np.prod(basis.S))
+    o = ScfOpts(tol_energy, tol_density, max_iter, history, alpha, band_tol, band_max_iter,
+                PRECOND[precond] if isinstance(precond, str) else int(precond), _prec(prec), occupation,
+                ctypes.c_void_p(0 if mlp is None else mlp.handle.value))
+    r = ScfReport()
+    L = lib()
+    st = L.jdft_scf(basis.handle, ctypes.cast(ptrs, ctypes.c_void_p), ld, nb, _field(vion, "vion", N),
+                    _field(n_r, "n_r", N), _ptr(eigs), ctypes.byref(o), ctypes.byref(r), _stream(stream))
+    out = r.as_dict()
+    out["status"] = STATUS.get(st, st)
+    if check and st != 0:
+        raise JdftError(st, "jdft_scf", L.jdft_last_error().decode())
+    return out
+
+
+class PcmReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
+                ("A_diel", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _cfield(t, name, N):
+    """Pointer of a complex128 box (a contiguous CUDA tensor of N values)."""
+    import torch
+    if not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous() or t.numel() != N:
+        raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor of {N} values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def jdft_field_I(basis, X, x, stream=None):
+    N = int(np.prod(basis.S))
+    _call("jdft_field_I", basis.handle, _cfield(X, "X", N), _cfield(x, "x", N), _stream(stream))
+
+
+def jdft_field_J(basis, x, X, stream=None):
+    N = int(np.prod(basis.S))
+    _call("jdft_field_J", basis.handle, _cfield(x, "x", N), _cfield(X, "X", N), _stream(stream))
+
+
+def jdft_pcm_hessian(basis, eps, phi_t, out_t, stream=None):
+    N = int(np.prod(basis.S))
+    _call("jdft_pcm_hessian", basis.handle, _field(eps, "eps", N), _cfield(phi_t, "phi_t", N),
+          _cfield(out_t, "out_t", N), _stream(stream))
+
+
+def jdft_pcm_solve(basis, eps, rho_t, phi_t, tol=1e-10, max_iter=500, stream=None, check=True) -> dict:
+    """phi_t = hessian^{-1} rho_t (G != 0) by preconditioned CG; returns the report (A_diel included)."""
+    N = int(np.prod(basis.S))
+    r = PcmReport()
+    L = lib()
+    st = L.jdft_pcm_solve(basis.handle, _field(eps, "eps", N), _cfield(rho_t, "rho_t", N), _cfield(phi_t, "phi_t", N),
+                          float(tol), int(max_iter), ctypes.byref(r), _stream(stream))
+    out = r.as_dict()
+    out["status"] = STATUS.get(st, st)
+    if check and st != 0:
+        raise JdftError(st, "jdft_pcm_solve", L.jdft_last_error().decode())
     return out
 
 

@@ -104,3 +104,36 @@ def test_more_null_and_size_arguments_rejected():
     buf = ctypes.create_string_buffer(1)
     assert L.jdft_profile_read(buf, 0) == E
     assert L.jdft_last_error() != b""
+
+
+def test_scf_entry_points_check_arguments_first():
+    """Hartree, LDA, Kohn-Sham potential, Pulay and SCF calls reject null
+    handles, pointers and out-of-range options before any CUDA call."""
+    L = jdft.lib()
+    assert L.jdft_hartree(None, None, None, None, None) == 1
+    assert L.jdft_xc_lda(None, None, None, None, None) == 1
+    assert L.jdft_ks_potential(None, None, None, None, None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.jdft_pulay_create(0, 4, ctypes.c_double(0.5), ctypes.byref(h)) == 1
+    assert L.jdft_pulay_create(100, 0, ctypes.c_double(0.5), ctypes.byref(h)) == 1
+    assert L.jdft_pulay_create(100, 17, ctypes.c_double(0.5), ctypes.byref(h)) == 1
+    assert L.jdft_pulay_create(100, 4, ctypes.c_double(0.0), ctypes.byref(h)) == 1
+    assert L.jdft_pulay_create(100, 4, ctypes.c_double(1.5), ctypes.byref(h)) == 1
+    assert L.jdft_pulay_create(100, 4, ctypes.c_double(0.5), None) == 1
+    assert not h.value
+    assert L.jdft_pulay_step(None, None, None, None, None) == 1
+    assert L.jdft_pulay_used(None, None, None) == 1
+    assert L.jdft_pulay_reset(None) == 1
+    assert L.jdft_pulay_destroy(None) == 0
+    r = jdft.ScfReport()
+    o = jdft.ScfOpts()
+    assert L.jdft_scf(None, None, 0, 1, None, None, None, ctypes.byref(o), ctypes.byref(r), None) == 1
+
+
+def test_field_and_dielectric_entry_points_check_arguments_first():
+    L = jdft.lib()
+    assert L.jdft_field_I(None, None, None, None) == 1
+    assert L.jdft_field_J(None, None, None, None) == 1
+    assert L.jdft_pcm_hessian(None, None, None, None, None) == 1
+    r = jdft.PcmReport()
+    assert L.jdft_pcm_solve(None, None, None, None, ctypes.c_double(1e-8), 10, ctypes.byref(r), None) == 1
