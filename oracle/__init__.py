@@ -15,4 +15,5 @@ Modules:
   scf         Hartree potential, LDA exchange-correlation, Pulay mixing and the
               self-consistent field loop around dense band solves
   pcm         the linear dielectric Poisson solve (hessian, CG, A_diel)
+  spinor      two-component bands in a noncollinear potential: H C, n and m
 """
