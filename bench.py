@@ -787,12 +787,20 @@ def pcm_measurements(device) -> dict:
     rho_t = torch.empty(N, dtype=torch.complex128, device=device)
     jdft.jdft_field_J(b, (-rho).to(torch.complex128), rho_t)
     phi = torch.empty_like(rho_t)
-    rep = None
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rep = jdft.jdft_pcm_solve(b, eps, rho_t, phi, tol=1e-10, max_iter=2000)
-        wall = time.perf_counter() - t0
+    solves = {}
+    for prec in ("fp64", "fp32"):
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = jdft.jdft_pcm_solve(b, eps, rho_t, phi, tol=1e-10, max_iter=2000, prec=prec)
+            wall = time.perf_counter() - t0
+            if best is None or wall < best[0]:
+                best = (wall, rep)
+        wall, rep = best
+        solves[prec] = {"iterations": rep["iterations"], "fp64_hessians": rep["fp64_hessians"],
+                        "residual": rep["residual"], "A_diel_Ha": rep["A_diel"], "solve_seconds": round(wall, 4),
+                        "ms_per_iteration": round(wall / max(1, rep["iterations"]) * 1e3, 4)}
     H = torch.empty_like(phi)
     stream = torch.cuda.current_stream()
     for _ in range(3):
@@ -807,9 +815,7 @@ def pcm_measurements(device) -> dict:
     t_h = a0.elapsed_time(a1) / reps / 1e3
     flops = 6 * 5.0 * N * math.log2(N)      # three inverse and three forward complex 3-D FFTs
     b.close()
-    return {"iterations": rep["iterations"], "residual": rep["residual"], "A_diel_Ha": rep["A_diel"],
-            "solve_seconds": round(wall, 4), "ms_per_iteration": round(wall / max(1, rep["iterations"]) * 1e3, 4),
-            "hessian_ms": round(t_h * 1e3, 4), "hessian_fp64_tflops": round(flops / t_h / 1e12, 3),
+    return {"solve": solves, "hessian_ms": round(t_h * 1e3, 4), "hessian_fp64_tflops": round(flops / t_h / 1e12, 3),
             "hessian_fp64_frac_of_nominal": round(flops / t_h / 1e12 / FP64_NOMINAL_TFLOPS, 3),
             "work": "hessian = 6 complex FP64 3-D FFTs of the box (5 n log2 n each) + gradient, eps product, "
                     "divergence fused into the axis passes"}

@@ -430,6 +430,31 @@ typedef struct {
 jdft_status jdft_scf(jdft_basis_t basis, void* const* C, int ldc, int nb, const double* vion, double* n_r,
                      double* eigs, const jdft_scf_opts* opts, jdft_scf_report* report, void* stream);
 
+/* ---- spinor bands (noncollinear magnetism, Sec. 2.2; ColumnBundle, Sec. 2.1)
+ * A spinor block of nb bands is 2 nb coefficient rows of a band-major block:
+ * row 2b holds band b's up component, row 2b + 1 its down component (same
+ * sphere, ldc >= npw).  The local potential is V 1 + M . sigma: V is the
+ * basis potential (jdft_set_potential), M a real 3-vector field given per
+ * call as device 3 x N doubles (M_x, then M_y, then M_z).  Pauli matrices
+ * sigma_x = [[0,1],[1,0]], sigma_y = [[0,-i],[i,0]], sigma_z = [[1,0],[0,-1]].
+ * JDFT_FP64 (complex128 blocks) or JDFT_FP32 (complex64, FP32 transforms).
+ * Both calls use a spinor workspace of the basis (real-space boxes of a chunk
+ * of bands, at most 256 MB plus the chunk's sphere rows; grown synchronously)
+ * besides the one jdft_apply_H / jdft_op_I use. */
+
+/* HC = H C for nb spinor bands: the scalar Hamiltonian of jdft_apply_H on
+ * every component row, plus Omega J((M . sigma) I C) coupling each band's two
+ * components.  C, HC must not overlap (ldhc >= npw).  Asynchronous. */
+jdft_status jdft_apply_H_spinor(jdft_basis_t basis, int ik, const double* M, const void* C, int ldc, void* HC,
+                                int ldhc, int nb, jdft_prec prec, void* stream);
+
+/* n_r[j] += w_ik sum_b f_b (|psi_up|^2 + |psi_dn|^2) and the magnetisation
+ * m_r[c N + j] += w_ik sum_b f_b psi^dag sigma_c psi (c = x, y, z), psi = I C.
+ * f: device nb doubles; n_r: device N doubles; m_r: device 3 N doubles (both
+ * accumulated; the caller zeroes them).  Asynchronous. */
+jdft_status jdft_density_spinor(jdft_basis_t basis, int ik, const void* C, int ldc, const double* f, int nb,
+                                double* n_r, double* m_r, jdft_prec prec, void* stream);
+
 /* ---- scalar fields and the linear dielectric (Sec. 2.1, Listing 1) --------
  * A reciprocal-space field (ScalarFieldTilde) is a full complex128 box X(G) of
  * N values (device, j2 fastest), slot iG mod S holding G = B iG with
@@ -454,11 +479,12 @@ jdft_status jdft_pcm_hessian(jdft_basis_t basis, const double* eps, const void* 
                              void* stream);
 
 typedef struct {
-    int iterations;         /* CG iterations (one hessian each) */
+    int iterations;         /* CG iterations (one hessian each; FP32 ones for JDFT_FP32) */
     int converged;
-    double residual;        /* |r| / |rho~| at exit (plain sums over the box, G != 0) */
+    double residual;        /* |r| / |rho~| at exit, r = rho~ - hessian(phi~) in FP64 (plain sums, G != 0) */
     double A_diel;          /* (1/2) Re sum_G conj(phi~ - 4 pi rho~ / G^2) Omega rho~ (Ha) */
     double seconds;         /* wall time of the call */
+    int fp64_hessians;      /* FP64 hessians applied (= iterations for JDFT_FP64) */
 } jdft_pcm_report;
 
 /* Solve -4 pi rho = div(eps grad phi) for phi~ by preconditioned conjugate
@@ -467,13 +493,21 @@ typedef struct {
  * Eq. (Adiel) (`getAdiel`).  The G = 0 term of rho~ is ignored (a neutral
  * charge) and phi~(0) = 0.  Preconditioner: the Coulomb kernel 4 pi / G^2 (the
  * exact inverse for eps = 1).  Start phi~ = 0; converged when
- * |r| <= tol |rho~|.  eps: device N doubles (> 0); rho_t, phi_t: device
- * complex128 boxes (phi_t overwritten, not overlapping rho_t).  report: host.
- * Synchronous (one host read of the residual per iteration); uses the basis
- * field workspace (six complex boxes and 1 MB).  JDFT_ERR_NOT_CONVERGED (phi_t
- * and report filled) if max_iter is reached. */
+ * |r| <= tol |rho~|, r = rho~ - hessian(phi~).
+ *   prec JDFT_FP64: CG in FP64 throughout.
+ *   prec JDFT_FP32: iterative refinement (the paper fixes no precision): each
+ *     round solves hessian(e) = r by the same CG in FP32 (fields, transforms
+ *     and eps in FP32, sums in FP64) to 1e-4 of |r|, adds e to phi~ in FP64 and
+ *     forms the new r with one FP64 hessian; it stops at the same tolerance
+ *     on the FP64 residual, or when a round no longer lowers it.
+ * eps: device N doubles (> 0); rho_t, phi_t: device complex128 boxes (phi_t
+ * overwritten, not overlapping rho_t).  max_iter: limit on CG iterations (all
+ * rounds).  report: host.  Synchronous (one host read of the residual per
+ * iteration); uses the basis field workspace (JDFT_FP64: six complex128
+ * boxes; JDFT_FP32: ten; and 1 MB).  JDFT_ERR_NOT_CONVERGED (phi_t and report
+ * filled) if the tolerance is not reached. */
 jdft_status jdft_pcm_solve(jdft_basis_t basis, const double* eps, const void* rho_t, void* phi_t, double tol,
-                           int max_iter, jdft_pcm_report* report, void* stream);
+                           int max_iter, jdft_prec prec, jdft_pcm_report* report, void* stream);
 
 /* ---- schedule autotuning (the paper has no counterpart) ------------------ */
 

@@ -512,16 +512,57 @@ __device__ __forceinline__ void line_index(const AxisGeom& g, int nw, int idx, i
     if (g.es == 1) { w = idx / g.n; t = idx - w * g.n; } else { t = idx / nw; w = idx - t * nw; }
 }
 
+// Complex element of type T from double parts, and back.
+template <typename T> __device__ __forceinline__ c_t<T> cx(double re, double im) { return mk<T>((T)re, (T)im); }
+
+// One axis pass over complex boxes of type T (batch of boxes via blockIdx.y,
+// bstride apart), in place or out of place.
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(kFieldThreads)
+field_axis_c_kernel(const c_t<T>* __restrict__ in, c_t<T>* __restrict__ out, AxisGeom g, FftPlan plan,
+                    const c_t<T>* __restrict__ tw, int64_t bstride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    c_t<T>* bufA = reinterpret_cast<c_t<T>*>(smem_raw);
+    c_t<T>* bufB = bufA + g.W * g.n;
+    int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
+    in += blockIdx.y * bstride;
+    out += blockIdx.y * bstride;
+    const int64_t l0 = (int64_t)blockIdx.x * g.W;
+    const int64_t left = g.nlines - l0;
+    const int nw = left < g.W ? (int)left : g.W;
+    const int n = g.n;
+    if (threadIdx.x < nw) {
+        const int64_t l = l0 + threadIdx.x;
+        const int64_t o = l / g.inner;
+        base[threadIdx.x] = o * g.ostride + (l - o * g.inner) * g.istride;
+    }
+    __syncthreads();
+    const int total = nw * n;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int w, t;
+        line_index(g, nw, idx, w, t);
+        bufA[w * n + t] = in[base[w] + (int64_t)t * g.es];
+    }
+    __syncthreads();
+    const c_t<T>* res = fft_lines<T, SIGN>(bufA, bufB, nw, n, plan, tw);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int w, t;
+        line_index(g, nw, idx, w, t);
+        out[base[w] + (int64_t)t * g.es] = res[w * n + t];
+    }
+}
+
 // Axis 0 of the gradient's inverse transform: for each line of X (reciprocal
 // space; lines along axis 0, l = m1 S2 + m2), Y_c = I_0 (i G_c X), c = 0, 1, 2
 // (boxes bstride apart).
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_grad_axis0_kernel(const double2* __restrict__ X, double2* __restrict__ Y, AxisGeom g, FftPlan plan,
-                      const double2* __restrict__ tw, GArgs q, int64_t bstride) {
+pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, AxisGeom g, FftPlan plan,
+                      const c_t<T>* __restrict__ tw, GArgs q, int64_t bstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* bufX = reinterpret_cast<double2*>(smem_raw);
-    double2* bufA = bufX + g.W * g.n;
-    double2* bufB = bufA + g.W * g.n;
+    c_t<T>* bufX = reinterpret_cast<c_t<T>*>(smem_raw);
+    c_t<T>* bufA = bufX + g.W * g.n;
+    c_t<T>* bufB = bufA + g.W * g.n;
     int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
@@ -541,13 +582,13 @@ pcm_grad_axis0_kernel(const double2* __restrict__ X, double2* __restrict__ Y, Ax
             const int w = idx / n, t = idx - w * n;
             const int64_t l = l0 + w;
             const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
-            const double G = g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
-            const double2 x = bufX[idx];
-            bufA[idx] = make_double2(-G * x.y, G * x.x);
+            const T G = (T)g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
+            const c_t<T> x = bufX[idx];
+            bufA[idx] = mk<T>(-G * x.y, G * x.x);
         }
         __syncthreads();
-        const double2* res = fft_lines<double, +1>(bufA, bufB, nw, n, plan, tw);
-        double2* Yc = Y + c * bstride;
+        const c_t<T>* res = fft_lines<T, +1>(bufA, bufB, nw, n, plan, tw);
+        c_t<T>* Yc = Y + c * bstride;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int w, t;
             line_index(g, nw, idx, w, t);
@@ -559,12 +600,13 @@ pcm_grad_axis0_kernel(const double2* __restrict__ X, double2* __restrict__ Y, Ax
 
 // Axis 2 (contiguous lines) of each gradient box (blockIdx.y): inverse
 // transform, pointwise product with eps(r), forward transform, in place.
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_eps_axis2_kernel(double2* __restrict__ Y, const double* __restrict__ eps, AxisGeom g, FftPlan plan,
-                     const double2* __restrict__ tw, int64_t bstride) {
+pcm_eps_axis2_kernel(c_t<T>* __restrict__ Y, const T* __restrict__ eps, AxisGeom g, FftPlan plan,
+                     const c_t<T>* __restrict__ tw, int64_t bstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* bufA = reinterpret_cast<double2*>(smem_raw);
-    double2* bufB = bufA + g.W * g.n;
+    c_t<T>* bufA = reinterpret_cast<c_t<T>*>(smem_raw);
+    c_t<T>* bufB = bufA + g.W * g.n;
     Y += blockIdx.y * bstride;
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
@@ -574,28 +616,29 @@ pcm_eps_axis2_kernel(double2* __restrict__ Y, const double* __restrict__ eps, Ax
     const int64_t off = l0 * n;   // axis 2: line l starts at l * S2, contiguous
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) bufA[idx] = Y[off + idx];
     __syncthreads();
-    double2* res = fft_lines<double, +1>(bufA, bufB, nw, n, plan, tw);
+    c_t<T>* res = fft_lines<T, +1>(bufA, bufB, nw, n, plan, tw);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const double e = eps[off + idx];
+        const T e = eps[off + idx];
         res[idx].x *= e;
         res[idx].y *= e;
     }
     __syncthreads();
-    double2* other = (res == bufA) ? bufB : bufA;
-    res = fft_lines<double, -1>(res, other, nw, n, plan, tw);
+    c_t<T>* other = (res == bufA) ? bufB : bufA;
+    res = fft_lines<T, -1>(res, other, nw, n, plan, tw);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) Y[off + idx] = res[idx];
 }
 
 // Axis 0 of the forward transforms and the divergence: out = scale *
 // sum_c i G_c F_0(Y_c); with din, per-block partial sums of Re conj(din) out.
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_div_axis0_kernel(const double2* __restrict__ Y, const double2* __restrict__ din, double2* __restrict__ out,
-                     AxisGeom g, FftPlan plan, const double2* __restrict__ tw, GArgs q, int64_t bstride,
+pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ din, c_t<T>* __restrict__ out,
+                     AxisGeom g, FftPlan plan, const c_t<T>* __restrict__ tw, GArgs q, int64_t bstride,
                      double scale, double* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* acc = reinterpret_cast<double2*>(smem_raw);
-    double2* bufA = acc + g.W * g.n;
-    double2* bufB = bufA + g.W * g.n;
+    c_t<T>* acc = reinterpret_cast<c_t<T>*>(smem_raw);
+    c_t<T>* bufA = acc + g.W * g.n;
+    c_t<T>* bufB = bufA + g.W * g.n;
     int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
@@ -603,60 +646,63 @@ pcm_div_axis0_kernel(const double2* __restrict__ Y, const double2* __restrict__ 
     const int n = g.n;
     if (threadIdx.x < nw) base[threadIdx.x] = l0 + threadIdx.x;
     const int total = nw * n;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) acc[idx] = make_double2(0.0, 0.0);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) acc[idx] = mk<T>(0, 0);
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
-        const double2* Yc = Y + c * bstride;
+        const c_t<T>* Yc = Y + c * bstride;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int w, t;
             line_index(g, nw, idx, w, t);
             bufA[w * n + t] = Yc[base[w] + (int64_t)t * g.es];
         }
         __syncthreads();
-        const double2* res = fft_lines<double, -1>(bufA, bufB, nw, n, plan, tw);
+        const c_t<T>* res = fft_lines<T, -1>(bufA, bufB, nw, n, plan, tw);
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
             const int64_t l = l0 + w;
             const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
-            const double G = g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
-            const double2 y = res[idx];
+            const T G = (T)g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
+            const c_t<T> y = res[idx];
             acc[idx].x -= G * y.y;
             acc[idx].y += G * y.x;
         }
         __syncthreads();
     }
-    double part = 0.0;
+    T part = 0;
+    const T sc = (T)scale;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int w, t;
         line_index(g, nw, idx, w, t);
         const int64_t addr = base[w] + (int64_t)t * g.es;
-        const double2 v = make_double2(scale * acc[w * n + t].x, scale * acc[w * n + t].y);
+        const c_t<T> v = mk<T>(sc * acc[w * n + t].x, sc * acc[w * n + t].y);
         out[addr] = v;
         if (din) {
-            const double2 dv = din[addr];
+            const c_t<T> dv = din[addr];
             part += dv.x * v.x + dv.y * v.y;
         }
     }
     if (din) {
-        const double t = block_sum(part);
+        const double t = block_sum((double)part);
         if (threadIdx.x == 0) partial[blockIdx.x] = t;
     }
 }
 
-// CG start: r = rho~ without its G = 0 term, x = 0, d = K r; partial sums of
-// |r|^2 and r.Kr (two per block).
+// CG start: r = rho~ without its G = 0 term (converted to T), x = 0 (if x),
+// d = K r; partial sums of |r|^2 and r.Kr (two per block).
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_init_kernel(const double2* __restrict__ rho, double2* __restrict__ x, double2* __restrict__ r,
-                double2* __restrict__ d, GArgs q, int64_t N, double* __restrict__ partial) {
+pcm_init_kernel(const double2* __restrict__ rho, c_t<T>* __restrict__ x, c_t<T>* __restrict__ r,
+                c_t<T>* __restrict__ d, GArgs q, int64_t N, double* __restrict__ partial) {
     double rr = 0.0, rz = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         const double G2 = g2_of_index(q, j);
         const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
         const double2 v = G2 > 0.0 ? rho[j] : make_double2(0.0, 0.0);
-        r[j] = v;
-        x[j] = make_double2(0.0, 0.0);
-        d[j] = make_double2(K * v.x, K * v.y);
-        const double a = v.x * v.x + v.y * v.y;
+        const c_t<T> vt = cx<T>(v.x, v.y);
+        r[j] = vt;
+        if (x) x[j] = mk<T>(0, 0);
+        d[j] = mk<T>((T)K * vt.x, (T)K * vt.y);
+        const double a = (double)vt.x * vt.x + (double)vt.y * vt.y;
         rr += a;
         rz += K * a;
     }
@@ -667,41 +713,80 @@ pcm_init_kernel(const double2* __restrict__ rho, double2* __restrict__ x, double
 
 // x += alpha d, r -= alpha Hd with alpha = rz / dHd (device scalars); partial
 // sums of |r|^2 and r.Kr of the new residual.
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_update_kernel(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ d,
-                  const double2* __restrict__ Hd, const double* __restrict__ rz, const double* __restrict__ dHd,
+pcm_update_kernel(c_t<T>* __restrict__ x, c_t<T>* __restrict__ r, const c_t<T>* __restrict__ d,
+                  const c_t<T>* __restrict__ Hd, const double* __restrict__ rz, const double* __restrict__ dHd,
                   GArgs q, int64_t N, double* __restrict__ partial) {
-    const double alpha = *rz / *dHd;
-    double rr = 0.0, rzn = 0.0;
+    const T alpha = (T)(*rz / *dHd);
+    T rr = 0, rzn = 0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double2 dv = d[j], hv = Hd[j];
-        double2 xv = x[j], rv = r[j];
+        const c_t<T> dv = d[j], hv = Hd[j];
+        c_t<T> xv = x[j], rv = r[j];
         xv.x += alpha * dv.x; xv.y += alpha * dv.y;
         rv.x -= alpha * hv.x; rv.y -= alpha * hv.y;
         x[j] = xv;
         r[j] = rv;
         const double G2 = g2_of_index(q, j);
-        const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
-        const double a = rv.x * rv.x + rv.y * rv.y;
+        const T K = G2 > 0.0 ? (T)(kFourPi / G2) : (T)0;
+        const T a = rv.x * rv.x + rv.y * rv.y;
         rr += a;
         rzn += K * a;
     }
-    const double s0 = block_sum(rr);
-    const double s1 = block_sum(rzn);
+    const double s0 = block_sum((double)rr);
+    const double s1 = block_sum((double)rzn);
     if (threadIdx.x == 0) { partial[2 * blockIdx.x] = s0; partial[2 * blockIdx.x + 1] = s1; }
 }
 
 // d = K r + beta d, beta = rz_new / rz_old (device scalars).
+template <typename T>
 __global__ void __launch_bounds__(kFieldThreads)
-pcm_direction_kernel(const double2* __restrict__ r, double2* __restrict__ d, const double* __restrict__ rz_new,
+pcm_direction_kernel(const c_t<T>* __restrict__ r, c_t<T>* __restrict__ d, const double* __restrict__ rz_new,
                      const double* __restrict__ rz_old, GArgs q, int64_t N) {
-    const double beta = *rz_new / *rz_old;
+    const T beta = (T)(*rz_new / *rz_old);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         const double G2 = g2_of_index(q, j);
-        const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
-        const double2 rv = r[j], dv = d[j];
-        d[j] = make_double2(K * rv.x + beta * dv.x, K * rv.y + beta * dv.y);
+        const T K = G2 > 0.0 ? (T)(kFourPi / G2) : (T)0;
+        const c_t<T> rv = r[j], dv = d[j];
+        d[j] = mk<T>(K * rv.x + beta * dv.x, K * rv.y + beta * dv.y);
     }
+}
+
+// Mixed solve, refinement step: x += e (FP32 correction), then (after the
+// FP64 hessian of x into Hx) r = rho~ - Hx on G != 0 with partial |r|^2.
+__global__ void __launch_bounds__(kFieldThreads)
+pcm_accumulate_kernel(double2* __restrict__ x, const float2* __restrict__ e, int64_t N) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const float2 ev = e[j];
+        double2 xv = x[j];
+        xv.x += (double)ev.x;
+        xv.y += (double)ev.y;
+        x[j] = xv;
+    }
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+pcm_residual_kernel(const double2* __restrict__ rho, const double2* __restrict__ Hx, double2* __restrict__ r, GArgs q,
+                    int64_t N, double* __restrict__ partial) {
+    double rr = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const double G2 = g2_of_index(q, j);
+        double2 v = make_double2(0.0, 0.0);
+        if (G2 > 0.0) {
+            const double2 a = rho[j], h = Hx[j];
+            v = make_double2(a.x - h.x, a.y - h.y);
+        }
+        r[j] = v;
+        rr += v.x * v.x + v.y * v.y;
+    }
+    const double s = block_sum(rr);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t N) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+        b[j] = (float)a[j];
 }
 
 // Partial sums of Re conj(phi~ - K rho~) rho~ over G != 0.
@@ -728,48 +813,124 @@ GArgs g_args(const jdft_basis_s* b) {
     return q;
 }
 
+template <typename T> const c_t<T>* twiddles_of(const jdft_basis_s* b);
+template <> const double2* twiddles_of<double>(const jdft_basis_s* b) { return b->tw64; }
+template <> const float2* twiddles_of<float>(const jdft_basis_s* b) { return b->tw32; }
+
 // hessian of X into out (out must overlap neither X nor the three gradient
 // boxes Yg); with din, partial sums of Re conj(din) out into partial.
-jdft_status pcm_hessian(jdft_basis_s* b, const double* eps, const double2* X, double2* out, double2* Yg,
-                        const double2* din, double* partial, int* nblocks, cudaStream_t st) {
+template <typename T>
+jdft_status pcm_hessian(jdft_basis_s* b, const T* eps, const c_t<T>* X, c_t<T>* out, c_t<T>* Yg,
+                        const c_t<T>* din, double* partial, int* nblocks, cudaStream_t st) {
     const GArgs q = g_args(b);
-    const AxisGeom g0 = axis_geom(b, 0), g2 = axis_geom(b, 2);
+    const AxisGeom g0 = axis_geom(b, 0), g1 = axis_geom(b, 1), g2 = axis_geom(b, 2);
     const int64_t grid0 = (g0.nlines + g0.W - 1) / g0.W;
+    const int64_t grid1 = (g1.nlines + g1.W - 1) / g1.W;
     const int64_t grid2 = (g2.nlines + g2.W - 1) / g2.W;
     if (grid0 > kPartialMax - 16) return set_error(JDFT_ERR_ARG, "box too large for the partial sums");
-    const size_t smem3 = (size_t)3 * g0.W * g0.n * sizeof(double2) + g0.W * sizeof(int64_t);
-    const size_t smem2 = (size_t)2 * g2.W * g2.n * sizeof(double2);
-    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_grad_axis0_kernel, smem3));
-    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_div_axis0_kernel, smem3));
-    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_eps_axis2_kernel, smem2));
-    const FftPlan p0 = b->plan[0], p2 = b->plan[2];
+    const size_t e = sizeof(c_t<T>);
+    const size_t smem3 = (size_t)3 * g0.W * g0.n * e + g0.W * sizeof(int64_t);
+    const size_t smem1 = (size_t)2 * g1.W * g1.n * e + g1.W * sizeof(int64_t);
+    const size_t smem2 = (size_t)2 * g2.W * g2.n * e;
+    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_grad_axis0_kernel<T>, smem3));
+    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_div_axis0_kernel<T>, smem3));
+    JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_eps_axis2_kernel<T>, smem2));
+    JDFT_CUDA_TRY(set_smem_attr((const void*)field_axis_c_kernel<T, +1>, smem1));
+    JDFT_CUDA_TRY(set_smem_attr((const void*)field_axis_c_kernel<T, -1>, smem1));
+    const FftPlan p0 = b->plan[0], p1 = b->plan[1], p2 = b->plan[2];
+    const c_t<T>* tw = twiddles_of<T>(b);
     const int64_t N = b->N;
     {
         Trace tr_("pcm_grad_axis0", st);
-        pcm_grad_axis0_kernel<<<(unsigned)grid0, kFieldThreads, smem3, st>>>(X, Yg, g0, p0, b->tw64 + p0.tw_offset,
-                                                                              q, N);
+        pcm_grad_axis0_kernel<T><<<(unsigned)grid0, kFieldThreads, smem3, st>>>(X, Yg, g0, p0, tw + p0.tw_offset, q,
+                                                                                 N);
     }
     jdft_status s = check_launch("pcm_grad_axis0");
     if (s) return s;
-    FieldArgs a = field_args(b, partial);
-    if ((s = launch_axis<+1, false, false, OUT_COMPLEX>("field_fft_axis1", b, 1, Yg, Yg, a, st, nullptr, 3)))
-        return s;
+    {
+        Trace tr_("field_fft_axis1_batch", st);
+        field_axis_c_kernel<T, +1><<<dim3((unsigned)grid1, 3), kFieldThreads, smem1, st>>>(Yg, Yg, g1, p1,
+                                                                                          tw + p1.tw_offset, N);
+    }
+    if ((s = check_launch("field_fft_axis1_batch"))) return s;
     {
         Trace tr_("pcm_eps_axis2", st);
-        pcm_eps_axis2_kernel<<<dim3((unsigned)grid2, 3), kFieldThreads, smem2, st>>>(Yg, eps, g2, p2,
-                                                                                    b->tw64 + p2.tw_offset, N);
+        pcm_eps_axis2_kernel<T><<<dim3((unsigned)grid2, 3), kFieldThreads, smem2, st>>>(Yg, eps, g2, p2,
+                                                                                       tw + p2.tw_offset, N);
     }
     if ((s = check_launch("pcm_eps_axis2"))) return s;
-    if ((s = launch_axis<-1, false, false, OUT_COMPLEX>("field_fft_axis1", b, 1, Yg, Yg, a, st, nullptr, 3)))
-        return s;
+    {
+        Trace tr_("field_fft_axis1_batch", st);
+        field_axis_c_kernel<T, -1><<<dim3((unsigned)grid1, 3), kFieldThreads, smem1, st>>>(Yg, Yg, g1, p1,
+                                                                                          tw + p1.tw_offset, N);
+    }
+    if ((s = check_launch("field_fft_axis1_batch"))) return s;
     {
         Trace tr_("pcm_div_axis0", st);
-        pcm_div_axis0_kernel<<<(unsigned)grid0, kFieldThreads, smem3, st>>>(
-            Yg, din, out, g0, p0, b->tw64 + p0.tw_offset, q, N, -1.0 / (kFourPi * (double)N), partial);
+        pcm_div_axis0_kernel<T><<<(unsigned)grid0, kFieldThreads, smem3, st>>>(
+            Yg, din, out, g0, p0, tw + p0.tw_offset, q, N, -1.0 / (kFourPi * (double)N), partial);
     }
     if (nblocks) *nblocks = (int)grid0;
     return check_launch("pcm_div_axis0");
 }
+
+// Preconditioned CG on hessian(x) = r0 for boxes of type T, from x = 0:
+// r0 is read from rho (FP64; its G = 0 term dropped).  Stops when
+// |r| <= rel_tol |r0| or after max_iter hessians.  Vectors: x, r, d, Hd, Yg
+// (3 boxes).  sc: 8 device doubles of scratch.  Returns the iterations taken
+// and |r| / |r0| at exit.
+template <typename T>
+jdft_status pcm_cg(jdft_basis_s* b, const T* eps, const double2* rho, c_t<T>* x, c_t<T>* r, c_t<T>* d,
+                   c_t<T>* Hd, c_t<T>* Yg, double* partial, double* sc, double rel_tol, int max_iter,
+                   int* iters, double* rel_res, double* r0norm, cudaStream_t st) {
+    const int64_t N = b->N;
+    const int grid = reduce_grid(N);
+    const GArgs q = g_args(b);
+    jdft_status s;
+    {
+        Trace tr_("pcm_init", st);
+        pcm_init_kernel<T><<<grid, kFieldThreads, 0, st>>>(rho, x, r, d, q, N, partial);
+    }
+    if ((s = check_launch("pcm_init"))) return s;
+    if ((s = launch_reduce(partial, grid, 2, 2, 1.0, sc + 2, false, st))) return s;
+    double host[2];
+    JDFT_CUDA_TRY(cudaMemcpyAsync(host, sc + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+    const double bnorm = std::sqrt(host[0]);
+    if (r0norm) *r0norm = bnorm;
+    double res = 0.0;
+    int it = 0;
+    if (bnorm > 0.0) {
+        res = 1.0;
+        for (it = 0; it < max_iter;) {
+            int nb0 = 0;
+            if ((s = pcm_hessian<T>(b, eps, d, Hd, Yg, d, partial, &nb0, st))) return s;
+            if ((s = launch_reduce(partial, nb0, 1, 1, 1.0, sc, false, st))) return s;
+            double* old = sc + 2 + 2 * (it & 1);
+            double* nw = sc + 2 + 2 * ((it + 1) & 1);
+            {
+                Trace tr_("pcm_update", st);
+                pcm_update_kernel<T><<<grid, kFieldThreads, 0, st>>>(x, r, d, Hd, old + 1, sc, q, N, partial);
+            }
+            if ((s = check_launch("pcm_update"))) return s;
+            if ((s = launch_reduce(partial, grid, 2, 2, 1.0, nw, false, st))) return s;
+            JDFT_CUDA_TRY(cudaMemcpyAsync(host, nw, sizeof(double), cudaMemcpyDeviceToHost, st));
+            JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+            ++it;
+            res = std::sqrt(host[0]) / bnorm;
+            if (!(res > rel_tol)) break;
+            {
+                Trace tr_("pcm_direction", st);
+                pcm_direction_kernel<T><<<grid, kFieldThreads, 0, st>>>(r, d, nw + 1, old + 1, q, N);
+            }
+            if ((s = check_launch("pcm_direction"))) return s;
+        }
+    }
+    *iters = it;
+    *rel_res = res;
+    return JDFT_OK;
+}
+
 }  // namespace
 }  // namespace jdft
 
@@ -1071,66 +1232,93 @@ jdft_status jdft_pcm_hessian(jdft_basis_t b, const double* eps, const void* phi_
     FieldWork w;
     jdft_status s = field_work(b, &w, 3);
     if (s) return s;
-    return pcm_hessian(b, eps, (const double2*)phi_t, (double2*)out_t, w.box, nullptr, w.partial, nullptr,
-                       (cudaStream_t)stream);
+    return pcm_hessian<double>(b, eps, (const double2*)phi_t, (double2*)out_t, w.box, nullptr, w.partial, nullptr,
+                               (cudaStream_t)stream);
 }
 
 jdft_status jdft_pcm_solve(jdft_basis_t b, const double* eps, const void* rho_t, void* phi_t, double tol,
-                           int max_iter, jdft_pcm_report* report, void* stream) {
+                           int max_iter, jdft_prec prec, jdft_pcm_report* report, void* stream) {
     clear_error();
     JDFT_CHECK_ARG(b && eps && rho_t && phi_t && report, "null argument");
     JDFT_CHECK_ARG(rho_t != phi_t, "phi_t must not overlap rho_t");
     JDFT_CHECK_ARG(tol > 0 && max_iter >= 1, "bad tolerance or iteration limit");
+    JDFT_CHECK_ARG(prec == JDFT_FP64 || prec == JDFT_FP32, "prec must be JDFT_FP64 or JDFT_FP32");
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     *report = jdft_pcm_report();
-    FieldWork w;
-    // boxes: three gradient components, r, d, Hd; scalars after the partial sums
-    jdft_status s = field_work(b, &w, 6);
-    if (s) return s;
     const int64_t N = b->N;
-    double2 *Yg = w.box, *r = w.box + 3 * N, *d = w.box + 4 * N, *Hd = w.box + 5 * N;
     double2* x = (double2*)phi_t;
     const double2* rho = (const double2*)rho_t;
-    double* sc = w.partial + kPartialMax - 8;    // [dHd, -, rr0, rz0, rr1, rz1, A]
-    const int grid = reduce_grid(N);
     const GArgs q = g_args(b);
-    {
-        Trace tr_("pcm_init", st);
-        pcm_init_kernel<<<grid, kFieldThreads, 0, st>>>(rho, x, r, d, q, N, w.partial);
-    }
-    if ((s = check_launch("pcm_init"))) return s;
-    if ((s = launch_reduce(w.partial, grid, 2, 2, 1.0, sc + 2, false, st))) return s;
-    double host[2];
-    JDFT_CUDA_TRY(cudaMemcpyAsync(host, sc + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    JDFT_CUDA_TRY(cudaStreamSynchronize(st));
-    const double bnorm = std::sqrt(host[0]);
+    const int grid = reduce_grid(N);
+    FieldWork w;
+    jdft_status s;
     double res = 0.0;
-    int it = 0;
-    if (bnorm > 0.0) {
-        res = 1.0;
-        for (it = 0; it < max_iter;) {
-            int nb0 = 0;
-            if ((s = pcm_hessian(b, eps, d, Hd, Yg, d, w.partial, &nb0, st))) return s;
-            if ((s = launch_reduce(w.partial, nb0, 1, 1, 1.0, sc, false, st))) return s;
-            double* old = sc + 2 + 2 * (it & 1);
-            double* nw = sc + 2 + 2 * ((it + 1) & 1);
+    int its = 0, its64 = 0;
+    if (prec == JDFT_FP64) {
+        // boxes: three gradient components, r, d, Hd
+        if ((s = field_work(b, &w, 6))) return s;
+        double* sc = w.partial + kPartialMax - 8;
+        if ((s = pcm_cg<double>(b, eps, rho, x, w.box + 3 * N, w.box + 4 * N, w.box + 5 * N, w.box, w.partial, sc, tol,
+                                max_iter, &its, &res, nullptr, st)))
+            return s;
+        its64 = its;
+    } else {
+        // FP32 corrections, FP64 residuals: FP64 boxes Yg (3), r, Hx; FP32 boxes
+        // Yg (3), r, d, Hd, e (8 bytes each, 4 per FP64 box slot pair) and eps.
+        const int64_t f64 = 5, f32_boxes = 7;
+        const int64_t nbox = f64 + (f32_boxes + 1) / 2 + 1;     // FP32 boxes packed two per slot, eps in one
+        if ((s = field_work(b, &w, (int)nbox))) return s;
+        double2 *Yg64 = w.box, *r64 = w.box + 3 * N, *Hx = w.box + 4 * N;
+        float2* f = reinterpret_cast<float2*>(w.box + f64 * N);
+        float2 *Yg32 = f, *r32 = f + 3 * N, *d32 = f + 4 * N, *Hd32 = f + 5 * N, *e32 = f + 6 * N;
+        float* eps32 = reinterpret_cast<float*>(f + 8 * N);
+        double* sc = w.partial + kPartialMax - 8;
+        {
+            Trace tr_("to_float", st);
+            to_float_kernel<<<grid, kFieldThreads, 0, st>>>(eps, eps32, N);
+        }
+        if ((s = check_launch("to_float"))) return s;
+        // x = 0, r = rho~ (G != 0): the residual of x = 0
+        {
+            Trace tr_("pcm_residual", st);
+            JDFT_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double2), st));
+            JDFT_CUDA_TRY(cudaMemsetAsync(Hx, 0, N * sizeof(double2), st));
+            pcm_residual_kernel<<<grid, kFieldThreads, 0, st>>>(rho, Hx, r64, q, N, w.partial);
+        }
+        if ((s = check_launch("pcm_residual"))) return s;
+        if ((s = launch_reduce(w.partial, grid, 1, 1, 1.0, sc + 7, false, st))) return s;
+        double host = 0.0;
+        JDFT_CUDA_TRY(cudaMemcpyAsync(&host, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+        JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+        const double bnorm = std::sqrt(host);
+        res = bnorm > 0.0 ? 1.0 : 0.0;
+        const double inner_tol = 1e-4;
+        while (res > tol && its < max_iter) {
+            int it_in = 0;
+            double rel_in = 0.0;
+            if ((s = pcm_cg<float>(b, eps32, r64, e32, r32, d32, Hd32, Yg32, w.partial, sc, inner_tol, max_iter - its,
+                                   &it_in, &rel_in, nullptr, st)))
+                return s;
+            its += it_in;
             {
-                Trace tr_("pcm_update", st);
-                pcm_update_kernel<<<grid, kFieldThreads, 0, st>>>(x, r, d, Hd, old + 1, sc, q, N, w.partial);
+                Trace tr_("pcm_accumulate", st);
+                pcm_accumulate_kernel<<<grid, kFieldThreads, 0, st>>>(x, e32, N);
             }
-            if ((s = check_launch("pcm_update"))) return s;
-            if ((s = launch_reduce(w.partial, grid, 2, 2, 1.0, nw, false, st))) return s;
-            JDFT_CUDA_TRY(cudaMemcpyAsync(host, nw, sizeof(double), cudaMemcpyDeviceToHost, st));
+            if ((s = check_launch("pcm_accumulate"))) return s;
+            if ((s = pcm_hessian<double>(b, eps, x, Hx, Yg64, nullptr, w.partial, nullptr, st))) return s;
+            ++its64;
+            {
+                Trace tr_("pcm_residual", st);
+                pcm_residual_kernel<<<grid, kFieldThreads, 0, st>>>(rho, Hx, r64, q, N, w.partial);
+            }
+            if ((s = check_launch("pcm_residual"))) return s;
+            if ((s = launch_reduce(w.partial, grid, 1, 1, 1.0, sc + 7, false, st))) return s;
+            JDFT_CUDA_TRY(cudaMemcpyAsync(&host, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
             JDFT_CUDA_TRY(cudaStreamSynchronize(st));
-            ++it;
-            res = std::sqrt(host[0]) / bnorm;
-            if (!(res > tol)) break;
-            {
-                Trace tr_("pcm_direction", st);
-                pcm_direction_kernel<<<grid, kFieldThreads, 0, st>>>(r, d, nw + 1, old + 1, q, N);
-            }
-            if ((s = check_launch("pcm_direction"))) return s;
+            const double prev = res;
+            res = std::sqrt(host) / bnorm;
+            if (it_in == 0 || !(res < prev)) break;   // no progress: the FP32 corrections are exhausted
         }
     }
     {
@@ -1138,13 +1326,16 @@ jdft_status jdft_pcm_solve(jdft_basis_t b, const double* eps, const void* rho_t,
         pcm_energy_kernel<<<grid, kFieldThreads, 0, st>>>(x, rho, q, N, w.partial);
     }
     if ((s = check_launch("pcm_energy"))) return s;
+    double* sc = w.partial + kPartialMax - 8;
     if ((s = launch_reduce(w.partial, grid, 1, 1, 0.5 * b->omega, sc + 6, false, st))) return s;
-    JDFT_CUDA_TRY(cudaMemcpyAsync(host, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double A = 0.0;
+    JDFT_CUDA_TRY(cudaMemcpyAsync(&A, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     JDFT_CUDA_TRY(cudaStreamSynchronize(st));
-    report->iterations = it;
+    report->iterations = its;
+    report->fp64_hessians = its64;
     report->residual = res;
     report->converged = (res <= tol) ? 1 : 0;
-    report->A_diel = host[0];
+    report->A_diel = A;
     report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (!report->converged) return set_error(JDFT_ERR_NOT_CONVERGED, "dielectric CG reached its iteration limit");
     return JDFT_OK;

@@ -127,10 +127,12 @@ _SIGS = {
     "jdft_pulay_step": [_vp, _vp, _vp, _vp, _vp],
     "jdft_pulay_used": [_vp, ctypes.POINTER(_i), _vp],
     "jdft_scf": [_vp, _vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(ScfOpts), ctypes.POINTER(ScfReport), _vp],
+    "jdft_apply_H_spinor": [_vp, _i, _vp, _vp, _i, _vp, _i, _i, _i, _vp],
+    "jdft_density_spinor": [_vp, _i, _vp, _i, _vp, _i, _vp, _vp, _i, _vp],
     "jdft_field_I": [_vp, _vp, _vp, _vp],
     "jdft_field_J": [_vp, _vp, _vp, _vp],
     "jdft_pcm_hessian": [_vp, _vp, _vp, _vp, _vp],
-    "jdft_pcm_solve": [_vp, _vp, _vp, _vp, _d, _i, _vp, _vp],
+    "jdft_pcm_solve": [_vp, _vp, _vp, _vp, _d, _i, _i, _vp, _vp],
     "jdft_profile_enable": [_i],
     "jdft_profile_read": [ctypes.c_char_p, _i],
 }
@@ -489,9 +491,30 @@ def jdft_scf(basis, C, vion, n_r, eigs=None, tol_energy=1e-8, tol_density=1e-6, 
     return out
 
 
+def jdft_apply_H_spinor(basis, ik, M, C, HC, prec="fp64", stream=None):
+    """C, HC: (2 nb, ld) blocks, rows alternating up, down; M: float64 CUDA tensor of 3 N (M_x, M_y, M_z)."""
+    p, ld, n2 = _block(C, prec, "C")
+    q, ldh, n2h = _block(HC, prec, "HC")
+    if n2 % 2 or n2h != n2:
+        raise ValueError("spinor blocks need an even number of rows (up, down per band), equal for C and HC")
+    N = int(np.prod(basis.S))
+    _call("jdft_apply_H_spinor", basis.handle, ik, _field(M, "M", 3 * N), p, ld, q, ldh, n2 // 2, _prec(prec),
+          _stream(stream))
+
+
+def jdft_density_spinor(basis, ik, C, f, n_r, m_r, prec="fp64", stream=None):
+    """n_r (N) and m_r (3 N) accumulate the density and magnetisation of the spinor block C (2 nb rows)."""
+    p, ld, n2 = _block(C, prec, "C")
+    if n2 % 2:
+        raise ValueError("spinor blocks need an even number of rows")
+    N = int(np.prod(basis.S))
+    _call("jdft_density_spinor", basis.handle, ik, p, ld, _field(f, "f", n2 // 2), n2 // 2, _field(n_r, "n_r", N),
+          _field(m_r, "m_r", 3 * N), _prec(prec), _stream(stream))
+
+
 class PcmReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
-                ("A_diel", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("A_diel", ctypes.c_double), ("seconds", ctypes.c_double), ("fp64_hessians", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -521,13 +544,15 @@ def jdft_pcm_hessian(basis, eps, phi_t, out_t, stream=None):
           _cfield(out_t, "out_t", N), _stream(stream))
 
 
-def jdft_pcm_solve(basis, eps, rho_t, phi_t, tol=1e-10, max_iter=500, stream=None, check=True) -> dict:
-    """phi_t = hessian^{-1} rho_t (G != 0) by preconditioned CG; returns the report (A_diel included)."""
+def jdft_pcm_solve(basis, eps, rho_t, phi_t, tol=1e-10, max_iter=500, prec="fp64", stream=None,
+                   check=True) -> dict:
+    """phi_t = hessian^{-1} rho_t (G != 0) by preconditioned CG ("fp64") or FP32 CG rounds with FP64
+    residuals ("fp32"); returns the report (A_diel included)."""
     N = int(np.prod(basis.S))
     r = PcmReport()
     L = lib()
     st = L.jdft_pcm_solve(basis.handle, _field(eps, "eps", N), _cfield(rho_t, "rho_t", N), _cfield(phi_t, "phi_t", N),
-                          float(tol), int(max_iter), ctypes.byref(r), _stream(stream))
+                          float(tol), int(max_iter), _prec(prec), ctypes.byref(r), _stream(stream))
     out = r.as_dict()
     out["status"] = STATUS.get(st, st)
     if check and st != 0:

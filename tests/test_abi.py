@@ -136,4 +136,10 @@ def test_field_and_dielectric_entry_points_check_arguments_first():
     assert L.jdft_field_J(None, None, None, None) == 1
     assert L.jdft_pcm_hessian(None, None, None, None, None) == 1
     r = jdft.PcmReport()
-    assert L.jdft_pcm_solve(None, None, None, None, ctypes.c_double(1e-8), 10, ctypes.byref(r), None) == 1
+    assert L.jdft_pcm_solve(None, None, None, None, ctypes.c_double(1e-8), 10, 0, ctypes.byref(r), None) == 1
+
+
+def test_spinor_entry_points_check_arguments_first():
+    L = jdft.lib()
+    assert L.jdft_apply_H_spinor(None, 0, None, None, 0, None, 0, 1, 0, None) == 1
+    assert L.jdft_density_spinor(None, 0, None, 0, None, 1, None, None, 0, None) == 1

@@ -105,8 +105,14 @@ def test_pcm_hessian_of_a_cosine_is_the_hand_divergence():
     basis.close()
 
 
-@pytest.mark.parametrize("name,R,S", BOXES[:3], ids=[b[0] for b in BOXES[:3]])
-def test_pcm_solve_matches_oracle(name, R, S):
+SOLVE_CASES = [(b, p) for b in BOXES[:3] for p in ("fp64", "fp32")]
+
+
+@pytest.mark.parametrize("box,prec", SOLVE_CASES, ids=[f"{b[0]}-{p}" for b, p in SOLVE_CASES])
+def test_pcm_solve_matches_oracle(box, prec):
+    """FP64 CG, and FP32 CG rounds refined with FP64 residuals, both to the
+    oracle's FP64 CG solution at the same tolerance."""
+    name, R, S = box
     basis = jdft.Basis(R, S, 1.0, [(0.0, 0.0, 0.0)])
     eps = _cavity_eps(R, S, 2, 7, eps_bulk=10.0, radius=1.5)
     rho = -pw.vloc_realspace(R, S, atom_positions(R, 2, 7), depth=0.5, width=0.9)
@@ -114,9 +120,13 @@ def test_pcm_solve_matches_oracle(name, R, S):
     ref = pcm.solve(R, S, eps, rho_t, tol=1e-11, max_iter=400)
     assert ref.converged
     phi = torch.empty(rho.size, dtype=torch.complex128, device=DEV)
-    rep = jdft.jdft_pcm_solve(basis, _d(eps), _c(rho_t), phi, tol=1e-11, max_iter=400)
+    rep = jdft.jdft_pcm_solve(basis, _d(eps), _c(rho_t), phi, tol=1e-11, max_iter=400, prec=prec)
     assert rep["converged"] == 1
-    assert abs(rep["iterations"] - ref.iterations) <= 1
+    if prec == "fp64":
+        assert abs(rep["iterations"] - ref.iterations) <= 1
+        assert rep["fp64_hessians"] == rep["iterations"]
+    else:
+        assert rep["fp64_hessians"] <= 6
     assert _rel(phi.cpu().numpy(), ref.phi) < 1e-9
     assert abs(rep["A_diel"] - ref.A_diel) < 1e-9 * abs(ref.A_diel)
     basis.close()
@@ -162,4 +172,30 @@ def test_pcm_energy_between_uniform_bounds_64cubed():
     _, EH = scf.hartree(R, S, rho)
     assert rep["converged"] == 1
     assert (1 / eps.min() - 1) * EH >= rep["A_diel"] >= (1 / eps.max() - 1) * EH
+    basis.close()
+
+
+def test_pcm_mixed_equals_fp64_on_a_128cubed_cavity():
+    """The bench's dielectric (eps 1 inside ~2 bohr of 64 centres, 78.4 outside)
+    on the 128^3 box: the FP32-refined solve reaches the FP64 tolerance and
+    agrees with the FP64 CG."""
+    R, S = np.eye(3) * 20.0, (128, 128, 128)
+    basis = jdft.Basis(R, S, 1.0, [(0.0, 0.0, 0.0)])
+    N = int(np.prod(S))
+    centres = atom_positions(R, 64, 78)
+    shape = torch.empty(N, dtype=torch.float64, device=DEV)
+    jdft.jdft_gaussian_potential(basis, centres, shape, depth=6.0, width=2.0)
+    eps = (1.0 + 77.4 * torch.exp(shape)).contiguous()
+    rho = torch.empty(N, dtype=torch.float64, device=DEV)
+    jdft.jdft_gaussian_potential(basis, centres, rho, depth=0.5, width=0.8)
+    rho_t = torch.empty(N, dtype=torch.complex128, device=DEV)
+    jdft.jdft_field_J(basis, (-rho).to(torch.complex128), rho_t)
+    p64 = torch.empty_like(rho_t)
+    p32 = torch.empty_like(rho_t)
+    r64 = jdft.jdft_pcm_solve(basis, eps, rho_t, p64, tol=1e-10, max_iter=2000, prec="fp64")
+    r32 = jdft.jdft_pcm_solve(basis, eps, rho_t, p32, tol=1e-10, max_iter=2000, prec="fp32")
+    assert r64["converged"] == 1 and r32["converged"] == 1
+    assert r32["residual"] <= 1e-10
+    assert _rel(p32.cpu().numpy(), p64.cpu().numpy()) < 1e-8
+    assert r32["A_diel"] == pytest.approx(r64["A_diel"], rel=1e-10)
     basis.close()
