@@ -356,6 +356,7 @@ jdft_status jdft_basis_destroy(jdft_basis_t b) {
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     cudaFree(b->fwork.ptr);
     cudaFree(b->fieldwork.ptr);
+    cudaFree(b->spinwork.ptr);
     cudaSetDevice(prev);
     delete b;
     return JDFT_OK;

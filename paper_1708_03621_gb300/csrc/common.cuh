@@ -155,6 +155,8 @@ struct jdft_basis_s {
     // full-box field transforms (Hartree, Kohn-Sham potential): a complex FP64
     // box and per-block partial sums (grown on first use)
     jdft::Workspace fieldwork;
+    // spinor calls: real-space boxes and sphere blocks of a band chunk
+    jdft::Workspace spinwork;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
