@@ -758,9 +758,59 @@ def scf_measurements(device, fp32: dict) -> dict:
                       "dE_vs_oracle_Ha": float(f"{abs(rep['energy'] - gold['energy']):.3e}") if gold else None}
     out["small_scf"] = runs
     out["pcm_128cubed"] = pcm_measurements(device)
+    out["spinor"] = spinor_measurements(device)
     out["small_scf_workload"] = ("48^3 'small' cell (L=10, Ecut=20, 4259 PW, 8 atoms, 16 bands, f=2), Gaussian "
                                  "V_ion + projectors, LDA (PZ81) + Hartree, Pulay 8 pairs alpha 0.5; band solves "
                                  "Teter-preconditioned CG warm-started each iteration")
+    return out
+
+
+def spinor_measurements(device) -> dict:
+    """Spinor bands in a noncollinear potential (jdft_apply_H_spinor): the 48^3
+    workload with 16 spinor bands (FP64 and FP32) and the 128^3 workload with
+    64 spinor bands (FP32), a smooth seeded M(r); CUDA events after warm-up.
+    One spinor band-apply = H applied to both components of one band."""
+    import torch
+
+    from paper_1708_03621_gb300 import jdft
+    from synth import WORKLOADS, atom_positions, random_coefficients
+    out = {}
+    stream = torch.cuda.current_stream()
+    for wname, nb, precs in (("small", 16, ("fp64", "fp32")), ("large", 64, ("fp32",))):
+        w = WORKLOADS[wname]
+        atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+        b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+        N = int(np.prod(w.S))
+        V = torch.empty(N, dtype=torch.float64, device=device)
+        jdft.jdft_gaussian_potential(b, atoms, V)
+        jdft.jdft_set_potential(b, V)
+        P = torch.empty((4 * w.natoms, b.npw(0)), dtype=torch.complex128, device=device)
+        jdft.jdft_gaussian_projectors(b, 0, atoms, P)
+        D = torch.tensor(np.diag(np.tile([0.5, -0.3, -0.3, -0.3], w.natoms)), device=device)
+        jdft.jdft_set_projectors(b, 0, P, D)
+        G = b.gvectors(0).astype(np.float64) + np.asarray(w.kfrac[0])
+        q = G @ (2 * np.pi * np.linalg.inv(w.R).T).T
+        C64 = torch.tensor(random_coefficients(np.einsum("ij,ij->i", q, q), 2 * nb, 31), device=device)
+        M = torch.empty(3 * N, dtype=torch.float64, device=device)
+        for c in range(3):
+            jdft.jdft_gaussian_potential(b, atom_positions(w.R, 4, 40 + c), M[c * N:(c + 1) * N], depth=0.2,
+                                         width=2.0)
+        for prec in precs:
+            C = C64 if prec == "fp64" else C64.to(torch.complex64)
+            HC = torch.empty_like(C)
+            for _ in range(3):
+                jdft.jdft_apply_H_spinor(b, 0, M, C, HC, prec)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            a0.record(stream)
+            for _ in range(reps):
+                jdft.jdft_apply_H_spinor(b, 0, M, C, HC, prec)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1) / reps
+            out[f"{wname}_{nb}bands_{prec}"] = {"ms_per_call": round(ms, 4),
+                                               "spinor_band_applies_per_s": round(nb / (ms / 1e3), 1)}
+        b.close()
     return out
 
 

@@ -494,18 +494,29 @@ __device__ __forceinline__ double g_comp(const GArgs& q, int c, double f0, doubl
     return f0 * q.B[3 * c] + f1 * q.B[3 * c + 1] + f2 * q.B[3 * c + 2];
 }
 
-__device__ __forceinline__ double g2_of_index(const GArgs& q, int64_t j) {
-    const int64_t plane = (int64_t)q.S[1] * q.S[2];
-    const int m0 = (int)(j / plane);
-    const int64_t rem = j - (int64_t)m0 * plane;
-    const int m1 = (int)(rem / q.S[2]), m2 = (int)(rem - (int64_t)m1 * q.S[2]);
-    const double f0 = fold(m0, q.S[0]), f1 = fold(m1, q.S[1]), f2 = fold(m2, q.S[2]);
-    double g2 = 0.0;
+// |G|^2 of box slot j in precision T (boxes hold fewer than 2^31 points).
+template <typename T>
+__device__ __forceinline__ T g2_of_index(const GArgs& q, int64_t jj) {
+    const int j = (int)jj;
+    const int plane = q.S[1] * q.S[2];
+    const int m0 = j / plane;
+    const int rem = j - m0 * plane;
+    const int m1 = rem / q.S[2], m2 = rem - m1 * q.S[2];
+    const T f0 = (T)fold(m0, q.S[0]), f1 = (T)fold(m1, q.S[1]), f2 = (T)fold(m2, q.S[2]);
+    T g2 = 0;
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double gc = g_comp(q, c, f0, f1, f2);
+        const T gc = f0 * (T)q.B[3 * c] + f1 * (T)q.B[3 * c + 1] + f2 * (T)q.B[3 * c + 2];
         g2 += gc * gc;
     }
     return g2;
+}
+
+// Coulomb kernel 4 pi / |G|^2 of slot j in precision T (0 at G = 0).
+template <typename T>
+__device__ __forceinline__ T coulomb_of_index(const GArgs& q, int64_t j) {
+    const T g2 = g2_of_index<T>(q, j);
+    return g2 > (T)0 ? (T)kFourPi / g2 : (T)0;
 }
 
 __device__ __forceinline__ void line_index(const AxisGeom& g, int nw, int idx, int& w, int& t) {
@@ -568,7 +579,14 @@ pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, Axis
     const int64_t left = g.nlines - l0;
     const int nw = left < g.W ? (int)left : g.W;
     const int n = g.n;
-    if (threadIdx.x < nw) base[threadIdx.x] = l0 + threadIdx.x;   // axis 0: line l starts at l
+    T* lineG = reinterpret_cast<T*>(base + g.W);                  // per line: sum over axes 1, 2 of G_c
+    if (threadIdx.x < nw) {
+        const int64_t l = l0 + threadIdx.x;
+        base[threadIdx.x] = l;                                      // axis 0: line l starts at l
+        const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
+        const double f1 = fold(m1, q.S[1]), f2 = fold(m2, q.S[2]);
+        for (int c = 0; c < 3; ++c) lineG[3 * threadIdx.x + c] = (T)(f1 * q.B[3 * c + 1] + f2 * q.B[3 * c + 2]);
+    }
     __syncthreads();
     const int total = nw * n;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -578,11 +596,10 @@ pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, Axis
     }
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
+        const T b0 = (T)q.B[3 * c];
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
-            const int64_t l = l0 + w;
-            const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
-            const T G = (T)g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
+            const T G = (T)fold(t, q.S[0]) * b0 + lineG[3 * w + c];
             const c_t<T> x = bufX[idx];
             bufA[idx] = mk<T>(-G * x.y, G * x.x);
         }
@@ -644,7 +661,14 @@ pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ di
     const int64_t left = g.nlines - l0;
     const int nw = left < g.W ? (int)left : g.W;
     const int n = g.n;
-    if (threadIdx.x < nw) base[threadIdx.x] = l0 + threadIdx.x;
+    T* lineG = reinterpret_cast<T*>(base + g.W);                  // per line: sum over axes 1, 2 of G_c
+    if (threadIdx.x < nw) {
+        const int64_t l = l0 + threadIdx.x;
+        base[threadIdx.x] = l;
+        const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
+        const double f1 = fold(m1, q.S[1]), f2 = fold(m2, q.S[2]);
+        for (int c = 0; c < 3; ++c) lineG[3 * threadIdx.x + c] = (T)(f1 * q.B[3 * c + 1] + f2 * q.B[3 * c + 2]);
+    }
     const int total = nw * n;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) acc[idx] = mk<T>(0, 0);
     __syncthreads();
@@ -657,11 +681,10 @@ pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ di
         }
         __syncthreads();
         const c_t<T>* res = fft_lines<T, -1>(bufA, bufB, nw, n, plan, tw);
+        const T b0 = (T)q.B[3 * c];
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
-            const int64_t l = l0 + w;
-            const int m1 = (int)(l / q.S[2]), m2 = (int)(l - (int64_t)m1 * q.S[2]);
-            const T G = (T)g_comp(q, c, fold(t, q.S[0]), fold(m1, q.S[1]), fold(m2, q.S[2]));
+            const T G = (T)fold(t, q.S[0]) * b0 + lineG[3 * w + c];
             const c_t<T> y = res[idx];
             acc[idx].x -= G * y.y;
             acc[idx].y += G * y.x;
@@ -695,7 +718,7 @@ pcm_init_kernel(const double2* __restrict__ rho, c_t<T>* __restrict__ x, c_t<T>*
                 c_t<T>* __restrict__ d, GArgs q, int64_t N, double* __restrict__ partial) {
     double rr = 0.0, rz = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double G2 = g2_of_index(q, j);
+        const double G2 = g2_of_index<double>(q, j);
         const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
         const double2 v = G2 > 0.0 ? rho[j] : make_double2(0.0, 0.0);
         const c_t<T> vt = cx<T>(v.x, v.y);
@@ -727,8 +750,7 @@ pcm_update_kernel(c_t<T>* __restrict__ x, c_t<T>* __restrict__ r, const c_t<T>* 
         rv.x -= alpha * hv.x; rv.y -= alpha * hv.y;
         x[j] = xv;
         r[j] = rv;
-        const double G2 = g2_of_index(q, j);
-        const T K = G2 > 0.0 ? (T)(kFourPi / G2) : (T)0;
+        const T K = coulomb_of_index<T>(q, j);
         const T a = rv.x * rv.x + rv.y * rv.y;
         rr += a;
         rzn += K * a;
@@ -745,8 +767,7 @@ pcm_direction_kernel(const c_t<T>* __restrict__ r, c_t<T>* __restrict__ d, const
                      const double* __restrict__ rz_old, GArgs q, int64_t N) {
     const T beta = (T)(*rz_new / *rz_old);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double G2 = g2_of_index(q, j);
-        const T K = G2 > 0.0 ? (T)(kFourPi / G2) : (T)0;
+        const T K = coulomb_of_index<T>(q, j);
         const c_t<T> rv = r[j], dv = d[j];
         d[j] = mk<T>(K * rv.x + beta * dv.x, K * rv.y + beta * dv.y);
     }
@@ -770,7 +791,7 @@ pcm_residual_kernel(const double2* __restrict__ rho, const double2* __restrict__
                     int64_t N, double* __restrict__ partial) {
     double rr = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double G2 = g2_of_index(q, j);
+        const double G2 = g2_of_index<double>(q, j);
         double2 v = make_double2(0.0, 0.0);
         if (G2 > 0.0) {
             const double2 a = rho[j], h = Hx[j];
@@ -795,7 +816,7 @@ pcm_energy_kernel(const double2* __restrict__ phi, const double2* __restrict__ r
                   double* __restrict__ partial) {
     double e = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const double G2 = g2_of_index(q, j);
+        const double G2 = g2_of_index<double>(q, j);
         if (G2 > 0.0) {
             const double K = kFourPi / G2;
             const double2 p = phi[j], v = rho[j];
@@ -829,7 +850,7 @@ jdft_status pcm_hessian(jdft_basis_s* b, const T* eps, const c_t<T>* X, c_t<T>* 
     const int64_t grid2 = (g2.nlines + g2.W - 1) / g2.W;
     if (grid0 > kPartialMax - 16) return set_error(JDFT_ERR_ARG, "box too large for the partial sums");
     const size_t e = sizeof(c_t<T>);
-    const size_t smem3 = (size_t)3 * g0.W * g0.n * e + g0.W * sizeof(int64_t);
+    const size_t smem3 = (size_t)3 * g0.W * g0.n * e + g0.W * sizeof(int64_t) + (size_t)3 * g0.W * sizeof(T);
     const size_t smem1 = (size_t)2 * g1.W * g1.n * e + g1.W * sizeof(int64_t);
     const size_t smem2 = (size_t)2 * g2.W * g2.n * e;
     JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_grad_axis0_kernel<T>, smem3));
