@@ -16,4 +16,5 @@ Modules:
               self-consistent field loop around dense band solves
   pcm         the linear dielectric Poisson solve (hessian, CG, A_diel)
   spinor      two-component bands in a noncollinear potential: H C, n and m
+  ultrasoft   augmented overlap S = Omega + P Q P^dag and generalised Rayleigh-Ritz
 """
