@@ -455,6 +455,46 @@ jdft_status jdft_apply_H_spinor(jdft_basis_t basis, int ik, const double* M, con
 jdft_status jdft_density_spinor(jdft_basis_t basis, int ik, const void* C, int ldc, const double* f, int nb,
                                 double* n_r, double* m_r, jdft_prec prec, void* stream);
 
+/* ---- augmented overlap (ultrasoft pseudopotentials, Sec. 2.2; O, Sec. 2.1) --
+ * With augmentation charges Q on the projectors of the nonlocal term, the
+ * overlap of coefficient blocks is S C = Omega C + P Q P^dag C and band
+ * energies are the eigenvalues of the pencil (C^dag H C, C^dag S C).  Only
+ * the calls of this section use Q; jdft_op_O, jdft_subspace, the
+ * orthonormalisation, jdft_hamiltonian_step and jdft_minimize_bands keep the
+ * plain O = Omega (the band minimiser does not solve the generalised
+ * problem). */
+
+/* Set (Q: device nproj x nproj doubles, row-major, symmetric; copied) or clear
+ * (Q = NULL) the augmentation of k-point ik's projectors.  Needs the
+ * projectors (jdft_set_projectors, which also clears Q).  Q is kept dense and
+ * as rows of its nonzeros (built on the host: synchronises `stream`).
+ * JDFT_ERR_ARG if Q is not symmetric or no projectors are set. */
+jdft_status jdft_set_augmentation(jdft_basis_t basis, int ik, const double* Q, void* stream);
+
+/* SC = S C = Omega C + P Q P^dag C for nb bands (band-major blocks, ldc, ldsc >=
+ * npw, not overlapping), through the same projector products and precisions
+ * as the nonlocal term of jdft_apply_H (complex128 for JDFT_FP64, complex64
+ * otherwise).  Without augmentation SC = Omega C.  May grow the basis
+ * workspace.  Asynchronous. */
+jdft_status jdft_op_S(jdft_basis_t basis, int ik, const void* C, int ldc, void* SC, int ldsc, int nb,
+                      jdft_prec prec, void* stream);
+
+/* Generalised subspace matrices of an FP64 block: CHC = C^dag (HC), CSC =
+ * C^dag S C (device complex128 nb x nb row-major, overwritten), and with eigs
+ * (device nb doubles, or NULL) the eigenvalues of the pencil (CHC, CSC),
+ * ascending: C^dag S C = L L^dag factored in FP64, then the eigenvalues of
+ * L^{-1} CHC L^{-dag} by cyclic Jacobi rotations (generalised Rayleigh-Ritz).
+ * C, HC: complex128 band-major (ldc, ldhc >= npw).  Synchronous; allocates
+ * its scratch (three blocks) for the call.  JDFT_ERR_NOT_POSDEF if C^dag S C
+ * is not positive definite. */
+jdft_status jdft_subspace_generalized(jdft_basis_t basis, int ik, const void* C, int ldc, const void* HC,
+                                      int ldhc, int nb, void* CHC, void* CSC, double* eigs, void* stream);
+
+/* C <- C L^{-dag} with C^dag S C = L L^dag (FP64), so that C^dag S C = 1
+ * afterwards.  C: complex128 band-major.  Synchronous; allocates its scratch
+ * for the call.  JDFT_ERR_NOT_POSDEF on linearly dependent bands. */
+jdft_status jdft_orthonormalize_generalized(jdft_basis_t basis, int ik, void* C, int ldc, int nb, void* stream);
+
 /* ---- scalar fields and the linear dielectric (Sec. 2.1, Listing 1) --------
  * A reciprocal-space field (ScalarFieldTilde) is a full complex128 box X(G) of
  * N values (device, j2 fastest), slot iG mod S holding G = B iG with

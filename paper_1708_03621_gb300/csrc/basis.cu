@@ -98,6 +98,7 @@ static void free_sphere(KSphere& s) {
     cudaFree(s.pw_col); cudaFree(s.pw_z); cudaFree(s.kin); cudaFree(s.kvec); cudaFree(s.kin32);
     cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.Psplit_t); cudaFree(s.D); cudaFree(s.Dcol);
     cudaFree(s.Dval);
+    cudaFree(s.Q); cudaFree(s.Qcol); cudaFree(s.Qval);
     s = KSphere();
 }
 
@@ -415,6 +416,12 @@ jdft_status jdft_set_projectors(jdft_basis_t b, int ik, const void* P, int nproj
         cudaFree(s.P); cudaFree(s.P32); cudaFree(s.Psplit); cudaFree(s.Psplit_t); cudaFree(s.D); cudaFree(s.Dcol);
         cudaFree(s.Dval);
         s.P = s.P32 = s.Psplit = s.Psplit_t = nullptr; s.D = nullptr; s.Dcol = nullptr; s.Dval = nullptr; s.Dw = 0;
+    }
+    if (s.Q) {
+        // the augmentation belongs to the projectors it was set for
+        JDFT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        cudaFree(s.Q); cudaFree(s.Qcol); cudaFree(s.Qval);
+        s.Q = nullptr; s.Qcol = nullptr; s.Qval = nullptr; s.Qw = 0;
     }
     s.nproj = nproj;
     if (nproj == 0) return JDFT_OK;

@@ -114,6 +114,12 @@ struct KSphere {
     int Dw = 0;
     int* Dcol = nullptr;        // nproj x Dw
     double* Dval = nullptr;     // nproj x Dw
+    // augmentation of the overlap (S = Omega + P Q P^dag), dense and as ELL
+    // rows like D; Q == nullptr when the overlap is the plain Omega
+    double* Q = nullptr;        // nproj x nproj
+    int Qw = 0;
+    int* Qcol = nullptr;
+    double* Qval = nullptr;
 };
 
 // Library-owned scratch buffer that only grows.

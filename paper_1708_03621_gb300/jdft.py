@@ -129,6 +129,10 @@ _SIGS = {
     "jdft_scf": [_vp, _vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(ScfOpts), ctypes.POINTER(ScfReport), _vp],
     "jdft_apply_H_spinor": [_vp, _i, _vp, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_density_spinor": [_vp, _i, _vp, _i, _vp, _i, _vp, _vp, _i, _vp],
+    "jdft_set_augmentation": [_vp, _i, _vp, _vp],
+    "jdft_op_S": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
+    "jdft_subspace_generalized": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp],
+    "jdft_orthonormalize_generalized": [_vp, _i, _vp, _i, _i, _vp],
     "jdft_field_I": [_vp, _vp, _vp, _vp],
     "jdft_field_J": [_vp, _vp, _vp, _vp],
     "jdft_pcm_hessian": [_vp, _vp, _vp, _vp, _vp],
@@ -510,6 +514,33 @@ def jdft_density_spinor(basis, ik, C, f, n_r, m_r, prec="fp64", stream=None):
     N = int(np.prod(basis.S))
     _call("jdft_density_spinor", basis.handle, ik, p, ld, _field(f, "f", n2 // 2), n2 // 2, _field(n_r, "n_r", N),
           _field(m_r, "m_r", 3 * N), _prec(prec), _stream(stream))
+
+
+def jdft_set_augmentation(basis, ik, Q, stream=None):
+    """Q: (nproj, nproj) float64 CUDA tensor (symmetric), or None to clear."""
+    _call("jdft_set_augmentation", basis.handle, ik, _ptr(Q), _stream(stream))
+
+
+def jdft_op_S(basis, ik, C, SC, prec="fp64", stream=None):
+    p, ld, nb = _block(C, prec, "C")
+    q, lds, nbs = _block(SC, prec, "SC")
+    if nbs != nb:
+        raise ValueError("C and SC must have the same number of bands")
+    _call("jdft_op_S", basis.handle, ik, p, ld, q, lds, nb, _prec(prec), _stream(stream))
+
+
+def jdft_subspace_generalized(basis, ik, C, HC, CHC, CSC, eigs=None, stream=None):
+    p, ld, nb = _block(C, "fp64", "C")
+    q, ldh, nbh = _block(HC, "fp64", "HC")
+    if nbh != nb:
+        raise ValueError("C and HC must have the same number of bands")
+    _call("jdft_subspace_generalized", basis.handle, ik, p, ld, q, ldh, nb, _ptr(CHC), _ptr(CSC), _ptr(eigs),
+          _stream(stream))
+
+
+def jdft_orthonormalize_generalized(basis, ik, C, stream=None):
+    p, ld, nb = _block(C, "fp64", "C")
+    _call("jdft_orthonormalize_generalized", basis.handle, ik, p, ld, nb, _stream(stream))
 
 
 class PcmReport(ctypes.Structure):

@@ -143,3 +143,11 @@ def test_spinor_entry_points_check_arguments_first():
     L = jdft.lib()
     assert L.jdft_apply_H_spinor(None, 0, None, None, 0, None, 0, 1, 0, None) == 1
     assert L.jdft_density_spinor(None, 0, None, 0, None, 1, None, None, 0, None) == 1
+
+
+def test_overlap_entry_points_check_arguments_first():
+    L = jdft.lib()
+    assert L.jdft_set_augmentation(None, 0, None, None) == 1
+    assert L.jdft_op_S(None, 0, None, 0, None, 0, 1, 0, None) == 1
+    assert L.jdft_subspace_generalized(None, 0, None, 0, None, 0, 1, None, None, None, None) == 1
+    assert L.jdft_orthonormalize_generalized(None, 0, None, 0, 1, None) == 1
