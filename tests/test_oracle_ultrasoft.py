@@ -95,3 +95,27 @@ def test_orthonormalised_block_is_S_orthonormal_with_the_same_span():
     # same span: the projector onto span(C) is unchanged
     Pc = C @ np.linalg.pinv(C)
     assert np.max(np.abs(Pc @ Co - Co)) < 1e-10 * np.max(np.abs(Co))
+
+
+def test_generalised_minimiser_finds_the_lowest_pencil_eigenvalues():
+    """Converged bands span the lowest nb eigenvectors of the dense pencil (H, S):
+    their Rayleigh-Ritz values are LAPACK's lowest generalised eigenvalues."""
+    b, V, P, D, Q = _system()
+    Sd = us.dense_S(b, P, Q)
+    H = pw.dense_H(b, V, P, D)
+    lam = scipy.linalg.eigh(H, Sd, eigvals_only=True)
+    C0 = random_coefficients(2 * b.T, 5, 9).T
+    C, eigs, it, res = us.minimize_bands_generalized(b, lambda X: pw.apply_H(b, V, X, P, D), P, Q, C0, tol=1e-9)
+    assert res < 1e-9
+    assert np.max(np.abs(eigs - lam[:5])) < 1e-12 * max(1.0, np.max(np.abs(lam[:5]))) + 1e-13
+    assert np.max(np.abs(C.conj().T @ us.op_S(b, C, P, Q) - np.eye(5))) < 1e-10
+
+
+def test_generalised_minimiser_without_augmentation_is_the_plain_one():
+    from oracle import minimize as mz
+    b, V, P, D, Q = _system()
+    C0 = random_coefficients(2 * b.T, 5, 10).T
+    Hap = lambda X: pw.apply_H(b, V, X, P, D)  # noqa: E731
+    _, e1, _, _ = us.minimize_bands_generalized(b, Hap, P, 0 * Q, C0, tol=1e-9)
+    e2 = mz.minimize_bands(b, Hap, C0, tol=1e-9).eigs
+    assert np.max(np.abs(e1 - e2)) < 1e-12
