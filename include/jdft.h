@@ -461,8 +461,8 @@ jdft_status jdft_density_spinor(jdft_basis_t basis, int ik, const void* C, int l
  * energies are the eigenvalues of the pencil (C^dag H C, C^dag S C).  Only
  * the calls of this section use Q; jdft_op_O, jdft_subspace, the
  * orthonormalisation, jdft_hamiltonian_step and jdft_minimize_bands keep the
- * plain O = Omega (the band minimiser does not solve the generalised
- * problem). */
+ * plain O = Omega; jdft_minimize_bands_generalized solves the generalised
+ * problem. */
 
 /* Set (Q: device nproj x nproj doubles, row-major, symmetric; copied) or clear
  * (Q = NULL) the augmentation of k-point ik's projectors.  Needs the
@@ -494,6 +494,22 @@ jdft_status jdft_subspace_generalized(jdft_basis_t basis, int ik, const void* C,
  * afterwards.  C: complex128 band-major.  Synchronous; allocates its scratch
  * for the call.  JDFT_ERR_NOT_POSDEF on linearly dependent bands. */
 jdft_status jdft_orthonormalize_generalized(jdft_basis_t basis, int ik, void* C, int ldc, int nb, void* stream);
+
+/* Lowest nb states of the generalised problem H c = e S c by all-band
+ * preconditioned conjugate gradients (Sec. 2.1 Minimize; the norm-conserving
+ * jdft_minimize_bands with S in place of Omega): C kept S-orthonormal; gradient
+ * G = H C - S C (C^dag H C); Teter or identity preconditioner; Polak-Ribiere
+ * directions made S-orthogonal to C; second-order line step halved while the
+ * energy of the S-orthonormalised trial block rises by more than 64 FP64 ulp;
+ * converged when ||G||_F / sqrt(Omega) < opts->tol.  FP64 only (opts->prec =
+ * JDFT_FP64); opts->switch_tol and opts->mlp are not used.  C: device
+ * complex128 band-major, in: start, out: converged S-orthonormal block.  eigs:
+ * device nb doubles or NULL.  report: host (iterations, energy f tr C^dag H C,
+ * residual, seconds).  Synchronous; allocates its working blocks for the call.
+ * JDFT_ERR_NOT_CONVERGED (with C and report filled) at max_iter. */
+jdft_status jdft_minimize_bands_generalized(jdft_basis_t basis, int ik, void* C, int ldc, int nb,
+                                           const jdft_min_opts* opts, double* eigs, jdft_min_report* report,
+                                           void* stream);
 
 /* ---- scalar fields and the linear dielectric (Sec. 2.1, Listing 1) --------
  * A reciprocal-space field (ScalarFieldTilde) is a full complex128 box X(G) of

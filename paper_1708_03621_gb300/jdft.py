@@ -133,6 +133,8 @@ _SIGS = {
     "jdft_op_S": [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp],
     "jdft_subspace_generalized": [_vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp],
     "jdft_orthonormalize_generalized": [_vp, _i, _vp, _i, _i, _vp],
+    "jdft_minimize_bands_generalized": [_vp, _i, _vp, _i, _i, ctypes.POINTER(MinOpts), _vp,
+                                        ctypes.POINTER(MinReport), _vp],
     "jdft_field_I": [_vp, _vp, _vp, _vp],
     "jdft_field_J": [_vp, _vp, _vp, _vp],
     "jdft_pcm_hessian": [_vp, _vp, _vp, _vp, _vp],
@@ -541,6 +543,23 @@ def jdft_subspace_generalized(basis, ik, C, HC, CHC, CSC, eigs=None, stream=None
 def jdft_orthonormalize_generalized(basis, ik, C, stream=None):
     p, ld, nb = _block(C, "fp64", "C")
     _call("jdft_orthonormalize_generalized", basis.handle, ik, p, ld, nb, _stream(stream))
+
+
+def jdft_minimize_bands_generalized(basis, ik, C, eigs=None, tol=1e-8, max_iter=1000, precond="teter",
+                                    occupation=2.0, stream=None, check=True) -> dict:
+    """Generalised (S-orthonormal) band CG in place on the complex128 block C; returns the report."""
+    p, ld, nb = _block(C, "fp64", "C")
+    o = MinOpts(tol, max_iter, PRECOND[precond] if isinstance(precond, str) else int(precond), 0, 0.0, occupation,
+                ctypes.c_void_p(0))
+    r = MinReport()
+    L = lib()
+    st = L.jdft_minimize_bands_generalized(basis.handle, ik, p, ld, nb, ctypes.byref(o), _ptr(eigs), ctypes.byref(r),
+                                           _stream(stream))
+    out = r.as_dict()
+    out["status"] = STATUS.get(st, st)
+    if check and st != 0:
+        raise JdftError(st, "jdft_minimize_bands_generalized", L.jdft_last_error().decode())
+    return out
 
 
 class PcmReport(ctypes.Structure):

@@ -151,3 +151,5 @@ def test_overlap_entry_points_check_arguments_first():
     assert L.jdft_op_S(None, 0, None, 0, None, 0, 1, 0, None) == 1
     assert L.jdft_subspace_generalized(None, 0, None, 0, None, 0, 1, None, None, None, None) == 1
     assert L.jdft_orthonormalize_generalized(None, 0, None, 0, 1, None) == 1
+    o, r = jdft.MinOpts(), jdft.MinReport()
+    assert L.jdft_minimize_bands_generalized(None, 0, None, 0, 1, ctypes.byref(o), None, ctypes.byref(r), None) == 1

@@ -6,6 +6,7 @@ from __future__ import annotations
 
 import numpy as np
 import pytest
+import scipy.linalg
 
 from oracle import planewave as pw
 from oracle import ultrasoft as us
@@ -23,6 +24,7 @@ DEV = torch.device("cuda:0")
 
 CASES = {
     "tiny": (np.diag([6.0, 6.5, 5.5]), (12, 15, 10), (0.1, 0.2, 0.3), 3.0, 2, 5),
+    "cell24": (np.diag([8.0, 8.5, 7.5]), (24, 25, 20), (0.1, 0.2, 0.3), 6.0, 4, 8),
     "small": (WORKLOADS["small"].R, WORKLOADS["small"].S, WORKLOADS["small"].kfrac[0], WORKLOADS["small"].ecut,
               WORKLOADS["small"].natoms, 16),
 }
@@ -110,4 +112,20 @@ def test_generalised_orthonormalisation():
     got = Cd.cpu().numpy().T
     # the same S-orthonormal block up to rounding (Cholesky fixes it uniquely)
     assert np.max(np.abs(got - Co)) < 1e-10 * np.max(np.abs(Co))
+    basis.close()
+
+
+@pytest.mark.parametrize("case,precond", [("tiny", "teter"), ("cell24", "teter"), ("cell24", "identity")])
+def test_generalised_minimiser_finds_the_lowest_pencil_eigenvalues(case, precond):
+    """GPU band CG for H c = e S c against LAPACK's dense pencil (the oracle's H and S)."""
+    ob, V, P, D, Q, basis, C, nb = _setup(case)
+    Cd = torch.tensor(C, device=DEV)
+    eigs = torch.empty(nb, dtype=torch.float64, device=DEV)
+    rep = jdft.jdft_minimize_bands_generalized(basis, 0, Cd, eigs, tol=1e-9, max_iter=3000, precond=precond)
+    assert rep["converged"] == 1
+    lam = scipy.linalg.eigh(pw.dense_H(ob, V, P, D), us.dense_S(ob, P, Q), eigvals_only=True)[:nb]
+    assert np.max(np.abs(np.sort(eigs.cpu().numpy()) - lam)) < 1e-9 * max(1.0, np.max(np.abs(lam)))
+    assert rep["energy"] == pytest.approx(2.0 * lam.sum(), abs=1e-8)
+    got = Cd.cpu().numpy().T
+    assert np.max(np.abs(got.conj().T @ us.op_S(ob, got, P, Q) - np.eye(nb))) < 1e-10
     basis.close()
