@@ -759,9 +759,69 @@ def scf_measurements(device, fp32: dict) -> dict:
     out["small_scf"] = runs
     out["pcm_128cubed"] = pcm_measurements(device)
     out["spinor"] = spinor_measurements(device)
+    out["augmented_overlap"] = overlap_measurements(device)
     out["small_scf_workload"] = ("48^3 'small' cell (L=10, Ecut=20, 4259 PW, 8 atoms, 16 bands, f=2), Gaussian "
                                  "V_ion + projectors, LDA (PZ81) + Hartree, Pulay 8 pairs alpha 0.5; band solves "
                                  "Teter-preconditioned CG warm-started each iteration")
+    return out
+
+
+def overlap_measurements(device) -> dict:
+    """The augmented overlap S = Omega + P Q P^dag (Q = diag(0.4, 0.1, 0.1, 0.1)
+    per atom): jdft_op_S over the 128^3 workload's 256-band block in BF16x3
+    (CUDA events), and the generalised band minimiser on the 48^3 workload
+    (16 bands, FP64, Teter, to 1e-8) beside the plain minimiser on the same
+    cell without augmentation."""
+    import torch
+
+    from paper_1708_03621_gb300 import jdft
+    from synth import WORKLOADS, atom_positions, random_coefficients
+    out = {}
+    stream = torch.cuda.current_stream()
+    for wname in ("large", "small"):
+        w = WORKLOADS[wname]
+        atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
+        b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())
+        N = int(np.prod(w.S))
+        V = torch.empty(N, dtype=torch.float64, device=device)
+        jdft.jdft_gaussian_potential(b, atoms, V)
+        jdft.jdft_set_potential(b, V)
+        P = torch.empty((4 * w.natoms, b.npw(0)), dtype=torch.complex128, device=device)
+        jdft.jdft_gaussian_projectors(b, 0, atoms, P)
+        D = torch.tensor(np.diag(np.tile([0.5, -0.3, -0.3, -0.3], w.natoms)), device=device)
+        jdft.jdft_set_projectors(b, 0, P, D)
+        G = b.gvectors(0).astype(np.float64) + np.asarray(w.kfrac[0])
+        q = G @ (2 * np.pi * np.linalg.inv(w.R).T).T
+        C0 = torch.tensor(random_coefficients(np.einsum("ij,ij->i", q, q), w.nbands, w.seed_coeffs), device=device)
+        Q = torch.tensor(np.diag(np.tile([0.4, 0.1, 0.1, 0.1], w.natoms)), device=device)
+        if wname == "large":
+            jdft.jdft_set_augmentation(b, 0, Q)
+            C = C0.to(torch.complex64)
+            SC = torch.empty_like(C)
+            for _ in range(3):
+                jdft.jdft_op_S(b, 0, C, SC, "bf16x3")
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(10):
+                jdft.jdft_op_S(b, 0, C, SC, "bf16x3")
+            a1.record(stream)
+            torch.cuda.synchronize()
+            out["op_S_128cubed_256bands_bf16x3_ms"] = round(a0.elapsed_time(a1) / 10, 4)
+        else:
+            res = {}
+            for name, aug in (("plain", False), ("augmented", True)):
+                jdft.jdft_set_augmentation(b, 0, Q if aug else None)
+                C = C0.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if aug:
+                    rep = jdft.jdft_minimize_bands_generalized(b, 0, C, tol=1e-8, max_iter=3000)
+                else:
+                    rep = jdft.jdft_minimize_bands(b, 0, C, tol=1e-8, max_iter=3000, precond="teter", prec="fp64")
+                res[name] = {"seconds": round(time.perf_counter() - t0, 4), "iterations": rep["iterations"],
+                             "energy_Ha": rep["energy"]}
+            out["small_minimise_fp64_teter"] = res
+        b.close()
     return out
 
 
