@@ -86,6 +86,12 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
 // The plane pass alone, two bands at a time (same contract as launch_plane_apply).
 jdft_status launch_plane_apply_pair(const ChainGeom& g, float2* colbuf, const float* Vp, int nb,
                                     const float2* tw_base, cudaStream_t st);
+// The plane pass of spinor rows: each pair (2p, 2p + 1) is one band's (up, down)
+// components, multiplied by V 1 + M . sigma between the transforms; Mp holds
+// M_x, M_y, M_z in Vp's permuted layout, one box after another (FP32).
+// JDFT_ERR_UNSUPPORTED, without launching, for shapes it is not compiled for.
+jdft_status launch_plane_apply_pair_spinor(const ChainGeom& g, float2* colbuf, const float* Vp, const float* Mp,
+                                           int nb, const float2* tw_base, cudaStream_t st);
 // One k-point (or cell on the same box) of a k-batched chain: its sphere
 // maps, blocks, column buffer and first plane-pass item (kbatch.cu).
 struct KJob {

@@ -177,11 +177,14 @@ struct PairPlane {
 // inverse, columns (inverse, density sums, x V, forward), rows forward, with a
 // block barrier after each phase.  g: the item's sphere maps; colbuf: its
 // column buffer of nb bands.
-template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN>
+// SPIN: the pair is one spinor band's (up, down) components and the potential
+// is V 1 + M . sigma, M's three fields in Mp (each in Vp's permuted layout).
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN, bool SPIN = false>
 __device__ __forceinline__ void pair_item(const ChainGeom& g, float2* __restrict__ colbuf, int nb,
                                           const double* __restrict__ f, const float* __restrict__ Vp, int j2, int b0,
                                           const float4* W0, const float4* W1, float2* wscr, float2* scr,
-                                          ulonglong2* A, uint32_t tb, int warp, int lane) {
+                                          ulonglong2* A, uint32_t tb, int warp, int lane,
+                                          const float* __restrict__ Mp = nullptr) {
     using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
     using FI = LineFFTP<N0, E0, +1, R0, WIN>;
     using LN = PLanes<N0, E0>;
@@ -224,8 +227,27 @@ __device__ __forceinline__ void pair_item(const ChainGeom& g, float2* __restrict
             tc::tmem_st16(tb + 16 * k, acc);
         }
         const float* Vq = Vp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
+        if constexpr (SPIN) {
+            // (up, down) <- [[V + M_z, M_x - i M_y], [M_x + i M_y, V - M_z]] (up, down)
+            const size_t nbox = (size_t)g.S2 * N1 * N0;
+            const float* Mq = Mp + ((size_t)j2 * N1 + (act ? j1 : 0)) * N0;
 #pragma unroll
-        for (int e = 0; e < E0; ++e) v[e] = act ? cp_scale(v[e], p_dup(Vq[FI::out_index(t, e)])) : cp_zero();
+            for (int e = 0; e < E0; ++e) {
+                const int o = FI::out_index(t, e);
+                const float V = Vq[o], mx = Mq[o], my = Mq[nbox + o], mz = Mq[2 * nbox + o];
+                float ru, rd, iu, id;
+                p_unpack(v[e].x, ru, rd);
+                p_unpack(v[e].y, iu, id);
+                const float pru = (V + mz) * ru + mx * rd + my * id;
+                const float piu = (V + mz) * iu + mx * id - my * rd;
+                const float prd = (V - mz) * rd + mx * ru - my * iu;
+                const float pid = (V - mz) * id + mx * iu + my * ru;
+                v[e] = act ? cpair{p_pack(pru, prd), p_pack(piu, pid)} : cp_zero();
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E0; ++e) v[e] = act ? cp_scale(v[e], p_dup(Vq[FI::out_index(t, e)])) : cp_zero();
+        }
         FI::run_adjoint(v, t, scr, W0);
         if (act) {
 #pragma unroll
@@ -245,10 +267,11 @@ __device__ __forceinline__ void pair_item(const ChainGeom& g, float2* __restrict
 // the sphere lies in the central quarter of the box along axes 0 and 1
 // (LineFFTP's window), so the transforms prune their first-stage butterflies
 // and the loads and stores outside it are skipped.
-template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN>
+template <int N0, int E0, class R0, int N1, int E1, class R1, int NW, bool DENS, bool WIN, bool SPIN = false>
 __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
     ChainGeom g, float2* __restrict__ colbuf, const float* __restrict__ Vp, int nb, const double* __restrict__ f,
-    double w, double* __restrict__ n_r, const float2* __restrict__ tw0, const float2* __restrict__ tw1) {
+    double w, double* __restrict__ n_r, const float2* __restrict__ tw0, const float2* __restrict__ tw1,
+    const float* __restrict__ Mp) {
     using PP = PairPlane<N0, E0, R0, N1, E1, R1, NW>;
     using FI = LineFFTP<N0, E0, +1, R0, WIN>;
     using LN = PLanes<N0, E0>;
@@ -303,8 +326,8 @@ __global__ void __launch_bounds__(32 * NW, 1) plane_apply_density_pair_kernel(
             zero();
             cur = j2;
         }
-        pair_item<N0, E0, R0, N1, E1, R1, NW, DENS, WIN>(g, colbuf, nb, f, Vp, j2, 2 * p, W0, W1, wscr, scr, A, tb,
-                                                          warp, lane);
+        pair_item<N0, E0, R0, N1, E1, R1, NW, DENS, WIN, SPIN>(g, colbuf, nb, f, Vp, j2, 2 * p, W0, W1, wscr, scr, A,
+                                                                tb, warp, lane, Mp);
     }
     if (DENS && cur >= 0) flush(cur);
     tc::tc_fence_before_sync();
@@ -389,17 +412,17 @@ static bool pair_window(const ChainGeom& g) {
     return g.i0min >= -N0 / 4 && g.i0min + g.nrows - 1 <= N0 / 4 - 1 && g.i1min >= -N1 / 4 && g.i1max <= N1 / 4 - 1;
 }
 
-template <int N0, int N1, bool DENS, bool WIN>
+template <int N0, int N1, bool DENS, bool WIN, bool SPIN = false>
 static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp, int nb, const double* f, double w,
-                             double* n_r, const float2* tw_base, cudaStream_t st) {
+                             double* n_r, const float2* tw_base, cudaStream_t st, const float* Mp = nullptr) {
     using C0 = PairCfg<N0>;
     using C1 = PairCfg<N1>;
     using PP = PairPlane<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps>;
-    const char* name = DENS ? "plane_apply_density_pair" : "plane_apply_pair";
+    const char* name = SPIN ? "plane_apply_spinor_pair" : DENS ? "plane_apply_density_pair" : "plane_apply_pair";
     const size_t smem = PP::smem(g.nrows);
     if (smem > 227 * 1024) return JDFT_ERR_UNSUPPORTED;
-    auto kern =
-        plane_apply_density_pair_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps, DENS, WIN>;
+    auto kern = plane_apply_density_pair_kernel<N0, C0::E, typename C0::R, N1, C1::E, typename C1::R, kPairWarps,
+                                                DENS, WIN, SPIN>;
     cudaError_t e = set_smem_attr((const void*)kern, smem);
     if (e != cudaSuccess) return set_error(JDFT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
     const int64_t items = (int64_t)g.S2 * ((nb + 1) / 2);
@@ -416,7 +439,7 @@ static jdft_status pair_impl(const ChainGeom& g, float2* colbuf, const float* Vp
     {
         Trace tr_(name, st);
         kern<<<grid, 32 * kPairWarps, smem, st>>>(g, colbuf, Vp, nb, f, w, n_r, tw_base + g.p0.tw_offset,
-                                                  tw_base + g.p1.tw_offset);
+                                                  tw_base + g.p1.tw_offset, Mp);
     }
     return check_launch(name);
 }
@@ -429,6 +452,18 @@ jdft_status launch_plane_apply_density_pair(const ChainGeom& g, float2* colbuf, 
         return pair_window<128, 128>(g) ? pair_impl<128, 128, true, true>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st)
                                         : pair_impl<128, 128, true, false>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
     if (g.S0 == 16 && g.S1 == 12) return pair_impl<16, 12, true, false>(g, colbuf, Vp, nb, f, w, n_r, tw_base, st);
+    return JDFT_ERR_UNSUPPORTED;
+}
+
+jdft_status launch_plane_apply_pair_spinor(const ChainGeom& g, float2* colbuf, const float* Vp, const float* Mp,
+                                           int nb, const float2* tw_base, cudaStream_t st) {
+    if (nb % 2) return set_error(JDFT_ERR_ARG, "spinor plane pass needs whole (up, down) pairs");
+    if (g.S0 == 128 && g.S1 == 128)
+        return pair_window<128, 128>(g)
+                   ? pair_impl<128, 128, false, true, true>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st, Mp)
+                   : pair_impl<128, 128, false, false, true>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st, Mp);
+    if (g.S0 == 16 && g.S1 == 12)
+        return pair_impl<16, 12, false, false, true>(g, colbuf, Vp, nb, nullptr, 0.0, nullptr, tw_base, st, Mp);
     return JDFT_ERR_UNSUPPORTED;
 }
 

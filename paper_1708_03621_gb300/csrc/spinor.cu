@@ -13,15 +13,22 @@
 //   * kinetic and projector terms act on each component alike;
 //   * n = sum_b f_b (|psi_up|^2 + |psi_dn|^2), m = sum_b f_b psi^dag sigma psi.
 //
-// Design: H C is the scalar Hamiltonian applied to all 2 nb rows (the fused
-// chain of jdft_apply_H) plus the M . sigma coupling, formed in chunks of bands:
-// psi = I C for the chunk's rows (jdft_op_I), the 2 x 2 product in place
-// (one kernel over band pairs), J of the result (jdft_op_J), and
-// HC += Omega * that.  The density and magnetisation come from the same
-// inverse transforms, summed per point over the chunk's bands.
+// Design.  FP32 blocks on boxes the band-pair plane kernel serves (128 x 128
+// planes): the chain of jdft_apply_H with the band-pair plane pass made spinor
+// -- a pair of rows (2b, 2b + 1) is band b's (up, down) components, so the
+// 2 x 2 product V 1 + M . sigma replaces the multiply by V inside the fused
+// pass (z pass in, plane pass, z pass out with the kinetic term), then the
+// nonlocal term on all rows.  Elsewhere (FP64, other boxes): the scalar
+// Hamiltonian on all 2 nb rows plus the coupling formed in chunks of bands:
+// psi = I C for the chunk's rows (jdft_op_I), the 2 x 2 product in place,
+// J of the result (jdft_op_J), and HC += Omega * that.  The density and
+// magnetisation come from the inverse transforms, summed per point over the
+// chunk's bands.
 #include <cmath>
 
+#include "chain.cuh"
 #include "common.cuh"
+#include "gemm.cuh"
 #include "profile.cuh"
 
 namespace jdft {
@@ -169,6 +176,60 @@ jdft_status spin_density(jdft_basis_s* b, int ik, const void* C, int ldc, const 
     return JDFT_OK;
 }
 
+// Mp[c N + (j2 S1 + j1) S0 + j0] = M[c N + (j0 S1 + j1) S2 + j2] in FP32 (the plane pass's layout).
+__global__ void __launch_bounds__(kThreads)
+permute_field3_kernel(const double* __restrict__ M, float* __restrict__ Mp, int S0, int S1, int S2) {
+    const int64_t N = (int64_t)S0 * S1 * S2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / N, j = i - c * N;
+        const int j2 = (int)(j % S2);
+        const int64_t r = j / S2;
+        const int j1 = (int)(r % S1), j0 = (int)(r / S1);
+        Mp[c * N + ((int64_t)j2 * S1 + j1) * S0 + j0] = (float)M[i];
+    }
+}
+
+// The fused FP32 path; JDFT_ERR_UNSUPPORTED (nothing launched) when the box has
+// no band-pair plane kernel.
+jdft_status spinor_fused(jdft_basis_s* b, int ik, const double* M, const void* C, int ldc, void* HC, int ldhc, int nb,
+                         jdft_prec prec, cudaStream_t st) {
+    const ChainGeom g = make_geom(b, ik);
+    if (!((g.S0 == 128 && g.S1 == 128) || (g.S0 == 16 && g.S1 == 12))) return JDFT_ERR_UNSUPPORTED;
+    if (!b->V32) return set_error(JDFT_ERR_ARG, "no potential set");
+    const KSphere& sp = b->ks[ik];
+    const int rows = 2 * nb;
+    const size_t rowbytes = (size_t)g.S2 * g.ncols * sizeof(float2);
+    int nc = (int)std::min<size_t>((size_t)rows, std::max<size_t>(2, ((size_t)512 << 20) / rowbytes));
+    nc &= ~1;
+    const size_t colbytes = ((size_t)nc * rowbytes + 255) / 256 * 256;
+    const size_t mbytes = 3 * (size_t)b->N * sizeof(float);
+    void* ws = nullptr;
+    jdft_status s = spin_ws(b, colbytes + mbytes, &ws);
+    if (s) return s;
+    float2* colbuf = reinterpret_cast<float2*>(ws);
+    float* Mp = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + colbytes);
+    {
+        Trace tr_("permute_field3", st);
+        permute_field3_kernel<<<grid_of(3 * b->N), kThreads, 0, st>>>(M, Mp, b->S[0], b->S[1], b->S[2]);
+    }
+    if ((s = check_launch("permute_field3"))) return s;
+    const float2* tw = b->tw32;
+    const float omega = (float)b->omega, invN = (float)(1.0 / (double)b->N);
+    for (int r0 = 0; r0 < rows; r0 += nc) {
+        const int n = std::min(nc, rows - r0);
+        const float2* Cc = reinterpret_cast<const float2*>(C) + (size_t)r0 * ldc;
+        float2* Hc = reinterpret_cast<float2*>(HC) + (size_t)r0 * ldhc;
+        if ((s = launch_zpass_inverse<float>(g, Cc, ldc, colbuf, n, tw, st))) return s;
+        if ((s = launch_plane_apply_pair_spinor(g, colbuf, b->V32, Mp, n, tw, st))) return s;
+        if ((s = launch_zpass_forward<float, 0>(g, colbuf, Cc, ldc, Hc, ldhc, n, sp.kin32, omega, invN, tw, st)))
+            return s;
+    }
+    if (sp.nproj == 0) return JDFT_OK;
+    if ((s = ensure_workspace(b, nonlocal_workspace_bytes(sp.nproj, rows, sizeof(float2), sp.npw, prec, true, true))))
+        return s;
+    return nonlocal_accumulate<float>(sp, C, ldc, HC, ldhc, rows, prec, b->work.ptr, st, true, nullptr, true);
+}
+
 jdft_status check_spinor_args(jdft_basis_s* b, int ik, const void* C, int ldc, int nb, jdft_prec prec) {
     JDFT_CHECK_ARG(b && C, "null argument");
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
@@ -194,6 +255,11 @@ jdft_status jdft_apply_H_spinor(jdft_basis_t b, int ik, const double* M, const v
     JDFT_CHECK_ARG(ldhc >= b->ks[ik].npw, "leading dimension below npw");
     JDFT_CHECK_ARG(C != HC, "C and HC must not overlap");
     cudaStream_t st = (cudaStream_t)stream;
+    if (!fp64(prec)) {
+        s = spinor_fused(b, ik, M, C, ldc, HC, ldhc, nb, prec, st);
+        if (s != JDFT_ERR_UNSUPPORTED) return s;
+        clear_error();
+    }
     // scalar part on every component row: Omega [T C + J(V I C)] + P D P^dag C
     if ((s = jdft_apply_H(b, ik, C, ldc, HC, ldhc, 2 * nb, prec, stream))) return s;
     return fp64(prec) ? couple<double>(b, ik, M, C, ldc, HC, ldhc, nb, prec, st)

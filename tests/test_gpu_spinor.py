@@ -35,6 +35,12 @@ def _field(R, S, seed):
 
 CASES = {
     "tiny": (np.diag([6.0, 6.5, 5.5]), (12, 15, 10), (0.1, 0.2, 0.3), 3.0, 2, 3),
+    # 16 x 12 planes: the band-pair plane kernel serves them (the fused FP32 spinor pass)
+    "pair16x12": (WORKLOADS["tiny_ortho"].R, WORKLOADS["tiny_ortho"].S, WORKLOADS["tiny_ortho"].kfrac[0],
+                  WORKLOADS["tiny_ortho"].ecut, 3, 5),
+    # the 128^3 workload with a few spinor bands (fused FP32 pass on 128 x 128 planes)
+    "large": (WORKLOADS["large"].R, WORKLOADS["large"].S, WORKLOADS["large"].kfrac[0], WORKLOADS["large"].ecut,
+              WORKLOADS["large"].natoms, 4),
     "small": (WORKLOADS["small"].R, WORKLOADS["small"].S, WORKLOADS["small"].kfrac[0], WORKLOADS["small"].ecut,
               WORKLOADS["small"].natoms, 16),
 }
@@ -60,8 +66,10 @@ def _setup(case, prec):
     return ob, V, P, D, basis, C, torch.tensor(C, device=DEV).to(ct), nb
 
 
-@pytest.mark.parametrize("case", ["tiny", "small"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+SPIN_CASES = [(c, p) for c in ("tiny", "pair16x12", "small") for p in ("fp64", "fp32")] + [("large", "fp32")]
+
+
+@pytest.mark.parametrize("case,prec", SPIN_CASES, ids=[f"{c}-{p}" for c, p in SPIN_CASES])
 def test_apply_H_spinor_matches_oracle(case, prec):
     ob, V, P, D, basis, C, Cd, nb = _setup(case, prec)
     M = _field(ob.R, ob.S, 23)
