@@ -378,7 +378,8 @@ jdft_status jdft_pulay_reset(jdft_pulay_t mixer);
  * order from one host thread. */
 jdft_status jdft_pulay_step(jdft_pulay_t mixer, const double* n_in, const double* n_out, double* n_next,
                             void* stream);
-/* Number of pairs the last step combined (host int; waits for `stream`). */
+/* Number of pairs the last step combined (host int; waits for `stream`); a
+ * diagnostic the paper has no counterpart for. */
 jdft_status jdft_pulay_used(jdft_pulay_t mixer, int* used, void* stream);
 
 typedef struct {

@@ -27,6 +27,9 @@ CASES = {
     "cell24": (np.diag([8.0, 8.5, 7.5]), (24, 25, 20), (0.1, 0.2, 0.3), 6.0, 4, 8),
     "small": (WORKLOADS["small"].R, WORKLOADS["small"].S, WORKLOADS["small"].kfrac[0], WORKLOADS["small"].ecut,
               WORKLOADS["small"].natoms, 16),
+    # the bench's S C workload (128^3, 256 projectors), 32 sampled bands of its 256
+    "large": (WORKLOADS["large"].R, WORKLOADS["large"].S, WORKLOADS["large"].kfrac[0], WORKLOADS["large"].ecut,
+              WORKLOADS["large"].natoms, 32),
 }
 
 
@@ -58,8 +61,11 @@ def _setup(case):
     return ob, V, P, D, Q, basis, C, nb
 
 
-@pytest.mark.parametrize("case", ["tiny", "small"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("bf16x3", 2e-6)])
+OPS_CASES = [(c, p, t) for c in ("tiny", "small") for p, t in (("fp64", 1e-12), ("fp32", 1e-6), ("bf16x3", 2e-6))]
+OPS_CASES += [("large", "bf16x3", 2e-6)]
+
+
+@pytest.mark.parametrize("case,prec,tol", OPS_CASES, ids=[f"{c}-{p}" for c, p, _ in OPS_CASES])
 def test_op_S_matches_oracle(case, prec, tol):
     ob, V, P, D, Q, basis, C, nb = _setup(case)
     ct = torch.complex128 if prec == "fp64" else torch.complex64
