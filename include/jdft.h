@@ -388,12 +388,15 @@ typedef struct {
     int max_iter;           /* SCF iterations (0 = 100) */
     int history;            /* Pulay pairs kept (0 = 8, at most 16) */
     double alpha;           /* Pulay mixing fraction (0 = 0.5) */
-    double band_tol;        /* band minimiser tolerance of every iteration (0 = 1e-9) */
+    double band_tol;        /* band minimiser tolerance of the converged iterations (0 = 1e-9) */
     int band_max_iter;      /* band minimiser iteration limit (0 = 1000) */
     jdft_precond precond;   /* band minimiser preconditioner */
     jdft_prec prec;         /* band minimiser precision schedule (JDFT_FP64 or a mixed mode) */
     double occupation;      /* f per band (0 = 2) */
     jdft_mlp_t mlp;         /* weights for JDFT_PRECOND_MLP, else NULL */
+    double band_tol_factor; /* iteration i solves the bands to max(band_tol, factor x the density residual
+                               of iteration i - 1), the first to max(band_tol, 1e-3): loose solves while
+                               the density is far from self-consistent (0 = 0.01; < 0: band_tol always) */
 } jdft_scf_opts;
 
 typedef struct {
@@ -418,7 +421,8 @@ typedef struct {
  * out: the orbitals of the last iteration (O-orthonormal).  vion: device N
  * doubles.  The start density is that of the orthonormalised starting blocks.
  * Each iteration: V_KS of the input density -> jdft_minimize_bands at every
- * k-point (warm-started) -> output density n_out -> total energy
+ * k-point (warm-started, to the tolerance band_tol_factor sets) -> output
+ * density n_out -> total energy
  *   E = sum_k w_k f sum_b eps_kb - (Omega/N) sum_j n_out,j (V_H + v_xc)[n_in]_j
  *       + E_H[n_out] + E_xc[n_out]
  * -> convergence test (both tolerances, from the second iteration) -> Pulay step.

@@ -1163,7 +1163,11 @@ jdft_status jdft_scf(jdft_basis_t b, void* const* C, int ldc, int nb, const doub
     if ((s = field_work(b, &w))) return fail(s);
     bool converged = false;
     int it = 0;
+    const double band_tol = mo.tol;
+    const double factor = opts->band_tol_factor == 0.0 ? 0.01 : opts->band_tol_factor;
     for (it = 1; it <= maxit; ++it) {
+        // loose band solves while the density is far from self-consistency
+        mo.tol = factor < 0.0 ? band_tol : std::max(band_tol, it == 1 ? 1e-3 : std::min(1e-3, factor * res));
         if ((s = jdft_ks_potential(b, nin, vion, vks, nullptr, stream))) return fail(s);
         if ((s = jdft_set_potential(b, vks, stream))) return fail(s);
         double Eband = 0.0;

@@ -59,7 +59,7 @@ class ScfOpts(ctypes.Structure):
     _fields_ = [("tol_energy", ctypes.c_double), ("tol_density", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("history", ctypes.c_int), ("alpha", ctypes.c_double), ("band_tol", ctypes.c_double),
                 ("band_max_iter", ctypes.c_int), ("precond", ctypes.c_int), ("prec", ctypes.c_int),
-                ("occupation", ctypes.c_double), ("mlp", ctypes.c_void_p)]
+                ("occupation", ctypes.c_double), ("mlp", ctypes.c_void_p), ("band_tol_factor", ctypes.c_double)]
 
 
 class ScfReport(ctypes.Structure):
@@ -472,7 +472,7 @@ class Pulay:
 
 def jdft_scf(basis, C, vion, n_r, eigs=None, tol_energy=1e-8, tol_density=1e-6, max_iter=100, history=8,
              alpha=0.5, band_tol=1e-9, band_max_iter=1000, precond="teter", prec="fp64", occupation=2.0,
-             mlp=None, stream=None, check=True) -> dict:
+             mlp=None, band_tol_factor=0.0, stream=None, check=True) -> dict:
     """SCF loop; C: list of nk complex128 (nb, ld) CUDA blocks (updated in place).  Returns the report."""
     if len(C) != basis.nk:
         raise ValueError("one coefficient block per k-point is required")
@@ -485,7 +485,7 @@ def jdft_scf(basis, C, vion, n_r, eigs=None, tol_energy=1e-8, tol_density=1e-6, 
     N = int(np.prod(basis.S))
     o = ScfOpts(tol_energy, tol_density, max_iter, history, alpha, band_tol, band_max_iter,
                 PRECOND[precond] if isinstance(precond, str) else int(precond), _prec(prec), occupation,
-                ctypes.c_void_p(0 if mlp is None else mlp.handle.value))
+                ctypes.c_void_p(0 if mlp is None else mlp.handle.value), band_tol_factor)
     r = ScfReport()
     L = lib()
     st = L.jdft_scf(basis.handle, ctypes.cast(ptrs, ctypes.c_void_p), ld, nb, _field(vion, "vion", N),

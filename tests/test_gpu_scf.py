@@ -229,7 +229,7 @@ def test_scf_uniform_electron_gas_on_gpu():
     basis.close()
 
 
-def _small_workload_on_gpu(prec="fp64", band_tol=1e-9):
+def _small_workload_on_gpu(prec="fp64", band_tol=1e-9, band_tol_factor=0.0):
     w = WORKLOADS["small"]
     atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
     ob = pw.Basis.build(w.R, w.S, w.kfrac[0], w.ecut)
@@ -245,20 +245,21 @@ def _small_workload_on_gpu(prec="fp64", band_tol=1e-9):
     n = torch.empty(N, dtype=torch.float64, device=DEV)
     eigs = torch.empty(w.nbands, dtype=torch.float64, device=DEV)
     rep = jdft.jdft_scf(basis, [C], vion, n, eigs, tol_energy=1e-9, tol_density=1e-7, band_tol=band_tol,
-                        prec=prec)
+                        prec=prec, band_tol_factor=band_tol_factor)
     out = (rep, n.cpu().numpy(), eigs.cpu().numpy())
     basis.close()
     return out
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("bf16x3", 1e-6)])
-def test_scf_48cubed_matches_golden(prec, tol):
+@pytest.mark.parametrize("prec,tol,factor", [("fp64", 1e-8, 0.0), ("fp64", 1e-8, -1.0), ("bf16x3", 1e-6, 0.0)],
+                         ids=["fp64-adaptive-band-tol", "fp64-fixed-band-tol", "bf16x3-adaptive-band-tol"])
+def test_scf_48cubed_matches_golden(prec, tol, factor):
     """The 'small' workload self-consistent (LDA, Pulay): energy, eigenvalues and
     density samples against the oracle's values (tests/golden/scf_small.json).
     BF16x3: the band solves run their bulk iterations with split-precision
     products and finish in FP64 (the minimiser's own schedule)."""
     g = json.load(open(GOLDEN))
-    rep, n, eigs = _small_workload_on_gpu(prec)
+    rep, n, eigs = _small_workload_on_gpu(prec, band_tol_factor=factor)
     assert rep["converged"] == 1
     assert abs(rep["energy"] - g["energy"]) < tol
     assert np.max(np.abs(eigs - np.array(g["eigs"]))) < 10 * tol
