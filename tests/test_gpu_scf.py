@@ -229,7 +229,7 @@ def test_scf_uniform_electron_gas_on_gpu():
     basis.close()
 
 
-def _small_workload_on_gpu(prec="fp64", band_tol=1e-9, band_tol_factor=0.0):
+def _small_workload_on_gpu(prec="fp64", band_tol=1e-9, band_tol_factor=0.0, precond="teter", mlp=None):
     w = WORKLOADS["small"]
     atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
     ob = pw.Basis.build(w.R, w.S, w.kfrac[0], w.ecut)
@@ -245,7 +245,7 @@ def _small_workload_on_gpu(prec="fp64", band_tol=1e-9, band_tol_factor=0.0):
     n = torch.empty(N, dtype=torch.float64, device=DEV)
     eigs = torch.empty(w.nbands, dtype=torch.float64, device=DEV)
     rep = jdft.jdft_scf(basis, [C], vion, n, eigs, tol_energy=1e-9, tol_density=1e-7, band_tol=band_tol,
-                        prec=prec, band_tol_factor=band_tol_factor)
+                        prec=prec, band_tol_factor=band_tol_factor, precond=precond, mlp=mlp)
     out = (rep, n.cpu().numpy(), eigs.cpu().numpy())
     basis.close()
     return out
@@ -268,3 +268,18 @@ def test_scf_48cubed_matches_golden(prec, tol, factor):
     w = WORKLOADS["small"]
     Omega = float(np.prod(w.L))
     assert Omega / n.size * n.sum() == pytest.approx(2.0 * w.nbands, rel=1e-10)
+
+
+def test_scf_with_the_learned_preconditioner_matches_golden():
+    """Mixed-precision band solves with the committed network as preconditioner
+    inside the SCF loop reach the oracle's self-consistent energy."""
+    from paper_1708_03621_gb300 import learned
+    wts = learned.load_weights()
+    if wts is None:
+        pytest.skip("no committed network weights")
+    net = jdft.Mlp(wts)
+    g = json.load(open(GOLDEN))
+    rep, n, eigs = _small_workload_on_gpu("bf16x3", precond="mlp", mlp=net)
+    assert rep["converged"] == 1
+    assert abs(rep["energy"] - g["energy"]) < 1e-6
+    assert np.max(np.abs(eigs - np.array(g["eigs"]))) < 1e-5
