@@ -838,7 +838,8 @@ def overlap_measurements(device) -> dict:
 def spinor_measurements(device) -> dict:
     """Spinor bands in a noncollinear potential (jdft_apply_H_spinor): the 48^3
     workload with 16 spinor bands (FP64 and FP32) and the 128^3 workload with
-    64 spinor bands (FP32), a smooth seeded M(r); CUDA events after warm-up.
+    64 spinor bands (FP32 transforms; projector products on CUDA cores or as
+    BF16x3 tensor-core products), a smooth seeded M(r); CUDA events after warm-up.
     One spinor band-apply = H applied to both components of one band."""
     import torch
 
@@ -846,7 +847,7 @@ def spinor_measurements(device) -> dict:
     from synth import WORKLOADS, atom_positions, random_coefficients
     out = {}
     stream = torch.cuda.current_stream()
-    for wname, nb, precs in (("small", 16, ("fp64", "fp32")), ("large", 64, ("fp32",))):
+    for wname, nb, precs in (("small", 16, ("fp64", "fp32")), ("large", 64, ("fp32", "bf16x3"))):
         w = WORKLOADS[wname]
         atoms = atom_positions(w.R, w.natoms, w.seed_atoms)
         b = jdft.Basis(w.R, w.S, w.ecut, w.kfrac, w.weights())

@@ -442,7 +442,9 @@ jdft_status jdft_scf(jdft_basis_t basis, void* const* C, int ldc, int nb, const 
  * basis potential (jdft_set_potential), M a real 3-vector field given per
  * call as device 3 x N doubles (M_x, then M_y, then M_z).  Pauli matrices
  * sigma_x = [[0,1],[1,0]], sigma_y = [[0,-i],[i,0]], sigma_z = [[1,0],[0,-1]].
- * JDFT_FP64 (complex128 blocks) or JDFT_FP32 (complex64, FP32 transforms).
+ * JDFT_FP64 (complex128 blocks), or JDFT_FP32, JDFT_TF32X3, JDFT_BF16X3 (complex64
+ * blocks, FP32 transforms; the precision selects the projector products as in
+ * jdft_apply_H).
  * Both calls use a spinor workspace of the basis (real-space boxes of a chunk
  * of bands, at most 256 MB plus the chunk's sphere rows; grown synchronously)
  * besides the one jdft_apply_H / jdft_op_I use. */

@@ -234,7 +234,7 @@ jdft_status check_spinor_args(jdft_basis_s* b, int ik, const void* C, int ldc, i
     JDFT_CHECK_ARG(b && C, "null argument");
     JDFT_CHECK_ARG(ik >= 0 && ik < b->nk, "k-point index out of range");
     JDFT_CHECK_ARG(nb >= 1, "nb must be >= 1");
-    JDFT_CHECK_ARG(prec == JDFT_FP64 || prec == JDFT_FP32, "spinor calls take JDFT_FP64 or JDFT_FP32");
+    JDFT_CHECK_ARG(prec >= JDFT_FP64 && prec <= JDFT_BF16X3, "unknown precision");
     JDFT_CHECK_ARG(ldc >= b->ks[ik].npw, "leading dimension below npw");
     return JDFT_OK;
 }

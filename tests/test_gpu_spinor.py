@@ -19,7 +19,7 @@ if not torch.cuda.is_available():
 from paper_1708_03621_gb300 import jdft  # noqa: E402
 
 DEV = torch.device("cuda:0")
-TOL = {"fp64": 1e-10, "fp32": 2e-5}
+TOL = {"fp64": 1e-10, "fp32": 2e-5, "bf16x3": 2e-5}
 
 
 def _field(R, S, seed):
@@ -66,7 +66,8 @@ def _setup(case, prec):
     return ob, V, P, D, basis, C, torch.tensor(C, device=DEV).to(ct), nb
 
 
-SPIN_CASES = [(c, p) for c in ("tiny", "pair16x12", "small") for p in ("fp64", "fp32")] + [("large", "fp32")]
+SPIN_CASES = [(c, p) for c in ("tiny", "pair16x12", "small") for p in ("fp64", "fp32")]
+SPIN_CASES += [("small", "bf16x3"), ("large", "fp32"), ("large", "bf16x3")]
 
 
 @pytest.mark.parametrize("case,prec", SPIN_CASES, ids=[f"{c}-{p}" for c, p in SPIN_CASES])
