@@ -138,6 +138,68 @@ __device__ __forceinline__ double block_sum(double x) {
     return t;
 }
 
+// Shared-memory lines are stored with one padding element after every 32:
+// element i of a buffer lives at pad_idx(i).  The radix-R passes write with
+// stride R (and 8 Ns between groups), which without padding puts 4 to 16
+// lanes of a warp on the same banks.
+__host__ __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ int padded_len(int m) { return m + (m >> 5) + 1; }
+
+// One Stockham pass of fft.cuh's transform over padded lines of length n.
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void stockham_pass_p(const c_t<T>* __restrict__ src, c_t<T>* __restrict__ dst, int nlines,
+                                                int n, int Ns, const c_t<T>* __restrict__ tw) {
+    const int nb = n / R;
+    const int twstep = n / (Ns * R);
+    const int total = nlines * nb;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l = idx / nb;
+        const int j = idx - l * nb;
+        const int k = j % Ns;
+        const int lb = l * n;
+        c_t<T> v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[pad_idx(lb + j + r * nb)];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const c_t<T> w = tw[r * k * twstep];
+                v[r] = (SIGN > 0) ? cmul(v[r], w) : cmulc(v[r], w);
+            }
+        }
+        if (R == 2) dft2<T, SIGN>(v);
+        if (R == 3) dft3<T, SIGN>(v);
+        if (R == 4) dft4<T, SIGN>(v);
+        if (R == 5) dft5<T, SIGN>(v);
+        if (R == 8) dft8<T, SIGN>(v);
+        const int ob = lb + (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[pad_idx(ob + r * Ns)] = v[r];
+    }
+}
+
+// fft_lines (fft.cuh) on padded lines: nlines lines of length plan.n, line l
+// at elements l * n.  Returns the buffer holding the result (block synchronised).
+template <typename T, int SIGN>
+__device__ c_t<T>* fft_lines_p(c_t<T>* a, c_t<T>* b, int nlines, const FftPlan& plan, const c_t<T>* __restrict__ tw) {
+    int Ns = 1;
+    const int n = plan.n;
+    for (int p = 0; p < plan.npass; ++p) {
+        const int R = plan.radix[p];
+        switch (R) {
+            case 2: stockham_pass_p<T, SIGN, 2>(a, b, nlines, n, Ns, tw); break;
+            case 3: stockham_pass_p<T, SIGN, 3>(a, b, nlines, n, Ns, tw); break;
+            case 4: stockham_pass_p<T, SIGN, 4>(a, b, nlines, n, Ns, tw); break;
+            case 5: stockham_pass_p<T, SIGN, 5>(a, b, nlines, n, Ns, tw); break;
+            default: stockham_pass_p<T, SIGN, 8>(a, b, nlines, n, Ns, tw); break;
+        }
+        __syncthreads();
+        c_t<T>* t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
 enum { OUT_COMPLEX = 0, OUT_REAL = 1, OUT_KS = 2 };
 
 // One axis of the full-box transform.  IN_REAL: the input is a real box
@@ -149,9 +211,10 @@ __global__ void __launch_bounds__(kFieldThreads)
 field_axis_kernel(const void* __restrict__ in, void* __restrict__ out, AxisGeom g, FftPlan plan,
                   const double2* __restrict__ tw, FieldArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plen = padded_len(g.W * g.n);
     double2* bufA = reinterpret_cast<double2*>(smem_raw);
-    double2* bufB = bufA + g.W * g.n;
-    int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
+    double2* bufB = bufA + plen;
+    int64_t* base = reinterpret_cast<int64_t*>(bufB + plen);
     if (!IN_REAL && OUT == OUT_COMPLEX && blockIdx.y > 0) {
         in = reinterpret_cast<const double2*>(in) + blockIdx.y * a.bstride;
         out = reinterpret_cast<double2*>(out) + blockIdx.y * a.bstride;
@@ -174,10 +237,10 @@ field_axis_kernel(const void* __restrict__ in, void* __restrict__ out, AxisGeom 
         double2 v;
         if (IN_REAL) { v.x = reinterpret_cast<const double*>(in)[addr]; v.y = 0.0; }
         else v = reinterpret_cast<const double2*>(in)[addr];
-        bufA[w * n + t] = v;
+        bufA[pad_idx(w * n + t)] = v;
     }
     __syncthreads();
-    double2* res = fft_lines<double, SIGN>(bufA, bufB, nw, n, plan, tw);
+    double2* res = fft_lines_p<double, SIGN>(bufA, bufB, nw, plan, tw);
     double part = 0.0;
     if (KERNEL) {
         // lines of axis 0: l = j1 * S2 + j2, position t = frequency index along axis 0
@@ -191,20 +254,20 @@ field_axis_kernel(const void* __restrict__ in, void* __restrict__ out, AxisGeom 
             const double gz = f0 * a.B[6] + f1 * a.B[7] + f2 * a.B[8];
             const double G2 = gx * gx + gy * gy + gz * gz;
             const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
-            double2 x = res[idx];
+            double2 x = res[pad_idx(idx)];
             x.x *= a.invN; x.y *= a.invN;
             part += K * (x.x * x.x + x.y * x.y);
-            res[idx] = make_double2(K * x.x, K * x.y);
+            res[pad_idx(idx)] = make_double2(K * x.x, K * x.y);
         }
         __syncthreads();
         double2* other = (res == bufA) ? bufB : bufA;
-        res = fft_lines<double, -SIGN>(res, other, nw, n, plan, tw);
+        res = fft_lines_p<double, -SIGN>(res, other, nw, plan, tw);
     }
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int w, t;
         if (g.es == 1) { w = idx / n; t = idx - w * n; } else { t = idx / nw; w = idx - t * nw; }
         const int64_t addr = base[w] + (int64_t)t * g.es;
-        const double2 v = res[w * n + t];
+        const double2 v = res[pad_idx(w * n + t)];
         if (OUT == OUT_COMPLEX) {
             reinterpret_cast<double2*>(out)[addr] = make_double2(a.scale * v.x, a.scale * v.y);
         } else if (OUT == OUT_REAL) {
@@ -288,7 +351,9 @@ jdft_status field_work(jdft_basis_s* b, FieldWork* w, int nbox = 1) {
     return JDFT_OK;
 }
 
-size_t axis_smem(const AxisGeom& g) { return (size_t)2 * g.W * g.n * sizeof(double2) + (size_t)g.W * sizeof(int64_t); }
+size_t axis_smem(const AxisGeom& g) {
+    return (size_t)2 * padded_len(g.W * g.n) * sizeof(double2) + (size_t)g.W * sizeof(int64_t);
+}
 
 template <int SIGN, bool IN_REAL, bool KERNEL, int OUT>
 jdft_status launch_axis(const char* name, jdft_basis_s* b, int axis, const void* in, void* out, const FieldArgs& a,
@@ -533,9 +598,10 @@ __global__ void __launch_bounds__(kFieldThreads)
 field_axis_c_kernel(const c_t<T>* __restrict__ in, c_t<T>* __restrict__ out, AxisGeom g, FftPlan plan,
                     const c_t<T>* __restrict__ tw, int64_t bstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plen = padded_len(g.W * g.n);
     c_t<T>* bufA = reinterpret_cast<c_t<T>*>(smem_raw);
-    c_t<T>* bufB = bufA + g.W * g.n;
-    int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
+    c_t<T>* bufB = bufA + plen;
+    int64_t* base = reinterpret_cast<int64_t*>(bufB + plen);
     in += blockIdx.y * bstride;
     out += blockIdx.y * bstride;
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
@@ -552,14 +618,14 @@ field_axis_c_kernel(const c_t<T>* __restrict__ in, c_t<T>* __restrict__ out, Axi
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int w, t;
         line_index(g, nw, idx, w, t);
-        bufA[w * n + t] = in[base[w] + (int64_t)t * g.es];
+        bufA[pad_idx(w * n + t)] = in[base[w] + (int64_t)t * g.es];
     }
     __syncthreads();
-    const c_t<T>* res = fft_lines<T, SIGN>(bufA, bufB, nw, n, plan, tw);
+    const c_t<T>* res = fft_lines_p<T, SIGN>(bufA, bufB, nw, plan, tw);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int w, t;
         line_index(g, nw, idx, w, t);
-        out[base[w] + (int64_t)t * g.es] = res[w * n + t];
+        out[base[w] + (int64_t)t * g.es] = res[pad_idx(w * n + t)];
     }
 }
 
@@ -571,10 +637,11 @@ __global__ void __launch_bounds__(kFieldThreads)
 pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, AxisGeom g, FftPlan plan,
                       const c_t<T>* __restrict__ tw, GArgs q, int64_t bstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plen = padded_len(g.W * g.n);
     c_t<T>* bufX = reinterpret_cast<c_t<T>*>(smem_raw);
-    c_t<T>* bufA = bufX + g.W * g.n;
-    c_t<T>* bufB = bufA + g.W * g.n;
-    int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
+    c_t<T>* bufA = bufX + plen;
+    c_t<T>* bufB = bufA + plen;
+    int64_t* base = reinterpret_cast<int64_t*>(bufB + plen);
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
     const int nw = left < g.W ? (int)left : g.W;
@@ -592,7 +659,7 @@ pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, Axis
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int w, t;
         line_index(g, nw, idx, w, t);
-        bufX[w * n + t] = X[base[w] + (int64_t)t * g.es];
+        bufX[pad_idx(w * n + t)] = X[base[w] + (int64_t)t * g.es];
     }
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
@@ -600,16 +667,16 @@ pcm_grad_axis0_kernel(const c_t<T>* __restrict__ X, c_t<T>* __restrict__ Y, Axis
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
             const T G = (T)fold(t, q.S[0]) * b0 + lineG[3 * w + c];
-            const c_t<T> x = bufX[idx];
-            bufA[idx] = mk<T>(-G * x.y, G * x.x);
+            const c_t<T> x = bufX[pad_idx(idx)];
+            bufA[pad_idx(idx)] = mk<T>(-G * x.y, G * x.x);
         }
         __syncthreads();
-        const c_t<T>* res = fft_lines<T, +1>(bufA, bufB, nw, n, plan, tw);
+        const c_t<T>* res = fft_lines_p<T, +1>(bufA, bufB, nw, plan, tw);
         c_t<T>* Yc = Y + c * bstride;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int w, t;
             line_index(g, nw, idx, w, t);
-            Yc[base[w] + (int64_t)t * g.es] = res[w * n + t];
+            Yc[base[w] + (int64_t)t * g.es] = res[pad_idx(w * n + t)];
         }
         __syncthreads();
     }
@@ -623,7 +690,7 @@ pcm_eps_axis2_kernel(c_t<T>* __restrict__ Y, const T* __restrict__ eps, AxisGeom
                      const c_t<T>* __restrict__ tw, int64_t bstride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     c_t<T>* bufA = reinterpret_cast<c_t<T>*>(smem_raw);
-    c_t<T>* bufB = bufA + g.W * g.n;
+    c_t<T>* bufB = bufA + padded_len(g.W * g.n);
     Y += blockIdx.y * bstride;
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
@@ -631,18 +698,18 @@ pcm_eps_axis2_kernel(c_t<T>* __restrict__ Y, const T* __restrict__ eps, AxisGeom
     const int n = g.n;
     const int total = nw * n;
     const int64_t off = l0 * n;   // axis 2: line l starts at l * S2, contiguous
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) bufA[idx] = Y[off + idx];
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) bufA[pad_idx(idx)] = Y[off + idx];
     __syncthreads();
-    c_t<T>* res = fft_lines<T, +1>(bufA, bufB, nw, n, plan, tw);
+    c_t<T>* res = fft_lines_p<T, +1>(bufA, bufB, nw, plan, tw);
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const T e = eps[off + idx];
-        res[idx].x *= e;
-        res[idx].y *= e;
+        res[pad_idx(idx)].x *= e;
+        res[pad_idx(idx)].y *= e;
     }
     __syncthreads();
     c_t<T>* other = (res == bufA) ? bufB : bufA;
-    res = fft_lines<T, -1>(res, other, nw, n, plan, tw);
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) Y[off + idx] = res[idx];
+    res = fft_lines_p<T, -1>(res, other, nw, plan, tw);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) Y[off + idx] = res[pad_idx(idx)];
 }
 
 // Axis 0 of the forward transforms and the divergence: out = scale *
@@ -653,10 +720,11 @@ pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ di
                      AxisGeom g, FftPlan plan, const c_t<T>* __restrict__ tw, GArgs q, int64_t bstride,
                      double scale, double* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plen = padded_len(g.W * g.n);
     c_t<T>* acc = reinterpret_cast<c_t<T>*>(smem_raw);
-    c_t<T>* bufA = acc + g.W * g.n;
-    c_t<T>* bufB = bufA + g.W * g.n;
-    int64_t* base = reinterpret_cast<int64_t*>(bufB + g.W * g.n);
+    c_t<T>* bufA = acc + plen;
+    c_t<T>* bufB = bufA + plen;
+    int64_t* base = reinterpret_cast<int64_t*>(bufB + plen);
     const int64_t l0 = (int64_t)blockIdx.x * g.W;
     const int64_t left = g.nlines - l0;
     const int nw = left < g.W ? (int)left : g.W;
@@ -670,24 +738,24 @@ pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ di
         for (int c = 0; c < 3; ++c) lineG[3 * threadIdx.x + c] = (T)(f1 * q.B[3 * c + 1] + f2 * q.B[3 * c + 2]);
     }
     const int total = nw * n;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) acc[idx] = mk<T>(0, 0);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) acc[pad_idx(idx)] = mk<T>(0, 0);
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
         const c_t<T>* Yc = Y + c * bstride;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             int w, t;
             line_index(g, nw, idx, w, t);
-            bufA[w * n + t] = Yc[base[w] + (int64_t)t * g.es];
+            bufA[pad_idx(w * n + t)] = Yc[base[w] + (int64_t)t * g.es];
         }
         __syncthreads();
-        const c_t<T>* res = fft_lines<T, -1>(bufA, bufB, nw, n, plan, tw);
+        const c_t<T>* res = fft_lines_p<T, -1>(bufA, bufB, nw, plan, tw);
         const T b0 = (T)q.B[3 * c];
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
             const T G = (T)fold(t, q.S[0]) * b0 + lineG[3 * w + c];
-            const c_t<T> y = res[idx];
-            acc[idx].x -= G * y.y;
-            acc[idx].y += G * y.x;
+            const c_t<T> y = res[pad_idx(idx)];
+            acc[pad_idx(idx)].x -= G * y.y;
+            acc[pad_idx(idx)].y += G * y.x;
         }
         __syncthreads();
     }
@@ -697,7 +765,8 @@ pcm_div_axis0_kernel(const c_t<T>* __restrict__ Y, const c_t<T>* __restrict__ di
         int w, t;
         line_index(g, nw, idx, w, t);
         const int64_t addr = base[w] + (int64_t)t * g.es;
-        const c_t<T> v = mk<T>(sc * acc[w * n + t].x, sc * acc[w * n + t].y);
+        const c_t<T> a = acc[pad_idx(w * n + t)];
+        const c_t<T> v = mk<T>(sc * a.x, sc * a.y);
         out[addr] = v;
         if (din) {
             const c_t<T> dv = din[addr];
@@ -850,9 +919,10 @@ jdft_status pcm_hessian(jdft_basis_s* b, const T* eps, const c_t<T>* X, c_t<T>* 
     const int64_t grid2 = (g2.nlines + g2.W - 1) / g2.W;
     if (grid0 > kPartialMax - 16) return set_error(JDFT_ERR_ARG, "box too large for the partial sums");
     const size_t e = sizeof(c_t<T>);
-    const size_t smem3 = (size_t)3 * g0.W * g0.n * e + g0.W * sizeof(int64_t) + (size_t)3 * g0.W * sizeof(T);
-    const size_t smem1 = (size_t)2 * g1.W * g1.n * e + g1.W * sizeof(int64_t);
-    const size_t smem2 = (size_t)2 * g2.W * g2.n * e;
+    const size_t smem3 = (size_t)3 * padded_len(g0.W * g0.n) * e + g0.W * sizeof(int64_t) +
+                         (size_t)3 * g0.W * sizeof(T);
+    const size_t smem1 = (size_t)2 * padded_len(g1.W * g1.n) * e + g1.W * sizeof(int64_t);
+    const size_t smem2 = (size_t)2 * padded_len(g2.W * g2.n) * e;
     JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_grad_axis0_kernel<T>, smem3));
     JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_div_axis0_kernel<T>, smem3));
     JDFT_CUDA_TRY(set_smem_attr((const void*)pcm_eps_axis2_kernel<T>, smem2));
