@@ -441,27 +441,37 @@ jdft_status hartree_chain(jdft_basis_s* b, const double* n, const double* vion, 
 // ---------------------------------------------------------------------------
 
 // Store the new pair in ring slot s (n_in, R = n_out - n_in) and sum, per
-// block, R . R_i for every stored slot i < count (slot s included).
+// block, R . R_i for the stored slots i < count (slot s included).  Block row
+// y of the grid takes slots [kPulayGroup y, kPulayGroup (y + 1)) (few
+// accumulators a thread, so many blocks fit an SM); row 0 also stores the pair.
+constexpr int kPulayGroup = 4;
+
 __global__ void __launch_bounds__(kFieldThreads)
 pulay_store_kernel(const double* __restrict__ nin, const double* __restrict__ nout, double* __restrict__ Nbuf,
                    double* __restrict__ Rbuf, int slot, int count, int64_t N, double* __restrict__ partial) {
-    double acc[kMaxHist];
+    const int i0 = blockIdx.y * kPulayGroup;
+    const bool store = blockIdx.y == 0;
+    double acc[kPulayGroup];
 #pragma unroll
-    for (int i = 0; i < kMaxHist; ++i) acc[i] = 0.0;
+    for (int q = 0; q < kPulayGroup; ++q) acc[q] = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         const double x = nin[j];
         const double r = nout[j] - x;
-        Nbuf[(int64_t)slot * N + j] = x;
-        Rbuf[(int64_t)slot * N + j] = r;
+        if (store) {
+            Nbuf[(int64_t)slot * N + j] = x;
+            Rbuf[(int64_t)slot * N + j] = r;
+        }
 #pragma unroll
-        for (int i = 0; i < kMaxHist; ++i)
-            if (i < count) acc[i] += r * (i == slot ? r : Rbuf[(int64_t)i * N + j]);
+        for (int q = 0; q < kPulayGroup; ++q) {
+            const int i = i0 + q;
+            if (i < count) acc[q] += r * (i == slot ? r : Rbuf[(int64_t)i * N + j]);
+        }
     }
 #pragma unroll
-    for (int i = 0; i < kMaxHist; ++i) {
-        if (i < count) {
-            const double s = block_sum(acc[i]);
-            if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kMaxHist + i] = s;
+    for (int q = 0; q < kPulayGroup; ++q) {
+        if (i0 + q < count) {
+            const double s = block_sum(acc[q]);
+            if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kMaxHist + i0 + q] = s;
         }
     }
 }
@@ -532,14 +542,16 @@ pulay_solve_kernel(const double* __restrict__ partial, int nblk, double* __restr
 __global__ void __launch_bounds__(kFieldThreads)
 pulay_mix_kernel(const double* __restrict__ Nbuf, const double* __restrict__ Rbuf, const double* __restrict__ coef,
                  int count, double alpha, int64_t N, double* __restrict__ out) {
-    double c[kMaxHist];
-#pragma unroll
-    for (int i = 0; i < kMaxHist; ++i) c[i] = i < count ? coef[i] : 0.0;
+    // the coefficients in shared memory (read uniformly), not in registers
+    __shared__ double c[kMaxHist];
+    if (threadIdx.x < kMaxHist) c[threadIdx.x] = threadIdx.x < count ? coef[threadIdx.x] : 0.0;
+    __syncthreads();
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
         double t = 0.0;
-#pragma unroll
-        for (int i = 0; i < kMaxHist; ++i)
-            if (i < count && c[i] != 0.0) t += c[i] * (Nbuf[(int64_t)i * N + j] + alpha * Rbuf[(int64_t)i * N + j]);
+        for (int i = 0; i < count; ++i) {
+            const double ci = c[i];
+            if (ci != 0.0) t += ci * (Nbuf[(int64_t)i * N + j] + alpha * Rbuf[(int64_t)i * N + j]);
+        }
         out[j] = t;
     }
 }
@@ -1136,8 +1148,9 @@ jdft_status jdft_pulay_step(jdft_pulay_t p, const double* n_in, const double* n_
     const int count = std::min(p->count + 1, p->hist);
     {
         Trace tr_("pulay_store", st);
-        pulay_store_kernel<<<p->nblk, kFieldThreads, 0, st>>>(n_in, n_out, p->Nbuf, p->Rbuf, slot, count, p->n,
-                                                              p->partial);
+        const dim3 grid(p->nblk, (count + kPulayGroup - 1) / kPulayGroup);
+        pulay_store_kernel<<<grid, kFieldThreads, 0, st>>>(n_in, n_out, p->Nbuf, p->Rbuf, slot, count, p->n,
+                                                           p->partial);
     }
     jdft_status s = check_launch("pulay_store");
     if (s) return s;
