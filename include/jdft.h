@@ -558,11 +558,14 @@ typedef struct {
  * exact inverse for eps = 1).  Start phi~ = 0; converged when
  * |r| <= tol |rho~|, r = rho~ - hessian(phi~).
  *   prec JDFT_FP64: CG in FP64 throughout.
- *   prec JDFT_FP32: iterative refinement (the paper fixes no precision): each
- *     round solves hessian(e) = r by the same CG in FP32 (fields, transforms
- *     and eps in FP32, sums in FP64) to 1e-4 of |r|, adds e to phi~ in FP64 and
- *     forms the new r with one FP64 hessian; it stops at the same tolerance
- *     on the FP64 residual, or when a round no longer lowers it.
+ *   prec JDFT_FP32: the same CG run in FP32 (fields, transforms and eps in
+ *     FP32, sums in FP64) on the correction e, with reliable updates (the
+ *     paper fixes no precision): whenever the FP32 residual has fallen by 1e-4
+ *     since the last update, or below tol |rho~| / 2, e is added to phi~ in FP64
+ *     and the residual is
+ *     replaced by r = rho~ - hessian(phi~) from one FP64 hessian (the search
+ *     direction kept); it stops at the same tolerance on that FP64 residual,
+ *     or when an update no longer lowers it.
  * eps: device N doubles (> 0); rho_t, phi_t: device complex128 boxes (phi_t
  * overwritten, not overlapping rho_t).  max_iter: limit on CG iterations (all
  * rounds).  report: host.  Synchronous (one host read of the residual per

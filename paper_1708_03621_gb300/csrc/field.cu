@@ -885,6 +885,26 @@ pcm_residual_kernel(const double2* __restrict__ rho, const double2* __restrict__
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// Residual replacement: r32 = r64 (the FP64 residual) in the block type, with
+// partial sums of |r|^2 and r.Kr (two per block).
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads)
+pcm_refresh_kernel(const double2* __restrict__ r64, c_t<T>* __restrict__ r, GArgs q, int64_t N,
+                   double* __restrict__ partial) {
+    double rr = 0.0, rz = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = r64[j];
+        const c_t<T> vt = cx<T>(v.x, v.y);
+        r[j] = vt;
+        const double a = (double)vt.x * vt.x + (double)vt.y * vt.y;
+        rr += a;
+        rz += (double)coulomb_of_index<T>(q, j) * a;
+    }
+    const double s0 = block_sum(rr);
+    const double s1 = block_sum(rz);
+    if (threadIdx.x == 0) { partial[2 * blockIdx.x] = s0; partial[2 * blockIdx.x + 1] = s1; }
+}
+
 __global__ void __launch_bounds__(kFieldThreads)
 to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t N) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
@@ -1401,32 +1421,77 @@ jdft_status jdft_pcm_solve(jdft_basis_t b, const double* eps, const void* rho_t,
         JDFT_CUDA_TRY(cudaStreamSynchronize(st));
         const double bnorm = std::sqrt(host);
         res = bnorm > 0.0 ? 1.0 : 0.0;
-        const double inner_tol = 1e-4;
-        while (res > tol && its < max_iter) {
-            int it_in = 0;
-            double rel_in = 0.0;
-            if ((s = pcm_cg<float>(b, eps32, r64, e32, r32, d32, Hd32, Yg32, w.partial, sc, inner_tol, max_iter - its,
-                                   &it_in, &rel_in, nullptr, st)))
-                return s;
-            its += it_in;
+        // One CG on the correction equation in FP32 (e32, r32, d32), its residual
+        // replaced by the FP64 one whenever it has fallen by kReplace since the
+        // last replacement or below half the tolerance: x += e, r = rho~ - H x in
+        // FP64, the direction kept (reliable updates).
+        const double kReplace = 1e-4;
+        if (res > tol) {
             {
-                Trace tr_("pcm_accumulate", st);
-                pcm_accumulate_kernel<<<grid, kFieldThreads, 0, st>>>(x, e32, N);
+                Trace tr_("pcm_init", st);
+                pcm_init_kernel<float><<<grid, kFieldThreads, 0, st>>>(r64, e32, r32, d32, q, N, w.partial);
             }
-            if ((s = check_launch("pcm_accumulate"))) return s;
-            if ((s = pcm_hessian<double>(b, eps, x, Hx, Yg64, nullptr, w.partial, nullptr, st))) return s;
-            ++its64;
-            {
-                Trace tr_("pcm_residual", st);
-                pcm_residual_kernel<<<grid, kFieldThreads, 0, st>>>(rho, Hx, r64, q, N, w.partial);
-            }
-            if ((s = check_launch("pcm_residual"))) return s;
-            if ((s = launch_reduce(w.partial, grid, 1, 1, 1.0, sc + 7, false, st))) return s;
-            JDFT_CUDA_TRY(cudaMemcpyAsync(&host, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+            if ((s = check_launch("pcm_init"))) return s;
+            if ((s = launch_reduce(w.partial, grid, 2, 2, 1.0, sc + 2, false, st))) return s;
+            JDFT_CUDA_TRY(cudaMemcpyAsync(&host, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
             JDFT_CUDA_TRY(cudaStreamSynchronize(st));
-            const double prev = res;
-            res = std::sqrt(host) / bnorm;
-            if (it_in == 0 || !(res < prev)) break;   // no progress: the FP32 corrections are exhausted
+        }
+        double rref = std::sqrt(host);
+        int k = 0;                 // parity of the (|r|^2, r.Kr) slots
+        while (res > tol && its < max_iter) {
+            int nb0 = 0;
+            if ((s = pcm_hessian<float>(b, eps32, d32, Hd32, Yg32, d32, w.partial, &nb0, st))) return s;
+            if ((s = launch_reduce(w.partial, nb0, 1, 1, 1.0, sc, false, st))) return s;
+            double* old = sc + 2 + 2 * (k & 1);
+            double* nw = sc + 2 + 2 * ((k + 1) & 1);
+            {
+                Trace tr_("pcm_update", st);
+                pcm_update_kernel<float><<<grid, kFieldThreads, 0, st>>>(e32, r32, d32, Hd32, old + 1, sc, q, N,
+                                                                         w.partial);
+            }
+            if ((s = check_launch("pcm_update"))) return s;
+            if ((s = launch_reduce(w.partial, grid, 2, 2, 1.0, nw, false, st))) return s;
+            JDFT_CUDA_TRY(cudaMemcpyAsync(&host, nw, sizeof(double), cudaMemcpyDeviceToHost, st));
+            JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+            ++its;
+            ++k;
+            // update when the residual has fallen by kReplace, or is near the
+            // tolerance itself (so the solve stops close to it)
+            if (std::sqrt(host) <= std::max(kReplace * rref, 0.5 * tol * bnorm) || its >= max_iter) {
+                {
+                    Trace tr_("pcm_accumulate", st);
+                    pcm_accumulate_kernel<<<grid, kFieldThreads, 0, st>>>(x, e32, N);
+                }
+                if ((s = check_launch("pcm_accumulate"))) return s;
+                JDFT_CUDA_TRY(cudaMemsetAsync(e32, 0, N * sizeof(float2), st));
+                if ((s = pcm_hessian<double>(b, eps, x, Hx, Yg64, nullptr, w.partial, nullptr, st))) return s;
+                ++its64;
+                {
+                    Trace tr_("pcm_residual", st);
+                    pcm_residual_kernel<<<grid, kFieldThreads, 0, st>>>(rho, Hx, r64, q, N, w.partial);
+                }
+                if ((s = check_launch("pcm_residual"))) return s;
+                if ((s = launch_reduce(w.partial, grid, 1, 1, 1.0, sc + 7, false, st))) return s;
+                JDFT_CUDA_TRY(cudaMemcpyAsync(&host, sc + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+                JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+                const double prev = res;
+                res = std::sqrt(host) / bnorm;
+                if (!(res > tol) || !(res < prev)) break;   // converged, or the FP32 corrections are exhausted
+                {
+                    Trace tr_("pcm_refresh", st);
+                    pcm_refresh_kernel<float><<<grid, kFieldThreads, 0, st>>>(r64, r32, q, N, w.partial);
+                }
+                if ((s = check_launch("pcm_refresh"))) return s;
+                if ((s = launch_reduce(w.partial, grid, 2, 2, 1.0, nw, false, st))) return s;
+                JDFT_CUDA_TRY(cudaMemcpyAsync(&host, nw, sizeof(double), cudaMemcpyDeviceToHost, st));
+                JDFT_CUDA_TRY(cudaStreamSynchronize(st));
+                rref = std::sqrt(host);
+            }
+            {
+                Trace tr_("pcm_direction", st);
+                pcm_direction_kernel<float><<<grid, kFieldThreads, 0, st>>>(r32, d32, nw + 1, old + 1, q, N);
+            }
+            if ((s = check_launch("pcm_direction"))) return s;
         }
     }
     {
