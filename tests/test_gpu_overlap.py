@@ -135,3 +135,19 @@ def test_generalised_minimiser_finds_the_lowest_pencil_eigenvalues(case, precond
     got = Cd.cpu().numpy().T
     assert np.max(np.abs(got.conj().T @ us.op_S(ob, got, P, Q) - np.eye(nb))) < 1e-10
     basis.close()
+
+
+def test_augmentation_needs_projectors_and_a_symmetric_Q():
+    R, S, k = np.diag([6.0, 6.5, 5.5]), (12, 15, 10), (0.1, 0.2, 0.3)
+    basis = jdft.Basis(R, S, 3.0, [k])
+    with pytest.raises(jdft.JdftError):
+        jdft.jdft_set_augmentation(basis, 0, torch.eye(8, dtype=torch.float64, device=DEV))
+    atoms = atom_positions(R, 2, 31)
+    Pd = torch.empty((8, basis.npw(0)), dtype=torch.complex128, device=DEV)
+    jdft.jdft_gaussian_projectors(basis, 0, atoms, Pd)
+    jdft.jdft_set_projectors(basis, 0, Pd, torch.eye(8, dtype=torch.float64, device=DEV))
+    Q = torch.zeros((8, 8), dtype=torch.float64, device=DEV)
+    Q[0, 1] = 0.1
+    with pytest.raises(jdft.JdftError):
+        jdft.jdft_set_augmentation(basis, 0, Q)
+    basis.close()

@@ -199,3 +199,31 @@ def test_pcm_mixed_equals_fp64_on_a_128cubed_cavity():
     assert _rel(p32.cpu().numpy(), p64.cpu().numpy()) < 1e-8
     assert r32["A_diel"] == pytest.approx(r64["A_diel"], rel=1e-10)
     basis.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pcm_zero_charge_gives_zero_potential(prec):
+    """Degenerate input: rho~ = 0 converges at once to phi~ = 0 and A_diel = 0."""
+    S = (18, 16, 20)
+    basis = jdft.Basis(TRICLINIC, S, 1.0, [(0.0, 0.0, 0.0)])
+    N = int(np.prod(S))
+    phi = torch.full((N,), 7.0 + 1j, dtype=torch.complex128, device=DEV)
+    rep = jdft.jdft_pcm_solve(basis, torch.full((N,), 2.0, dtype=torch.float64, device=DEV),
+                              torch.zeros(N, dtype=torch.complex128, device=DEV), phi, tol=1e-10, prec=prec)
+    torch.cuda.synchronize()
+    assert rep["converged"] == 1 and rep["iterations"] == 0
+    assert rep["A_diel"] == 0.0
+    assert torch.count_nonzero(phi).item() == 0
+    basis.close()
+
+
+def test_pcm_iteration_limit_reports_not_converged():
+    R, S = np.diag([8.0, 8.5, 7.5]), (24, 25, 20)
+    basis = jdft.Basis(R, S, 1.0, [(0.0, 0.0, 0.0)])
+    eps = _cavity_eps(R, S, 2, 7, eps_bulk=10.0, radius=1.5)
+    rho_t = pcm.op_J(S, -pw.vloc_realspace(R, S, atom_positions(R, 2, 7), depth=0.5, width=0.9))
+    phi = torch.empty(rho_t.size, dtype=torch.complex128, device=DEV)
+    rep = jdft.jdft_pcm_solve(basis, _d(eps), _c(rho_t), phi, tol=1e-12, max_iter=3, check=False)
+    assert rep["status"] == "ERR_NOT_CONVERGED" and rep["converged"] == 0 and rep["iterations"] == 3
+    assert 0 < rep["residual"] < 1
+    basis.close()

@@ -283,3 +283,28 @@ def test_scf_with_the_learned_preconditioner_matches_golden():
     assert rep["converged"] == 1
     assert abs(rep["energy"] - g["energy"]) < 1e-6
     assert np.max(np.abs(eigs - np.array(g["eigs"]))) < 1e-5
+
+
+def test_pulay_with_one_pair_is_linear_mixing():
+    N = 700
+    rng = np.random.default_rng(44)
+    mix = jdft.Pulay(N, 1, 0.35)
+    out = torch.empty(N, dtype=torch.float64, device=DEV)
+    for _ in range(3):
+        x, fx = rng.normal(size=N), rng.normal(size=N)
+        mix.step(_dev(x), _dev(fx), out)
+        assert np.allclose(out.cpu().numpy(), x + 0.35 * (fx - x), rtol=0, atol=1e-14)
+        assert mix.used() == 1
+    mix.close()
+
+
+def test_scf_iteration_limit_reports_not_converged():
+    R, S, atoms, kpts, cells, Vion = _small_cell_oracle()
+    basis, vion, blocks, _ = _gpu_cell(R, S, 6.0, kpts, [0.5, 0.5], atoms, 6, [7, 8])
+    n = torch.empty(int(np.prod(S)), dtype=torch.float64, device=DEV)
+    rep = jdft.jdft_scf(basis, blocks, vion, n, max_iter=2, check=False)
+    assert rep["status"] == "ERR_NOT_CONVERGED" and rep["converged"] == 0 and rep["iterations"] == 2
+    Omega = float(np.prod(np.diag(R)))
+    # the output density still holds every electron
+    assert Omega / n.numel() * n.sum().item() == pytest.approx(2.0 * 6, rel=1e-10)
+    basis.close()

@@ -118,3 +118,17 @@ def test_uniform_field_is_the_scalar_operator_plus_zeeman_term():
     got = HC.cpu().numpy()
     assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
     basis.close()
+
+
+def test_single_spinor_band_on_the_fused_pass():
+    """One spinor band (a single (up, down) pair) through the fused FP32 pass."""
+    ob, V, P, D, basis, C, Cd, nb = _setup("pair16x12", "fp32")
+    C1, Cd1 = C[:2], Cd[:2].contiguous()
+    M = _field(ob.R, ob.S, 29)
+    HC = torch.empty_like(Cd1)
+    jdft.jdft_apply_H_spinor(basis, 0, torch.tensor(M.reshape(-1), device=DEV), Cd1, HC, "fp32")
+    torch.cuda.synchronize()
+    ref = spinor.apply_H_spinor(ob, V, M, C1.T, P, D).T
+    err = np.max(np.linalg.norm(HC.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1))
+    assert err < TOL["fp32"], err
+    basis.close()
