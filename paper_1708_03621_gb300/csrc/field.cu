@@ -102,26 +102,33 @@ __device__ __forceinline__ int fold(int m, int S) { return m < (S + 1) / 2 ? m :
 // potential v at density n (both zero for n <= 0).
 __device__ __forceinline__ void lda_pz(double n, double& e, double& v) {
     if (!(n > 0.0)) { e = 0.0; v = 0.0; return; }
+    // one cube root and one reciprocal per point (FP64 transcendentals and
+    // divisions are the cost of this epilogue on this GPU's FP64 rate)
     const double cx = -0.73855876638202240588423003065;   // -(3/4)(3/pi)^{1/3}
-    const double ex = cx * cbrt(n);
-    const double rs = cbrt(3.0 / (4.0 * M_PI * n));
+    const double kr = 0.62035049089940001666800681204778;  // (3/(4 pi))^{1/3}
+    const double third = 1.0 / 3.0;
+    const double c = cbrt(n);
+    const double ex = cx * c;
+    const double rs = kr / c;
     double ec, vc;
     if (rs >= 1.0) {
         const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
         const double sq = sqrt(rs);
-        const double den = 1.0 + b1 * sq + b2 * rs;
-        ec = g / den;
-        const double dec = -g * (0.5 * b1 / sq + b2) / (den * den);
-        vc = ec - rs / 3.0 * dec;
+        const double iden = 1.0 / (1.0 + b1 * sq + b2 * rs);
+        ec = g * iden;
+        // r_s de_c/dr_s = -g (b1 sqrt(r_s) / 2 + b2 r_s) / den^2
+        const double rdec = -g * (0.5 * b1 * sq + b2 * rs) * iden * iden;
+        vc = ec - third * rdec;
     } else {
         const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
         const double lr = log(rs);
         ec = A * lr + B + C * rs * lr + D * rs;
-        const double dec = A / rs + C * (lr + 1.0) + D;
-        vc = ec - rs / 3.0 * dec;
+        // r_s de_c/dr_s = A + r_s (C (ln r_s + 1) + D)
+        const double rdec = A + rs * (C * (lr + 1.0) + D);
+        vc = ec - third * rdec;
     }
     e = ex + ec;
-    v = (4.0 / 3.0) * ex + vc;
+    v = (4.0 * third) * ex + vc;
 }
 
 // Sum over the block; thread 0 returns the total (others: partial values).
@@ -243,15 +250,23 @@ field_axis_kernel(const void* __restrict__ in, void* __restrict__ out, AxisGeom 
     double2* res = fft_lines_p<double, SIGN>(bufA, bufB, nw, plan, tw);
     double part = 0.0;
     if (KERNEL) {
-        // lines of axis 0: l = j1 * S2 + j2, position t = frequency index along axis 0
+        // lines of axis 0: l = j1 * S2 + j2, position t = frequency index along
+        // axis 0; each line's axis-1 and axis-2 part of G formed once (over the
+        // W * 3 doubles after `base`)
+        double* lineG = reinterpret_cast<double*>(base + g.W);
+        if (threadIdx.x < nw) {
+            const int64_t l = l0 + threadIdx.x;
+            const int m1 = (int)(l / a.S[2]), m2 = (int)(l - (int64_t)m1 * a.S[2]);
+            const double f1 = fold(m1, a.S[1]), f2 = fold(m2, a.S[2]);
+            for (int c = 0; c < 3; ++c) lineG[3 * threadIdx.x + c] = f1 * a.B[3 * c + 1] + f2 * a.B[3 * c + 2];
+        }
+        __syncthreads();
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int w = idx / n, t = idx - w * n;
-            const int64_t l = l0 + w;
-            const int m1 = (int)(l / a.S[2]), m2 = (int)(l - (int64_t)m1 * a.S[2]);
-            const double f0 = fold(t, a.S[0]), f1 = fold(m1, a.S[1]), f2 = fold(m2, a.S[2]);
-            const double gx = f0 * a.B[0] + f1 * a.B[1] + f2 * a.B[2];
-            const double gy = f0 * a.B[3] + f1 * a.B[4] + f2 * a.B[5];
-            const double gz = f0 * a.B[6] + f1 * a.B[7] + f2 * a.B[8];
+            const double f0 = fold(t, a.S[0]);
+            const double gx = f0 * a.B[0] + lineG[3 * w];
+            const double gy = f0 * a.B[3] + lineG[3 * w + 1];
+            const double gz = f0 * a.B[6] + lineG[3 * w + 2];
             const double G2 = gx * gx + gy * gy + gz * gz;
             const double K = G2 > 0.0 ? kFourPi / G2 : 0.0;
             double2 x = res[pad_idx(idx)];
@@ -352,7 +367,9 @@ jdft_status field_work(jdft_basis_s* b, FieldWork* w, int nbox = 1) {
 }
 
 size_t axis_smem(const AxisGeom& g) {
-    return (size_t)2 * padded_len(g.W * g.n) * sizeof(double2) + (size_t)g.W * sizeof(int64_t);
+    // two padded buffers, the line bases and (for the Coulomb-kernel pass) 3 doubles a line
+    return (size_t)2 * padded_len(g.W * g.n) * sizeof(double2) + (size_t)g.W * sizeof(int64_t) +
+           (size_t)3 * g.W * sizeof(double);
 }
 
 template <int SIGN, bool IN_REAL, bool KERNEL, int OUT>
