@@ -445,13 +445,17 @@ jdft_status jdft_scf(jdft_basis_t basis, void* const* C, int ldc, int nb, const 
  * JDFT_FP64 (complex128 blocks), or JDFT_FP32, JDFT_TF32X3, JDFT_BF16X3 (complex64
  * blocks, FP32 transforms; the precision selects the projector products as in
  * jdft_apply_H).
- * Both calls use a spinor workspace of the basis (real-space boxes of a chunk
- * of bands, at most 256 MB plus the chunk's sphere rows; grown synchronously)
- * besides the one jdft_apply_H / jdft_op_I use. */
+ * Both calls use a spinor workspace of the basis, grown synchronously, besides
+ * the one jdft_apply_H / jdft_op_I use: for FP32 blocks on boxes of 128 x 128
+ * (or 16 x 12) planes, the fused chain's column buffer (up to 512 MB of
+ * component rows) and M in FP32; otherwise the real-space boxes of a chunk of
+ * bands (at most 256 MB) plus the chunk's sphere rows. */
 
 /* HC = H C for nb spinor bands: the scalar Hamiltonian of jdft_apply_H on
  * every component row, plus Omega J((M . sigma) I C) coupling each band's two
- * components.  C, HC must not overlap (ldhc >= npw).  Asynchronous. */
+ * components (on the fused path the 2 x 2 product V + M . sigma replaces the
+ * multiply by V inside the plane pass).  C, HC must not overlap (ldhc >= npw).
+ * Asynchronous. */
 jdft_status jdft_apply_H_spinor(jdft_basis_t basis, int ik, const double* M, const void* C, int ldc, void* HC,
                                 int ldhc, int nb, jdft_prec prec, void* stream);
 
