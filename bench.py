@@ -445,7 +445,7 @@ def run_ours(args, world, rank, local, pg):
     n_host = torch.empty_like(p.n, device="cpu").pin_memory()
     CHC_host = torch.empty_like(p.CHC, device="cpu").pin_memory()
     COC_host = torch.empty_like(p.COC, device="cpu").pin_memory()
-    e2e_steps = max(4, args.steps // 2)
+    e2e_steps = max(4, args.steps)   # as many pipelined steps as the device-timed region
     # double-buffered: step i+1's input copy (one stream) and step i-1's output
     # copy (another: the two directions use separate copy engines) run while the
     # compute stream runs step i (two device buffer sets)
